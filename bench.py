@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 ROIBIN-SZ compression hot path.
+
+One step = one roibin_compress call over a batch of 1,000 CSPAD-like frames
+(32 x 185 x 388 float32, 20..100 Bragg peaks each, ROI 17x17, bin 2x2,
+eb 10): peak finding, ROI extraction, binning, prequantisation, Lorenzo
+prediction, codes, histogram, Huffman codebook and bit-packing, all on the
+device.  Frames are resident in HBM when the timed region starts; the batch
+(9.19 GB) is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead
+(on the host cores, bounded samples of the same workload).
+Run on N GPUs with torchrun: each rank compresses its own 1,000 frames
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic import RECIPES, make_batch_threaded, make_frame  # noqa: E402
+
+WORKLOAD = "cspad_batch"
+N_FRAMES = 1000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=N_FRAMES)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--min-load-seconds", type=float, default=2.0,
+                    help="keep the GPU busy at least this long before timing (clock sampling)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(2)
+
+    def summary(self, t0: float, t1: float):
+        rows = [p for t, p in self.rows if t0 <= t <= t1] or [p for _, p in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(p[1]) for p in rows if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in rows if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in rows for i in range(4) if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(p[3]) for p in rows if p[3].replace(".", "").isdigit()), default=None)}
+
+
+# ----------------------------------------------------------------- workload
+def make_inputs(n_frames: int, first: int):
+    recipe = RECIPES[WORKLOAD]
+    import torch
+    host = torch.empty((n_frames, *recipe.geometry), dtype=torch.float32).pin_memory()
+    make_batch_threaded(recipe, n_frames, first=first, out=host.numpy())
+    return host
+
+
+def cpu_baseline(frames_np: np.ndarray, params, budget_s: float = 20.0):
+    """The oracle, as it stands, over the host cores (one frame per worker
+    thread; ctypes releases the GIL).  Sample: a prefix of the same frames,
+    sized for about budget_s of CPU work."""
+    import oracle
+    op = oracle.make_params(**params)
+    oracle.lib()
+    t = time.perf_counter()
+    oracle.compress_frame(frames_np[0], op)
+    per_frame = max(time.perf_counter() - t, 1e-3)
+    n = int(min(len(frames_np), max(4, budget_s / per_frame)))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(cores) as ex:
+        sizes = list(ex.map(lambda k: len(oracle.compress_frame(frames_np[k], op)[1]), range(n)))
+    dt = time.perf_counter() - t0
+    gb = n * frames_np[0].nbytes / 1e9
+    return {"value": gb / dt, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of the {len(frames_np)} frames, one frame per worker thread",
+            "frames_per_s": n / dt, "seconds": dt, "mean_stream_bytes": float(np.mean(sizes))}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    recipe = RECIPES[WORKLOAD]
+    import oracle
+    p = dict(oracle.DEFAULTS)
+    cores = os.cpu_count() or 1
+    sample = max(cores, 2 * cores)
+    frames = np.stack([make_frame(recipe, k) for k in range(sample)])
+    op = oracle.make_params(**p)
+    oracle.lib()
+
+    def step():
+        with cf.ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda k: oracle.compress_frame(frames[k], op), range(sample)))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    gbs = args.steps * sample * frames[0].nbytes / 1e9 / dt
+    line = {"impl": "reference", "metric": "input GB/s (compression, CSPAD-like frames)", "value": gbs,
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{N_FRAMES} CSPAD-like frames 32x185x388 f32, 20-100 peaks, ROI 17x17, "
+                                   f"bin 2x2, eb 10 (each step a {sample}-frame sample)"},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} frames per step, one frame per worker thread"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, rank, local, world):
+    import torch
+    import paper_2206_11297_gb300 as rb
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    recipe = RECIPES[WORKLOAD]
+    n = args.frames
+    params = rb.default_params()
+    host = make_inputs(n, first=rank * n)
+    frames = host.to(dev, non_blocking=False)
+    frame_bytes = host[0].numel() * 4
+    stride = rb.compress_bound(recipe.geometry, params)
+    ctx = rb.Context(recipe.geometry, params, max_frames=n, device=local)
+    out = torch.empty((n, stride), dtype=torch.uint8, device=dev)
+    nbytes = torch.empty(n, dtype=torch.int64, device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_path(path: int):
+        ctx.set_path(path)
+        # warm-up: at least W steps and min_load_seconds of work (clock sampling)
+        t_end = time.time() + args.min_load_seconds
+        k = 0
+        while k < args.warmup or time.time() < t_end:
+            ctx.compress(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
+            k += 1
+            if k % 8 == 0:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        ctx.enable_timing(True)
+        ctx.kernel_times()  # reset
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        ev[0].record(stream)
+        for i in range(args.steps):
+            ctx.compress(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        t1 = time.time()
+        launches = ctx.last_launch_count * args.steps
+        kt = ctx.kernel_times()
+        ctx.enable_timing(False)
+        steps_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        st = status.cpu().numpy()
+        nb = nbytes.cpu().numpy()
+        assert (st == 0).all(), f"frame status {np.unique(st)}"
+        return dict(total_ms=total_ms, steps_ms=steps_ms, kernels=kt, launches=launches,
+                    out_bytes=int(nb.sum()), t0=t0, t1=t1)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+    res = {}
+    paths = [rb.PATH_PLAIN]
+    if ctx.resolved_path == rb.PATH_FUSED:
+        paths.append(rb.PATH_FUSED)
+    for path in paths:
+        res[path] = timed_path(path)
+    main = paths[-1]
+    r = res[main]
+    sampler.stop()
+    clocks = sampler.summary(r["t0"], r["t1"])
+
+    # end to end: host frames in, packed streams out, through roibin_compress_host
+    e2e = None
+    if not args.no_e2e:
+        ctx.set_path(main)
+        ctx.reserve_host_path()
+        h_out = torch.empty(int(r["out_bytes"] * 1.5) + (1 << 20), dtype=torch.uint8).pin_memory()
+        h_nb = torch.empty(n, dtype=torch.int64)
+        h_st = torch.empty(n, dtype=torch.int32)
+        for _ in range(max(1, args.warmup // 2)):
+            ctx.compress_host(host, h_out, h_nb, h_st)
+        e_steps = max(3, min(args.steps, 10))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            ctx.compress_host(host, h_out, h_nb, h_st)
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": sum_over_ranks(e_steps * n * frame_bytes / 1e9, world) / dt, "unit": "GB/s",
+               "h2d_bytes_per_step": n * frame_bytes, "d2h_bytes_per_step": int(h_nb.sum()),
+               "steps": e_steps, "ms_per_step": dt / e_steps * 1e3}
+
+    total_s = max_over_ranks(r["total_ms"] / 1e3, world)
+    job_bytes = sum_over_ranks(args.steps * n * frame_bytes, world)
+    gbs = job_bytes / 1e9 / total_s
+    steps_ms = sorted(r["steps_ms"])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    # dominant kernel: the one with the largest share of the timed region
+    kname, (kms, kcnt) = max(r["kernels"].items(), key=lambda kv: kv[1][0])
+    per_launch_s = kms / 1e3 / kcnt
+    # algorithmic bytes per launch: every launch processes the whole batch;
+    # the frames are read once (4 B/px), the streams are written once
+    algo = n * frame_bytes + (r["out_bytes"] if kname == "fused" else 0)
+    achieved = algo / 1e9 / per_launch_s
+    line = {
+        "metric": "input GB/s (compression, CSPAD-like frames)",
+        "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n} CSPAD-like frames 32x185x388 f32 per GPU, 20-100 peaks, ROI 17x17, "
+                               "bin 2x2, eb 10, batched",
+                   "frames_per_step": n, "path": {1: "plain", 2: "fused"}[main],
+                   "l2": "inputs (9.19 GB per step) larger than L2; no flush"},
+        "frames_per_s": gbs * 1e9 / frame_bytes,
+        "latency_ms": {"p50": steps_ms[len(steps_ms) // 2],
+                       "p99": steps_ms[min(len(steps_ms) - 1, int(0.99 * len(steps_ms)))],
+                       "unit": "per 1,000-frame batch"},
+        "compression_ratio": {"vs_f32": n * frame_bytes / r["out_bytes"],
+                              "vs_u16": n * frame_bytes / 2 / r["out_bytes"]},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in r["kernels"].items()},
+        "gpu_launches": r["launches"],
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rb.PATH_PLAIN in res and main != rb.PATH_PLAIN:
+        pr = res[rb.PATH_PLAIN]
+        line["plain"] = {"value": args.steps * n * frame_bytes / 1e9 / (pr["total_ms"] / 1e3), "unit": "GB/s",
+                         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in pr["kernels"].items()}}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(host.numpy(), params.as_dict())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    rank, local, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, local, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * roibin.h - C ABI of the GB300 ROIBIN-SZ compression library (libroibin).
+ *
+ * ROIBIN-SZ (arXiv 2206.11297) compresses serial-crystallography detector
+ * frames: a peak finder marks Bragg spots (§4.2), a window around each spot is
+ * kept losslessly (§4, §4.1), the whole frame is binned (§4.1, §6) and the
+ * binned background is coded with an absolute error bound (§5.3.3) by an
+ * SZ-style predictor/quantiser/entropy coder (§5.3.2).  Every step runs in
+ * CUDA kernels for sm_103a; this header is the only boundary.
+ *
+ * Conventions (all entry points):
+ *  - Pointers named d_* are device pointers, h_* host pointers.  The caller
+ *    owns every buffer it passes; the context owns only its own scratch.
+ *  - A frame is float32[n_panels][rows][cols], little-endian, contiguous;
+ *    frames of a batch follow each other (4-D events x panel x row x col,
+ *    the panel-aware layout of §4.1).
+ *  - Calls taking a stream enqueue asynchronously on it (cudaStream_t passed
+ *    as void*; NULL = legacy default stream) unless stated otherwise.
+ *  - Every call returns a status (ROIBIN_OK or a negative ROIBIN_ERR_*).
+ *    Argument errors are detected on the host before anything is enqueued.
+ *    Per-frame conditions found on the device (too many peaks, output too
+ *    small, corrupt input stream) are written to the caller's per-frame status
+ *    array; they never trap the GPU.
+ *  - One call at a time per context: calls on the same context must be ordered
+ *    (same stream, or synchronised), since they share its scratch; one host
+ *    thread drives a context.
+ *
+ * Stream format (version 1, little-endian; the paper defines no container):
+ *   [0,96)  header: u32 magic "RBSZ" | u32 version | u32 n_panels, rows, cols |
+ *           u16 roi_h, roi_w, bin_h, bin_w | f32 abs_eb | u32 quant_radius |
+ *           u32 n_peaks | u32 n_lorenzo_outliers | u32 n_prequant_outliers |
+ *           u32 n_symbols | u32 chunk_symbols (4096) | u32 n_chunks |
+ *           u32 bitstream_words | u64 total_bytes | 24 zero bytes
+ *   then, each starting on a 16-byte boundary, zero padded:
+ *     peaks       u16[n_peaks][3] (panel, row, col)
+ *     roi         f32[n_peaks][roi_h][roi_w]
+ *     lengths     u8[2 * quant_radius]        Huffman code length per symbol
+ *     chunk index u32[n_chunks]               word offset of each 4096-symbol chunk
+ *     lorenzo     (u32 bin index, i32 delta)[n_lorenzo_outliers], ascending
+ *     prequant    (u32 bin index, u32 float bits)[n_prequant_outliers], ascending
+ *     bitstream   u32[bitstream_words]; inside a chunk, codeword bits are
+ *                 appended MSB first, stream bit b is bit 31-(b%32) of word b/32;
+ *                 every chunk starts on a word boundary.
+ */
+#ifndef ROIBIN_H
+#define ROIBIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define ROIBIN_OK 0
+#define ROIBIN_ERR_INVALID_ARG (-1)    /* bad pointer, geometry or parameter          */
+#define ROIBIN_ERR_CAPACITY (-2)       /* > max_peaks peaks, or frame > output stride */
+#define ROIBIN_ERR_CORRUPT_STREAM (-3) /* decompression input fails validation       */
+#define ROIBIN_ERR_OUT_OF_BUDGET (-4)  /* scratch would exceed the HBM budget         */
+#define ROIBIN_ERR_CUDA (-5)           /* a CUDA runtime call failed                  */
+#define ROIBIN_ERR_TIMEOUT (-6)        /* a bounded device-side wait gave up          */
+#define ROIBIN_ERR_CODE_LENGTH (-7)    /* Huffman code > 32 bits (cannot occur for
+                                          frames below 5,702,887 bins)                */
+
+/* ---- execution paths for roibin_compress ----------------------------- */
+#define ROIBIN_PATH_AUTO 0  /* fused when the geometry allows it, else plain          */
+#define ROIBIN_PATH_PLAIN 1 /* one kernel per stage, intermediates in device memory  */
+#define ROIBIN_PATH_FUSED 2 /* one persistent cluster kernel per batch; codes stay on
+                               chip (distributed shared memory)                      */
+
+typedef struct roibin_ctx roibin_ctx;
+
+/* Detector geometry: every frame is n_panels panels of rows x cols pixels
+ * (CSPAD 32x185x388, epix10k 16x352x384, JUNGFRAU 8x512x1024; §4.2). */
+typedef struct {
+  uint32_t n_panels, rows, cols;
+} roibin_geometry;
+
+/* Method parameters.  All are user-configurable (§4.2); defaults from
+ * roibin_default_params are the paper's values where it gives one.
+ *   Peak finder (§4.2): a pixel is a candidate when it is the maximum of its
+ *   (2 rank + 1)^2 window clipped to the panel (ties: the first pixel in
+ *   row-major order wins) and >= amax_thr (300).  The background is the mean
+ *   and population standard deviation (fp64) of the in-panel ring
+ *   ring_r0^2 <= di^2 + dj^2 < (ring_r0 + ring_dr)^2 (5, 2).  Peak pixels are
+ *   window pixels with I - bkg > pix_nsigma * sigma (3; 0 = the paper's plain
+ *   above-zero test).  A candidate is kept when npix_min <= npix <= npix_max
+ *   (2, 30), atot > atot_thr (600) and atot > son_min * sigma * sqrt(npix) (10).
+ *   ROI (§4): roi_h x roi_w window centred on each peak (17 x 17), fill 0 past
+ *   the panel edge.  Binning (§4.1, §6): bin_h x bin_w mean per panel (2 x 2).
+ *   Coding (§5.3.3): |b - b^| <= abs_eb on every binned value; quant_radius R
+ *   gives 2R symbols (512 -> 1024); max_peaks (2048, §4) caps the peak list. */
+typedef struct {
+  float amax_thr, atot_thr, son_min, pix_nsigma;
+  int32_t rank, ring_r0, ring_dr, npix_min, npix_max;
+  int32_t roi_h, roi_w, bin_h, bin_w;
+  float abs_eb;
+  int32_t quant_radius, max_peaks;
+} roibin_params;
+
+/* Fills *p with the defaults listed above.  Never fails for non-NULL p. */
+int roibin_default_params(roibin_params* p);
+
+/* Validates geometry + parameters without creating anything.  Limits:
+ * 1 <= n_panels, rows, cols <= 65535; cols/bin_w <= 8192; 1 <= bin <= 8;
+ * 1 <= roi <= 63; 1 <= rank <= 7; ring_r0, ring_dr >= 1, r0 + dr <= 16;
+ * 2 <= quant_radius <= 512; 0 <= max_peaks <= 8192; pix_nsigma >= 0;
+ * abs_eb > 0 with 2 abs_eb and 1/(2 abs_eb) finite; binned size below
+ * 5,702,887 (so that no Huffman code exceeds 32 bits). */
+int roibin_validate(const roibin_geometry* g, const roibin_params* p);
+
+/* Worst-case compressed size of one frame (bytes, a multiple of 16); 0 when
+ * the arguments are invalid.  An output stride of this size never overflows. */
+uint64_t roibin_compress_bound(const roibin_geometry* g, const roibin_params* p);
+
+/* Creates a context on CUDA device `device` for frames of geometry g and
+ * parameters p, with preallocated device scratch for up to
+ * max_frames_per_call frames per call (the zero-allocation principle of §4.1:
+ * no call below allocates).  hbm_budget_bytes caps the scratch (0 = no cap);
+ * ROIBIN_ERR_OUT_OF_BUDGET when it would be exceeded.  *out is NULL on error.
+ * The context keeps its own copies of g and p. */
+int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_params* p,
+                      uint32_t max_frames_per_call, uint64_t hbm_budget_bytes, int device);
+
+/* Frees the context and its scratch.  Synchronises the device first.  NULL ok. */
+int roibin_ctx_destroy(roibin_ctx* ctx);
+
+/* Bytes of device scratch the context holds. */
+uint64_t roibin_ctx_scratch_bytes(const roibin_ctx* ctx);
+
+/* Selects the kernel path for later roibin_compress calls (ROIBIN_PATH_*).
+ * ROIBIN_ERR_INVALID_ARG when FUSED is asked for a geometry it cannot hold
+ * on chip.  Both paths write identical bytes. */
+int roibin_ctx_set_path(roibin_ctx* ctx, int path);
+/* The path AUTO resolves to for this context (PLAIN or FUSED). */
+int roibin_ctx_resolved_path(const roibin_ctx* ctx);
+
+/* Compresses n_frames frames (1 <= n_frames <= max_frames_per_call).
+ *   d_frames        float32[n_frames][P][H][W], 16-byte aligned.
+ *   d_peaks,d_npeaks optional caller-supplied peak lists (§4.2 allows the
+ *                   regions of interest to be given as coordinates): d_peaks is
+ *                   u16[n_frames][max_peaks][3] (panel,row,col), d_npeaks
+ *                   u32[n_frames].  Both NULL -> the peak finder runs.  User
+ *                   peaks are stored in the order given; out-of-range
+ *                   coordinates give the frame ROIBIN_ERR_INVALID_ARG and more
+ *                   than max_peaks gives ROIBIN_ERR_CAPACITY.
+ *   d_out           u8; frame k's stream is written at d_out + k*out_stride.
+ *   out_stride      bytes per frame slot, a multiple of 16.
+ *   d_frame_bytes   u64[n_frames] out: stream size of each frame (on CAPACITY
+ *                   because of out_stride: the size it needs; else 0 on error).
+ *   d_frame_status  i32[n_frames] out: ROIBIN_OK or the frame's error.
+ *   stream          cudaStream_t as void*.
+ * Returns ROIBIN_OK when the work was enqueued. */
+int roibin_compress(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames,
+                    const uint16_t* d_peaks, const uint32_t* d_npeaks, uint8_t* d_out,
+                    uint64_t out_stride, uint64_t* d_frame_bytes, int32_t* d_frame_status,
+                    void* stream);
+
+/* Decompresses n_frames streams back to float32 frames (the round trip of
+ * §4.1: ROIs restored exactly over the up-sampled background).
+ *   d_in             u8 buffer of in_bytes bytes holding the streams.
+ *   d_frame_offsets  u64[n_frames]: byte offset of each frame's stream in d_in
+ *                    (16-byte aligned).
+ *   d_frames_out     float32[n_frames][P][H][W].
+ *   d_frame_status   i32[n_frames] out: ROIBIN_OK or ROIBIN_ERR_CORRUPT_STREAM
+ *                    (header, geometry, size, index or code mismatch).  A
+ *                    corrupt frame's output is unspecified.
+ * Streams must come from a context of the same geometry (other parameters are
+ * read from each header). */
+int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes,
+                      const uint64_t* d_frame_offsets, uint32_t n_frames, float* d_frames_out,
+                      int32_t* d_frame_status, void* stream);
+
+/* Reserves the device staging area that roibin_compress_host needs:
+ * max_frames_per_call input frames, the same number of output slots of
+ * roibin_compress_bound bytes, and a packed output buffer.  This is the only
+ * call besides roibin_ctx_create that allocates; calling it again is a no-op.
+ * ROIBIN_ERR_OUT_OF_BUDGET when the context budget would be exceeded. */
+int roibin_ctx_reserve_host_path(roibin_ctx* ctx);
+
+/* End-to-end compression from HOST memory: copies h_frames (pinned memory
+ * recommended) to the context's device staging area, compresses, packs the
+ * streams back to back on the device and copies them to h_out.  Synchronous:
+ * returns after h_out, h_frame_bytes and h_frame_status are written.
+ *   h_out            receives the streams packed back to back (each padded to
+ *                    16 bytes); frame k starts at the sum of the sizes before it.
+ *   h_out_capacity   bytes available at h_out; ROIBIN_ERR_CAPACITY if the packed
+ *                    total is larger (h_frame_bytes still filled).
+ * The copies are pipelined with compression in slices of the batch.  Needs
+ * roibin_ctx_reserve_host_path first and n_frames <= max_frames_per_call. */
+int roibin_compress_host(roibin_ctx* ctx, const float* h_frames, uint32_t n_frames,
+                         uint8_t* h_out, uint64_t h_out_capacity, uint64_t* h_frame_bytes,
+                         int32_t* h_frame_status, void* stream);
+
+/* ROI mask of each frame: u8 per pixel, 1 where some peak's window covers an
+ * in-panel pixel (the pixels the round trip restores exactly), else 0.
+ *   d_peaks u16[n_frames][max_peaks][3], d_npeaks u32[n_frames] (clamped to
+ *   max_peaks), d_mask u8[n_frames][P][H][W]. */
+int roibin_roi_mask(roibin_ctx* ctx, const uint16_t* d_peaks, const uint32_t* d_npeaks,
+                    uint32_t n_frames, uint8_t* d_mask, void* stream);
+
+/* Peak lists found by the last roibin_compress call on this context, copied
+ * to caller buffers (d_peaks as above, d_npeaks may exceed max_peaks when the
+ * frame overflowed).  Enqueued on `stream`, which must be ordered after that
+ * call. */
+int roibin_last_peaks(roibin_ctx* ctx, uint16_t* d_peaks, uint32_t* d_npeaks, uint32_t n_frames,
+                      void* stream);
+
+/* Per-kernel timing with CUDA events on the launch stream.  While enabled,
+ * every compress call records an event pair around each of its kernels.
+ * roibin_ctx_kernel_times synchronises, writes up to max_kernels entries
+ * (kernel name, total ms, launches) summed over the calls since the last
+ * read, and resets the sums.  Names are static strings owned by the library. */
+int roibin_ctx_enable_timing(roibin_ctx* ctx, int enable);
+int roibin_ctx_kernel_times(roibin_ctx* ctx, const char** names, double* total_ms,
+                            uint32_t* launches, int max_kernels, int* n_kernels);
+
+/* Number of kernel launches the last compress call enqueued. */
+uint32_t roibin_ctx_last_launch_count(const roibin_ctx* ctx);
+
+/* Human-readable text for a status code (static string). */
+const char* roibin_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROIBIN_H */

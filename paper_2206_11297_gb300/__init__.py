@@ -1,0 +1,283 @@
+"""Python binding of libroibin, the GB300 ROIBIN-SZ compression library.
+
+This module only marshals arguments: every step of the method runs in the CUDA
+kernels behind the C ABI of include/roibin.h.  PyTorch supplies device memory
+and streams.  There is no fallback: if the CUDA library is missing or cannot be
+loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+__all__ = ["Geometry", "Params", "Context", "library", "default_params", "validate",
+           "compress_bound", "status_string", "GEOMETRIES", "PATH_AUTO", "PATH_PLAIN",
+           "PATH_FUSED", "EXPORTED_SYMBOLS"]
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CAPACITY = -2
+ERR_CORRUPT_STREAM = -3
+ERR_OUT_OF_BUDGET = -4
+ERR_CUDA = -5
+ERR_TIMEOUT = -6
+ERR_CODE_LENGTH = -7
+
+PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
+
+GEOMETRIES = {"cspad": (32, 185, 388), "epix10k": (16, 352, 384), "jungfrau": (8, 512, 1024)}
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_panels", ctypes.c_uint32), ("rows", ctypes.c_uint32), ("cols", ctypes.c_uint32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("amax_thr", ctypes.c_float), ("atot_thr", ctypes.c_float),
+        ("son_min", ctypes.c_float), ("pix_nsigma", ctypes.c_float),
+        ("rank", ctypes.c_int32), ("ring_r0", ctypes.c_int32), ("ring_dr", ctypes.c_int32),
+        ("npix_min", ctypes.c_int32), ("npix_max", ctypes.c_int32),
+        ("roi_h", ctypes.c_int32), ("roi_w", ctypes.c_int32),
+        ("bin_h", ctypes.c_int32), ("bin_w", ctypes.c_int32),
+        ("abs_eb", ctypes.c_float), ("quant_radius", ctypes.c_int32), ("max_peaks", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_u32, _i32, _u64 = ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64
+_G, _Pr = ctypes.POINTER(Geometry), ctypes.POINTER(Params)
+
+# name -> (restype, argtypes); every symbol include/roibin.h declares
+_SIGNATURES = {
+    "roibin_default_params": (ctypes.c_int, [_Pr]),
+    "roibin_validate": (ctypes.c_int, [_G, _Pr]),
+    "roibin_compress_bound": (_u64, [_G, _Pr]),
+    "roibin_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), _G, _Pr, _u32, _u64, ctypes.c_int]),
+    "roibin_ctx_destroy": (ctypes.c_int, [_P]),
+    "roibin_ctx_scratch_bytes": (_u64, [_P]),
+    "roibin_ctx_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
+    "roibin_ctx_resolved_path": (ctypes.c_int, [_P]),
+    "roibin_compress": (ctypes.c_int, [_P, _P, _u32, _P, _P, _P, _u64, _P, _P, _P]),
+    "roibin_decompress": (ctypes.c_int, [_P, _P, _u64, _P, _u32, _P, _P, _P]),
+    "roibin_ctx_reserve_host_path": (ctypes.c_int, [_P]),
+    "roibin_compress_host": (ctypes.c_int, [_P, _P, _u32, _P, _u64, _P, _P, _P]),
+    "roibin_roi_mask": (ctypes.c_int, [_P, _P, _P, _u32, _P, _P]),
+    "roibin_last_peaks": (ctypes.c_int, [_P, _P, _P, _u32, _P]),
+    "roibin_ctx_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "roibin_ctx_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p),
+                                               ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_uint32), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]),
+    "roibin_ctx_last_launch_count": (_u32, [_P]),
+    "roibin_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+EXPORTED_SYMBOLS = sorted(_SIGNATURES)
+
+_lib = None
+
+
+def library(build_if_needed: bool = True):
+    """Loads libroibin.so (building it first if asked); raises if unavailable."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_needed and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libroibin.so is not built ({path}); run __graft_entry__.build()")
+        try:
+            import torch  # noqa: F401  (load PyTorch's CUDA runtime first; the library shares it)
+        except ImportError:
+            pass
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return library().roibin_status_string(code).decode()
+
+
+class RoibinError(RuntimeError):
+    def __init__(self, where: str, code: int):
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+        self.code = code
+
+
+def _check(where, code):
+    if code != OK:
+        raise RoibinError(where, code)
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    _check("roibin_default_params", library().roibin_default_params(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def validate(geometry, params: Params) -> int:
+    g = Geometry(*geometry)
+    return library().roibin_validate(ctypes.byref(g), ctypes.byref(params))
+
+
+def compress_bound(geometry, params: Params) -> int:
+    g = Geometry(*geometry)
+    return int(library().roibin_compress_bound(ctypes.byref(g), ctypes.byref(params)))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One compression context: geometry, parameters and preallocated scratch."""
+
+    def __init__(self, geometry, params: Params | None = None, max_frames: int = 1,
+                 hbm_budget: int = 0, device: int = 0):
+        self.lib = library()
+        self.geometry = tuple(int(x) for x in geometry)
+        self.params = params if params is not None else default_params()
+        self.max_frames = int(max_frames)
+        self.device = int(device)
+        g = Geometry(*self.geometry)
+        h = ctypes.c_void_p()
+        _check("roibin_ctx_create", self.lib.roibin_ctx_create(
+            ctypes.byref(h), ctypes.byref(g), ctypes.byref(self.params), self.max_frames,
+            int(hbm_budget), self.device))
+        self._h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.roibin_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- properties
+    @property
+    def bound(self) -> int:
+        return compress_bound(self.geometry, self.params)
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(self.lib.roibin_ctx_scratch_bytes(self._h))
+
+    def set_path(self, path: int):
+        _check("roibin_ctx_set_path", self.lib.roibin_ctx_set_path(self._h, int(path)))
+
+    @property
+    def resolved_path(self) -> int:
+        return int(self.lib.roibin_ctx_resolved_path(self._h))
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(self.lib.roibin_ctx_last_launch_count(self._h))
+
+    # -- compression
+    def compress(self, frames, out=None, out_stride=None, peaks=None, npeaks=None,
+                 frame_bytes=None, status=None, stream=None):
+        """frames: CUDA float32 [n, P, H, W].  Returns (out u8 [n, stride], frame_bytes int64 [n],
+        status int32 [n]); all asynchronous on `stream` (default: torch's current stream)."""
+        import torch
+        n = frames.shape[0]
+        assert frames.dtype == torch.float32 and frames.is_cuda and frames.is_contiguous()
+        assert tuple(frames.shape[1:]) == self.geometry
+        stride = int(out_stride or self.bound)
+        dev = frames.device
+        if out is None:
+            out = torch.empty((n, stride), dtype=torch.uint8, device=dev)
+        if frame_bytes is None:
+            frame_bytes = torch.empty(n, dtype=torch.int64, device=dev)
+        if status is None:
+            status = torch.empty(n, dtype=torch.int32, device=dev)
+        _check("roibin_compress", self.lib.roibin_compress(
+            self._h, _ptr(frames), n, _ptr(peaks), _ptr(npeaks), _ptr(out), stride,
+            _ptr(frame_bytes), _ptr(status), _stream_handle(stream)))
+        return out, frame_bytes, status
+
+    def decompress(self, data, offsets, n_frames, out=None, status=None, stream=None):
+        """data: CUDA u8 buffer; offsets: CUDA int64 [n] byte offsets.  Returns (frames, status)."""
+        import torch
+        dev = data.device
+        if out is None:
+            out = torch.empty((n_frames, *self.geometry), dtype=torch.float32, device=dev)
+        if status is None:
+            status = torch.empty(n_frames, dtype=torch.int32, device=dev)
+        _check("roibin_decompress", self.lib.roibin_decompress(
+            self._h, _ptr(data), data.numel(), _ptr(offsets), n_frames, _ptr(out), _ptr(status),
+            _stream_handle(stream)))
+        return out, status
+
+    def reserve_host_path(self):
+        _check("roibin_ctx_reserve_host_path", self.lib.roibin_ctx_reserve_host_path(self._h))
+
+    def compress_host(self, frames, out, frame_bytes, status, stream=None):
+        """Host (ideally pinned) CPU tensors in and out; synchronous."""
+        n = frames.shape[0]
+        _check("roibin_compress_host", self.lib.roibin_compress_host(
+            self._h, _ptr(frames), n, _ptr(out), out.numel(), _ptr(frame_bytes), _ptr(status),
+            _stream_handle(stream)))
+
+    def roi_mask(self, peaks, npeaks, n_frames, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((n_frames, *self.geometry), dtype=torch.uint8, device=peaks.device)
+        _check("roibin_roi_mask", self.lib.roibin_roi_mask(
+            self._h, _ptr(peaks), _ptr(npeaks), n_frames, _ptr(out), _stream_handle(stream)))
+        return out
+
+    def last_peaks(self, n_frames, stream=None):
+        import torch
+        mp = max(int(self.params.max_peaks), 1)
+        peaks = torch.zeros((n_frames, mp, 3), dtype=torch.int16, device=f"cuda:{self.device}")
+        npeaks = torch.zeros(n_frames, dtype=torch.int32, device=f"cuda:{self.device}")
+        _check("roibin_last_peaks", self.lib.roibin_last_peaks(
+            self._h, _ptr(peaks), _ptr(npeaks), n_frames, _stream_handle(stream)))
+        return peaks, npeaks
+
+    # -- timing
+    def enable_timing(self, on: bool = True):
+        _check("roibin_ctx_enable_timing", self.lib.roibin_ctx_enable_timing(self._h, int(on)))
+
+    def kernel_times(self):
+        """{kernel name: (total ms, launches)} since the last read; synchronises."""
+        maxk = 32
+        names = (ctypes.c_char_p * maxk)()
+        ms = (ctypes.c_double * maxk)()
+        cnt = (ctypes.c_uint32 * maxk)()
+        nk = ctypes.c_int(0)
+        _check("roibin_ctx_kernel_times", self.lib.roibin_ctx_kernel_times(
+            self._h, names, ms, cnt, maxk, ctypes.byref(nk)))
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(nk.value, maxk))}

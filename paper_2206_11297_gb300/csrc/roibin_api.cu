@@ -1,0 +1,592 @@
+// roibin_api.cu - host side of the C ABI declared in include/roibin.h:
+// argument validation, the context (preallocated scratch, §4.1's
+// zero-allocation principle), launch sequencing and the host-memory path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "roibin.h"
+#include "roibin_internal.cuh"
+
+using namespace roibin;
+
+namespace roibin {
+// fused_kernel.cu
+bool fused_supported(const DevParams& p, int device);
+cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st,
+                         int num_sms);
+uint64_t fused_scratch_bytes_per_frame(const DevParams& p);
+}  // namespace roibin
+
+struct TimedLaunch {
+  int id;
+  cudaEvent_t start, stop;
+};
+
+struct roibin_ctx {
+  int device = 0;
+  int num_sms = 0;
+  roibin_geometry g{};
+  roibin_params prm{};
+  DevParams dp{};
+  Scratch s{};
+  void* scratch = nullptr;
+  uint64_t scratch_bytes = 0;
+  uint64_t budget = 0;
+  uint32_t max_frames = 0;
+  int path_req = ROIBIN_PATH_AUTO;
+  bool fused_ok = false;
+  uint32_t last_launches = 0;
+  // timing
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> free_events;
+  // host path
+  void* host_stage = nullptr;
+  uint64_t host_stage_bytes = 0;
+  float* h_frames_dev = nullptr;
+  uint8_t* h_out_dev = nullptr;
+  uint8_t* h_packed_dev = nullptr;
+  uint64_t* h_bytes_dev = nullptr;
+  uint64_t* h_offsets_dev = nullptr;
+  int32_t* h_status_dev = nullptr;
+  uint64_t h_stride = 0;
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> slice_events;
+};
+
+namespace {
+
+int validate_impl(const roibin_geometry* g, const roibin_params* p) {
+  if (!g || !p) return ROIBIN_ERR_INVALID_ARG;
+  if (g->n_panels < 1 || g->rows < 1 || g->cols < 1) return ROIBIN_ERR_INVALID_ARG;
+  if (g->n_panels > 65535 || g->rows > 65535 || g->cols > 65535) return ROIBIN_ERR_INVALID_ARG;
+  if (p->bin_h < 1 || p->bin_w < 1 || p->bin_h > 8 || p->bin_w > 8) return ROIBIN_ERR_INVALID_ARG;
+  if (p->roi_h < 1 || p->roi_w < 1 || p->roi_h > 63 || p->roi_w > 63) return ROIBIN_ERR_INVALID_ARG;
+  if (p->rank < 1 || p->rank > 7) return ROIBIN_ERR_INVALID_ARG;
+  if (p->ring_r0 < 1 || p->ring_dr < 1 || p->ring_r0 + p->ring_dr > 16) return ROIBIN_ERR_INVALID_ARG;
+  if (p->npix_min < 0 || p->npix_max < p->npix_min) return ROIBIN_ERR_INVALID_ARG;
+  if (p->quant_radius < 2 || p->quant_radius > 512) return ROIBIN_ERR_INVALID_ARG;
+  if (p->max_peaks < 0 || p->max_peaks > (int32_t)kMaxPeaksLimit) return ROIBIN_ERR_INVALID_ARG;
+  if (!(p->pix_nsigma >= 0.0f) || std::isnan(p->amax_thr) || std::isnan(p->atot_thr) ||
+      std::isnan(p->son_min))
+    return ROIBIN_ERR_INVALID_ARG;
+  const float two_eb = 2.0f * p->abs_eb;
+  if (!(p->abs_eb > 0.0f) || !std::isfinite(two_eb) || !std::isfinite(1.0f / two_eb))
+    return ROIBIN_ERR_INVALID_ARG;
+  const uint64_t hb = (g->rows + p->bin_h - 1) / p->bin_h, wb = (g->cols + p->bin_w - 1) / p->bin_w;
+  if (wb > 8192) return ROIBIN_ERR_INVALID_ARG;
+  if ((uint64_t)g->n_panels * hb * wb > kMaxBinsPerFrame) return ROIBIN_ERR_INVALID_ARG;
+  return ROIBIN_OK;
+}
+
+DevParams make_dev_params(const roibin_geometry& g, const roibin_params& p) {
+  DevParams d{};
+  d.P = g.n_panels;
+  d.H = g.rows;
+  d.W = g.cols;
+  d.bh = p.bin_h;
+  d.bw = p.bin_w;
+  d.Hb = (g.rows + p.bin_h - 1) / p.bin_h;
+  d.Wb = (g.cols + p.bin_w - 1) / p.bin_w;
+  d.M = d.P * d.Hb * d.Wb;
+  d.n_chunks = ceil_div(d.M, kChunk);
+  d.frame_px = (uint64_t)d.P * d.H * d.W;
+  d.amax = p.amax_thr;
+  d.atot_thr = p.atot_thr;
+  d.son_min = p.son_min;
+  d.pix_nsigma = p.pix_nsigma;
+  d.rank = p.rank;
+  d.ring_r0 = p.ring_r0;
+  d.ring_dr = p.ring_dr;
+  d.npix_min = p.npix_min;
+  d.npix_max = p.npix_max;
+  d.roi_h = p.roi_h;
+  d.roi_w = p.roi_w;
+  d.eb = p.abs_eb;
+  // host float arithmetic, one IEEE rounding each
+  volatile float two = 2.0f * p.abs_eb;
+  d.two_eb = two;
+  volatile float rec = 1.0f / d.two_eb;
+  d.recip = rec;
+  d.R = p.quant_radius;
+  d.nsym = 2u * (uint32_t)p.quant_radius;
+  d.max_peaks = (uint32_t)p.max_peaks;
+  d.thr_cap = kThrCap;
+  return d;
+}
+
+uint64_t bound_impl(const DevParams& d) {
+  const uint64_t m = d.M;
+  uint64_t o = kHeaderBytes;
+  o += align16((uint64_t)d.max_peaks * 6);
+  o += align16((uint64_t)d.max_peaks * d.roi_h * d.roi_w * 4);
+  o += align16(d.nsym);
+  o += align16((uint64_t)d.n_chunks * 4);
+  o += align16(m * 8);  // Lorenzo outliers
+  o += align16(m * 8);  // prequantisation outliers
+  o += align16(m * 4);  // at most 32 bits per symbol
+  return o;
+}
+
+struct Carver {
+  uint8_t* base;
+  uint64_t off = 0;
+  template <class T>
+  T* take(uint64_t count) {
+    off = (off + 255) & ~uint64_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Lays out the per-frame scratch for n frames; with base == nullptr only sizes it.
+uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s) {
+  Carver c{base};
+  Scratch t{};
+  t.thr_count = c.take<uint32_t>(n);
+  t.thr_idx = c.take<uint32_t>((uint64_t)n * d.thr_cap);
+  t.peak_count = c.take<uint32_t>(n);
+  t.peak_key = c.take<uint32_t>((uint64_t)n * std::max<uint32_t>(d.max_peaks, 1));
+  t.hist = c.take<uint32_t>((uint64_t)n * kMaxSymbols);
+  t.cb_len = c.take<uint8_t>((uint64_t)n * kMaxSymbols);
+  t.cb_code = c.take<uint32_t>((uint64_t)n * kMaxSymbols);
+  t.codes = c.take<uint16_t>((uint64_t)n * d.n_chunks * kChunk);
+  t.lo_delta = c.take<int32_t>((uint64_t)n * d.M);
+  t.pq_bits = c.take<uint32_t>((uint64_t)n * d.M);
+  t.chunk_words = c.take<uint32_t>((uint64_t)n * d.n_chunks);
+  t.chunk_lo = c.take<uint32_t>((uint64_t)n * d.n_chunks);
+  t.chunk_pq = c.take<uint32_t>((uint64_t)n * d.n_chunks);
+  t.plan = c.take<FramePlan>(n);
+  t.status = c.take<int32_t>(n);
+  t.dec_table = c.take<uint32_t>((uint64_t)n * kDecTableWords);
+  t.dec_zero = c.take<uint32_t>(n);
+  t.dec_info = c.take<DecInfo>(n);
+  t.dq = t.lo_delta;
+  t.bhat = reinterpret_cast<float*>(t.pq_bits);
+  if (s) *s = t;
+  return c.off + 256;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? ROIBIN_OK : ROIBIN_ERR_CUDA; }
+
+cudaEvent_t get_event(roibin_ctx* ctx) {
+  if (!ctx->free_events.empty()) {
+    cudaEvent_t e = ctx->free_events.back();
+    ctx->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Runs one launcher, bracketed by timing events when enabled.
+template <class F>
+cudaError_t timed(roibin_ctx* ctx, int id, cudaStream_t st, F&& launch) {
+  ctx->last_launches++;
+  if (!ctx->timing) return launch();
+  TimedLaunch t{id, get_event(ctx), get_event(ctx)};
+  cudaEventRecord(t.start, st);
+  const cudaError_t e = launch();
+  cudaEventRecord(t.stop, st);
+  ctx->pending.push_back(t);
+  return e;
+}
+
+void choose_shape(const roibin_ctx* ctx, uint32_t n_frames, PlainArgs* a) {
+  const DevParams& d = ctx->dp;
+  a->rows_per_step = std::max<uint32_t>(1, std::min<uint32_t>(16, 2048 / std::max<uint32_t>(d.Wb, 1)));
+  const uint32_t target = 4u * (uint32_t)std::max(ctx->num_sms, 1);
+  const uint32_t base = d.P * n_frames;
+  uint32_t bands = 1;
+  if (base < target) bands = ceil_div(target, base);
+  bands = std::min<uint32_t>(bands, std::max<uint32_t>(1, ceil_div(d.Hb, 2)));
+  a->bands_per_panel = bands;
+}
+
+int compress_plain(roibin_ctx* ctx, const PlainArgs& a, cudaStream_t st) {
+  const DevParams& p = ctx->dp;
+  const Scratch& s = ctx->s;
+  cudaError_t e;
+  if ((e = timed(ctx, K_RESET, st, [&] { return launch_reset(p, s, a.n_frames, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_STREAM, st, [&] { return launch_stream(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if (!a.user_peaks)
+    if ((e = timed(ctx, K_PEAKS, st, [&] { return launch_peaks(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_PEAKS_FINAL, st, [&] { return launch_peaks_final(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_HUFFMAN, st, [&] { return launch_huffman(p, s, a.n_frames, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_CHUNKS, st, [&] { return launch_chunks(p, s, a.n_frames, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_PLAN, st, [&] { return launch_plan(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_ENCODE, st, [&] { return launch_encode(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if (p.max_peaks > 0)
+    if ((e = timed(ctx, K_ROI, st, [&] { return launch_roi(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  return ROIBIN_OK;
+}
+
+int resolved_path(const roibin_ctx* ctx) {
+  if (ctx->path_req == ROIBIN_PATH_PLAIN) return ROIBIN_PATH_PLAIN;
+  if (ctx->path_req == ROIBIN_PATH_FUSED) return ROIBIN_PATH_FUSED;
+  return ctx->fused_ok ? ROIBIN_PATH_FUSED : ROIBIN_PATH_PLAIN;
+}
+
+int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, const uint16_t* d_peaks,
+                    const uint32_t* d_npeaks, uint8_t* d_out, uint64_t out_stride, uint64_t* d_frame_bytes,
+                    int32_t* d_frame_status, cudaStream_t st) {
+  PlainArgs a{};
+  a.frames = d_frames;
+  a.n_frames = n_frames;
+  a.user_peaks = d_peaks;
+  a.user_npeaks = d_npeaks;
+  a.out = d_out;
+  a.out_stride = out_stride;
+  a.frame_bytes = d_frame_bytes;
+  a.frame_status = d_frame_status;
+  choose_shape(ctx, n_frames, &a);
+  if (resolved_path(ctx) == ROIBIN_PATH_FUSED) {
+    cudaError_t e = timed(ctx, K_FUSED, st, [&] { return launch_fused(ctx->dp, ctx->s, a, st, ctx->num_sms); });
+    return cuda_status(e);
+  }
+  return compress_plain(ctx, a, st);
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int roibin_default_params(roibin_params* p) {
+  if (!p) return ROIBIN_ERR_INVALID_ARG;
+  p->amax_thr = 300.0f;
+  p->atot_thr = 600.0f;
+  p->son_min = 10.0f;
+  p->pix_nsigma = 3.0f;
+  p->rank = 3;
+  p->ring_r0 = 5;
+  p->ring_dr = 2;
+  p->npix_min = 2;
+  p->npix_max = 30;
+  p->roi_h = 17;
+  p->roi_w = 17;
+  p->bin_h = 2;
+  p->bin_w = 2;
+  p->abs_eb = 10.0f;
+  p->quant_radius = 512;
+  p->max_peaks = 2048;
+  return ROIBIN_OK;
+}
+
+int roibin_validate(const roibin_geometry* g, const roibin_params* p) { return validate_impl(g, p); }
+
+uint64_t roibin_compress_bound(const roibin_geometry* g, const roibin_params* p) {
+  if (validate_impl(g, p) != ROIBIN_OK) return 0;
+  return bound_impl(make_dev_params(*g, *p));
+}
+
+int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_params* p,
+                      uint32_t max_frames_per_call, uint64_t hbm_budget_bytes, int device) {
+  if (!out) return ROIBIN_ERR_INVALID_ARG;
+  *out = nullptr;
+  int st = validate_impl(g, p);
+  if (st != ROIBIN_OK) return st;
+  if (max_frames_per_call < 1 || max_frames_per_call > 65535) return ROIBIN_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return ROIBIN_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  roibin_ctx* ctx = new (std::nothrow) roibin_ctx();
+  if (!ctx) return ROIBIN_ERR_OUT_OF_BUDGET;
+  ctx->device = device;
+  ctx->g = *g;
+  ctx->prm = *p;
+  ctx->dp = make_dev_params(*g, *p);
+  ctx->max_frames = max_frames_per_call;
+  ctx->budget = hbm_budget_bytes;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  ctx->fused_ok = fused_supported(ctx->dp, device);
+  const uint64_t need = carve_scratch(ctx->dp, max_frames_per_call, nullptr, nullptr) +
+                        (ctx->fused_ok ? fused_scratch_bytes_per_frame(ctx->dp) * 0 : 0);
+  if (hbm_budget_bytes && need > hbm_budget_bytes) {
+    delete ctx;
+    return ROIBIN_ERR_OUT_OF_BUDGET;
+  }
+  if (cudaMalloc(&ctx->scratch, need) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return ROIBIN_ERR_OUT_OF_BUDGET;
+  }
+  ctx->scratch_bytes = need;
+  carve_scratch(ctx->dp, max_frames_per_call, static_cast<uint8_t*>(ctx->scratch), &ctx->s);
+  *out = ctx;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_destroy(roibin_ctx* ctx) {
+  if (!ctx) return ROIBIN_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& t : ctx->pending) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  for (auto e : ctx->free_events) cudaEventDestroy(e);
+  for (auto e : ctx->slice_events) cudaEventDestroy(e);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->host_stage) cudaFree(ctx->host_stage);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  delete ctx;
+  return ROIBIN_OK;
+}
+
+uint64_t roibin_ctx_scratch_bytes(const roibin_ctx* ctx) {
+  return ctx ? ctx->scratch_bytes + ctx->host_stage_bytes : 0;
+}
+
+int roibin_ctx_set_path(roibin_ctx* ctx, int path) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  if (path != ROIBIN_PATH_AUTO && path != ROIBIN_PATH_PLAIN && path != ROIBIN_PATH_FUSED)
+    return ROIBIN_ERR_INVALID_ARG;
+  if (path == ROIBIN_PATH_FUSED && !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
+  ctx->path_req = path;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_resolved_path(const roibin_ctx* ctx) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  return resolved_path(ctx);
+}
+
+int roibin_compress(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, const uint16_t* d_peaks,
+                    const uint32_t* d_npeaks, uint8_t* d_out, uint64_t out_stride, uint64_t* d_frame_bytes,
+                    int32_t* d_frame_status, void* stream) {
+  if (!ctx || !d_frames || !d_out || !d_frame_bytes || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
+  if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
+  if ((d_peaks == nullptr) != (d_npeaks == nullptr)) return ROIBIN_ERR_INVALID_ARG;
+  if (out_stride < 16 || out_stride % 16 != 0) return ROIBIN_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_frames) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0)
+    return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  ctx->last_launches = 0;
+  return compress_device(ctx, d_frames, n_frames, d_peaks, d_npeaks, d_out, out_stride, d_frame_bytes,
+                         d_frame_status, static_cast<cudaStream_t>(stream));
+}
+
+int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes, const uint64_t* d_frame_offsets,
+                      uint32_t n_frames, float* d_frames_out, int32_t* d_frame_status, void* stream) {
+  if (!ctx || !d_in || !d_frame_offsets || !d_frames_out || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
+  if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_in) % 16 != 0) return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DecArgs a{d_in, in_bytes, d_frame_offsets, n_frames, d_frames_out, d_frame_status};
+  const DevParams& p = ctx->dp;
+  const Scratch& s = ctx->s;
+  ctx->last_launches = 0;
+  cudaError_t e;
+  if ((e = timed(ctx, K_DEC_PARSE, st, [&] { return launch_dec_parse(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_DEC_DECODE, st, [&] { return launch_dec_decode(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_DEC_LORENZO, st, [&] { return launch_dec_lorenzo(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_DEC_ROWS, st, [&] { return launch_dec_rows(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_DEC_COLS, st, [&] { return launch_dec_cols(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_DEC_PQ, st, [&] { return launch_dec_pq(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_DEC_UPSAMPLE, st, [&] { return launch_dec_upsample(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if ((e = timed(ctx, K_DEC_ROI, st, [&] { return launch_dec_roi(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_reserve_host_path(roibin_ctx* ctx) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  if (ctx->host_stage) return ROIBIN_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  const uint64_t n = ctx->max_frames;
+  const uint64_t stride = bound_impl(ctx->dp);
+  Carver c{nullptr};
+  c.take<float>(n * ctx->dp.frame_px);
+  c.take<uint8_t>(n * stride);
+  c.take<uint8_t>(n * stride);
+  c.take<uint64_t>(n + 1);
+  c.take<uint64_t>(n + 1);
+  c.take<int32_t>(n);
+  const uint64_t need = c.off + 256;
+  if (ctx->budget && ctx->scratch_bytes + need > ctx->budget) return ROIBIN_ERR_OUT_OF_BUDGET;
+  void* base = nullptr;
+  if (cudaMalloc(&base, need) != cudaSuccess) {
+    cudaGetLastError();
+    return ROIBIN_ERR_OUT_OF_BUDGET;
+  }
+  Carver d{static_cast<uint8_t*>(base)};
+  ctx->h_frames_dev = d.take<float>(n * ctx->dp.frame_px);
+  ctx->h_out_dev = d.take<uint8_t>(n * stride);
+  ctx->h_packed_dev = d.take<uint8_t>(n * stride);
+  ctx->h_bytes_dev = d.take<uint64_t>(n + 1);
+  ctx->h_offsets_dev = d.take<uint64_t>(n + 1);
+  ctx->h_status_dev = d.take<int32_t>(n);
+  ctx->h_stride = stride;
+  ctx->host_stage = base;
+  ctx->host_stage_bytes = need;
+  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  return ROIBIN_OK;
+}
+
+}  // extern "C"
+
+namespace roibin {
+// exclusive scan of frame sizes -> packed offsets; offsets[n] = total
+__global__ void k_pack_offsets(const uint64_t* sizes, uint64_t* offsets, uint32_t n) {
+  __shared__ uint64_t carry;
+  __shared__ uint64_t tmp[1024];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t b = 0; b < n; b += blockDim.x) {
+    const uint32_t i = b + threadIdx.x;
+    const uint64_t v = i < n ? sizes[i] : 0;
+    tmp[threadIdx.x] = v;
+    __syncthreads();
+    for (uint32_t d = 1; d < blockDim.x; d <<= 1) {
+      const uint64_t add = threadIdx.x >= d ? tmp[threadIdx.x - d] : 0;
+      __syncthreads();
+      tmp[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < n) offsets[i] = carry + tmp[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += tmp[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offsets[n] = carry;
+}
+}  // namespace roibin
+
+extern "C" {
+
+int roibin_compress_host(roibin_ctx* ctx, const float* h_frames, uint32_t n_frames, uint8_t* h_out,
+                         uint64_t h_out_capacity, uint64_t* h_frame_bytes, int32_t* h_frame_status,
+                         void* stream) {
+  if (!ctx || !h_frames || !h_out || !h_frame_bytes || !h_frame_status) return ROIBIN_ERR_INVALID_ARG;
+  if (!ctx->host_stage) return ROIBIN_ERR_INVALID_ARG;
+  if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t frame_bytes = ctx->dp.frame_px * 4;
+  // slices: copy slice i+1 while slice i compresses
+  const uint32_t n_slices = std::min<uint32_t>(8, n_frames);
+  const uint32_t per = ceil_div(n_frames, n_slices);
+  while (ctx->slice_events.size() < n_slices + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return ROIBIN_ERR_CUDA;
+    ctx->slice_events.push_back(e);
+  }
+  // the copy stream must not overwrite staging still read by a previous call
+  cudaEvent_t fence = ctx->slice_events[n_slices];
+  cudaEventRecord(fence, st);
+  cudaStreamWaitEvent(ctx->copy_stream, fence, 0);
+  for (uint32_t k = 0; k < n_slices; ++k) {
+    const uint32_t f0 = k * per, f1 = std::min(n_frames, f0 + per);
+    if (f0 >= f1) break;
+    if (cudaMemcpyAsync(ctx->h_frames_dev + (size_t)f0 * ctx->dp.frame_px, h_frames + (size_t)f0 * ctx->dp.frame_px,
+                        (size_t)(f1 - f0) * frame_bytes, cudaMemcpyHostToDevice, ctx->copy_stream) != cudaSuccess)
+      return ROIBIN_ERR_CUDA;
+    cudaEventRecord(ctx->slice_events[k], ctx->copy_stream);
+  }
+  ctx->last_launches = 0;
+  for (uint32_t k = 0; k < n_slices; ++k) {
+    const uint32_t f0 = k * per, f1 = std::min(n_frames, f0 + per);
+    if (f0 >= f1) break;
+    cudaStreamWaitEvent(st, ctx->slice_events[k], 0);
+    const int rc = compress_device(ctx, ctx->h_frames_dev + (size_t)f0 * ctx->dp.frame_px, f1 - f0, nullptr,
+                                   nullptr, ctx->h_out_dev + (size_t)f0 * ctx->h_stride, ctx->h_stride,
+                                   ctx->h_bytes_dev + f0, ctx->h_status_dev + f0, st);
+    if (rc != ROIBIN_OK) return rc;
+  }
+  k_pack_offsets<<<1, 1024, 0, st>>>(ctx->h_bytes_dev, ctx->h_offsets_dev, n_frames);
+  if (cudaGetLastError() != cudaSuccess) return ROIBIN_ERR_CUDA;
+  if (launch_pack(ctx->h_out_dev, ctx->h_stride, ctx->h_bytes_dev, ctx->h_offsets_dev, n_frames,
+                  ctx->h_packed_dev, st) != cudaSuccess)
+    return ROIBIN_ERR_CUDA;
+  ctx->last_launches += 2;
+  uint64_t total = 0;
+  if (cudaMemcpyAsync(&total, ctx->h_offsets_dev + n_frames, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(h_frame_bytes, ctx->h_bytes_dev, (size_t)n_frames * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(h_frame_status, ctx->h_status_dev, (size_t)n_frames * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ROIBIN_ERR_CUDA;
+  if (total > h_out_capacity) return ROIBIN_ERR_CAPACITY;
+  if (cudaMemcpyAsync(h_out, ctx->h_packed_dev, total, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ROIBIN_ERR_CUDA;
+  return ROIBIN_OK;
+}
+
+int roibin_roi_mask(roibin_ctx* ctx, const uint16_t* d_peaks, const uint32_t* d_npeaks, uint32_t n_frames,
+                    uint8_t* d_mask, void* stream) {
+  if (!ctx || !d_peaks || !d_npeaks || !d_mask || n_frames < 1) return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  return cuda_status(launch_roi_mask(ctx->dp, d_peaks, d_npeaks, n_frames, d_mask,
+                                     static_cast<cudaStream_t>(stream)));
+}
+
+int roibin_last_peaks(roibin_ctx* ctx, uint16_t* d_peaks, uint32_t* d_npeaks, uint32_t n_frames, void* stream) {
+  if (!ctx || !d_peaks || !d_npeaks || n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  return cuda_status(launch_last_peaks(ctx->dp, ctx->s, d_peaks, d_npeaks, n_frames,
+                                       static_cast<cudaStream_t>(stream)));
+}
+
+int roibin_ctx_enable_timing(roibin_ctx* ctx, int enable) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  ctx->timing = enable != 0;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_kernel_times(roibin_ctx* ctx, const char** names, double* total_ms, uint32_t* launches,
+                            int max_kernels, int* n_kernels) {
+  if (!ctx || !n_kernels) return ROIBIN_ERR_INVALID_ARG;
+  double sum[K_COUNT] = {0};
+  uint32_t cnt[K_COUNT] = {0};
+  int rc = ROIBIN_OK;
+  for (auto& t : ctx->pending) {
+    if (cudaEventSynchronize(t.stop) != cudaSuccess) rc = ROIBIN_ERR_CUDA;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+      sum[t.id] += ms;
+      cnt[t.id]++;
+    }
+    ctx->free_events.push_back(t.start);
+    ctx->free_events.push_back(t.stop);
+  }
+  ctx->pending.clear();
+  int k = 0;
+  for (int id = 0; id < K_COUNT; ++id) {
+    if (!cnt[id]) continue;
+    if (k < max_kernels) {
+      if (names) names[k] = kernel_name(id);
+      if (total_ms) total_ms[k] = sum[id];
+      if (launches) launches[k] = cnt[id];
+    }
+    ++k;
+  }
+  *n_kernels = k;
+  return rc;
+}
+
+uint32_t roibin_ctx_last_launch_count(const roibin_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+const char* roibin_status_string(int status) {
+  switch (status) {
+    case ROIBIN_OK: return "ok";
+    case ROIBIN_ERR_INVALID_ARG: return "invalid argument";
+    case ROIBIN_ERR_CAPACITY: return "capacity exceeded (peaks or output stride)";
+    case ROIBIN_ERR_CORRUPT_STREAM: return "corrupt compressed stream";
+    case ROIBIN_ERR_OUT_OF_BUDGET: return "device memory budget exceeded";
+    case ROIBIN_ERR_CUDA: return "CUDA runtime error";
+    case ROIBIN_ERR_TIMEOUT: return "bounded device wait timed out";
+    case ROIBIN_ERR_CODE_LENGTH: return "Huffman code longer than 32 bits";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,464 @@
+// roibin_internal.cuh - shared device code of the ROIBIN-SZ CUDA library.
+//
+// The arithmetic of every step lives here once, as __device__ functions, so
+// that the per-stage kernels (plain_kernels.cu) and the fused cluster kernel
+// (fused_kernel.cu) compute bit-identical results.  Float steps round exactly
+// once each, in a fixed order (explicit _rn intrinsics; the library is also
+// built with -fmad=false), so results do not depend on the launch shape.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "roibin.h"
+
+namespace roibin {
+
+// ---- stream format version 1 -------------------------------------------
+constexpr uint32_t kMagic = 0x5A534252u;  // bytes "RBSZ"
+constexpr uint32_t kVersion = 1u;
+constexpr uint32_t kHeaderBytes = 96u;
+constexpr uint32_t kChunk = 4096u;         // symbols per chunk of the bitstream
+constexpr uint32_t kCanonicalNaN = 0x7FC00000u;
+constexpr float kPqLimit = 268435456.0f;   // |q| < 2^28 keeps every delta in int32
+constexpr uint32_t kMaxSymbols = 1024u;    // 2 * quant_radius <= 1024
+constexpr uint32_t kMaxBinsPerFrame = 5702886u;
+constexpr uint32_t kMaxPeaksLimit = 8192u;
+constexpr uint32_t kThrCap = 16384u;       // pixels >= amax_thr listed per frame
+                                           // before the dense candidate scan
+
+// Everything a kernel needs to know about the geometry and the parameters.
+struct DevParams {
+  uint32_t P, H, W;   // panels, rows, cols
+  uint32_t Hb, Wb;    // binned rows / cols per panel
+  uint32_t M;         // bins per frame = P * Hb * Wb
+  uint32_t n_chunks;  // ceil(M / kChunk)
+  uint64_t frame_px;  // P * H * W
+  int32_t bh, bw;
+  float amax, atot_thr, son_min, pix_nsigma;
+  int32_t rank, ring_r0, ring_dr, npix_min, npix_max;
+  int32_t roi_h, roi_w;
+  float eb, two_eb, recip;  // two_eb = fl(2 eb), recip = fl(1 / two_eb)
+  int32_t R;                // quant radius
+  uint32_t nsym;            // 2R
+  uint32_t max_peaks;
+  uint32_t thr_cap;
+};
+
+// Byte layout of one frame's stream, filled by the plan step.
+struct FramePlan {
+  uint32_t n_peaks, n_lo, n_pq, n_words;
+  uint64_t off_peaks, off_roi, off_len, off_cidx, off_lo, off_pq, off_bits, total;
+};
+
+// Per-frame parameters read back from a stream header by the decompressor.
+struct DecInfo {
+  FramePlan pl;
+  uint64_t base;      // byte offset of the stream in the input buffer
+  float eb, two_eb;
+  int32_t R, roi_h, roi_w;
+  uint32_t nsym;
+};
+
+// Per-frame scratch owned by the context (indexed by frame slot).
+struct Scratch {
+  uint32_t* thr_count;    // [n] pixels >= amax_thr seen (may exceed thr_cap)
+  uint32_t* thr_idx;      // [n][thr_cap] pixel index within the frame
+  uint32_t* peak_count;   // [n] accepted peaks (may exceed max_peaks)
+  uint32_t* peak_key;     // [n][max_peaks] pixel index within the frame
+  uint32_t* hist;         // [n][kMaxSymbols]
+  uint8_t* cb_len;        // [n][kMaxSymbols]
+  uint32_t* cb_code;      // [n][kMaxSymbols]
+  uint16_t* codes;        // [n][n_chunks * kChunk] (plain path); bit 15 marks a
+                          // prequantisation outlier, bits 0..9 hold the code
+  int32_t* lo_delta;      // [n][M] Lorenzo-outlier deltas, written at their bin
+  uint32_t* pq_bits;      // [n][M] prequantisation-outlier float bits, at their bin
+  uint32_t* chunk_words;  // [n][n_chunks] words per chunk -> word offset of chunk
+  uint32_t* chunk_lo;     // [n][n_chunks] Lorenzo outliers per chunk -> offset
+  uint32_t* chunk_pq;     // [n][n_chunks] prequant outliers per chunk -> offset
+  FramePlan* plan;        // [n]
+  int32_t* status;        // [n]
+  // decompression (aliases lo_delta / pq_bits: a context runs one call at a time)
+  int32_t* dq;            // [n][M] delta, then q
+  float* bhat;            // [n][M]
+  uint32_t* dec_table;    // [n][kDecTableWords] canonical decoding tables
+  uint32_t* dec_zero;     // [n] code-0 symbols decoded
+  DecInfo* dec_info;      // [n]
+};
+
+constexpr uint32_t kDecTableWords = 34 + 34 + 34 + kMaxSymbols;  // count, first, index, symbols
+
+// ---- small helpers -------------------------------------------------------
+__host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15u) & ~uint64_t(15u); }
+__host__ __device__ inline uint32_t ceil_div(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
+
+__device__ inline uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ inline uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// Inclusive warp scan of a u32.
+__device__ inline uint32_t warp_incl_scan(uint32_t v) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xffffffffu, v, d);
+    if ((int)lane_id() >= d) v += n;
+  }
+  return v;
+}
+
+// Exclusive block scan of one u32 per thread (blockDim.x <= 1024, multiple of
+// 32).  `tmp` holds >= 33 words of shared memory.  Returns the exclusive prefix;
+// *total receives the block sum.  Contains __syncthreads.
+__device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* tmp, uint32_t* total) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t incl = warp_incl_scan(v);
+  if (lane == 31) tmp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < nwarps ? tmp[lane] : 0u;
+    const uint32_t wi = warp_incl_scan(w);
+    if (lane < nwarps) tmp[lane] = wi - w;
+    if (lane == 31) tmp[32] = wi;
+  }
+  __syncthreads();
+  const uint32_t r = tmp[warp] + incl - v;
+  *total = tmp[32];
+  __syncthreads();
+  return r;
+}
+
+// ---- a4 + a5: one bin's value and its prequantisation ---------------------
+// Bin mean: the block's first pixel, plus the others in row-major order, in
+// float32, then one IEEE division by the number of in-panel pixels (§4.1, §6).
+// Prequantisation (§5.3.3, dual quantisation): t = rint(b * recip); outlier
+// when b is not finite, |t| >= 2^28 or |b - fl(t * 2eb)| > eb in fp64.
+struct Quant {
+  int32_t q;
+  uint32_t outlier_bits;  // valid when outlier
+  bool outlier;
+};
+
+__device__ __forceinline__ Quant prequantize(float b, const DevParams& p) {
+  Quant r;
+  const float t = rintf(__fmul_rn(b, p.recip));
+  bool out = !isfinite(b) || !(fabsf(t) < kPqLimit);
+  if (!out) {
+    const float bh = __fmul_rn(t, p.two_eb);
+    if (fabs(__dadd_rn((double)b, -(double)bh)) > (double)p.eb) out = true;
+  }
+  r.outlier = out;
+  r.q = out ? 0 : (int32_t)t;
+  r.outlier_bits = isnan(b) ? kCanonicalNaN : __float_as_uint(b);
+  return r;
+}
+
+// a7: code of a Lorenzo residual (code 0 = outlier).
+__device__ __forceinline__ uint32_t quant_code(int32_t delta, int32_t R) {
+  return (delta > -R && delta < R) ? (uint32_t)(delta + R) : 0u;
+}
+
+// ---- a1: local-maximum candidate (§4.2) ----------------------------------
+// >= every pixel of the panel-clipped window, > every pixel before it in
+// row-major order, and >= amax_thr.
+__device__ inline bool is_candidate(const float* __restrict__ panel, int H, int W, int r, int c,
+                                    int rank, float amax) {
+  const float v = panel[(size_t)r * W + c];
+  if (!(v >= amax)) return false;
+  for (int dr = -rank; dr <= rank; ++dr) {
+    const int rr = r + dr;
+    if (rr < 0 || rr >= H) continue;
+    for (int dc = -rank; dc <= rank; ++dc) {
+      const int cc = c + dc;
+      if (cc < 0 || cc >= W || (dr == 0 && dc == 0)) continue;
+      const float u = __ldg(panel + (size_t)rr * W + cc);
+      const bool precedes = dr < 0 || (dr == 0 && dc < 0);
+      if (precedes ? !(v > u) : !(v >= u)) return false;
+    }
+  }
+  return true;
+}
+
+// ---- a2: candidate evaluation (§4.2), fp64 in a fixed order ---------------
+__device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int W, int r, int c,
+                                     const DevParams& p) {
+  const int r0 = p.ring_r0, outer = p.ring_r0 + p.ring_dr, reach = outer - 1;
+  double sum = 0.0;
+  int n = 0;
+  for (int dr = -reach; dr <= reach; ++dr) {
+    for (int dc = -reach; dc <= reach; ++dc) {
+      const int d2 = dr * dr + dc * dc;
+      if (d2 < r0 * r0 || d2 >= outer * outer) continue;
+      const int rr = r + dr, cc = c + dc;
+      if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+      sum = __dadd_rn(sum, (double)__ldg(panel + (size_t)rr * W + cc));
+      ++n;
+    }
+  }
+  double bkg = 0.0, var = 0.0;
+  if (n > 0) {
+    bkg = __ddiv_rn(sum, (double)n);
+    double ss = 0.0;
+    for (int dr = -reach; dr <= reach; ++dr) {
+      for (int dc = -reach; dc <= reach; ++dc) {
+        const int d2 = dr * dr + dc * dc;
+        if (d2 < r0 * r0 || d2 >= outer * outer) continue;
+        const int rr = r + dr, cc = c + dc;
+        if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+        const double d = __dadd_rn((double)__ldg(panel + (size_t)rr * W + cc), -bkg);
+        ss = __dadd_rn(ss, __dmul_rn(d, d));
+      }
+    }
+    var = __ddiv_rn(ss, (double)n);
+  }
+  const double sigma = __dsqrt_rn(var);
+  const double thr = __dmul_rn((double)p.pix_nsigma, sigma);
+  int npix = 0;
+  double atot = 0.0;
+  for (int dr = -p.rank; dr <= p.rank; ++dr) {
+    for (int dc = -p.rank; dc <= p.rank; ++dc) {
+      const int rr = r + dr, cc = c + dc;
+      if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+      const double d = __dadd_rn((double)__ldg(panel + (size_t)rr * W + cc), -bkg);
+      if (d > thr) {
+        ++npix;
+        atot = __dadd_rn(atot, d);
+      }
+    }
+  }
+  if (npix < p.npix_min || npix > p.npix_max) return false;
+  if (!(atot > (double)p.atot_thr)) return false;
+  const double noise = __dmul_rn(__dmul_rn((double)p.son_min, sigma), __dsqrt_rn((double)npix));
+  return atot > noise;
+}
+
+// ---- a9: deterministic Huffman codebook, built by one CTA ------------------
+// Leaves are the symbols with a non-zero count sorted by (count, symbol); the
+// two-queue merge takes the leaf on equal weights; code length = leaf depth
+// (a lone symbol gets 1); canonical codes by (length, symbol) ascending.
+struct HuffSmem {
+  uint32_t f[kMaxSymbols];        // compacted counts (symbol order), then sorted
+  uint16_t s[kMaxSymbols];        // compacted symbols, then sorted
+  uint32_t sf[kMaxSymbols];
+  uint16_t ss[kMaxSymbols];
+  uint32_t w[2 * kMaxSymbols];    // node weights: leaves [0,n), internal [n,2n-1)
+  uint16_t parent[2 * kMaxSymbols];
+  uint32_t cnt_len[34];
+  uint32_t first_code[34];
+  uint32_t running[34];
+  uint32_t warp_cnt[32][34];
+  uint32_t scan_tmp[33];
+  uint32_t n;
+  int32_t status;
+};
+
+// hist: counts in shared or global memory (kMaxSymbols entries, nsym used).
+// Writes len[nsym] and code[nsym] (shared or global).  Returns ROIBIN_OK or
+// ROIBIN_ERR_CODE_LENGTH (same value in every thread).  All threads of the
+// block must call it; blockDim.x must be a multiple of 32.
+__device__ inline int build_codebook(const uint32_t* hist, uint32_t nsym, HuffSmem& h,
+                                     uint8_t* len_out, uint32_t* code_out) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  // 1. compact the non-zero symbols, keeping symbol order
+  uint32_t base = 0;
+  for (uint32_t s0 = 0; s0 < nsym; s0 += nt) {
+    const uint32_t s = s0 + tid;
+    const uint32_t f = s < nsym ? hist[s] : 0u;
+    uint32_t tot;
+    const uint32_t pos = block_excl_scan(f > 0 ? 1u : 0u, h.scan_tmp, &tot);
+    if (f > 0) {
+      h.f[base + pos] = f;
+      h.s[base + pos] = (uint16_t)s;
+    }
+    base += tot;
+  }
+  if (tid == 0) {
+    h.n = base;
+    h.status = ROIBIN_OK;
+  }
+  for (uint32_t L = tid; L < 34; L += nt) {
+    h.cnt_len[L] = 0;
+    h.running[L] = 0;
+  }
+  __syncthreads();
+  const uint32_t n = h.n;
+  // 2. rank sort by (count, symbol): symbols are already ascending
+  for (uint32_t i = tid; i < n; i += nt) {
+    const uint32_t fi = h.f[i];
+    uint32_t rank = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+      const uint32_t fj = h.f[j];
+      rank += (fj < fi) || (fj == fi && j < i);
+    }
+    h.sf[rank] = fi;
+    h.ss[rank] = h.s[i];
+  }
+  __syncthreads();
+  for (uint32_t s = tid; s < nsym; s += nt) len_out[s] = 0;
+  // 3. two-queue merge (sequential by nature; one thread)
+  if (tid == 0 && n >= 2) {
+    for (uint32_t i = 0; i < n; ++i) h.w[i] = h.sf[i];
+    uint32_t nl = 0, ni = n, nc = n;
+    for (uint32_t k = 0; k + 1 < n; ++k) {
+      uint32_t a, b;
+      if (nl < n && (ni >= nc || h.w[nl] <= h.w[ni])) a = nl++; else a = ni++;
+      if (nl < n && (ni >= nc || h.w[nl] <= h.w[ni])) b = nl++; else b = ni++;
+      h.w[nc] = h.w[a] + h.w[b];
+      h.parent[a] = (uint16_t)nc;
+      h.parent[b] = (uint16_t)nc;
+      ++nc;
+    }
+  }
+  __syncthreads();
+  // 4. depths by walking to the root
+  for (uint32_t i = tid; i < n; i += nt) {
+    uint32_t d = 1;
+    if (n >= 2) {
+      const uint32_t root = 2 * n - 2;
+      uint32_t x = i;
+      d = 0;
+      while (x != root && d <= 40) {
+        x = h.parent[x];
+        ++d;
+      }
+    }
+    if (d > 32) h.status = ROIBIN_ERR_CODE_LENGTH;
+    const uint32_t L = d > 33 ? 33 : d;
+    len_out[h.ss[i]] = (uint8_t)L;
+    atomicAdd(&h.cnt_len[L], 1u);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint64_t c = 0;
+    uint32_t prev = 0;
+    for (uint32_t L = 1; L <= 32; ++L) {
+      h.first_code[L] = 0;
+      if (h.cnt_len[L] == 0) continue;
+      c = prev == 0 ? 0 : (c + h.cnt_len[prev]) << (L - prev);
+      h.first_code[L] = (uint32_t)c;
+      prev = L;
+    }
+  }
+  __syncthreads();
+  // 5. canonical codes: first_code[L] + rank among same-length symbols
+  const uint32_t warp = tid >> 5, nwarps = nt >> 5;
+  for (uint32_t s0 = 0; s0 < nsym; s0 += nt) {
+    const uint32_t s = s0 + tid;
+    const uint32_t L = s < nsym ? len_out[s] : 0u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, L);
+    const uint32_t lower = __popc(peers & lanemask_lt());
+    for (uint32_t k = tid; k < 32 * 34; k += nt) (&h.warp_cnt[0][0])[k] = 0;
+    __syncthreads();
+    if (s < nsym && L > 0 && lower == 0) h.warp_cnt[warp][L] = __popc(peers);
+    __syncthreads();
+    if (s < nsym && L > 0 && L <= 32) {
+      uint32_t before = h.running[L];
+      for (uint32_t w = 0; w < warp; ++w) before += h.warp_cnt[w][L];
+      code_out[s] = h.first_code[L] + before + lower;
+    } else if (s < nsym) {
+      code_out[s] = 0;
+    }
+    __syncthreads();
+    if (tid < 34) {
+      uint32_t add = 0;
+      for (uint32_t w = 0; w < nwarps; ++w) add += h.warp_cnt[w][tid];
+      h.running[tid] += add;
+    }
+    __syncthreads();
+  }
+  const int st = h.status;
+  __syncthreads();
+  return st;
+}
+
+// ---- a10: append a codeword into a zeroed word buffer in shared memory -------
+// bit position `pos` counts from the chunk start; MSB of the codeword first.
+__device__ __forceinline__ void put_bits(uint32_t* buf, uint32_t pos, uint32_t cw, uint32_t L) {
+  const uint32_t w = pos >> 5, o = pos & 31u;
+  if (o + L <= 32u) {
+    atomicOr(buf + w, cw << (32u - o - L));
+  } else {
+    atomicOr(buf + w, cw >> (o + L - 32u));
+    atomicOr(buf + w + 1, cw << (64u - o - L));
+  }
+}
+
+// ---- launchers (one translation unit each) --------------------------------
+struct PlainArgs {
+  const float* frames;
+  uint32_t n_frames;
+  const uint16_t* user_peaks;   // nullable
+  const uint32_t* user_npeaks;  // nullable
+  uint8_t* out;
+  uint64_t out_stride;
+  uint64_t* frame_bytes;
+  int32_t* frame_status;
+  uint32_t bands_per_panel;
+  uint32_t rows_per_step;
+};
+
+// Each launcher enqueues one kernel and returns cudaGetLastError().
+// `timer` may be null; when set, it brackets the launch with events.
+struct KernelTimer {
+  void (*begin)(void* self, int kernel_id, cudaStream_t s);
+  void (*end)(void* self, int kernel_id, cudaStream_t s);
+  void* self;
+};
+
+enum KernelId {
+  K_RESET = 0,
+  K_STREAM,
+  K_PEAKS,
+  K_PEAKS_FINAL,
+  K_HUFFMAN,
+  K_CHUNKS,
+  K_PLAN,
+  K_ENCODE,
+  K_ROI,
+  K_FUSED,
+  K_DEC_PARSE,
+  K_DEC_DECODE,
+  K_DEC_LORENZO,
+  K_DEC_ROWS,
+  K_DEC_COLS,
+  K_DEC_PQ,
+  K_DEC_UPSAMPLE,
+  K_DEC_ROI,
+  K_ROI_MASK,
+  K_PACK,
+  K_COUNT
+};
+const char* kernel_name(int id);
+
+cudaError_t launch_reset(const DevParams& p, const Scratch& s, uint32_t n, cudaStream_t st);
+cudaError_t launch_stream(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
+cudaError_t launch_peaks(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
+cudaError_t launch_peaks_final(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
+cudaError_t launch_huffman(const DevParams& p, const Scratch& s, uint32_t n, cudaStream_t st);
+cudaError_t launch_chunks(const DevParams& p, const Scratch& s, uint32_t n, cudaStream_t st);
+cudaError_t launch_plan(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
+cudaError_t launch_encode(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
+cudaError_t launch_roi(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
+cudaError_t launch_last_peaks(const DevParams& p, const Scratch& s, uint16_t* peaks, uint32_t* npeaks,
+                              uint32_t n, cudaStream_t st);
+
+struct DecArgs {
+  const uint8_t* in;
+  uint64_t in_bytes;
+  const uint64_t* offsets;
+  uint32_t n_frames;
+  float* out;
+  int32_t* frame_status;
+};
+cudaError_t launch_dec_parse(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_decode(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_lorenzo(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_rows(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_cols(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_pq(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_upsample(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_roi(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_roi_mask(const DevParams& p, const uint16_t* peaks, const uint32_t* npeaks,
+                            uint32_t n, uint8_t* mask, cudaStream_t st);
+cudaError_t launch_pack(const uint8_t* src, uint64_t stride, const uint64_t* sizes, const uint64_t* offsets,
+                        uint32_t n, uint8_t* dst, cudaStream_t st);
+
+}  // namespace roibin

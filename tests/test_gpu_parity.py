@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle,
+byte for byte on the compressed streams and bit for bit on the
+reconstructions, over seeded synthetic frames: small cases spanning several
+tiles and ragged tails, the paper's detector shapes, and the edge cases."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins
+import paper_2206_11297_gb300 as rb
+from gpu_util import assert_parity, gpu_compress, gpu_decompress, oparams
+from synthetic import RECIPES, FrameRecipe, make_frame
+
+pytestmark = pytest.mark.gpu
+
+PATHS = [rb.PATH_PLAIN]
+
+
+def small_batch(geom, n, seed, peaks=("uniform", 2, 12), **kw):
+    r = FrameRecipe(geom, peaks=peaks, seed=seed, **kw)
+    return np.stack([make_frame(r, k) for k in range(n)])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rb.library()
+    oracle.lib()
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("geom", [(2, 12, 13), (1, 7, 8), (3, 21, 27), (4, 37, 52), (2, 64, 100), (1, 3, 1)])
+def test_small_geometries(geom, path):
+    f = small_batch(geom, 3, seed=sum(geom))
+    assert_parity(f, rb.default_params(atot_thr=300.0), path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("change", [
+    dict(bin_h=1, bin_w=1), dict(bin_h=3, bin_w=3), dict(bin_h=2, bin_w=3), dict(bin_h=4, bin_w=1),
+    dict(abs_eb=1.0), dict(abs_eb=0.5), dict(abs_eb=90.0), dict(quant_radius=4), dict(quant_radius=64),
+    dict(roi_h=5, roi_w=7), dict(roi_h=16, roi_w=16), dict(rank=1), dict(rank=2),
+    dict(pix_nsigma=0.0, npix_max=49), dict(ring_r0=3, ring_dr=1), dict(max_peaks=0),
+])
+def test_parameters(change, path):
+    f = small_batch((3, 45, 62), 2, seed=7, peaks=("uniform", 5, 20))
+    p = rb.default_params(atot_thr=300.0)
+    for k, v in change.items():
+        setattr(p, k, v)
+    assert_parity(f, p, path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_tiny_frames_with_planted_features(path):
+    f = np.stack([oracle_pins.tiny_frame(s, shape=(2, 12, 13)) for s in range(4)])
+    assert_parity(f, rb.default_params(atot_thr=300.0), path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_cspad_single_frame(path):
+    f = make_frame(RECIPES["cspad_single"], 0)[None]
+    st, nb, _ = assert_parity(f, rb.default_params(), path)
+    assert st[0] == 0 and nb[0] < f.nbytes / 50
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_cspad_batch(path):
+    r = RECIPES["cspad_batch"]
+    f = np.stack([make_frame(r, k) for k in range(6)])
+    assert_parity(f, rb.default_params(), path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("eb", [1.0, 10.0, 50.0])
+def test_epix_hot_pixels(eb, path):
+    r = RECIPES["epix_hot"]
+    f = np.stack([make_frame(r, k) for k in range(3)])
+    assert_parity(f, rb.default_params(abs_eb=eb), path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_jungfrau(path):
+    r = RECIPES["jungfrau_mixed"]
+    f = np.stack([make_frame(r, k) for k in range(2)])
+    assert_parity(f, rb.default_params(), path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_special_frames(path):
+    geom = (3, 40, 44)
+    rng = np.random.default_rng(0)
+    const = np.full(geom, 20.0, np.float32)
+    zeros = np.zeros(geom, np.float32)
+    bright = (400 + rng.normal(0, 5, geom)).astype(np.float32)  # every pixel >= amax: dense scan
+    nonfinite = small_batch(geom, 1, 3)[0]
+    nonfinite[0, 3, 4] = np.nan
+    nonfinite[1, 10, 10:14] = np.inf
+    nonfinite[2, 20, 20] = -np.inf
+    nonfinite[2, 30, 30] = np.array([0xFFC01234], np.uint32).view(np.float32)[0]
+    huge = small_batch(geom, 1, 4)[0]
+    huge[0, :4, :4] = 1e30
+    huge[1, 5:9, 5:9] = -3e9
+    negative = (rng.normal(-50, 30, geom)).astype(np.float32)
+    f = np.stack([const, zeros, bright, nonfinite, huge, negative])
+    assert_parity(f, rb.default_params(atot_thr=300.0), path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_dense_candidate_fallback_large(path):
+    # more pixels >= amax than the per-frame list holds (16384): the dense scan runs
+    geom = (2, 150, 160)
+    rng = np.random.default_rng(5)
+    f = (350 + rng.normal(0, 20, (1, *geom))).astype(np.float32)
+    assert_parity(f, rb.default_params(atot_thr=300.0, max_peaks=8192), path)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_user_peaks(path):
+    geom = (3, 30, 33)
+    f = small_batch(geom, 3, 9)
+    p = rb.default_params()
+    peaks = np.zeros((3, p.max_peaks, 3), np.uint16)
+    npk = np.array([3, 0, 2], np.uint32)
+    peaks[0, :3] = [[2, 29, 32], [0, 0, 0], [1, 15, 16]]
+    peaks[2, :2] = [[1, 3, 3], [1, 3, 3]]  # duplicates are kept
+    assert_parity(f, p, path, peaks=peaks, npeaks=npk)
+    bad = peaks.copy()
+    bad[1, 0] = [3, 0, 0]  # panel out of range
+    st, _, _ = gpu_compress(f, p, path=path, peaks=bad, npeaks=np.array([3, 1, 2], np.uint32))
+    assert st.tolist() == [0, rb.ERR_INVALID_ARG, 0]
+    st, _, _ = gpu_compress(f, p, path=path, peaks=peaks, npeaks=np.array([3, p.max_peaks + 1, 2], np.uint32))
+    assert st[1] == rb.ERR_CAPACITY
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_capacity_errors(path):
+    geom = (2, 40, 48)
+    f = small_batch(geom, 2, 12, peaks=("fixed", 6))
+    p = rb.default_params(atot_thr=300.0)
+    ref_sizes = [len(oracle.compress_frame(f[k], oparams(p))[1]) for k in range(2)]
+    stride = (min(ref_sizes) // 16) * 16
+    st, nb, _ = gpu_compress(f, p, path=path, out_stride=stride)
+    for k in range(2):
+        if ref_sizes[k] > stride:
+            assert st[k] == rb.ERR_CAPACITY and nb[k] == ref_sizes[k]
+        else:
+            assert st[k] == 0
+    p2 = rb.default_params(atot_thr=300.0, max_peaks=1)
+    st, nb, _ = gpu_compress(f, p2, path=path)
+    for k in range(2):
+        ost, _ = oracle.compress_frame(f[k], oparams(p2))
+        assert st[k] == ost
+
+
+def test_corrupt_streams_are_rejected():
+    geom = (2, 24, 28)
+    f = small_batch(geom, 1, 13)
+    p = rb.default_params(atot_thr=300.0)
+    st, ref = oracle.compress_frame(f[0], oparams(p))
+    h = oracle.parse_header(ref)
+    o = oracle.section_offsets(h)
+    bad_magic = ref.copy()
+    bad_magic[0] ^= 0xFF
+    bad_total = ref.copy()
+    bad_total[64] ^= 0x10
+    bad_index = ref.copy()
+    if h["n_chunks"] > 1:
+        bad_index[o["chunk_index"] + 4:o["chunk_index"] + 8] = 0xFF
+    bad_len = ref.copy()
+    bad_len[o["lengths"]:o["lengths"] + 2 * h["quant_radius"]] = 0
+    bad_bits = ref.copy()
+    bad_bits[o["bitstream"]:o["end"]] = 0xFF
+    rec, dst = gpu_decompress([bad_magic, bad_total, bad_len, bad_bits, ref], geom, p)
+    assert dst.tolist()[:4] == [rb.ERR_CORRUPT_STREAM] * 4 and dst[4] == 0
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_roi_mask_and_peaks_match_oracle(path):
+    import torch
+    geom = (3, 50, 60)
+    f = small_batch(geom, 3, 21, peaks=("uniform", 5, 15))
+    p = rb.default_params(atot_thr=300.0)
+    with rb.Context(geom, p, max_frames=3) as ctx:
+        ctx.set_path(path)
+        ctx.compress(torch.from_numpy(f).cuda())
+        peaks, npk = ctx.last_peaks(3)
+        mask = ctx.roi_mask(peaks, npk, 3)
+        torch.cuda.synchronize()
+        peaks = peaks.cpu().numpy().view(np.uint16)
+        npk, mask = npk.cpu().numpy(), mask.cpu().numpy()
+    for k in range(3):
+        st, opk, n = oracle.find_peaks(f[k], oparams(p))
+        assert npk[k] == n and np.array_equal(peaks[k, :n], opk)
+        assert np.array_equal(mask[k], oracle.roi_mask(geom, oparams(p), opk))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_batch_composition_invariance(path):
+    """A frame compresses to the same bytes alone and inside any batch."""
+    r = RECIPES["cspad_batch"]
+    f = np.stack([make_frame(r, k) for k in range(4)])
+    p = rb.default_params()
+    _, _, together = gpu_compress(f, p, path=path)
+    for k in (0, 3):
+        _, _, alone = gpu_compress(f[k:k + 1], p, path=path)
+        assert np.array_equal(alone[0], together[k])
