@@ -80,32 +80,30 @@ __device__ __forceinline__ void phase_a_v4(const float* __restrict__ panel, cons
       if (it >= items) continue;
       const uint32_t il = it / NP, pr = it - il * NP;
       const uint32_t i = i0 + il, j0 = 2 * pr;
-      float s0 = __fadd_rn(a[u].x, a[u].y), s1 = __fadd_rn(a[u].z, a[u].w);
-      float c = 2.0f;
-      if (two[u]) {
-        s0 = __fadd_rn(__fadd_rn(s0, b[u].x), b[u].y);
-        s1 = __fadd_rn(__fadd_rn(s1, b[u].z), b[u].w);
-        c = 4.0f;
-      }
-      const Quant q0 = prequantize(__fdiv_rn(s0, c), p);
-      const Quant q1 = prequantize(__fdiv_rn(s1, c), p);
-      qrow0[(size_t)il * p.Wb + j0] = q0.q;
-      qrow0[(size_t)il * p.Wb + j0 + 1] = q1.q;
+      float v0, v1;
+      bin_pair(a[u], b[u], two[u], v0, v1);
+      const Quant q0 = prequantize(v0, p);
+      const Quant q1 = prequantize(v1, p);
+      *reinterpret_cast<int2*>(qrow0 + (size_t)il * p.Wb + j0) = make_int2(q0.q, q1.q);
       if (kOwn) {
         pqf[(size_t)il * p.Wb + j0] = q0.outlier;
         pqf[(size_t)il * p.Wb + j0 + 1] = q1.outlier;
         const uint32_t bin0 = (pn * p.Hb + i) * p.Wb + j0;
         if (q0.outlier) s.pq_bits[(size_t)f * p.M + bin0] = q0.outlier_bits;
         if (q1.outlier) s.pq_bits[(size_t)f * p.M + bin0 + 1] = q1.outlier_bits;
-        // pixels >= amax_thr for the peak finder (rare: plain atomics)
-        const float px[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
-        const int npx = two[u] ? 8 : 4;
-        for (int k = 0; k < npx; ++k) {
-          if (px[k] >= p.amax) {
-            const uint32_t r = 2 * i + (k >> 2), col = 4 * pr + (k & 3);
-            const uint32_t slot = atomicAdd(s.thr_count + f, 1u);
-            if (slot < p.thr_cap)
-              s.thr_idx[(size_t)f * p.thr_cap + slot] = (pn * p.H + r) * p.W + col;
+        // pixels >= amax_thr for the peak finder (rare: screen with the max)
+        const float m = fmaxf(fmaxf(fmaxf(a[u].x, a[u].y), fmaxf(a[u].z, a[u].w)),
+                              fmaxf(fmaxf(b[u].x, b[u].y), fmaxf(b[u].z, b[u].w)));
+        if (m >= p.amax) {
+          const float px[8] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
+          const int npx = two[u] ? 8 : 4;
+          for (int k = 0; k < npx; ++k) {
+            if (px[k] >= p.amax) {
+              const uint32_t r = 2 * i + (k >> 2), col = 4 * pr + (k & 3);
+              const uint32_t slot = atomicAdd(s.thr_count + f, 1u);
+              if (slot < p.thr_cap)
+                s.thr_idx[(size_t)f * p.thr_cap + slot] = (pn * p.H + r) * p.W + col;
+            }
           }
         }
       }
@@ -200,8 +198,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(DevParams p, Scratch 
         codes[bin] = (uint16_t)(code | flag);
         if (code == 0) s.lo_delta[(size_t)f * p.M + bin] = delta;
       }
-      const uint32_t peers = __match_any_sync(0xffffffffu, code);
-      if (code != 0xFFFFu && (peers & lanemask_lt()) == 0) atomicAdd(&sm.hist[code], __popc(peers));
+      hist_add_warp(sm.hist, code, (uint32_t)p.R);
     }
     __syncthreads();
     // the last row of this step is the row above the next one
@@ -215,33 +212,46 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(DevParams p, Scratch 
 
 // ---------------------------------------------------------------------------
 // peaks: local-maximum test and evaluation of every listed pixel (or, when
-// the list overflowed, of every pixel of the frame).  Accepted peaks are
-// appended in any order; peaks_final sorts them.
-constexpr int kPeakBlocks = 64;
+// the list overflowed, of every pixel >= amax_thr of the frame), one warp per
+// pixel.  Accepted peaks are appended in any order; peaks_final sorts them.
+constexpr int kPeakBlocks = 16;
+constexpr int kPeakWarps = 8;
 
-__global__ void __launch_bounds__(256) k_peaks(DevParams p, Scratch s, PlainArgs a) {
+__global__ void __launch_bounds__(kPeakWarps * 32) k_peaks(DevParams p, Scratch s, PlainArgs a) {
+  extern __shared__ float nb_all[];
+  const int side = 2 * peak_reach(p) + 1;
+  float* nb = nb_all + (threadIdx.x >> 5) * side * side;
   const uint32_t f = blockIdx.y;
   const float* frame = a.frames + (size_t)f * p.frame_px;
   const uint32_t count = s.thr_count[f];
-  const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool dense = count > p.thr_cap;
-  const uint64_t n_items = dense ? p.frame_px : count;
-  for (uint64_t e = t0; e < n_items; e += stride) {
-    uint32_t px;
-    if (dense) {
-      px = (uint32_t)e;
-      if (!(__ldg(frame + px) >= p.amax)) continue;
-    } else {
-      px = s.thr_idx[(size_t)f * p.thr_cap + e];
-    }
-    const uint32_t pn = px / (p.H * p.W), rem = px - pn * p.H * p.W;
+  const uint32_t warp = blockIdx.x * kPeakWarps + (threadIdx.x >> 5);
+  const uint32_t nwarps = gridDim.x * kPeakWarps;
+  const uint32_t plane = p.H * p.W;
+  auto test = [&](uint32_t px) {
+    const uint32_t pn = px / plane, rem = px - pn * plane;
     const uint32_t r = rem / p.W, c = rem - r * p.W;
-    const float* panel = frame + (size_t)pn * p.H * p.W;
-    if (!is_candidate(panel, p.H, p.W, r, c, p.rank, p.amax)) continue;
-    if (!evaluate_peak(panel, p.H, p.W, r, c, p)) continue;
-    const uint32_t slot = atomicAdd(s.peak_count + f, 1u);
-    if (slot < p.max_peaks) s.peak_key[(size_t)f * p.max_peaks + slot] = px;
+    const float* panel = frame + (size_t)pn * plane;
+    if (warp_peak_test(panel, p.H, p.W, r, c, p, nb, [](const float* q) { return __ldg(q); })) {
+      if (lane_id() == 0) {
+        const uint32_t slot = atomicAdd(s.peak_count + f, 1u);
+        if (slot < p.max_peaks) s.peak_key[(size_t)f * p.max_peaks + slot] = px;
+      }
+    }
+  };
+  if (count <= p.thr_cap) {
+    for (uint32_t e = warp; e < count; e += nwarps) test(s.thr_idx[(size_t)f * p.thr_cap + e]);
+    return;
+  }
+  // dense: the warp takes 32 pixels at a time and tests those >= amax_thr
+  for (uint64_t base = (uint64_t)warp * 32; base < p.frame_px; base += (uint64_t)nwarps * 32) {
+    const uint64_t px = base + lane_id();
+    const bool hot = px < p.frame_px && __ldg(frame + px) >= p.amax;
+    uint32_t m = __ballot_sync(0xffffffffu, hot);
+    while (m) {
+      const uint32_t l = __ffs(m) - 1;
+      m &= m - 1;
+      test((uint32_t)(base + l));
+    }
   }
 }
 
@@ -627,8 +637,10 @@ cudaError_t launch_stream(const DevParams& p, const Scratch& s, const PlainArgs&
 
 cudaError_t launch_peaks(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st) {
   if (a.user_peaks) return cudaSuccess;
+  const int side = 2 * peak_reach(p) + 1;
+  const size_t smem = (size_t)kPeakWarps * side * side * sizeof(float);
   dim3 grid(kPeakBlocks, a.n_frames);
-  k_peaks<<<grid, 256, 0, st>>>(p, s, a);
+  k_peaks<<<grid, kPeakWarps * 32, smem, st>>>(p, s, a);
   return cudaGetLastError();
 }
 

@@ -15,14 +15,6 @@
 
 using namespace roibin;
 
-namespace roibin {
-// fused_kernel.cu
-bool fused_supported(const DevParams& p, int device);
-cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st,
-                         int num_sms);
-uint64_t fused_scratch_bytes_per_frame(const DevParams& p);
-}  // namespace roibin
-
 struct TimedLaunch {
   int id;
   cudaEvent_t start, stop;
@@ -41,6 +33,9 @@ struct roibin_ctx {
   uint32_t max_frames = 0;
   int path_req = ROIBIN_PATH_AUTO;
   bool fused_ok = false;
+  FusedShape fshape{};
+  Scratch fs{};
+  void* fscratch = nullptr;
   uint32_t last_launches = 0;
   // timing
   bool timing = false;
@@ -114,6 +109,13 @@ DevParams make_dev_params(const roibin_geometry& g, const roibin_params& p) {
   d.two_eb = two;
   volatile float rec = 1.0f / d.two_eb;
   d.recip = rec;
+  if (p.abs_eb >= 1e-30f) {
+    d.eb_lo = (float)((double)p.abs_eb * (1.0 - 1.0 / 1048576.0));
+    d.eb_hi = (float)((double)p.abs_eb * (1.0 + 1.0 / 1048576.0));
+  } else {  // tiny bounds: always take the exact test
+    d.eb_lo = 0.0f;
+    d.eb_hi = INFINITY;
+  }
   d.R = p.quant_radius;
   d.nsym = 2u * (uint32_t)p.quant_radius;
   d.max_peaks = (uint32_t)p.max_peaks;
@@ -248,8 +250,14 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
   a.frame_bytes = d_frame_bytes;
   a.frame_status = d_frame_status;
   choose_shape(ctx, n_frames, &a);
+  a.peaks_key_out = ctx->s.peak_key;
+  a.peaks_count_out = ctx->s.peak_count;
   if (resolved_path(ctx) == ROIBIN_PATH_FUSED) {
-    cudaError_t e = timed(ctx, K_FUSED, st, [&] { return launch_fused(ctx->dp, ctx->s, a, st, ctx->num_sms); });
+    // the per-slot counters start at zero (the kernel resets them after each frame)
+    cudaError_t e = cudaMemsetAsync(ctx->fs.thr_count, 0, sizeof(uint32_t) * ctx->fshape.n_clusters, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fs.peak_count, 0, sizeof(uint32_t) * ctx->fshape.n_clusters, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = timed(ctx, K_FUSED, st, [&] { return launch_fused(ctx->dp, ctx->fs, a, ctx->fshape, st); });
     return cuda_status(e);
   }
   return compress_plain(ctx, a, st);
@@ -307,9 +315,9 @@ int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_p
   ctx->max_frames = max_frames_per_call;
   ctx->budget = hbm_budget_bytes;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  ctx->fused_ok = fused_supported(ctx->dp, device);
-  const uint64_t need = carve_scratch(ctx->dp, max_frames_per_call, nullptr, nullptr) +
-                        (ctx->fused_ok ? fused_scratch_bytes_per_frame(ctx->dp) * 0 : 0);
+  ctx->fused_ok = fused_plan(ctx->dp, device, ctx->num_sms, &ctx->fshape);
+  const uint64_t fneed = ctx->fused_ok ? carve_scratch(ctx->dp, ctx->fshape.n_clusters, nullptr, nullptr) : 0;
+  const uint64_t need = carve_scratch(ctx->dp, max_frames_per_call, nullptr, nullptr) + fneed;
   if (hbm_budget_bytes && need > hbm_budget_bytes) {
     delete ctx;
     return ROIBIN_ERR_OUT_OF_BUDGET;
@@ -321,6 +329,10 @@ int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_p
   }
   ctx->scratch_bytes = need;
   carve_scratch(ctx->dp, max_frames_per_call, static_cast<uint8_t*>(ctx->scratch), &ctx->s);
+  if (ctx->fused_ok) {
+    const uint64_t off = (need - fneed + 255) & ~uint64_t(255);
+    carve_scratch(ctx->dp, ctx->fshape.n_clusters, static_cast<uint8_t*>(ctx->scratch) + off, &ctx->fs);
+  }
   *out = ctx;
   return ROIBIN_OK;
 }

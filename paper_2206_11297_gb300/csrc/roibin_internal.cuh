@@ -39,6 +39,7 @@ struct DevParams {
   int32_t rank, ring_r0, ring_dr, npix_min, npix_max;
   int32_t roi_h, roi_w;
   float eb, two_eb, recip;  // two_eb = fl(2 eb), recip = fl(1 / two_eb)
+  float eb_lo, eb_hi;       // screen of the bound test (see prequantize)
   int32_t R;                // quant radius
   uint32_t nsym;            // 2R
   uint32_t max_peaks;
@@ -137,18 +138,53 @@ struct Quant {
   bool outlier;
 };
 
+// The fp64 test |b - b^| > eb is the definition.  It is evaluated as an fp32
+// screen: d = fl(|b - b^|) has relative error <= 2^-24, so d < eb_lo proves
+// "within" and d > eb_hi proves "outside" (eb_lo, eb_hi = eb (1 -+ 2^-20));
+// only the rare d in [eb_lo, eb_hi] takes the exact fp64 test.  A non-finite b
+// gives a non-finite t, so the |t| < 2^28 test also rejects NaN and Inf.
 __device__ __forceinline__ Quant prequantize(float b, const DevParams& p) {
   Quant r;
   const float t = rintf(__fmul_rn(b, p.recip));
-  bool out = !isfinite(b) || !(fabsf(t) < kPqLimit);
+  bool out = !(fabsf(t) < kPqLimit);
   if (!out) {
     const float bh = __fmul_rn(t, p.two_eb);
-    if (fabs(__dadd_rn((double)b, -(double)bh)) > (double)p.eb) out = true;
+    const float d = fabsf(__fsub_rn(b, bh));
+    if (d > p.eb_hi) out = true;
+    else if (d >= p.eb_lo) out = fabs(__dadd_rn((double)b, -(double)bh)) > (double)p.eb;
   }
   r.outlier = out;
   r.q = out ? 0 : (int32_t)t;
   r.outlier_bits = isnan(b) ? kCanonicalNaN : __float_as_uint(b);
   return r;
+}
+
+// 2x2 bin pair from two float4 (4 pixels of raw row 2i and of row 2i+1):
+// sum in row-major order from the first pixel, one IEEE division.
+__device__ __forceinline__ void bin_pair(const float4& a, const float4& b, bool two, float& b0, float& b1) {
+  float s0 = __fadd_rn(a.x, a.y), s1 = __fadd_rn(a.z, a.w);
+  float c = 2.0f;
+  if (two) {
+    s0 = __fadd_rn(__fadd_rn(s0, b.x), b.y);
+    s1 = __fadd_rn(__fadd_rn(s1, b.z), b.w);
+    c = 4.0f;
+  }
+  b0 = __fdiv_rn(s0, c);
+  b1 = __fdiv_rn(s1, c);
+}
+
+// Histogram update by a whole warp (every lane calls; code 0xFFFF = no item).
+// Lanes holding the frame's most common code (`common`, the zero residual)
+// are counted with one ballot; the others are aggregated by value.
+__device__ __forceinline__ void hist_add_warp(uint32_t* hist, uint32_t code, uint32_t common) {
+  const uint32_t mc = __ballot_sync(0xffffffffu, code == common);
+  if (mc && lane_id() == (uint32_t)(__ffs(mc) - 1)) atomicAdd(hist + common, (uint32_t)__popc(mc));
+  const bool rest = code != common && code != 0xFFFFu;
+  const uint32_t mr = __ballot_sync(0xffffffffu, rest);
+  if (rest) {
+    const uint32_t peers = __match_any_sync(mr, code);
+    if ((peers & lanemask_lt()) == 0) atomicAdd(hist + code, (uint32_t)__popc(peers));
+  }
 }
 
 // a7: code of a Lorenzo residual (code 0 = outlier).
@@ -178,8 +214,11 @@ __device__ inline bool is_candidate(const float* __restrict__ panel, int H, int 
 }
 
 // ---- a2: candidate evaluation (§4.2), fp64 in a fixed order ---------------
-__device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int W, int r, int c,
-                                     const DevParams& p) {
+// `px(dr, dc)` returns the pixel at (r + dr, c + dc); it is only called for
+// in-panel positions.  The sums run in row-major order and round once per
+// operation, so the result does not depend on where the pixels come from.
+template <class Px>
+__device__ inline bool evaluate_peak_at(Px px, int H, int W, int r, int c, const DevParams& p) {
   const int r0 = p.ring_r0, outer = p.ring_r0 + p.ring_dr, reach = outer - 1;
   double sum = 0.0;
   int n = 0;
@@ -189,7 +228,7 @@ __device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int
       if (d2 < r0 * r0 || d2 >= outer * outer) continue;
       const int rr = r + dr, cc = c + dc;
       if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
-      sum = __dadd_rn(sum, (double)__ldg(panel + (size_t)rr * W + cc));
+      sum = __dadd_rn(sum, (double)px(dr, dc));
       ++n;
     }
   }
@@ -203,7 +242,7 @@ __device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int
         if (d2 < r0 * r0 || d2 >= outer * outer) continue;
         const int rr = r + dr, cc = c + dc;
         if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
-        const double d = __dadd_rn((double)__ldg(panel + (size_t)rr * W + cc), -bkg);
+        const double d = __dadd_rn((double)px(dr, dc), -bkg);
         ss = __dadd_rn(ss, __dmul_rn(d, d));
       }
     }
@@ -217,7 +256,7 @@ __device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int
     for (int dc = -p.rank; dc <= p.rank; ++dc) {
       const int rr = r + dr, cc = c + dc;
       if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
-      const double d = __dadd_rn((double)__ldg(panel + (size_t)rr * W + cc), -bkg);
+      const double d = __dadd_rn((double)px(dr, dc), -bkg);
       if (d > thr) {
         ++npix;
         atot = __dadd_rn(atot, d);
@@ -228,6 +267,55 @@ __device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int
   if (!(atot > (double)p.atot_thr)) return false;
   const double noise = __dmul_rn(__dmul_rn((double)p.son_min, sigma), __dsqrt_rn((double)npix));
   return atot > noise;
+}
+
+__device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int W, int r, int c,
+                                     const DevParams& p) {
+  return evaluate_peak_at([&](int dr, int dc) { return __ldg(panel + (size_t)(r + dr) * W + (c + dc)); },
+                          H, W, r, c, p);
+}
+
+// Reach of the neighbourhood a candidate needs: its window and its ring.
+__host__ __device__ inline int peak_reach(const DevParams& p) {
+  const int ring = p.ring_r0 + p.ring_dr - 1;
+  return p.rank > ring ? p.rank : ring;
+}
+
+// One warp tests and evaluates the pixel (r, c) of `panel` (a1 + a2).  The
+// lanes stage its (2 reach + 1)^2 neighbourhood in `nb` (per-warp shared
+// memory) with one round of independent loads, test the local-maximum rule
+// in parallel (pure comparisons), and lane 0 runs the fp64 evaluation in its
+// fixed order.  `load(addr)` reads global memory (plain or L2-only).  Every
+// lane returns the same answer.
+template <class Load>
+__device__ inline bool warp_peak_test(const float* __restrict__ panel, int H, int W, int r, int c,
+                                      const DevParams& p, float* nb, Load load) {
+  const int reach = peak_reach(p), side = 2 * reach + 1, n = side * side;
+  const uint32_t lane = lane_id();
+  for (int e = (int)lane; e < n; e += 32) {
+    const int rr = r + e / side - reach, cc = c + e % side - reach;
+    nb[e] = (rr >= 0 && rr < H && cc >= 0 && cc < W) ? load(panel + (size_t)rr * W + cc) : 0.0f;
+  }
+  __syncwarp();
+  const float v = nb[reach * side + reach];
+  const int wside = 2 * p.rank + 1;
+  bool ok = v >= p.amax;
+  for (int e = (int)lane; e < wside * wside; e += 32) {
+    const int dr = e / wside - p.rank, dc = e % wside - p.rank;
+    const int rr = r + dr, cc = c + dc;
+    if ((dr == 0 && dc == 0) || rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+    const float u = nb[(dr + reach) * side + (dc + reach)];
+    const bool precedes = dr < 0 || (dr == 0 && dc < 0);
+    if (precedes ? !(v > u) : !(v >= u)) ok = false;
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  bool keep = false;
+  if (ok && lane == 0)
+    keep = evaluate_peak_at([&](int dr, int dc) { return nb[(dr + reach) * side + (dc + reach)]; }, H, W, r,
+                            c, p);
+  keep = __shfl_sync(0xffffffffu, keep, 0);
+  __syncwarp();
+  return keep;
 }
 
 // ---- a9: deterministic Huffman codebook, built by one CTA ------------------
@@ -393,7 +481,26 @@ struct PlainArgs {
   int32_t* frame_status;
   uint32_t bands_per_panel;
   uint32_t rows_per_step;
+  uint32_t* peaks_key_out;    // fused path: each frame's final peak list, for roibin_last_peaks
+  uint32_t* peaks_count_out;
 };
+
+// Shape of the fused cluster kernel, chosen on the host (fused_kernel.cu).
+struct FusedShape {
+  uint32_t C;               // CTAs per cluster (one frame per cluster at a time)
+  uint32_t rows_per_cta;    // global binned rows per CTA (even)
+  uint32_t cap_bins;        // rows_per_cta * Wb, a multiple of 4
+  uint32_t RB;              // binned rows per TMA stage
+  uint32_t stages;          // ring depth
+  uint32_t stage_bytes;     // 2 * RB * W * 4
+  uint32_t n_clusters;      // clusters launched = scratch slots
+  uint32_t chunks_per_cta;  // upper bound of the chunks a CTA owns
+  uint32_t off_bar, off_hist, off_cb_len, off_cb_code, off_own, off_misc, off_pq, off_qbuf, off_codes,
+      off_union, union_bytes, smem;
+};
+bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out);
+cudaError_t launch_fused(const DevParams& p, const Scratch& fs, const PlainArgs& a, const FusedShape& sh,
+                         cudaStream_t st);
 
 // Each launcher enqueues one kernel and returns cudaGetLastError().
 // `timer` may be null; when set, it brackets the launch with events.

@@ -13,7 +13,7 @@ from synthetic import RECIPES, FrameRecipe, make_frame
 
 pytestmark = pytest.mark.gpu
 
-PATHS = [rb.PATH_PLAIN]
+PATHS = [rb.PATH_PLAIN, rb.PATH_FUSED]
 
 
 def small_batch(geom, n, seed, peaks=("uniform", 2, 12), **kw):
@@ -28,6 +28,16 @@ def _cuda():
         pytest.skip("no CUDA device")
     rb.library()
     oracle.lib()
+
+
+def fused_or_skip(geom, params, path):
+    """The fused path covers bin 2x2 with cols % 4 == 0; other shapes run the plain path."""
+    if path != rb.PATH_FUSED:
+        return
+    with rb.Context(geom, params, max_frames=1) as ctx:
+        ctx.set_path(rb.PATH_AUTO)
+        if ctx.resolved_path != rb.PATH_FUSED:
+            pytest.skip("fused path not available for this shape")
 
 
 @pytest.mark.parametrize("path", PATHS)
