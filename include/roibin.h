@@ -66,8 +66,8 @@ extern "C" {
 /* ---- execution paths for roibin_compress ----------------------------- */
 #define ROIBIN_PATH_AUTO 0  /* fused when the geometry allows it, else plain          */
 #define ROIBIN_PATH_PLAIN 1 /* one kernel per stage, intermediates in device memory  */
-#define ROIBIN_PATH_FUSED 2 /* one persistent cluster kernel per batch; codes stay on
-                               chip (distributed shared memory)                      */
+#define ROIBIN_PATH_FUSED 2 /* one persistent kernel per batch: (frame, panel) work
+                               items, the last CTA of a frame finalises it          */
 
 typedef struct roibin_ctx roibin_ctx;
 
@@ -130,11 +130,30 @@ int roibin_ctx_destroy(roibin_ctx* ctx);
 uint64_t roibin_ctx_scratch_bytes(const roibin_ctx* ctx);
 
 /* Selects the kernel path for later roibin_compress calls (ROIBIN_PATH_*).
- * ROIBIN_ERR_INVALID_ARG when FUSED is asked for a geometry it cannot hold
- * on chip.  Both paths write identical bytes. */
+ * ROIBIN_ERR_INVALID_ARG when FUSED is asked for a shape it does not cover
+ * (it needs bin 2x2 and cols % 4 == 0).  Both paths write identical bytes. */
 int roibin_ctx_set_path(roibin_ctx* ctx, int path);
 /* The path AUTO resolves to for this context (PLAIN or FUSED). */
 int roibin_ctx_resolved_path(const roibin_ctx* ctx);
+
+/* Tuning hook of the fused path: ctas_per_sm resident CTAs per SM (1..8,
+ * capped by what fits) stream rows_per_step binned rows per step (0 = the
+ * default for the geometry, else 1..16).  ROIBIN_ERR_INVALID_ARG when the
+ * shape does not fit or the context has no fused path; the previous shape is
+ * then kept.  Results are identical for every shape; only speed changes. */
+int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t rows_per_step);
+/* Current fused shape: CTAs per SM, rows per step, grid size, shared memory
+ * bytes per CTA.  Any output pointer may be NULL. */
+int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* rows_per_step,
+                           uint32_t* grid_ctas, uint32_t* smem_bytes);
+
+/* Phase trace of the fused path: for frames f < n_frames of later calls, the
+ * CTA that finalises frame f writes 10 globaltimer stamps (ns) to
+ * d_trace[f * 10 + i]: 0 finalisation start, 1 peak list gathered, 2 codebook
+ * built, 3 chunk sizes done, 4 header written, 5 bitstream written, 6 ROI
+ * written (7..9 unused).  n_frames = 0 switches tracing off.
+ * d_trace: device u64[n_frames * 10], owned by the caller. */
+int roibin_ctx_set_trace(roibin_ctx* ctx, uint64_t* d_trace, uint32_t n_frames);
 
 /* Compresses n_frames frames (1 <= n_frames <= max_frames_per_call).
  *   d_frames        float32[n_frames][P][H][W], 16-byte aligned.

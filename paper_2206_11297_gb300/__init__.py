@@ -63,6 +63,10 @@ _SIGNATURES = {
     "roibin_ctx_scratch_bytes": (_u64, [_P]),
     "roibin_ctx_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
     "roibin_ctx_resolved_path": (ctypes.c_int, [_P]),
+    "roibin_ctx_set_fused_shape": (ctypes.c_int, [_P, _u32, _u32]),
+    "roibin_ctx_fused_shape": (ctypes.c_int, [_P, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                                              ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    "roibin_ctx_set_trace": (ctypes.c_int, [_P, _P, _u32]),
     "roibin_compress": (ctypes.c_int, [_P, _P, _u32, _P, _P, _P, _u64, _P, _P, _P]),
     "roibin_decompress": (ctypes.c_int, [_P, _P, _u64, _P, _u32, _P, _P, _P]),
     "roibin_ctx_reserve_host_path": (ctypes.c_int, [_P]),
@@ -196,6 +200,22 @@ class Context:
 
     def set_path(self, path: int):
         _check("roibin_ctx_set_path", self.lib.roibin_ctx_set_path(self._h, int(path)))
+
+    def set_fused_shape(self, ctas_per_sm: int, rows_per_step: int = 0):
+        _check("roibin_ctx_set_fused_shape",
+               self.lib.roibin_ctx_set_fused_shape(self._h, int(ctas_per_sm), int(rows_per_step)))
+
+    @property
+    def fused_shape(self):
+        """(CTAs per SM, rows per step, grid CTAs, shared memory bytes) or None."""
+        v = [_u32() for _ in range(4)]
+        if self.lib.roibin_ctx_fused_shape(self._h, *[ctypes.byref(x) for x in v]) != OK:
+            return None
+        return tuple(x.value for x in v)
+
+    def set_trace(self, trace=None, n_frames: int = 0):
+        """trace: CUDA int64 tensor of n_frames * 10 entries (None switches tracing off)."""
+        _check("roibin_ctx_set_trace", self.lib.roibin_ctx_set_trace(self._h, _ptr(trace), int(n_frames)))
 
     @property
     def resolved_path(self) -> int:

@@ -1,152 +1,64 @@
-// fused_kernel.cu - the persistent cluster kernel: the whole method for a
+// fused_kernel.cu - the persistent batched kernel: the whole method for a
 // batch of frames in one launch.
 //
-// A cluster of C CTAs owns one frame at a time (frames c, c + n_clusters, ...).
-// The frame's binned rows are split into C contiguous ranges, one per CTA.
-//
-// Phase 1 (per CTA, HBM-bound): raw rows stream into a ring of shared-memory
-// stages by TMA bulk copies (cp.async.bulk + mbarrier); each stage is binned,
-// prequantised, Lorenzo-predicted and coded.  The codes stay on chip: one
-// byte per bin in the CTA's shared memory (byte = residual + 128 for
-// |residual| <= 126, 0 = Lorenzo outlier, 255 = escape to a side array), so a
-// CSPAD frame's 577,344 codes fit in the cluster's distributed shared memory.
-// Pixels >= amax_thr are listed for the peak finder.
-//
-// Phase 2 (per cluster): candidate evaluation (a1, a2), the cluster-wide
-// histogram read through distributed shared memory and the Huffman codebook
-// (a9, built redundantly by every CTA), then per-chunk sizes, a cluster-wide
-// scan, the frame layout, and the chunk-parallel bit-packing (a10) with the
-// outliers (a11) and the ROI windows (a3) written straight to the output.
-//
-// Frames never exchange data, so the clusters never wait on one another;
-// within a cluster, cluster barriers order the phases.  Every wait on an
-// mbarrier is bounded: on timeout the frame is marked ROIBIN_ERR_TIMEOUT.
-#include <cooperative_groups.h>
+// Work items are (frame, panel) pairs handed out in order by an atomic
+// counter to a grid of resident CTAs (several per SM).  For its panel a CTA:
+//   - streams the raw rows (16-byte loads, L2 evict-first, the next step's
+//     loads in flight while the current step is coded), bins them,
+//     prequantises, predicts with the 2-D Lorenzo rule and writes one byte per
+//     bin (byte = residual + 128 for residuals in [-127, 126], 0 = Lorenzo
+//     outlier, 255 = escape whose code sits in a side array);
+//   - keeps the panel's histogram, prequantisation-outlier bits and pixels
+//     >= amax_thr in shared memory and flushes them to per-(frame, panel)
+//     slots with plain stores (no zeroing, no cross-CTA atomics);
+//   - tests and evaluates the panel's candidates right away, while its rows
+//     are still in L2, and stores its sorted peak list.
+// The CTA that completes a frame's last panel finalises the frame (the "last
+// block" pattern): histogram sum, Huffman codebook, chunk sizes, scan,
+// header, bit-packing, outliers and ROI windows.  Meanwhile the other CTAs
+// keep streaming, so the latency-bound finalisation overlaps the HBM-bound
+// streaming.  After use, the frame's code bytes are dropped from L2 without a
+// write-back.
 #include <cuda_runtime.h>
 
 #include "roibin_internal.cuh"
 
-namespace cg = cooperative_groups;
-
 namespace roibin {
 
-constexpr int kFT = 512;       // threads per CTA
-constexpr int kFW = kFT / 32;  // warps per CTA
-constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier wait
+constexpr int kPT = 256;       // threads per CTA
+constexpr int kPW = kPT / 32;  // warps per CTA
+constexpr int kItems = 2;      // bin-pair items per thread per step
+constexpr uint32_t kThrLocalCap = 512;
 
-struct FusedMisc {
-  FramePlan pl;
-  int32_t status;
-  int32_t timeout;
-  uint32_t n_peaks;
-  uint32_t bad;
-  uint32_t tmp[33];
-  uint32_t carry[3];
-};
-
-// ---- small PTX helpers ------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-// ---- geometry helpers (bin 2x2) ---------------------------------------------
-// First raw row (global numbering p * H + r) of global binned row g.
-__device__ __forceinline__ uint32_t raw_begin(const DevParams& p, uint32_t g) {
-  const uint32_t pn = g / p.Hb, i = g - pn * p.Hb;
-  return pn * p.H + 2 * i;
+// 16-byte streaming load: no L1 allocation, first in line for L2 eviction.
+__device__ __forceinline__ float4 ld_stream(const float* ptr, uint64_t policy) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(ptr), "l"(policy));
+  return v;
 }
-__device__ __forceinline__ uint32_t raw_end(const DevParams& p, uint32_t g) {
-  const uint32_t pn = g / p.Hb, i = g - pn * p.Hb;
-  return pn * p.H + min(2 * i + 2, p.H);
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// Drops a 128-byte line from L2 without writing it back (its contents are dead).
+__device__ __forceinline__ void discard_line(const void* ptr) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(ptr) : "memory");
 }
 
-// Symbol of a stored byte.
-__device__ __forceinline__ uint32_t byte_code(uint32_t b, uint32_t bin, const DevParams& p,
-                                              const uint16_t* esc) {
+// Symbol of a stored code byte.
+__device__ __forceinline__ uint32_t byte_code(uint32_t b, const uint16_t* esc_bin, int32_t R) {
   if (b == 0) return 0;
-  if (b == 255) return __ldcg(esc + bin);
-  return b - 128 + (uint32_t)p.R;
-}
-
-struct Layout {
-  uint64_t* bars;
-  uint32_t* hist;       // [kMaxSymbols] this CTA's histogram
-  uint8_t* cb_len;      // [kMaxSymbols]
-  uint32_t* cb_code;    // [kMaxSymbols]
-  uint32_t* own;        // [3][chunks_per_cta] per-chunk words / lo / pq of own chunks
-  FusedMisc* misc;
-  uint32_t* pq;         // [cap_bins / 32 + 1] prequantisation-outlier bits of own bins
-  int32_t* qbuf;        // [(RB + 1) * Wb]
-  uint8_t* codes;       // [cap_bins (+16)]
-  unsigned char* un;    // union: ring | peak-test buffers | Huffman scratch | keys + chunk scans
-};
-
-__device__ __forceinline__ Layout layout_of(unsigned char* sm, const FusedShape& sh) {
-  Layout L;
-  L.bars = reinterpret_cast<uint64_t*>(sm + sh.off_bar);
-  L.hist = reinterpret_cast<uint32_t*>(sm + sh.off_hist);
-  L.cb_len = sm + sh.off_cb_len;
-  L.cb_code = reinterpret_cast<uint32_t*>(sm + sh.off_cb_code);
-  L.own = reinterpret_cast<uint32_t*>(sm + sh.off_own);
-  L.misc = reinterpret_cast<FusedMisc*>(sm + sh.off_misc);
-  L.pq = reinterpret_cast<uint32_t*>(sm + sh.off_pq);
-  L.qbuf = reinterpret_cast<int32_t*>(sm + sh.off_qbuf);
-  L.codes = sm + sh.off_codes;
-  L.un = sm + sh.off_union;
-  return L;
-}
-
-// q of one global binned row straight from global memory (the halo row above a
-// CTA's range when that range starts inside a panel).
-__device__ void halo_row(const float* frame, const DevParams& p, uint32_t g, int32_t* qrow) {
-  const uint32_t pn = g / p.Hb, i = g - pn * p.Hb;
-  const float* panel = frame + (size_t)pn * p.H * p.W;
-  const uint32_t NP = p.W >> 2;
-  for (uint32_t pr = threadIdx.x; pr < NP; pr += kFT) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(panel + (size_t)(2 * i) * p.W) + pr);
-    const bool two = 2 * i + 1 < p.H;
-    const float4 b = two ? __ldg(reinterpret_cast<const float4*>(panel + (size_t)(2 * i + 1) * p.W) + pr)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-    float v0, v1;
-    bin_pair(a, b, two, v0, v1);
-    qrow[2 * pr] = prequantize(v0, p).q;
-    qrow[2 * pr + 1] = prequantize(v1, p).q;
-  }
+  if (b == 255) return __ldcg(esc_bin);
+  return b - 128 + (uint32_t)R;
 }
 
 // Writes the header, the peaks, the code lengths, the chunk index and every
@@ -201,540 +113,619 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
   zero(pl.off_bits + (uint64_t)pl.n_words * 4, pl.total);
 }
 
-__device__ __forceinline__ uint32_t chunk_begin_of(uint32_t rank, const FusedShape& sh, const DevParams& p) {
-  const uint64_t b = (uint64_t)rank * sh.cap_bins;
-  const uint64_t k = (b + kChunk - 1) / kChunk;
-  return k < p.n_chunks ? (uint32_t)k : p.n_chunks;
+// Shared-memory views (byte offsets from FusedShape).  The streaming role and
+// the finalising role of a CTA never overlap in time, so their buffers share
+// one allocation; the control words sit in front of both.
+struct StreamView {
+  uint32_t* hist;  // [nsym]
+  int32_t* qbuf;   // [qrows][Wb], circular by binned row
+  uint32_t* mask;  // [mask_words] prequantisation-outlier bits of the panel
+  uint32_t* thr;   // [kThrLocalCap] pixels >= amax_thr (panel-local index)
+  float* nb;       // [kPW][side^2] peak-test neighbourhoods
+  uint32_t* acc;   // [sort_n2] accepted peaks of the panel
+  uint32_t* ctl;
+};
+struct FinView {
+  HuffSmem* hs;
+  uint32_t* total;  // [kMaxSymbols]
+  uint8_t* cb_len;  // [kMaxSymbols]
+  uint32_t* cb_code;
+  uint32_t* keys;  // [peak_cap]
+  uint32_t* cw;    // [n_chunks] chunk words -> word offsets; then lo, pq
+  uint32_t* clo;
+  uint32_t* cpq;
+  uint32_t* ctl;
+};
+enum {
+  CTL_THR = 0,
+  CTL_ACC,
+  CTL_ITEM,
+  CTL_LAST,
+  CTL_BAD,
+  CTL_STATUS,
+  CTL_CARRY0,
+  CTL_CARRY1,
+  CTL_CARRY2,
+  CTL_TMP,
+  CTL_OFFS = CTL_TMP + 33,  // per-panel peak offsets (first 1024 panels)
+  CTL_WORDS = CTL_OFFS + 1024
+};
+
+__device__ __forceinline__ StreamView stream_view(unsigned char* sm, const FusedShape& sh) {
+  StreamView v;
+  v.hist = reinterpret_cast<uint32_t*>(sm + sh.off_hist);
+  v.qbuf = reinterpret_cast<int32_t*>(sm + sh.off_qbuf);
+  v.mask = reinterpret_cast<uint32_t*>(sm + sh.off_mask);
+  v.thr = reinterpret_cast<uint32_t*>(sm + sh.off_thr);
+  v.nb = reinterpret_cast<float*>(sm + sh.off_nb);
+  v.acc = reinterpret_cast<uint32_t*>(sm + sh.off_acc);
+  v.ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
+  return v;
+}
+__device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape& sh) {
+  FinView v;
+  v.hs = reinterpret_cast<HuffSmem*>(sm + sh.off_huff);
+  v.total = reinterpret_cast<uint32_t*>(sm + sh.off_total);
+  v.cb_len = sm + sh.off_cblen;
+  v.cb_code = reinterpret_cast<uint32_t*>(sm + sh.off_cbcode);
+  v.keys = reinterpret_cast<uint32_t*>(sm + sh.off_keys);
+  v.cw = reinterpret_cast<uint32_t*>(sm + sh.off_cw);
+  v.clo = v.cw + sh.n_chunks;
+  v.cpq = v.clo + sh.n_chunks;
+  v.ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
+  return v;
 }
 
-__global__ void __launch_bounds__(kFT, 1) k_fused(DevParams p, Scratch fs, PlainArgs a, FusedShape sh) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  cg::cluster_group cl = cg::this_cluster();
-  const uint32_t rank = cl.block_rank();
-  const uint32_t C = sh.C;
-  const uint32_t cid = blockIdx.x / C;
+// ---------------------------------------------------------------------------
+// One panel: stream, code, list and evaluate candidates, flush.
+__device__ void process_panel(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                              const StreamView& v, uint32_t f, uint32_t pn, uint64_t pol) {
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-  Layout L = layout_of(sm, sh);
-  FusedMisc& ms = *L.misc;
+  const uint32_t NP = p.W >> 2, Mp = p.Hb * p.Wb;
+  const float* panel = a.frames + (size_t)f * p.frame_px + (size_t)pn * p.H * p.W;
+  const size_t fbin = (size_t)f * p.M + (size_t)pn * Mp;  // first bin of the panel in the frame arrays
+  uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride + (size_t)pn * Mp;
+  uint16_t* esc = s.codes + fbin;
+  int32_t* lo_delta = s.lo_delta + fbin;
+  uint32_t* pq_bits = s.pq_bits + fbin;
 
-  const uint32_t g_total = p.P * p.Hb;
-  const uint32_t g0 = min(g_total, rank * sh.rows_per_cta);
-  const uint32_t g1 = min(g_total, g0 + sh.rows_per_cta);
-  const uint32_t bin0 = g0 * p.Wb;  // first bin owned by this CTA
-  const uint32_t n_steps = g1 > g0 ? ceil_div(g1 - g0, sh.RB) : 0;
-  const uint32_t k_lo = chunk_begin_of(rank, sh, p), k_hi = chunk_begin_of(rank + 1, sh, p);
-  const uint32_t NP = p.W >> 2;
-  const int side = 2 * peak_reach(p) + 1;
+  for (uint32_t k = tid; k < p.nsym; k += kPT) v.hist[k] = 0;
+  for (uint32_t k = tid; k < sh.mask_words; k += kPT) v.mask[k] = 0;
+  if (tid == 0) v.ctl[CTL_THR] = 0;
 
-  // slot-local global scratch
-  uint32_t* thr_count = fs.thr_count + cid;
-  uint32_t* thr_idx = fs.thr_idx + (size_t)cid * p.thr_cap;
-  uint32_t* peak_count = fs.peak_count + cid;
-  uint32_t* peak_key = fs.peak_key + (size_t)cid * (p.max_peaks ? p.max_peaks : 1);
-  int32_t* lo_delta = fs.lo_delta + (size_t)cid * p.M;
-  uint32_t* pq_bits = fs.pq_bits + (size_t)cid * p.M;
-  uint16_t* esc = fs.codes + (size_t)cid * p.M;
-
-  if (tid == 0) {
-    for (uint32_t b = 0; b < sh.stages; ++b) mbar_init(L.bars + b, 1);
-    fence_mbar_init();
+  // the thread's items within a step (the same for every step)
+  uint32_t il[kItems], pr[kItems];
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    const uint32_t it = tid + k * kPT;
+    il[k] = it / NP;
+    pr[k] = it - il[k] * NP;
   }
+  const uint32_t n_steps = ceil_div(p.Hb, sh.RB);
+  float4 va[kItems], vb[kItems];
+  auto load_step = [&](uint32_t i0) {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t i = i0 + il[k];
+      va[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      vb[k] = va[k];
+      if (il[k] < sh.RB && i < p.Hb) {
+        const float* row = panel + (size_t)(2 * i) * p.W + 4 * pr[k];
+        va[k] = ld_stream(row, pol);
+        if (2 * i + 1 < p.H) vb[k] = ld_stream(row + p.W, pol);
+      }
+    }
+  };
+  load_step(0);
+  __syncthreads();  // hist, mask and counters are zero
+  const bool find = a.user_peaks == nullptr;
+  uint32_t n_common = 0;  // codes equal to R (zero residual), counted in a register
+  for (uint32_t st = 0; st < n_steps; ++st) {
+    const uint32_t i0 = st * sh.RB;
+    // phase A: q of the step's bins into the circular buffer
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t i = i0 + il[k];
+      if (il[k] >= sh.RB || i >= p.Hb) continue;
+      const bool two = 2 * i + 1 < p.H;
+      float v0, v1;
+      bin_pair(va[k], vb[k], two, v0, v1);
+      const Quant q0 = prequantize(v0, p), q1 = prequantize(v1, p);
+      const uint32_t j0 = 2 * pr[k];
+      *reinterpret_cast<int2*>(v.qbuf + (size_t)(i % sh.qrows) * p.Wb + j0) = make_int2(q0.q, q1.q);
+      if (q0.outlier | q1.outlier) {
+        const uint32_t lb = i * p.Wb + j0;
+        atomicOr(v.mask + (lb >> 5), ((uint32_t)q0.outlier | ((uint32_t)q1.outlier << 1)) << (lb & 31));
+        if (q0.outlier) pq_bits[lb] = q0.outlier_bits;
+        if (q1.outlier) pq_bits[lb + 1] = q1.outlier_bits;
+      }
+      const float m = fmaxf(fmaxf(fmaxf(va[k].x, va[k].y), fmaxf(va[k].z, va[k].w)),
+                            fmaxf(fmaxf(vb[k].x, vb[k].y), fmaxf(vb[k].z, vb[k].w)));
+      if (find && m >= p.amax) {
+        const float px[8] = {va[k].x, va[k].y, va[k].z, va[k].w, vb[k].x, vb[k].y, vb[k].z, vb[k].w};
+        const int npx = two ? 8 : 4;
+        for (int e = 0; e < npx; ++e) {
+          if (px[e] >= p.amax) {
+            const uint32_t slot = atomicAdd(v.ctl + CTL_THR, 1u);
+            if (slot < kThrLocalCap) v.thr[slot] = (2 * i + (e >> 2)) * p.W + 4 * pr[k] + (e & 3);
+          }
+        }
+      }
+    }
+    // the next step's loads fly while this step is coded
+    if (st + 1 < n_steps) load_step(i0 + sh.RB);
+    __syncthreads();
+    // phase B: residuals, code bytes, histogram, outliers.  The circular
+    // buffer holds 2 RB + 1 rows, so the next phase A never overwrites a row
+    // this phase B still reads: one barrier per step is enough.
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t i = i0 + il[k];
+      uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
+      if (il[k] < sh.RB && i < p.Hb) {
+        const uint32_t j0 = 2 * pr[k];
+        const int32_t* cur = v.qbuf + (size_t)(i % sh.qrows) * p.Wb;
+        const int2 qc = *reinterpret_cast<const int2*>(cur + j0);
+        int2 qu = make_int2(0, 0);
+        int32_t ql = 0, qd = 0;
+        if (i > 0) {
+          const int32_t* up = v.qbuf + (size_t)((i - 1) % sh.qrows) * p.Wb;
+          qu = *reinterpret_cast<const int2*>(up + j0);
+          if (j0 > 0) qd = up[j0 - 1];
+        }
+        if (j0 > 0) ql = cur[j0 - 1];
+        const int32_t d0 = qc.x - qu.x - ql + qd;
+        const int32_t d1 = qc.y - qu.y - qc.x + qu.x;
+        c0 = quant_code(d0, p.R);
+        c1 = quant_code(d1, p.R);
+        const uint32_t lb = i * p.Wb + j0;
+        auto to_byte = [&](int32_t d, uint32_t c, uint32_t bin) -> uint32_t {
+          if (c == 0) {
+            lo_delta[bin] = d;
+            return 0u;
+          }
+          if (d >= -127 && d <= 126) return (uint32_t)(d + 128);
+          esc[bin] = (uint16_t)c;
+          return 255u;
+        };
+        const uint32_t b0 = to_byte(d0, c0, lb), b1 = to_byte(d1, c1, lb + 1);
+        codes[lb] = (uint8_t)b0;
+        codes[lb + 1] = (uint8_t)b1;
+      }
+      n_common += (c0 == (uint32_t)p.R) + (c1 == (uint32_t)p.R);
+      const bool r0 = c0 != 0xFFFFu && c0 != (uint32_t)p.R, r1 = c1 != 0xFFFFu && c1 != (uint32_t)p.R;
+      if (__any_sync(0xffffffffu, r0 | r1)) {
+        hist_add_warp(v.hist, r0 ? c0 : 0xFFFFu, 0xFFFFFFFFu);
+        hist_add_warp(v.hist, r1 ? c1 : 0xFFFFu, 0xFFFFFFFFu);
+      }
+    }
+  }
+  // the zero residual's count: one add per warp
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) n_common += __shfl_xor_sync(0xffffffffu, n_common, d);
+  if (lane == 0 && n_common) atomicAdd(v.hist + p.R, n_common);
   __syncthreads();
-  uint32_t ring_iter = 0;  // stages consumed so far (uniform in the CTA)
+  // flush the panel's histogram and outlier bits (disjoint per-panel slots)
+  const size_t fp = (size_t)f * p.P + pn;
+  for (uint32_t k = tid; k < p.nsym; k += kPT) s.hist_part[fp * kMaxSymbols + k] = v.hist[k];
+  for (uint32_t k = tid; k < sh.mask_words; k += kPT) s.pq_mask[fp * sh.mask_words + k] = v.mask[k];
 
-  for (uint32_t f = cid; f < a.n_frames; f += sh.n_clusters) {
-    const float* frame = a.frames + (size_t)f * p.frame_px;
-    uint8_t* out = a.out + (size_t)f * a.out_stride;
-    // ================= phase 1: stream, bin, quantise, predict, code =================
-    for (uint32_t k = tid; k < p.nsym; k += kFT) L.hist[k] = 0;
-    for (uint32_t k = tid; k < sh.cap_bins / 32 + 1; k += kFT) L.pq[k] = 0;
-    if (tid == 0) ms.timeout = 0;
-    auto issue = [&](uint32_t st) {  // thread 0 only
-      const uint32_t gA = g0 + st * sh.RB, gB = min(g1, gA + sh.RB);
-      const uint32_t r0 = raw_begin(p, gA), r1 = raw_end(p, gB - 1);
-      const uint32_t slot = (ring_iter + st) % sh.stages;
-      const uint32_t bytes = (r1 - r0) * p.W * 4;
-      fence_proxy_async();
-      mbar_expect_tx(L.bars + slot, bytes);
-      tma_load_1d(L.un + (size_t)slot * sh.stage_bytes, frame + (size_t)r0 * p.W, bytes, L.bars + slot);
+  // a1 + a2 on the panel's listed pixels (on every pixel >= amax_thr if the list overflowed)
+  if (find) {
+    if (tid == 0) v.ctl[CTL_ACC] = 0;
+    __syncthreads();
+    const uint32_t cnt = v.ctl[CTL_THR];
+    float* nb = v.nb + warp * sh.side * sh.side;
+    auto test = [&](uint32_t lp) {  // lp: pixel index within the panel
+      const uint32_t r = lp / p.W, c = lp - r * p.W;
+      if (warp_peak_test(panel, p.H, p.W, r, c, p, nb, [](const float* q) { return __ldg(q); }) && lane == 0) {
+        const uint32_t slot = atomicAdd(v.ctl + CTL_ACC, 1u);
+        if (slot < sh.sort_n2) v.acc[slot] = lp;
+      }
     };
-    if (tid == 0)
-      for (uint32_t st = 0; st < min(sh.stages, n_steps); ++st) issue(st);
-    // the row above the range
-    if (g0 > 0 && g0 % p.Hb != 0 && g0 < g1) halo_row(frame, p, g0 - 1, L.qbuf);
-    else
-      for (uint32_t j = tid; j < p.Wb; j += kFT) L.qbuf[j] = 0;
-    __syncthreads();
-
-    for (uint32_t st = 0; st < n_steps; ++st) {
-      const uint32_t slot = (ring_iter + st) % sh.stages;
-      const uint32_t parity = ((ring_iter + st) / sh.stages) & 1u;
-      const uint32_t gA = g0 + st * sh.RB, rows = min(sh.RB, g1 - gA);
-      const uint32_t rA = raw_begin(p, gA);
-      if (!mbar_wait(L.bars + slot, parity)) ms.timeout = 1;
-      const float4* ring = reinterpret_cast<const float4*>(L.un + (size_t)slot * sh.stage_bytes);
-      // phase A: q of every bin of the stage
-      const uint32_t items = rows * NP;
-      for (uint32_t it = tid; it < items; it += kFT) {
-        const uint32_t il = it / NP, pr = it - il * NP;
-        const uint32_t g = gA + il;
-        const uint32_t pn = g / p.Hb, i = g - pn * p.Hb;
-        const uint32_t ra = pn * p.H + 2 * i - rA;
-        const bool two = 2 * i + 1 < p.H;
-        const float4 va = ring[(size_t)ra * NP + pr];
-        const float4 vb = two ? ring[(size_t)(ra + 1) * NP + pr] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float v0, v1;
-        bin_pair(va, vb, two, v0, v1);
-        const Quant q0 = prequantize(v0, p), q1 = prequantize(v1, p);
-        *reinterpret_cast<int2*>(L.qbuf + (size_t)(il + 1) * p.Wb + 2 * pr) = make_int2(q0.q, q1.q);
-        const uint32_t lb = (g - g0) * p.Wb + 2 * pr;  // local bin of the pair
-        if (q0.outlier | q1.outlier) {
-          atomicOr(L.pq + (lb >> 5), ((uint32_t)q0.outlier | ((uint32_t)q1.outlier << 1)) << (lb & 31));
-          if (q0.outlier) pq_bits[bin0 + lb] = q0.outlier_bits;
-          if (q1.outlier) pq_bits[bin0 + lb + 1] = q1.outlier_bits;
-        }
-        const float m = fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)),
-                              fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
-        if (m >= p.amax) {
-          const float px[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-          const int npx = two ? 8 : 4;
-          for (int k = 0; k < npx; ++k) {
-            if (px[k] >= p.amax) {
-              const uint32_t r = 2 * i + (k >> 2), col = 4 * pr + (k & 3);
-              const uint32_t s = atomicAdd(thr_count, 1u);
-              if (s < p.thr_cap) thr_idx[s] = (pn * p.H + r) * p.W + col;
-            }
-          }
-        }
-      }
-      __syncthreads();
-      if (tid == 0 && st + sh.stages < n_steps) issue(st + sh.stages);  // the slot is free again
-      // phase B: residuals, codes, histogram, outliers
-      const uint32_t iters = ceil_div(items, kFT);
-      for (uint32_t t = 0; t < iters; ++t) {
-        const uint32_t it = t * kFT + tid;
-        uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
-        if (it < items) {
-          const uint32_t il = it / NP, pr = it - il * NP;
-          const uint32_t g = gA + il;
-          const uint32_t i = g % p.Hb;
-          const uint32_t j0 = 2 * pr;
-          const int32_t* cur = L.qbuf + (size_t)(il + 1) * p.Wb;
-          const int32_t* up = L.qbuf + (size_t)il * p.Wb;
-          const int2 qc = *reinterpret_cast<const int2*>(cur + j0);
-          int2 qu = make_int2(0, 0);
-          if (i > 0) qu = *reinterpret_cast<const int2*>(up + j0);
-          const int32_t ql = j0 > 0 ? cur[j0 - 1] : 0;
-          const int32_t qd = (j0 > 0 && i > 0) ? up[j0 - 1] : 0;
-          const int32_t d0 = qc.x - qu.x - ql + qd;
-          const int32_t d1 = qc.y - qu.y - qc.x + qu.x;
-          c0 = quant_code(d0, p.R);
-          c1 = quant_code(d1, p.R);
-          const uint32_t lb = (g - g0) * p.Wb + j0;
-          auto to_byte = [&](int32_t d, uint32_t c, uint32_t bin) -> uint32_t {
-            if (c == 0) {
-              lo_delta[bin] = d;
-              return 0u;
-            }
-            if (d >= -127 && d <= 126) return (uint32_t)(d + 128);
-            esc[bin] = (uint16_t)c;
-            return 255u;
-          };
-          const uint32_t b0 = to_byte(d0, c0, bin0 + lb), b1 = to_byte(d1, c1, bin0 + lb + 1);
-          *reinterpret_cast<uint16_t*>(L.codes + lb) = (uint16_t)(b0 | (b1 << 8));
-        }
-        hist_add_warp(L.hist, c0, (uint32_t)p.R);
-        hist_add_warp(L.hist, c1, (uint32_t)p.R);
-      }
-      __syncthreads();
-      for (uint32_t j = tid; j < p.Wb; j += kFT) L.qbuf[j] = L.qbuf[(size_t)rows * p.Wb + j];
-      __syncthreads();
-    }
-    ring_iter += n_steps;
-
-    // ================= phase 2 =================
-    cl.sync();  // A: codes, histograms and the amax list of the frame are complete
-    const bool user = a.user_peaks != nullptr;
-    if (!user) {  // a1 + a2: candidates, one warp per listed pixel
-      float* nb = reinterpret_cast<float*>(L.un) + warp * side * side;
-      const uint32_t cnt = __ldcg(thr_count);
-      const uint32_t plane = p.H * p.W;
-      auto test = [&](uint32_t px) {
-        const uint32_t pn = px / plane, rem = px - pn * plane;
-        const uint32_t r = rem / p.W, c = rem - r * p.W;
-        const float* panel = frame + (size_t)pn * plane;
-        if (warp_peak_test(panel, p.H, p.W, r, c, p, nb, [](const float* q) { return __ldg(q); }) &&
-            lane == 0) {
-          const uint32_t s = atomicAdd(peak_count, 1u);
-          if (s < p.max_peaks) peak_key[s] = px;
-        }
-      };
-      const uint32_t gw = rank * kFW + warp, nw = C * kFW;
-      if (cnt <= p.thr_cap) {
-        for (uint32_t e = gw; e < cnt; e += nw) test(__ldcg(thr_idx + e));
-      } else {
-        for (uint64_t base = (uint64_t)gw * 32; base < p.frame_px; base += (uint64_t)nw * 32) {
-          const uint64_t px = base + lane;
-          const bool hot = px < p.frame_px && __ldg(frame + px) >= p.amax;
-          uint32_t m = __ballot_sync(0xffffffffu, hot);
-          while (m) {
-            const uint32_t l = __ffs(m) - 1;
-            m &= m - 1;
-            test((uint32_t)(base + l));
-          }
-        }
-      }
-    }
-    __syncthreads();
-    // a8 + a9: cluster histogram and codebook (every CTA builds the same one)
-    HuffSmem& hs = *reinterpret_cast<HuffSmem*>(L.un);
-    uint32_t* total = reinterpret_cast<uint32_t*>(L.un + sizeof(HuffSmem));
-    for (uint32_t s = tid; s < p.nsym; s += kFT) {
-      uint32_t v = 0;
-      for (uint32_t r = 0; r < C; ++r) v += cl.map_shared_rank(L.hist, r)[s];
-      total[s] = v;
-    }
-    __syncthreads();
-    const int cb_status = build_codebook(total, p.nsym, hs, L.cb_len, L.cb_code);
-    cl.sync();  // B: the peak list is complete
-    // the frame's peaks: keys in the union (sorted when found, as given when supplied)
-    uint32_t* keys = reinterpret_cast<uint32_t*>(L.un);
-    if (tid == 0) {
-      ms.status = cb_status;
-      ms.bad = 0;
-    }
-    __syncthreads();
-    uint32_t n_pk;
-    if (user) {
-      n_pk = a.user_npeaks[f];
-      if (n_pk > p.max_peaks) {
-        if (tid == 0 && ms.status == ROIBIN_OK) ms.status = ROIBIN_ERR_CAPACITY;
-      } else {
-        const uint16_t* up = a.user_peaks + (size_t)f * p.max_peaks * 3;
-        for (uint32_t k = tid; k < n_pk; k += kFT) {
-          const uint32_t pn = up[3 * k], r = up[3 * k + 1], c = up[3 * k + 2];
-          if (pn >= p.P || r >= p.H || c >= p.W) ms.bad = 1;
-          else keys[k] = (pn * p.H + r) * p.W + c;
-        }
-        __syncthreads();
-        if (tid == 0 && ms.bad && ms.status == ROIBIN_OK) ms.status = ROIBIN_ERR_INVALID_ARG;
-      }
+    if (cnt <= kThrLocalCap) {
+      for (uint32_t e = warp; e < cnt; e += kPW) test(v.thr[e]);
     } else {
-      n_pk = __ldcg(peak_count);
-      if (n_pk > p.max_peaks) {
-        if (tid == 0 && ms.status == ROIBIN_OK) ms.status = ROIBIN_ERR_CAPACITY;
-      } else {
-        uint32_t n2 = 1;
-        while (n2 < n_pk) n2 <<= 1;
-        for (uint32_t k = tid; k < n2; k += kFT) keys[k] = k < n_pk ? __ldcg(peak_key + k) : 0xFFFFFFFFu;
-        __syncthreads();
-        for (uint32_t size = 2; size <= n2; size <<= 1) {
-          for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t k = tid; k < n2; k += kFT) {
-              const uint32_t partner = k ^ stride;
-              if (partner > k) {
-                const bool upw = (k & size) == 0;
-                const uint32_t x = keys[k], y = keys[partner];
-                if ((x > y) == upw) {
-                  keys[k] = y;
-                  keys[partner] = x;
-                }
-              }
-            }
-            __syncthreads();
-          }
+      const uint32_t plane = p.H * p.W;
+      for (uint32_t base = warp * 32; base < plane; base += kPW * 32) {
+        const uint32_t lp = base + lane;
+        const bool hot = lp < plane && __ldg(panel + lp) >= p.amax;
+        uint32_t m = __ballot_sync(0xffffffffu, hot);
+        while (m) {
+          const uint32_t l = __ffs(m) - 1;
+          m &= m - 1;
+          test(base + l);
         }
       }
     }
     __syncthreads();
-    const int32_t status0 = ms.status;
-    if (rank == 0) {  // the frame's peak list, for roibin_last_peaks
-      if (tid == 0) a.peaks_count_out[f] = n_pk;
-      if (n_pk <= p.max_peaks)
-        for (uint32_t k = tid; k < n_pk; k += kFT) a.peaks_key_out[(size_t)f * p.max_peaks + k] = keys[k];
-    }
-    // a10/a11 sizes of the chunks this CTA owns (one warp per chunk, 128 symbols per lane)
-    auto owner_of = [&](uint32_t bin) { return bin / sh.cap_bins; };
-    auto load4 = [&](uint32_t bin, uint32_t& w, uint32_t& pqn) {  // bin % 4 == 0
-      const uint32_t o = owner_of(bin), local = bin - o * sh.cap_bins;
-      const uint8_t* cptr = o == rank ? L.codes : cl.map_shared_rank(L.codes, o);
-      const uint32_t* pptr = o == rank ? L.pq : cl.map_shared_rank(L.pq, o);
-      w = *reinterpret_cast<const uint32_t*>(cptr + local);
-      pqn = (pptr[local >> 5] >> (local & 31)) & 0xFu;
-    };
-    if (status0 == ROIBIN_OK) {
-      for (uint32_t k = k_lo + warp; k < k_hi; k += kFW) {
-        const uint32_t s0 = min(p.M, k * kChunk + lane * 128), s1 = min(p.M, min((k + 1) * kChunk, s0 + 128));
-        uint32_t bits = 0, nlo = 0, npq = 0;
-        for (uint32_t i = s0; i < s1; i += 4) {
-          uint32_t w, pqn;
-          load4(i, w, pqn);
-          for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
-            const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, i + t, p, esc);
-            bits += L.cb_len[code];
-            nlo += code == 0;
-            npq += (pqn >> t) & 1u;
-          }
-        }
-        for (int d = 16; d > 0; d >>= 1) {
-          bits += __shfl_xor_sync(0xffffffffu, bits, d);
-          nlo += __shfl_xor_sync(0xffffffffu, nlo, d);
-          npq += __shfl_xor_sync(0xffffffffu, npq, d);
-        }
-        if (lane == 0) {
-          L.own[k - k_lo] = (bits + 31) / 32;
-          L.own[sh.chunks_per_cta + k - k_lo] = nlo;
-          L.own[2 * sh.chunks_per_cta + k - k_lo] = npq;
-        }
-      }
-    }
-    cl.sync();  // C: chunk sizes visible; every CTA has read the peak counters
-    if (rank == 0 && tid == 0) {
-      *thr_count = 0;
-      *peak_count = 0;
-    }
-    if (status0 == ROIBIN_OK) {
-      // every chunk's offsets, from the owners' shared memory
-      uint32_t* keys_end = keys + (n_pk > 0 ? n_pk : 1);
-      uint32_t* cw = reinterpret_cast<uint32_t*>(
-          (reinterpret_cast<uintptr_t>(keys_end) + 15) & ~uintptr_t(15));
-      uint32_t* clo = cw + p.n_chunks;
-      uint32_t* cpq = clo + p.n_chunks;
-      for (uint32_t k = tid; k < p.n_chunks; k += kFT) {
-        const uint32_t o = owner_of(min(p.M - 1, k * kChunk));
-        const uint32_t* ow = o == rank ? L.own : cl.map_shared_rank(L.own, o);
-        const uint32_t kk = k - chunk_begin_of(o, sh, p);
-        cw[k] = ow[kk];
-        clo[k] = ow[sh.chunks_per_cta + kk];
-        cpq[k] = ow[2 * sh.chunks_per_cta + kk];
-      }
-      if (tid < 3) ms.carry[tid] = 0;
+    const uint32_t n_acc = v.ctl[CTL_ACC];
+    if (n_acc <= p.max_peaks) {  // sort the panel's peaks (row-major order)
+      uint32_t n2 = 1;
+      while (n2 < n_acc) n2 <<= 1;
+      for (uint32_t k = n_acc + tid; k < n2; k += kPT) v.acc[k] = 0xFFFFFFFFu;
       __syncthreads();
-      for (uint32_t k0 = 0; k0 < p.n_chunks; k0 += kFT) {
-        const uint32_t k = k0 + tid;
-        const uint32_t w = k < p.n_chunks ? cw[k] : 0u, l = k < p.n_chunks ? clo[k] : 0u,
-                       q = k < p.n_chunks ? cpq[k] : 0u;
-        uint32_t tw, tl, tq;
-        const uint32_t ew = block_excl_scan(w, ms.tmp, &tw);
-        const uint32_t el = block_excl_scan(l, ms.tmp, &tl);
-        const uint32_t eq = block_excl_scan(q, ms.tmp, &tq);
-        if (k < p.n_chunks) {
-          cw[k] = ms.carry[0] + ew;
-          clo[k] = ms.carry[1] + el;
-          cpq[k] = ms.carry[2] + eq;
-        }
-        __syncthreads();
-        if (tid == 0) {
-          ms.carry[0] += tw;
-          ms.carry[1] += tl;
-          ms.carry[2] += tq;
-        }
-        __syncthreads();
-      }
-      FramePlan pl;
-      pl.n_peaks = n_pk;
-      pl.n_words = ms.carry[0];
-      pl.n_lo = ms.carry[1];
-      pl.n_pq = ms.carry[2];
-      pl.off_peaks = kHeaderBytes;
-      pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
-      pl.off_len = pl.off_roi + align16((uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4);
-      pl.off_cidx = pl.off_len + align16(p.nsym);
-      pl.off_lo = pl.off_cidx + align16((uint64_t)p.n_chunks * 4);
-      pl.off_pq = pl.off_lo + align16((uint64_t)pl.n_lo * 8);
-      pl.off_bits = pl.off_pq + align16((uint64_t)pl.n_pq * 8);
-      pl.total = pl.off_bits + align16((uint64_t)pl.n_words * 4);
-      const bool fits = pl.total <= a.out_stride;
-      if (rank == 0 && tid == 0) {
-        int32_t timeout = 0;
-        for (uint32_t r = 0; r < C; ++r) timeout |= cl.map_shared_rank(&ms.timeout, r)[0];
-        a.frame_bytes[f] = pl.total;
-        a.frame_status[f] = fits ? (timeout ? ROIBIN_ERR_TIMEOUT : ROIBIN_OK) : ROIBIN_ERR_CAPACITY;
-      }
-      if (fits) {
-        if (rank == 0) write_frame_head(out, p, pl, keys, L.cb_len, cw);
-        // a10 + a11: bit-packing and outliers of the own chunks
-        uint32_t* words = reinterpret_cast<uint32_t*>(out + pl.off_bits);
-        uint2* lo_out = reinterpret_cast<uint2*>(out + pl.off_lo);
-        uint2* pq_out = reinterpret_cast<uint2*>(out + pl.off_pq);
-        for (uint32_t k = k_lo + warp; k < k_hi; k += kFW) {
-          const uint32_t w0 = cw[k], nw = (k + 1 < p.n_chunks ? cw[k + 1] : pl.n_words) - w0;
-          for (uint32_t w = lane; w < nw; w += 32) words[w0 + w] = 0;
-          __threadfence_block();
-          __syncwarp();
-          const uint32_t s0 = min(p.M, k * kChunk + lane * 128), s1 = min(p.M, min((k + 1) * kChunk, s0 + 128));
-          uint32_t bits = 0, nlo = 0, npq = 0;
-          for (uint32_t i = s0; i < s1; i += 4) {
-            uint32_t w, pqn;
-            load4(i, w, pqn);
-            for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
-              const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, i + t, p, esc);
-              bits += L.cb_len[code];
-              nlo += code == 0;
-              npq += (pqn >> t) & 1u;
-            }
-          }
-          const uint32_t bit_incl = warp_incl_scan(bits), lo_incl = warp_incl_scan(nlo),
-                         pq_incl = warp_incl_scan(npq);
-          const uint32_t start = bit_incl - bits;
-          uint32_t wi = w0 + start / 32;
-          const uint32_t o = start & 31u;
-          uint64_t acc = 0;
-          uint32_t nacc = o;
-          bool first = o != 0;  // the first word is shared with the previous lane
-          uint32_t lo_pos = clo[k] + lo_incl - nlo, pq_pos = cpq[k] + pq_incl - npq;
-          for (uint32_t i = s0; i < s1; i += 4) {
-            uint32_t w, pqn;
-            load4(i, w, pqn);
-            for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
-              const uint32_t bin = i + t;
-              const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, bin, p, esc);
-              const uint32_t Lc = L.cb_len[code];
-              acc |= (uint64_t)L.cb_code[code] << (64 - nacc - Lc);
-              nacc += Lc;
-              if (nacc >= 32) {
-                const uint32_t word = (uint32_t)(acc >> 32);
-                if (first) atomicOr(words + wi, word);
-                else words[wi] = word;
-                first = false;
-                ++wi;
-                acc <<= 32;
-                nacc -= 32;
+      for (uint32_t size = 2; size <= n2; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t k = tid; k < n2; k += kPT) {
+            const uint32_t partner = k ^ stride;
+            if (partner > k) {
+              const bool upw = (k & size) == 0;
+              const uint32_t x = v.acc[k], y = v.acc[partner];
+              if ((x > y) == upw) {
+                v.acc[k] = y;
+                v.acc[partner] = x;
               }
-              if (code == 0) lo_out[lo_pos++] = make_uint2(bin, (uint32_t)__ldcg(lo_delta + bin));
-              if ((pqn >> t) & 1u) pq_out[pq_pos++] = make_uint2(bin, __ldcg(pq_bits + bin));
             }
           }
-          if (nacc > 0) atomicOr(words + wi, (uint32_t)(acc >> 32));  // shared with the next lane
-        }
-        // a3: ROI windows of peaks k = rank, rank + C, ... (one warp per peak)
-        float* roi = reinterpret_cast<float*>(out + pl.off_roi);
-        const uint32_t win = (uint32_t)(p.roi_h * p.roi_w), plane = p.H * p.W;
-        for (uint32_t k = rank + C * warp; k < n_pk; k += C * kFW) {
-          const uint32_t px = keys[k];
-          const uint32_t pn = px / plane, rem = px - pn * plane;
-          const int r = (int)(rem / p.W), c = (int)(rem % p.W);
-          const float* panel = frame + (size_t)pn * plane;
-          const int r0 = r - p.roi_h / 2, c0 = c - p.roi_w / 2;
-          for (uint32_t e = lane; e < win; e += 32) {
-            const int rr = r0 + (int)(e / p.roi_w), cc = c0 + (int)(e % p.roi_w);
-            const bool in = rr >= 0 && rr < (int)p.H && cc >= 0 && cc < (int)p.W;
-            roi[(size_t)k * win + e] = in ? __ldg(panel + (size_t)rr * p.W + cc) : 0.0f;
-          }
+          __syncthreads();
         }
       }
-    } else if (rank == 0 && tid == 0) {
-      a.frame_bytes[f] = 0;
-      a.frame_status[f] = status0;
+      for (uint32_t k = tid; k < n_acc; k += kPT) s.peak_part[fp * sh.peak_cap + k] = pn * p.H * p.W + v.acc[k];
     }
-    cl.sync();  // D: nobody reads this frame's codes any more
+    if (tid == 0) s.peak_part_count[fp] = n_acc;
   }
 }
 
 // ---------------------------------------------------------------------------
-// host side: shape, support check, launch
-static bool make_shape(const DevParams& p, uint32_t C, uint32_t stages, FusedShape* out) {
+// Finalises frame f (one CTA).  Everything other CTAs wrote is read through
+// L2 only (ld.global.cg).
+__device__ void finalize_frame(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                               const FinView& v, uint32_t f) {
+  const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  uint64_t* trace = (a.trace && f < a.trace_frames && tid == 0) ? a.trace + (size_t)f * kTracePoints : nullptr;
+  if (trace) trace[0] = global_ns();
+  const uint32_t Mp = p.Hb * p.Wb;
+  const uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride;
+  const uint16_t* esc = s.codes + (size_t)f * p.M;
+  const int32_t* lo_delta = s.lo_delta + (size_t)f * p.M;
+  const uint32_t* pq_bits = s.pq_bits + (size_t)f * p.M;
+  const uint32_t* pq_mask = s.pq_mask + (size_t)f * p.P * sh.mask_words;
+  uint8_t* out = a.out + (size_t)f * a.out_stride;
+  const float* frame = a.frames + (size_t)f * p.frame_px;
+
+  // a8: the frame's histogram
+  for (uint32_t k = tid; k < p.nsym; k += kPT) {
+    uint32_t t = 0;
+    for (uint32_t pn = 0; pn < p.P; ++pn) t += __ldcg(s.hist_part + ((size_t)f * p.P + pn) * kMaxSymbols + k);
+    v.total[k] = t;
+  }
+  // the frame's peaks: the per-panel sorted lists, concatenated in panel order
+  if (tid == 0) {
+    v.ctl[CTL_STATUS] = ROIBIN_OK;
+    v.ctl[CTL_BAD] = 0;
+    v.ctl[CTL_CARRY0] = 0;
+  }
+  __syncthreads();
+  if (a.user_peaks) {
+    const uint32_t n = a.user_npeaks[f];
+    if (tid == 0) v.ctl[CTL_CARRY0] = n;
+    if (n > p.max_peaks) {
+      if (tid == 0) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_CAPACITY;
+    } else {
+      const uint16_t* up = a.user_peaks + (size_t)f * p.max_peaks * 3;
+      for (uint32_t k = tid; k < n; k += kPT) {
+        const uint32_t pn = up[3 * k], r = up[3 * k + 1], c = up[3 * k + 2];
+        if (pn >= p.P || r >= p.H || c >= p.W) v.ctl[CTL_BAD] = 1;
+        else v.keys[k] = (pn * p.H + r) * p.W + c;
+      }
+    }
+  } else {
+    if (tid == 0) {
+      uint32_t n = 0;
+      bool over = false;
+      for (uint32_t pn = 0; pn < p.P; ++pn) {
+        const uint32_t c = __ldcg(s.peak_part_count + (size_t)f * p.P + pn);
+        if (c > p.max_peaks) over = true;
+        if (pn < 1024) v.ctl[CTL_OFFS + pn] = n;
+        n += c;
+      }
+      if (over || n > p.max_peaks) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_CAPACITY;
+      v.ctl[CTL_CARRY0] = n;
+    }
+    __syncthreads();
+    if (v.ctl[CTL_STATUS] == ROIBIN_OK) {
+      for (uint32_t pn = warp; pn < p.P; pn += kPW) {
+        const uint32_t c = __ldcg(s.peak_part_count + (size_t)f * p.P + pn);
+        uint32_t off = 0;
+        if (pn < 1024) {
+          off = v.ctl[CTL_OFFS + pn];
+        } else {
+          for (uint32_t q = 0; q < pn; ++q) off += __ldcg(s.peak_part_count + (size_t)f * p.P + q);
+        }
+        for (uint32_t k = lane; k < c; k += 32)
+          v.keys[off + k] = __ldcg(s.peak_part + ((size_t)f * p.P + pn) * sh.peak_cap + k);
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t n_pk = v.ctl[CTL_CARRY0];
+  if (tid == 0 && v.ctl[CTL_BAD] && v.ctl[CTL_STATUS] == ROIBIN_OK) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_INVALID_ARG;
+  if (tid == 0) a.peaks_count_out[f] = n_pk;
+  __syncthreads();
+  if (v.ctl[CTL_STATUS] == ROIBIN_OK)
+    for (uint32_t k = tid; k < n_pk; k += kPT) a.peaks_key_out[(size_t)f * p.max_peaks + k] = v.keys[k];
+  if (trace) trace[1] = global_ns();
+  // a9: codebook
+  const int cb = build_codebook(v.total, p.nsym, *v.hs, v.cb_len, v.cb_code);
+  if (tid == 0 && cb != ROIBIN_OK && v.ctl[CTL_STATUS] == ROIBIN_OK) v.ctl[CTL_STATUS] = (uint32_t)cb;
+  __syncthreads();
+  if (trace) trace[2] = global_ns();
+  const int32_t status0 = (int32_t)v.ctl[CTL_STATUS];
+  if (status0 != ROIBIN_OK) {
+    if (tid == 0) {
+      a.frame_bytes[f] = 0;
+      a.frame_status[f] = status0;
+    }
+    return;
+  }
+  auto pq_bit = [&](uint32_t bin) -> uint32_t {
+    const uint32_t pn = bin / Mp, lb = bin - pn * Mp;
+    return (__ldcg(pq_mask + (size_t)pn * sh.mask_words + (lb >> 5)) >> (lb & 31)) & 1u;
+  };
+  // a10/a11 sizes per chunk: one warp per chunk, 128 consecutive symbols per lane
+  for (uint32_t k = warp; k < p.n_chunks; k += kPW) {
+    const uint32_t s0 = min(p.M, k * kChunk + lane * 128), s1 = min(p.M, min((k + 1) * kChunk, s0 + 128));
+    uint32_t bits = 0, nlo = 0, npq = 0;
+    for (uint32_t i = s0; i < s1; i += 4) {
+      const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(codes + i));
+      for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
+        const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, esc + i + t, p.R);
+        bits += v.cb_len[code];
+        nlo += code == 0;
+      }
+    }
+    for (uint32_t i = s0; i < s1; ++i) npq += pq_bit(i);
+    for (int d = 16; d > 0; d >>= 1) {
+      bits += __shfl_xor_sync(0xffffffffu, bits, d);
+      nlo += __shfl_xor_sync(0xffffffffu, nlo, d);
+      npq += __shfl_xor_sync(0xffffffffu, npq, d);
+    }
+    if (lane == 0) {
+      v.cw[k] = (bits + 31) / 32;
+      v.clo[k] = nlo;
+      v.cpq[k] = npq;
+    }
+  }
+  if (tid < 3) v.ctl[CTL_CARRY0 + tid] = 0;
+  __syncthreads();
+  if (trace) trace[3] = global_ns();
+  for (uint32_t k0 = 0; k0 < p.n_chunks; k0 += kPT) {
+    const uint32_t k = k0 + tid;
+    const uint32_t w = k < p.n_chunks ? v.cw[k] : 0u, l = k < p.n_chunks ? v.clo[k] : 0u,
+                   q = k < p.n_chunks ? v.cpq[k] : 0u;
+    uint32_t tw, tl, tq;
+    const uint32_t ew = block_excl_scan(w, v.ctl + CTL_TMP, &tw);
+    const uint32_t el = block_excl_scan(l, v.ctl + CTL_TMP, &tl);
+    const uint32_t eq = block_excl_scan(q, v.ctl + CTL_TMP, &tq);
+    if (k < p.n_chunks) {
+      v.cw[k] = v.ctl[CTL_CARRY0] + ew;
+      v.clo[k] = v.ctl[CTL_CARRY1] + el;
+      v.cpq[k] = v.ctl[CTL_CARRY2] + eq;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      v.ctl[CTL_CARRY0] += tw;
+      v.ctl[CTL_CARRY1] += tl;
+      v.ctl[CTL_CARRY2] += tq;
+    }
+    __syncthreads();
+  }
+  FramePlan pl;
+  pl.n_peaks = n_pk;
+  pl.n_words = v.ctl[CTL_CARRY0];
+  pl.n_lo = v.ctl[CTL_CARRY1];
+  pl.n_pq = v.ctl[CTL_CARRY2];
+  pl.off_peaks = kHeaderBytes;
+  pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
+  pl.off_len = pl.off_roi + align16((uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4);
+  pl.off_cidx = pl.off_len + align16(p.nsym);
+  pl.off_lo = pl.off_cidx + align16((uint64_t)p.n_chunks * 4);
+  pl.off_pq = pl.off_lo + align16((uint64_t)pl.n_lo * 8);
+  pl.off_bits = pl.off_pq + align16((uint64_t)pl.n_pq * 8);
+  pl.total = pl.off_bits + align16((uint64_t)pl.n_words * 4);
+  const bool fits = pl.total <= a.out_stride;
+  if (tid == 0) {
+    a.frame_bytes[f] = pl.total;
+    a.frame_status[f] = fits ? ROIBIN_OK : ROIBIN_ERR_CAPACITY;
+  }
+  if (!fits) return;
+  write_frame_head(out, p, pl, v.keys, v.cb_len, v.cw);
+  if (trace) trace[4] = global_ns();
+  // a10 + a11: bit-packing and outliers, one warp per chunk
+  uint32_t* words = reinterpret_cast<uint32_t*>(out + pl.off_bits);
+  uint2* lo_out = reinterpret_cast<uint2*>(out + pl.off_lo);
+  uint2* pq_out = reinterpret_cast<uint2*>(out + pl.off_pq);
+  for (uint32_t k = warp; k < p.n_chunks; k += kPW) {
+    const uint32_t w0 = v.cw[k], nw = (k + 1 < p.n_chunks ? v.cw[k + 1] : pl.n_words) - w0;
+    for (uint32_t w = lane; w < nw; w += 32) words[w0 + w] = 0;
+    __threadfence_block();
+    __syncwarp();
+    const uint32_t s0 = min(p.M, k * kChunk + lane * 128), s1 = min(p.M, min((k + 1) * kChunk, s0 + 128));
+    uint32_t bits = 0, nlo = 0, npq = 0;
+    for (uint32_t i = s0; i < s1; i += 4) {
+      const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(codes + i));
+      for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
+        const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, esc + i + t, p.R);
+        bits += v.cb_len[code];
+        nlo += code == 0;
+      }
+    }
+    for (uint32_t i = s0; i < s1; ++i) npq += pq_bit(i);
+    const uint32_t bit_incl = warp_incl_scan(bits), lo_incl = warp_incl_scan(nlo), pq_incl = warp_incl_scan(npq);
+    const uint32_t start = bit_incl - bits;
+    uint32_t wi = w0 + start / 32;
+    uint64_t accb = 0;
+    uint32_t nacc = start & 31u;
+    bool first = nacc != 0;  // the first word is shared with the previous lane
+    uint32_t lo_pos = v.clo[k] + lo_incl - nlo, pq_pos = v.cpq[k] + pq_incl - npq;
+    for (uint32_t i = s0; i < s1; i += 4) {
+      const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(codes + i));
+      for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
+        const uint32_t bin = i + t;
+        const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, esc + bin, p.R);
+        const uint32_t Lc = v.cb_len[code];
+        accb |= (uint64_t)v.cb_code[code] << (64 - nacc - Lc);
+        nacc += Lc;
+        if (nacc >= 32) {
+          const uint32_t word = (uint32_t)(accb >> 32);
+          if (first) atomicOr(words + wi, word);
+          else words[wi] = word;
+          first = false;
+          ++wi;
+          accb <<= 32;
+          nacc -= 32;
+        }
+        if (code == 0) lo_out[lo_pos++] = make_uint2(bin, (uint32_t)__ldcg(lo_delta + bin));
+      }
+    }
+    if (nacc > 0) atomicOr(words + wi, (uint32_t)(accb >> 32));  // shared with the next lane
+    if (npq)
+      for (uint32_t i = s0; i < s1; ++i)
+        if (pq_bit(i)) pq_out[pq_pos++] = make_uint2(i, __ldcg(pq_bits + i));
+  }
+  if (trace) trace[5] = global_ns();
+  // a3: ROI windows (one warp per peak)
+  float* roi = reinterpret_cast<float*>(out + pl.off_roi);
+  const uint32_t win = (uint32_t)(p.roi_h * p.roi_w), plane = p.H * p.W;
+  for (uint32_t k = warp; k < n_pk; k += kPW) {
+    const uint32_t px = v.keys[k];
+    const uint32_t pn = px / plane, rem = px - pn * plane;
+    const int r = (int)(rem / p.W), c = (int)(rem % p.W);
+    const float* panel = frame + (size_t)pn * plane;
+    const int r0 = r - p.roi_h / 2, c0 = c - p.roi_w / 2;
+    for (uint32_t e = lane; e < win; e += 32) {
+      const int rr = r0 + (int)(e / p.roi_w), cc = c0 + (int)(e % p.roi_w);
+      const bool in = rr >= 0 && rr < (int)p.H && cc >= 0 && cc < (int)p.W;
+      roi[(size_t)k * win + e] = in ? __ldg(panel + (size_t)rr * p.W + cc) : 0.0f;
+    }
+  }
+  // the frame's code bytes are dead: drop them from L2 without a write-back
+  __syncthreads();
+  const uint32_t lines = ceil_div(p.M, 128);
+  for (uint32_t l = tid; l < lines; l += kPT) discard_line(codes + (size_t)l * 128);
+  if (trace) trace[6] = global_ns();
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainArgs a, FusedShape sh) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const StreamView sv = stream_view(sm, sh);
+  const FinView fv = fin_view(sm, sh);
+  const uint64_t pol = evict_first_policy();
+  const uint32_t n_items = a.n_frames * p.P;
+  for (;;) {
+    if (threadIdx.x == 0) sv.ctl[CTL_ITEM] = atomicAdd(s.work, 1u);
+    __syncthreads();
+    const uint32_t item = sv.ctl[CTL_ITEM];
+    __syncthreads();
+    if (item >= n_items) break;
+    const uint32_t f = item / p.P, pn = item - f * p.P;
+    process_panel(p, s, a, sh, sv, f, pn, pol);
+    // publish the panel; the CTA that completes the frame finalises it
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sv.ctl[CTL_LAST] = atomicAdd(s.frame_done + f, 1u) == p.P - 1 ? 1u : 0u;
+    __syncthreads();
+    if (sv.ctl[CTL_LAST]) {
+      __threadfence();
+      finalize_frame(p, s, a, sh, fv, f);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, FusedShape* out) {
   FusedShape sh{};
-  sh.C = C;
-  const uint32_t g_total = p.P * p.Hb;
-  uint32_t rows = ceil_div(g_total, C);
-  rows += rows & 1u;  // even: keeps cap_bins a multiple of 4
-  sh.rows_per_cta = rows;
-  sh.cap_bins = rows * p.Wb;
-  sh.RB = max(1u, min(16u, (uint32_t)(4 * kFT) / p.W));
-  sh.stages = stages;
-  sh.stage_bytes = 2 * sh.RB * p.W * 4;
-  sh.chunks_per_cta = ceil_div(sh.cap_bins, kChunk) + 1;
-  const int side = 2 * peak_reach(p) + 1;
+  const uint32_t NP = p.W / 4;
+  uint32_t RB = rb ? rb : max(1u, (uint32_t)(kItems * kPT) / max(NP, 1u));
+  RB = min(RB, min(16u, p.Hb));
+  if (RB * NP > (uint32_t)(kItems * kPT)) return false;  // a step must fit the thread items
+  sh.RB = RB;
+  sh.qrows = 2 * RB + 1;
+  sh.ctas_per_sm = ctas_per_sm;
+  sh.mask_words = ceil_div(p.Hb * p.Wb, 32) + 1;
+  sh.side = 2 * (uint32_t)peak_reach(p) + 1;
   uint32_t n2 = 1;
   while (n2 < max(p.max_peaks, 1u)) n2 <<= 1;
-  const uint64_t ring = (uint64_t)stages * sh.stage_bytes;
-  const uint64_t nbuf = (uint64_t)kFW * side * side * 4;
-  const uint64_t huff = sizeof(HuffSmem) + kMaxSymbols * 4;
-  const uint64_t scans = (uint64_t)n2 * 4 + 16 + 3ull * p.n_chunks * 4;
-  uint64_t un = ring;
-  if (nbuf > un) un = nbuf;
-  if (huff > un) un = huff;
-  if (scans > un) un = scans;
+  sh.sort_n2 = n2;
+  sh.peak_cap = max(p.max_peaks, 1u);
+  sh.n_chunks = p.n_chunks;
+  sh.codes_stride = p.n_chunks * kChunk;
   uint64_t off = 0;
-  auto take = [&](uint64_t bytes, uint64_t align) {
-    off = (off + align - 1) / align * align;
+  auto take = [&](uint64_t bytes) {
+    off = (off + 15) / 16 * 16;
     const uint64_t o = off;
     off += bytes;
     return (uint32_t)o;
   };
-  sh.off_bar = take(8 * stages, 16);
-  sh.off_hist = take(kMaxSymbols * 4, 16);
-  sh.off_cb_len = take(kMaxSymbols, 16);
-  sh.off_cb_code = take(kMaxSymbols * 4, 16);
-  sh.off_own = take(3ull * sh.chunks_per_cta * 4, 16);
-  sh.off_misc = take(sizeof(FusedMisc), 16);
-  sh.off_pq = take((sh.cap_bins / 32 + 1) * 4, 16);
-  sh.off_qbuf = take((uint64_t)(sh.RB + 1) * p.Wb * 4, 16);
-  sh.off_codes = take(sh.cap_bins + 16, 16);
-  sh.off_union = take(un, 128);
-  sh.union_bytes = (uint32_t)un;
-  sh.smem = (uint32_t)off;
+  sh.off_ctl = take((uint64_t)CTL_WORDS * 4);  // both roles use the control words
+  const uint64_t base = off;
+  // streaming role
+  sh.off_hist = take(kMaxSymbols * 4);
+  sh.off_qbuf = take((uint64_t)sh.qrows * p.Wb * 4);
+  sh.off_mask = take((uint64_t)sh.mask_words * 4);
+  sh.off_thr = take(kThrLocalCap * 4);
+  sh.off_nb = take((uint64_t)kPW * sh.side * sh.side * 4);
+  sh.off_acc = take((uint64_t)n2 * 4);
+  const uint64_t stream_end = off;
+  // finalising role (overlaps the streaming role)
+  off = base;
+  sh.off_huff = take(sizeof(HuffSmem));
+  sh.off_total = take(kMaxSymbols * 4);
+  sh.off_cblen = take(kMaxSymbols);
+  sh.off_cbcode = take(kMaxSymbols * 4);
+  sh.off_keys = take((uint64_t)sh.peak_cap * 4);
+  sh.off_cw = take(3ull * p.n_chunks * 4);
+  const uint64_t fin_end = off;
+  sh.smem = (uint32_t)(stream_end > fin_end ? stream_end : fin_end);
   *out = sh;
-  return off <= 227 * 1024;
+  return sh.smem <= 227 * 1024;
+}
+
+bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, FusedShape* out) {
+  if (p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > (uint32_t)(kItems * kPT)) return false;
+  if (ctas_per_sm < 1 || ctas_per_sm > 8 || rows_per_step > 16) return false;
+  FusedShape sh;
+  if (!make_shape(p, ctas_per_sm, rows_per_step, &sh)) return false;
+  if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, kPT, sh.smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  sh.ctas_per_sm = min((uint32_t)per_sm, ctas_per_sm);
+  sh.n_ctas = sh.ctas_per_sm * (uint32_t)sms;
+  *out = sh;
+  return true;
 }
 
 bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out) {
-  if (p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.n_chunks > 4096) return false;
-  cudaFuncSetAttribute(k_fused, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  const uint32_t cands[][2] = {{16, 4}, {16, 3}, {16, 2}, {8, 4}, {8, 3}, {8, 2}};
-  for (const auto& cs : cands) {
-    FusedShape sh;
-    if (!make_shape(p, cs[0], cs[1], &sh)) continue;
-    if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(sh.C * 64, 1, 1);
-    cfg.blockDim = dim3(kFT, 1, 1);
-    cfg.dynamicSmemBytes = sh.smem;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = sh.C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n_clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&n_clusters, (void*)k_fused, &cfg) != cudaSuccess || n_clusters < 1) {
-      cudaGetLastError();
-      continue;
-    }
-    sh.n_clusters = (uint32_t)n_clusters;
-    (void)device;
-    (void)num_sms;
-    *out = sh;
-    return true;
-  }
-  return false;
+  (void)device;
+  (void)num_sms;
+  return fused_shape_for(p, 4, 0, out);
 }
 
-cudaError_t launch_fused(const DevParams& p, const Scratch& fs, const PlainArgs& a, const FusedShape& sh,
+cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
                          cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+  // per-frame completion counters and the work counter start at zero
+  cudaError_t e = cudaMemsetAsync(s.frame_done, 0, sizeof(uint32_t) * (a.n_frames + 1), st);
   if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  const uint32_t n_clusters = min(sh.n_clusters, a.n_frames);
-  FusedShape s2 = sh;
-  s2.n_clusters = n_clusters;
-  cfg.gridDim = dim3(sh.C * n_clusters, 1, 1);
-  cfg.blockDim = dim3(kFT, 1, 1);
-  cfg.dynamicSmemBytes = sh.smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = sh.C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_fused, p, fs, a, s2);
+  e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+  if (e != cudaSuccess) return e;
+  Scratch s2 = s;
+  s2.work = s.frame_done + a.n_frames;
+  const uint32_t grid = min(sh.n_ctas, a.n_frames * p.P);
+  k_fused<<<grid, kPT, sh.smem, st>>>(p, s2, a, sh);
+  return cudaGetLastError();
 }
 
 }  // namespace roibin

@@ -34,8 +34,8 @@ struct roibin_ctx {
   int path_req = ROIBIN_PATH_AUTO;
   bool fused_ok = false;
   FusedShape fshape{};
-  Scratch fs{};
-  void* fscratch = nullptr;
+  uint64_t* trace = nullptr;
+  uint32_t trace_frames = 0;
   uint32_t last_launches = 0;
   // timing
   bool timing = false;
@@ -172,6 +172,13 @@ uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s
   t.dec_info = c.take<DecInfo>(n);
   t.dq = t.lo_delta;
   t.bhat = reinterpret_cast<float*>(t.pq_bits);
+  const uint64_t mask_words = ceil_div(d.Hb * d.Wb, 32) + 1;
+  t.codes8 = c.take<uint8_t>((uint64_t)n * d.n_chunks * kChunk);
+  t.pq_mask = c.take<uint32_t>((uint64_t)n * d.P * mask_words);
+  t.hist_part = c.take<uint32_t>((uint64_t)n * d.P * kMaxSymbols);
+  t.peak_part = c.take<uint32_t>((uint64_t)n * d.P * std::max<uint32_t>(d.max_peaks, 1));
+  t.peak_part_count = c.take<uint32_t>((uint64_t)n * d.P);
+  t.frame_done = c.take<uint32_t>((uint64_t)n + 1);
   if (s) *s = t;
   return c.off + 256;
 }
@@ -252,12 +259,11 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
   choose_shape(ctx, n_frames, &a);
   a.peaks_key_out = ctx->s.peak_key;
   a.peaks_count_out = ctx->s.peak_count;
-  if (resolved_path(ctx) == ROIBIN_PATH_FUSED) {
-    // the per-slot counters start at zero (the kernel resets them after each frame)
-    cudaError_t e = cudaMemsetAsync(ctx->fs.thr_count, 0, sizeof(uint32_t) * ctx->fshape.n_clusters, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fs.peak_count, 0, sizeof(uint32_t) * ctx->fshape.n_clusters, st);
-    if (e != cudaSuccess) return cuda_status(e);
-    e = timed(ctx, K_FUSED, st, [&] { return launch_fused(ctx->dp, ctx->fs, a, ctx->fshape, st); });
+  a.trace = ctx->trace;
+  a.trace_frames = ctx->trace_frames;
+  if (resolved_path(ctx) == ROIBIN_PATH_FUSED && (uint64_t)n_frames * ctx->dp.P < (1ull << 31)) {
+    ctx->last_launches++;  // the counter reset
+    cudaError_t e = timed(ctx, K_FUSED, st, [&] { return launch_fused(ctx->dp, ctx->s, a, ctx->fshape, st); });
     return cuda_status(e);
   }
   return compress_plain(ctx, a, st);
@@ -316,8 +322,7 @@ int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_p
   ctx->budget = hbm_budget_bytes;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   ctx->fused_ok = fused_plan(ctx->dp, device, ctx->num_sms, &ctx->fshape);
-  const uint64_t fneed = ctx->fused_ok ? carve_scratch(ctx->dp, ctx->fshape.n_clusters, nullptr, nullptr) : 0;
-  const uint64_t need = carve_scratch(ctx->dp, max_frames_per_call, nullptr, nullptr) + fneed;
+  const uint64_t need = carve_scratch(ctx->dp, max_frames_per_call, nullptr, nullptr);
   if (hbm_budget_bytes && need > hbm_budget_bytes) {
     delete ctx;
     return ROIBIN_ERR_OUT_OF_BUDGET;
@@ -329,10 +334,6 @@ int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_p
   }
   ctx->scratch_bytes = need;
   carve_scratch(ctx->dp, max_frames_per_call, static_cast<uint8_t*>(ctx->scratch), &ctx->s);
-  if (ctx->fused_ok) {
-    const uint64_t off = (need - fneed + 255) & ~uint64_t(255);
-    carve_scratch(ctx->dp, ctx->fshape.n_clusters, static_cast<uint8_t*>(ctx->scratch) + off, &ctx->fs);
-  }
   *out = ctx;
   return ROIBIN_OK;
 }
@@ -364,6 +365,32 @@ int roibin_ctx_set_path(roibin_ctx* ctx, int path) {
     return ROIBIN_ERR_INVALID_ARG;
   if (path == ROIBIN_PATH_FUSED && !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
   ctx->path_req = path;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t rows_per_step) {
+  if (!ctx || !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  FusedShape sh;
+  if (!fused_shape_for(ctx->dp, ctas_per_sm, rows_per_step, &sh)) return ROIBIN_ERR_INVALID_ARG;
+  ctx->fshape = sh;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* rows_per_step,
+                           uint32_t* grid_ctas, uint32_t* smem_bytes) {
+  if (!ctx || !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
+  if (ctas_per_sm) *ctas_per_sm = ctx->fshape.ctas_per_sm;
+  if (rows_per_step) *rows_per_step = ctx->fshape.RB;
+  if (grid_ctas) *grid_ctas = ctx->fshape.n_ctas;
+  if (smem_bytes) *smem_bytes = ctx->fshape.smem;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_set_trace(roibin_ctx* ctx, uint64_t* d_trace, uint32_t n_frames) {
+  if (!ctx || (n_frames > 0 && !d_trace)) return ROIBIN_ERR_INVALID_ARG;
+  ctx->trace = n_frames ? d_trace : nullptr;
+  ctx->trace_frames = n_frames;
   return ROIBIN_OK;
 }
 

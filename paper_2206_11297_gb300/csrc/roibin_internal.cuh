@@ -85,6 +85,14 @@ struct Scratch {
   uint32_t* dec_table;    // [n][kDecTableWords] canonical decoding tables
   uint32_t* dec_zero;     // [n] code-0 symbols decoded
   DecInfo* dec_info;      // [n]
+  // persistent batched path (codes: esc side array; lo_delta, pq_bits shared)
+  uint8_t* codes8;          // [n][n_chunks * kChunk] one code byte per bin
+  uint32_t* pq_mask;        // [n][P][mask_words] prequantisation-outlier bits per panel
+  uint32_t* hist_part;      // [n][P][kMaxSymbols] per-panel histograms
+  uint32_t* peak_part;      // [n][P][max(max_peaks, 1)] per-panel sorted peaks
+  uint32_t* peak_part_count;  // [n][P]
+  uint32_t* frame_done;     // [n + 1] panels finished per frame; [n] = work counter
+  uint32_t* work;           // set per launch
 };
 
 constexpr uint32_t kDecTableWords = 34 + 34 + 34 + kMaxSymbols;  // count, first, index, symbols
@@ -483,22 +491,28 @@ struct PlainArgs {
   uint32_t rows_per_step;
   uint32_t* peaks_key_out;    // fused path: each frame's final peak list, for roibin_last_peaks
   uint32_t* peaks_count_out;
+  uint64_t* trace;            // fused path: kTracePoints globaltimer stamps per traced frame
+  uint32_t trace_frames;
 };
+constexpr uint32_t kTracePoints = 10;
 
-// Shape of the fused cluster kernel, chosen on the host (fused_kernel.cu).
+// Shape of the persistent batched kernel, chosen on the host (fused_kernel.cu).
 struct FusedShape {
-  uint32_t C;               // CTAs per cluster (one frame per cluster at a time)
-  uint32_t rows_per_cta;    // global binned rows per CTA (even)
-  uint32_t cap_bins;        // rows_per_cta * Wb, a multiple of 4
-  uint32_t RB;              // binned rows per TMA stage
-  uint32_t stages;          // ring depth
-  uint32_t stage_bytes;     // 2 * RB * W * 4
-  uint32_t n_clusters;      // clusters launched = scratch slots
-  uint32_t chunks_per_cta;  // upper bound of the chunks a CTA owns
-  uint32_t off_bar, off_hist, off_cb_len, off_cb_code, off_own, off_misc, off_pq, off_qbuf, off_codes,
-      off_union, union_bytes, smem;
+  uint32_t ctas_per_sm, n_ctas;  // resident CTAs per SM, grid size
+  uint32_t RB;                   // binned rows per streaming step
+  uint32_t qrows;                // rows of the circular q buffer (2 RB + 1)
+  uint32_t mask_words;           // prequantisation-outlier bitmask words per panel
+  uint32_t side;                 // side of the peak-test neighbourhood
+  uint32_t sort_n2;              // power of two >= max_peaks
+  uint32_t peak_cap;             // max(max_peaks, 1)
+  uint32_t n_chunks;
+  uint32_t codes_stride;         // code bytes per frame slot (n_chunks * kChunk)
+  uint32_t off_ctl, off_hist, off_qbuf, off_mask, off_thr, off_nb, off_acc;  // streaming role
+  uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw;     // finalising role
+  uint32_t smem;
 };
 bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out);
+bool fused_shape_for(const DevParams& p, uint32_t C, uint32_t stages, FusedShape* out);
 cudaError_t launch_fused(const DevParams& p, const Scratch& fs, const PlainArgs& a, const FusedShape& sh,
                          cudaStream_t st);
 
