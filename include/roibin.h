@@ -151,8 +151,11 @@ int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_
  * CTA that finalises frame f writes 10 globaltimer stamps (ns) to
  * d_trace[f * 10 + i]: 0 finalisation start, 1 peak list gathered, 2 codebook
  * built, 3 chunk sizes done, 4 header written, 5 bitstream written, 6 ROI
- * written (7..9 unused).  n_frames = 0 switches tracing off.
- * d_trace: device u64[n_frames * 10], owned by the caller. */
+ * written (7..9 unused).  After those n_frames * 10 stamps, every panel item
+ * (f, p) of a traced frame writes 4 stamps at index n_frames * 10 + (f * P +
+ * p) * 4: start, streaming done, peaks done (3 unused).  n_frames = 0
+ * switches tracing off.  d_trace: device u64[n_frames * (10 + 4 P)], owned
+ * by the caller. */
 int roibin_ctx_set_trace(roibin_ctx* ctx, uint64_t* d_trace, uint32_t n_frames);
 
 /* Compresses n_frames frames (1 <= n_frames <= max_frames_per_call).

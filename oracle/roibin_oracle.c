@@ -61,7 +61,7 @@ int orc_is_peak_candidate(const float* panel, uint32_t rows, uint32_t cols, uint
  * pixels above zero form the peak, total intensity over 600, SNR over 10, and
  * between 2 and 30 pixels.  It defines neither the background nor the noise.  Reading:
  *   - background ring: in-panel pixels with r0^2 <= di^2 + dj^2 < (r0+dr)^2;
- *     bkg = mean, sigma = population standard deviation (two passes), fp64,
+ *     bkg = mean, sigma = population standard deviation (two passes),
  *     row-major order; an empty ring gives bkg = 0, sigma = 0;
  *   - peak pixels: in-panel pixels of the local-maximum window with
  *     I - bkg > pix_nsigma * sigma (pix_nsigma = 0 gives the paper's plain
@@ -69,13 +69,16 @@ int orc_is_peak_candidate(const float* panel, uint32_t rows, uint32_t cols, uint
  *   - npix = their count, atot = sum of (I - bkg) over them;
  *   - keep iff npix_min <= npix <= npix_max, atot > atot_thr and
  *     atot > son_min * sigma * sqrt(npix)  (SNR = atot / (sigma sqrt(npix))).
+ * The accept/reject decision is taken in float32, the precision of the data
+ * and of the kernel (the paper fixes none): every operation rounds once, in
+ * the order written, and sqrtf is correctly rounded.
  * ------------------------------------------------------------------------ */
 int orc_evaluate_peak(const float* panel, uint32_t rows, uint32_t cols, uint32_t r, uint32_t c,
                       const orc_params* p) {
   const long r0 = p->ring_r0, outer = (long)p->ring_r0 + p->ring_dr;
   const long reach = outer - 1;
 
-  double sum = 0.0;
+  float sum = 0.0f;
   long n = 0;
   for (long dr = -reach; dr <= reach; ++dr) {
     for (long dc = -reach; dc <= reach; ++dc) {
@@ -83,36 +86,36 @@ int orc_evaluate_peak(const float* panel, uint32_t rows, uint32_t cols, uint32_t
       if (d2 < r0 * r0 || d2 >= outer * outer) continue;
       const long rr = (long)r + dr, cc = (long)c + dc;
       if (!in_panel(rr, cc, rows, cols)) continue;
-      sum += (double)panel[(size_t)rr * cols + (size_t)cc];
+      sum += panel[(size_t)rr * cols + (size_t)cc];
       ++n;
     }
   }
-  double bkg = 0.0, var = 0.0;
+  float bkg = 0.0f, var = 0.0f;
   if (n > 0) {
-    bkg = sum / (double)n;
-    double ss = 0.0;
+    bkg = sum / (float)n;
+    float ss = 0.0f;
     for (long dr = -reach; dr <= reach; ++dr) {
       for (long dc = -reach; dc <= reach; ++dc) {
         const long d2 = dr * dr + dc * dc;
         if (d2 < r0 * r0 || d2 >= outer * outer) continue;
         const long rr = (long)r + dr, cc = (long)c + dc;
         if (!in_panel(rr, cc, rows, cols)) continue;
-        const double d = (double)panel[(size_t)rr * cols + (size_t)cc] - bkg;
+        const float d = panel[(size_t)rr * cols + (size_t)cc] - bkg;
         ss += d * d;
       }
     }
-    var = ss / (double)n;
+    var = ss / (float)n;
   }
-  const double sigma = sqrt(var);
-  const double thr = (double)p->pix_nsigma * sigma;
+  const float sigma = sqrtf(var);
+  const float thr = p->pix_nsigma * sigma;
 
   long npix = 0;
-  double atot = 0.0;
+  float atot = 0.0f;
   for (long dr = -p->rank; dr <= p->rank; ++dr) {
     for (long dc = -p->rank; dc <= p->rank; ++dc) {
       const long rr = (long)r + dr, cc = (long)c + dc;
       if (!in_panel(rr, cc, rows, cols)) continue;
-      const double d = (double)panel[(size_t)rr * cols + (size_t)cc] - bkg;
+      const float d = panel[(size_t)rr * cols + (size_t)cc] - bkg;
       if (d > thr) {
         ++npix;
         atot += d;
@@ -120,8 +123,8 @@ int orc_evaluate_peak(const float* panel, uint32_t rows, uint32_t cols, uint32_t
     }
   }
   if (npix < p->npix_min || npix > p->npix_max) return 0;
-  if (!(atot > (double)p->atot_thr)) return 0;
-  if (!(atot > (double)p->son_min * sigma * sqrt((double)npix))) return 0;
+  if (!(atot > p->atot_thr)) return 0;
+  if (!(atot > p->son_min * sigma * sqrtf((float)npix))) return 0;
   return 1;
 }
 

@@ -146,6 +146,7 @@ enum {
   CTL_CARRY0,
   CTL_CARRY1,
   CTL_CARRY2,
+  CTL_PQ,
   CTL_TMP,
   CTL_OFFS = CTL_TMP + 33,  // per-panel peak offsets (first 1024 panels)
   CTL_WORDS = CTL_OFFS + 1024
@@ -189,9 +190,16 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
   int32_t* lo_delta = s.lo_delta + fbin;
   uint32_t* pq_bits = s.pq_bits + fbin;
 
+  uint64_t* trace = (a.trace && f < a.trace_frames && tid == 0)
+                       ? a.trace + (size_t)a.trace_frames * kTracePoints + ((size_t)f * p.P + pn) * 4
+                       : nullptr;
+  if (trace) trace[0] = global_ns();
   for (uint32_t k = tid; k < p.nsym; k += kPT) v.hist[k] = 0;
   for (uint32_t k = tid; k < sh.mask_words; k += kPT) v.mask[k] = 0;
-  if (tid == 0) v.ctl[CTL_THR] = 0;
+  if (tid == 0) {
+    v.ctl[CTL_THR] = 0;
+    v.ctl[CTL_PQ] = 0;
+  }
 
   // the thread's items within a step (the same for every step)
   uint32_t il[kItems], pr[kItems];
@@ -235,6 +243,7 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       *reinterpret_cast<int2*>(v.qbuf + (size_t)(i % sh.qrows) * p.Wb + j0) = make_int2(q0.q, q1.q);
       if (q0.outlier | q1.outlier) {
         const uint32_t lb = i * p.Wb + j0;
+        atomicAdd(v.ctl + CTL_PQ, (uint32_t)q0.outlier + (uint32_t)q1.outlier);
         atomicOr(v.mask + (lb >> 5), ((uint32_t)q0.outlier | ((uint32_t)q1.outlier << 1)) << (lb & 31));
         if (q0.outlier) pq_bits[lb] = q0.outlier_bits;
         if (q1.outlier) pq_bits[lb + 1] = q1.outlier_bits;
@@ -305,10 +314,14 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
   for (int d = 16; d > 0; d >>= 1) n_common += __shfl_xor_sync(0xffffffffu, n_common, d);
   if (lane == 0 && n_common) atomicAdd(v.hist + p.R, n_common);
   __syncthreads();
+  if (trace) trace[1] = global_ns();
   // flush the panel's histogram and outlier bits (disjoint per-panel slots)
   const size_t fp = (size_t)f * p.P + pn;
   for (uint32_t k = tid; k < p.nsym; k += kPT) s.hist_part[fp * kMaxSymbols + k] = v.hist[k];
-  for (uint32_t k = tid; k < sh.mask_words; k += kPT) s.pq_mask[fp * sh.mask_words + k] = v.mask[k];
+  const uint32_t n_pq = v.ctl[CTL_PQ];
+  if (n_pq)
+    for (uint32_t k = tid; k < sh.mask_words; k += kPT) s.pq_mask[fp * sh.mask_words + k] = v.mask[k];
+  if (tid == 0) s.pq_part_count[fp] = n_pq;
 
   // a1 + a2 on the panel's listed pixels (on every pixel >= amax_thr if the list overflowed)
   if (find) {
@@ -365,6 +378,7 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
     }
     if (tid == 0) s.peak_part_count[fp] = n_acc;
   }
+  if (trace) trace[2] = global_ns();
 }
 
 // ---------------------------------------------------------------------------
@@ -384,6 +398,12 @@ __device__ void finalize_frame(const DevParams& p, const Scratch& s, const Plain
   uint8_t* out = a.out + (size_t)f * a.out_stride;
   const float* frame = a.frames + (size_t)f * p.frame_px;
 
+  // prequantisation outliers in the frame (their bits are only read when some exist)
+  if (tid == 0) {
+    uint32_t t = 0;
+    for (uint32_t pn = 0; pn < p.P; ++pn) t += __ldcg(s.pq_part_count + (size_t)f * p.P + pn);
+    v.ctl[CTL_PQ] = t;
+  }
   // a8: the frame's histogram
   for (uint32_t k = tid; k < p.nsym; k += kPT) {
     uint32_t t = 0;
@@ -463,19 +483,37 @@ __device__ void finalize_frame(const DevParams& p, const Scratch& s, const Plain
     const uint32_t pn = bin / Mp, lb = bin - pn * Mp;
     return (__ldcg(pq_mask + (size_t)pn * sh.mask_words + (lb >> 5)) >> (lb & 31)) & 1u;
   };
+  const bool any_pq = v.ctl[CTL_PQ] != 0;
+  // a lane's 128 consecutive code bytes, loaded at once
+  auto load_lane = [&](uint32_t s0, uint4 (&cv)[8]) {
+    const uint4* src = reinterpret_cast<const uint4*>(codes + s0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cv[q] = __ldcg(src + q);
+  };
+  auto byte_of = [](const uint4& u, uint32_t j) -> uint32_t {  // j < 16
+    const uint32_t w = (j >> 2) == 0 ? u.x : (j >> 2) == 1 ? u.y : (j >> 2) == 2 ? u.z : u.w;
+    return (w >> (8 * (j & 3))) & 0xFFu;
+  };
   // a10/a11 sizes per chunk: one warp per chunk, 128 consecutive symbols per lane
   for (uint32_t k = warp; k < p.n_chunks; k += kPW) {
-    const uint32_t s0 = min(p.M, k * kChunk + lane * 128), s1 = min(p.M, min((k + 1) * kChunk, s0 + 128));
+    // s0 stays 16-byte aligned and inside the frame's padded code slot even
+    // past the last bin; s1 bounds the symbols actually used
+    const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
     uint32_t bits = 0, nlo = 0, npq = 0;
-    for (uint32_t i = s0; i < s1; i += 4) {
-      const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(codes + i));
-      for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
-        const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, esc + i + t, p.R);
+    uint4 cv[8];
+    load_lane(s0, cv);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      for (uint32_t j = 0; j < 16; ++j) {
+        const uint32_t bin = s0 + 16 * q + j;
+        if (bin >= s1) break;
+        const uint32_t code = byte_code(byte_of(cv[q], j), esc + bin, p.R);
         bits += v.cb_len[code];
         nlo += code == 0;
       }
     }
-    for (uint32_t i = s0; i < s1; ++i) npq += pq_bit(i);
+    if (any_pq)
+      for (uint32_t i = s0; i < s1; ++i) npq += pq_bit(i);
     for (int d = 16; d > 0; d >>= 1) {
       bits += __shfl_xor_sync(0xffffffffu, bits, d);
       nlo += __shfl_xor_sync(0xffffffffu, nlo, d);
@@ -541,17 +579,24 @@ __device__ void finalize_frame(const DevParams& p, const Scratch& s, const Plain
     for (uint32_t w = lane; w < nw; w += 32) words[w0 + w] = 0;
     __threadfence_block();
     __syncwarp();
-    const uint32_t s0 = min(p.M, k * kChunk + lane * 128), s1 = min(p.M, min((k + 1) * kChunk, s0 + 128));
+    // s0 stays 16-byte aligned and inside the frame's padded code slot even
+    // past the last bin; s1 bounds the symbols actually used
+    const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
     uint32_t bits = 0, nlo = 0, npq = 0;
-    for (uint32_t i = s0; i < s1; i += 4) {
-      const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(codes + i));
-      for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
-        const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, esc + i + t, p.R);
+    uint4 cv[8];
+    load_lane(s0, cv);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      for (uint32_t j = 0; j < 16; ++j) {
+        const uint32_t bin = s0 + 16 * q + j;
+        if (bin >= s1) break;
+        const uint32_t code = byte_code(byte_of(cv[q], j), esc + bin, p.R);
         bits += v.cb_len[code];
         nlo += code == 0;
       }
     }
-    for (uint32_t i = s0; i < s1; ++i) npq += pq_bit(i);
+    if (any_pq)
+      for (uint32_t i = s0; i < s1; ++i) npq += pq_bit(i);
     const uint32_t bit_incl = warp_incl_scan(bits), lo_incl = warp_incl_scan(nlo), pq_incl = warp_incl_scan(npq);
     const uint32_t start = bit_incl - bits;
     uint32_t wi = w0 + start / 32;
@@ -559,11 +604,12 @@ __device__ void finalize_frame(const DevParams& p, const Scratch& s, const Plain
     uint32_t nacc = start & 31u;
     bool first = nacc != 0;  // the first word is shared with the previous lane
     uint32_t lo_pos = v.clo[k] + lo_incl - nlo, pq_pos = v.cpq[k] + pq_incl - npq;
-    for (uint32_t i = s0; i < s1; i += 4) {
-      const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(codes + i));
-      for (uint32_t t = 0; t < 4 && i + t < s1; ++t) {
-        const uint32_t bin = i + t;
-        const uint32_t code = byte_code((w >> (8 * t)) & 0xFFu, esc + bin, p.R);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      for (uint32_t j = 0; j < 16; ++j) {
+        const uint32_t bin = s0 + 16 * q + j;
+        if (bin >= s1) break;
+        const uint32_t code = byte_code(byte_of(cv[q], j), esc + bin, p.R);
         const uint32_t Lc = v.cb_len[code];
         accb |= (uint64_t)v.cb_code[code] << (64 - nacc - Lc);
         nacc += Lc;

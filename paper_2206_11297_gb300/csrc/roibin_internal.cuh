@@ -91,6 +91,7 @@ struct Scratch {
   uint32_t* hist_part;      // [n][P][kMaxSymbols] per-panel histograms
   uint32_t* peak_part;      // [n][P][max(max_peaks, 1)] per-panel sorted peaks
   uint32_t* peak_part_count;  // [n][P]
+  uint32_t* pq_part_count;    // [n][P] prequantisation outliers per panel
   uint32_t* frame_done;     // [n + 1] panels finished per frame; [n] = work counter
   uint32_t* work;           // set per launch
 };
@@ -151,6 +152,12 @@ struct Quant {
 // "within" and d > eb_hi proves "outside" (eb_lo, eb_hi = eb (1 -+ 2^-20));
 // only the rare d in [eb_lo, eb_hi] takes the exact fp64 test.  A non-finite b
 // gives a non-finite t, so the |t| < 2^28 test also rejects NaN and Inf.
+// The exact test, out of line so that its fp64 work is never hoisted out of
+// the rare branch that needs it (fp64 throughput is low on this GPU).
+static __device__ __noinline__ bool bound_exceeded_exact(float b, float bh, float eb) {
+  return fabs(__dadd_rn((double)b, -(double)bh)) > (double)eb;
+}
+
 __device__ __forceinline__ Quant prequantize(float b, const DevParams& p) {
   Quant r;
   const float t = rintf(__fmul_rn(b, p.recip));
@@ -159,7 +166,7 @@ __device__ __forceinline__ Quant prequantize(float b, const DevParams& p) {
     const float bh = __fmul_rn(t, p.two_eb);
     const float d = fabsf(__fsub_rn(b, bh));
     if (d > p.eb_hi) out = true;
-    else if (d >= p.eb_lo) out = fabs(__dadd_rn((double)b, -(double)bh)) > (double)p.eb;
+    else if (d >= p.eb_lo) out = bound_exceeded_exact(b, bh, p.eb);
   }
   r.outlier = out;
   r.q = out ? 0 : (int32_t)t;
@@ -221,14 +228,16 @@ __device__ inline bool is_candidate(const float* __restrict__ panel, int H, int 
   return true;
 }
 
-// ---- a2: candidate evaluation (§4.2), fp64 in a fixed order ---------------
+// ---- a2: candidate evaluation (§4.2), float32 in a fixed order ------------
 // `px(dr, dc)` returns the pixel at (r + dr, c + dc); it is only called for
 // in-panel positions.  The sums run in row-major order and round once per
 // operation, so the result does not depend on where the pixels come from.
+// The decision is taken in float32 (the data's precision); the sums are
+// chained in one lane so that the order is fixed.
 template <class Px>
 __device__ inline bool evaluate_peak_at(Px px, int H, int W, int r, int c, const DevParams& p) {
   const int r0 = p.ring_r0, outer = p.ring_r0 + p.ring_dr, reach = outer - 1;
-  double sum = 0.0;
+  float sum = 0.0f;
   int n = 0;
   for (int dr = -reach; dr <= reach; ++dr) {
     for (int dc = -reach; dc <= reach; ++dc) {
@@ -236,44 +245,44 @@ __device__ inline bool evaluate_peak_at(Px px, int H, int W, int r, int c, const
       if (d2 < r0 * r0 || d2 >= outer * outer) continue;
       const int rr = r + dr, cc = c + dc;
       if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
-      sum = __dadd_rn(sum, (double)px(dr, dc));
+      sum = __fadd_rn(sum, px(dr, dc));
       ++n;
     }
   }
-  double bkg = 0.0, var = 0.0;
+  float bkg = 0.0f, var = 0.0f;
   if (n > 0) {
-    bkg = __ddiv_rn(sum, (double)n);
-    double ss = 0.0;
+    bkg = __fdiv_rn(sum, (float)n);
+    float ss = 0.0f;
     for (int dr = -reach; dr <= reach; ++dr) {
       for (int dc = -reach; dc <= reach; ++dc) {
         const int d2 = dr * dr + dc * dc;
         if (d2 < r0 * r0 || d2 >= outer * outer) continue;
         const int rr = r + dr, cc = c + dc;
         if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
-        const double d = __dadd_rn((double)px(dr, dc), -bkg);
-        ss = __dadd_rn(ss, __dmul_rn(d, d));
+        const float d = __fsub_rn(px(dr, dc), bkg);
+        ss = __fadd_rn(ss, __fmul_rn(d, d));
       }
     }
-    var = __ddiv_rn(ss, (double)n);
+    var = __fdiv_rn(ss, (float)n);
   }
-  const double sigma = __dsqrt_rn(var);
-  const double thr = __dmul_rn((double)p.pix_nsigma, sigma);
+  const float sigma = __fsqrt_rn(var);
+  const float thr = __fmul_rn(p.pix_nsigma, sigma);
   int npix = 0;
-  double atot = 0.0;
+  float atot = 0.0f;
   for (int dr = -p.rank; dr <= p.rank; ++dr) {
     for (int dc = -p.rank; dc <= p.rank; ++dc) {
       const int rr = r + dr, cc = c + dc;
       if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
-      const double d = __dadd_rn((double)px(dr, dc), -bkg);
+      const float d = __fsub_rn(px(dr, dc), bkg);
       if (d > thr) {
         ++npix;
-        atot = __dadd_rn(atot, d);
+        atot = __fadd_rn(atot, d);
       }
     }
   }
   if (npix < p.npix_min || npix > p.npix_max) return false;
-  if (!(atot > (double)p.atot_thr)) return false;
-  const double noise = __dmul_rn(__dmul_rn((double)p.son_min, sigma), __dsqrt_rn((double)npix));
+  if (!(atot > p.atot_thr)) return false;
+  const float noise = __fmul_rn(__fmul_rn(p.son_min, sigma), __fsqrt_rn((float)npix));
   return atot > noise;
 }
 

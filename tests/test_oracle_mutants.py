@@ -25,11 +25,11 @@ MUTANTS = {
     # a2 evaluation
     "ring_inner_inclusive": ("if (d2 < r0 * r0 || d2 >= outer * outer) continue;\n      const long rr = (long)r + dr, cc = (long)c + dc;\n      if (!in_panel(rr, cc, rows, cols)) continue;\n      sum +=",
                              "if (d2 <= r0 * r0 || d2 >= outer * outer) continue;\n      const long rr = (long)r + dr, cc = (long)c + dc;\n      if (!in_panel(rr, cc, rows, cols)) continue;\n      sum +="),
-    "sample_variance": ("var = ss / (double)n;", "var = n > 1 ? ss / (double)(n - 1) : 0.0;"),
-    "snr_without_sqrt": ("sigma * sqrt((double)npix)", "sigma * (double)npix"),
-    "atot_not_strict": ("if (!(atot > (double)p->atot_thr)) return 0;", "if (!(atot >= (double)p->atot_thr)) return 0;"),
+    "sample_variance": ("var = ss / (float)n;", "var = n > 1 ? ss / (float)(n - 1) : 0.0f;"),
+    "snr_without_sqrt": ("sigma * sqrtf((float)npix)", "sigma * (float)npix"),
+    "atot_not_strict": ("if (!(atot > p->atot_thr)) return 0;", "if (!(atot >= p->atot_thr)) return 0;"),
     "npix_max_off_by_one": ("npix > p->npix_max", "npix >= p->npix_max"),
-    "threshold_ignores_sigma": ("const double thr = (double)p->pix_nsigma * sigma;", "const double thr = (double)p->pix_nsigma;"),
+    "threshold_ignores_sigma": ("const float thr = p->pix_nsigma * sigma;", "const float thr = p->pix_nsigma;"),
     # a3 ROI
     "roi_off_centre": ("const long r0 = (long)peaks[3 * k + 1] - p->roi_h / 2;\n    const long c0 = (long)peaks[3 * k + 2] - p->roi_w / 2;\n    for (long i = 0; i < p->roi_h; ++i) {",
                        "const long r0 = (long)peaks[3 * k + 1] - p->roi_h / 2 + 1;\n    const long c0 = (long)peaks[3 * k + 2] - p->roi_w / 2;\n    for (long i = 0; i < p->roi_h; ++i) {"),
