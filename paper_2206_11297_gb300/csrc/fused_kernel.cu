@@ -13,11 +13,10 @@
 //     slots with plain stores (no zeroing, no cross-CTA atomics);
 //   - tests and evaluates the panel's candidates right away, while its rows
 //     are still in L2, and stores its sorted peak list.
-// The CTA that completes a frame's last panel finalises the frame (the "last
-// block" pattern): histogram sum, Huffman codebook, chunk sizes, scan,
-// header, bit-packing, outliers and ROI windows.  Meanwhile the other CTAs
-// keep streaming, so the latency-bound finalisation overlaps the HBM-bound
-// streaming.  After use, the frame's code bytes are dropped from L2 without a
+// The rest of a frame's work (codebook, chunk sizes, layout, bit-packing)
+// runs as later work items of the same kernel (see the stages below), so the
+// latency-bound coding of earlier frames overlaps the HBM-bound streaming of
+// later ones.  After use, a frame's code bytes are dropped from L2 without a
 // write-back.
 #include <cuda_runtime.h>
 
@@ -62,7 +61,8 @@ __device__ __forceinline__ uint32_t byte_code(uint32_t b, const uint16_t* esc_bi
 }
 
 // Writes the header, the peaks, the code lengths, the chunk index and every
-// padding byte of a frame (block-cooperative).  keys: pixel index per peak.
+// padding byte of a frame (block-cooperative).  keys (pixel index per peak)
+// and cb_len are global arrays written by other CTAs: read through L2.
 __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePlan& pl, const uint32_t* keys,
                                  const uint8_t* cb_len, const uint32_t* chunk_word_off) {
   if (threadIdx.x == 0) {
@@ -92,7 +92,7 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
   const uint32_t plane = p.H * p.W;
   uint16_t* pk = reinterpret_cast<uint16_t*>(out + pl.off_peaks);
   for (uint32_t k = threadIdx.x; k < pl.n_peaks; k += blockDim.x) {
-    const uint32_t px = keys[k];
+    const uint32_t px = __ldcg(keys + k);
     const uint32_t pn = px / plane, rem = px - pn * plane;
     pk[3 * k] = (uint16_t)pn;
     pk[3 * k + 1] = (uint16_t)(rem / p.W);
@@ -103,7 +103,7 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
   };
   zero(pl.off_peaks + (uint64_t)pl.n_peaks * 6, pl.off_roi);
   zero(pl.off_roi + (uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4, pl.off_len);
-  for (uint32_t k = threadIdx.x; k < p.nsym; k += blockDim.x) out[pl.off_len + k] = cb_len[k];
+  for (uint32_t k = threadIdx.x; k < p.nsym; k += blockDim.x) out[pl.off_len + k] = __ldcg(cb_len + k);
   zero(pl.off_len + p.nsym, pl.off_cidx);
   uint32_t* ci = reinterpret_cast<uint32_t*>(out + pl.off_cidx);
   for (uint32_t k = threadIdx.x; k < p.n_chunks; k += blockDim.x) ci[k] = chunk_word_off[k];
@@ -147,6 +147,7 @@ enum {
   CTL_CARRY1,
   CTL_CARRY2,
   CTL_PQ,
+  CTL_WAIT,
   CTL_TMP,
   CTL_OFFS = CTL_TMP + 33,  // per-panel peak offsets (first 1024 panels)
   CTL_WORDS = CTL_OFFS + 1024
@@ -382,41 +383,84 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
 }
 
 // ---------------------------------------------------------------------------
-// Finalises frame f (one CTA).  Everything other CTAs wrote is read through
-// L2 only (ld.global.cg).
-__device__ void finalize_frame(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
-                               const FinView& v, uint32_t f) {
+// After its panels, a frame moves through three more stages:
+//   (1) the CTA that completes the frame's last panel gathers the peak list
+//       and builds the codebook;
+//   (2) chunk-size items count the bits and outliers of groups of chunks;
+//       the last one scans, lays the frame out and writes its head;
+//   (3) chunk-write items pack the bits, write the outliers and the ROI
+//       windows, and drop their code bytes from L2.
+// One atomic ticket counter orders all work: round r holds the panels of
+// frame r, the size items of frame r - lag and the write items of frame
+// r - 2 lag.  Stages hand over through release/acquire flags.  A CTA only
+// ever waits for work handed out to an earlier ticket, which is running or
+// done, so every wait ends; waits are bounded anyway (ROIBIN_ERR_TIMEOUT).
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+struct SyncWords {
+  uint32_t *panel_done, *size_done, *ready_cb, *ready_plan, *ticket;
+};
+__device__ __forceinline__ SyncWords sync_words(const Scratch& s, uint32_t n) {
+  SyncWords w;
+  w.panel_done = s.frame_done;
+  w.size_done = s.frame_done + n;
+  w.ready_cb = s.frame_done + 2 * n;
+  w.ready_plan = s.frame_done + 3 * n;
+  w.ticket = s.frame_done + 4 * n;
+  return w;
+}
+
+__device__ __forceinline__ void flag_release(uint32_t* f) {
+  __threadfence();
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(1u) : "memory");
+}
+__device__ __forceinline__ uint32_t flag_acquire(const uint32_t* f) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+  return v;
+}
+// Thread 0 waits (bounded) for a flag; every thread gets the outcome.
+__device__ bool wait_flag(const uint32_t* f, uint32_t* slot) {
+  if (threadIdx.x == 0) {
+    uint32_t ok = 0;
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+      if (flag_acquire(f)) {
+        ok = 1;
+        break;
+      }
+      __nanosleep(128);
+    }
+    *slot = ok;
+  }
+  __syncthreads();
+  const bool ok = *slot != 0;
+  __syncthreads();
+  return ok;
+}
+
+// (1) peak list + codebook of frame f, by the CTA that completed its last panel.
+__device__ void frame_codebook(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                               const FinView& v, uint32_t f, const SyncWords& sw) {
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint64_t* trace = (a.trace && f < a.trace_frames && tid == 0) ? a.trace + (size_t)f * kTracePoints : nullptr;
   if (trace) trace[0] = global_ns();
-  const uint32_t Mp = p.Hb * p.Wb;
-  const uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride;
-  const uint16_t* esc = s.codes + (size_t)f * p.M;
-  const int32_t* lo_delta = s.lo_delta + (size_t)f * p.M;
-  const uint32_t* pq_bits = s.pq_bits + (size_t)f * p.M;
-  const uint32_t* pq_mask = s.pq_mask + (size_t)f * p.P * sh.mask_words;
-  uint8_t* out = a.out + (size_t)f * a.out_stride;
-  const float* frame = a.frames + (size_t)f * p.frame_px;
-
-  // prequantisation outliers in the frame (their bits are only read when some exist)
-  if (tid == 0) {
-    uint32_t t = 0;
-    for (uint32_t pn = 0; pn < p.P; ++pn) t += __ldcg(s.pq_part_count + (size_t)f * p.P + pn);
-    v.ctl[CTL_PQ] = t;
-  }
-  // a8: the frame's histogram
+  // a8: the frame's histogram; prequantisation outliers in the frame
   for (uint32_t k = tid; k < p.nsym; k += kPT) {
     uint32_t t = 0;
     for (uint32_t pn = 0; pn < p.P; ++pn) t += __ldcg(s.hist_part + ((size_t)f * p.P + pn) * kMaxSymbols + k);
     v.total[k] = t;
   }
-  // the frame's peaks: the per-panel sorted lists, concatenated in panel order
   if (tid == 0) {
+    uint32_t t = 0;
+    for (uint32_t pn = 0; pn < p.P; ++pn) t += __ldcg(s.pq_part_count + (size_t)f * p.P + pn);
+    s.plan[f].n_pq = t;  // provisional: read by the size items to skip the outlier bits
     v.ctl[CTL_STATUS] = ROIBIN_OK;
     v.ctl[CTL_BAD] = 0;
     v.ctl[CTL_CARRY0] = 0;
   }
   __syncthreads();
+  // the peak list: per-panel sorted lists concatenated in panel order, or the user's
+  uint32_t* keys = a.peaks_key_out + (size_t)f * p.max_peaks;
   if (a.user_peaks) {
     const uint32_t n = a.user_npeaks[f];
     if (tid == 0) v.ctl[CTL_CARRY0] = n;
@@ -427,7 +471,7 @@ __device__ void finalize_frame(const DevParams& p, const Scratch& s, const Plain
       for (uint32_t k = tid; k < n; k += kPT) {
         const uint32_t pn = up[3 * k], r = up[3 * k + 1], c = up[3 * k + 2];
         if (pn >= p.P || r >= p.H || c >= p.W) v.ctl[CTL_BAD] = 1;
-        else v.keys[k] = (pn * p.H + r) * p.W + c;
+        else keys[k] = (pn * p.H + r) * p.W + c;
       }
     }
   } else {
@@ -454,164 +498,269 @@ __device__ void finalize_frame(const DevParams& p, const Scratch& s, const Plain
           for (uint32_t q = 0; q < pn; ++q) off += __ldcg(s.peak_part_count + (size_t)f * p.P + q);
         }
         for (uint32_t k = lane; k < c; k += 32)
-          v.keys[off + k] = __ldcg(s.peak_part + ((size_t)f * p.P + pn) * sh.peak_cap + k);
+          keys[off + k] = __ldcg(s.peak_part + ((size_t)f * p.P + pn) * sh.peak_cap + k);
       }
     }
   }
   __syncthreads();
-  const uint32_t n_pk = v.ctl[CTL_CARRY0];
-  if (tid == 0 && v.ctl[CTL_BAD] && v.ctl[CTL_STATUS] == ROIBIN_OK) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_INVALID_ARG;
-  if (tid == 0) a.peaks_count_out[f] = n_pk;
-  __syncthreads();
-  if (v.ctl[CTL_STATUS] == ROIBIN_OK)
-    for (uint32_t k = tid; k < n_pk; k += kPT) a.peaks_key_out[(size_t)f * p.max_peaks + k] = v.keys[k];
+  if (tid == 0) {
+    if (v.ctl[CTL_BAD] && v.ctl[CTL_STATUS] == ROIBIN_OK) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_INVALID_ARG;
+    a.peaks_count_out[f] = v.ctl[CTL_CARRY0];
+  }
   if (trace) trace[1] = global_ns();
-  // a9: codebook
+  // a9: the codebook, published in the frame's global tables
   const int cb = build_codebook(v.total, p.nsym, *v.hs, v.cb_len, v.cb_code);
-  if (tid == 0 && cb != ROIBIN_OK && v.ctl[CTL_STATUS] == ROIBIN_OK) v.ctl[CTL_STATUS] = (uint32_t)cb;
+  for (uint32_t k = tid; k < p.nsym; k += kPT) {
+    s.cb_len[(size_t)f * kMaxSymbols + k] = v.cb_len[k];
+    s.cb_code[(size_t)f * kMaxSymbols + k] = v.cb_code[k];
+  }
+  if (tid == 0) {
+    int32_t st = (int32_t)v.ctl[CTL_STATUS];
+    if (st == ROIBIN_OK && cb != ROIBIN_OK) st = cb;
+    s.status[f] = st;
+  }
   __syncthreads();
   if (trace) trace[2] = global_ns();
-  const int32_t status0 = (int32_t)v.ctl[CTL_STATUS];
-  if (status0 != ROIBIN_OK) {
-    if (tid == 0) {
-      a.frame_bytes[f] = 0;
-      a.frame_status[f] = status0;
-    }
-    return;
-  }
-  auto pq_bit = [&](uint32_t bin) -> uint32_t {
-    const uint32_t pn = bin / Mp, lb = bin - pn * Mp;
-    return (__ldcg(pq_mask + (size_t)pn * sh.mask_words + (lb >> 5)) >> (lb & 31)) & 1u;
-  };
-  const bool any_pq = v.ctl[CTL_PQ] != 0;
-  // a lane's 128 consecutive code bytes, loaded at once
-  auto load_lane = [&](uint32_t s0, uint4 (&cv)[8]) {
-    const uint4* src = reinterpret_cast<const uint4*>(codes + s0);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) cv[q] = __ldcg(src + q);
-  };
-  auto byte_of = [](const uint4& u, uint32_t j) -> uint32_t {  // j < 16
-    const uint32_t w = (j >> 2) == 0 ? u.x : (j >> 2) == 1 ? u.y : (j >> 2) == 2 ? u.z : u.w;
-    return (w >> (8 * (j & 3))) & 0xFFu;
-  };
-  // a10/a11 sizes per chunk: one warp per chunk, 128 consecutive symbols per lane
-  for (uint32_t k = warp; k < p.n_chunks; k += kPW) {
-    // s0 stays 16-byte aligned and inside the frame's padded code slot even
-    // past the last bin; s1 bounds the symbols actually used
-    const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
-    uint32_t bits = 0, nlo = 0, npq = 0;
-    uint4 cv[8];
-    load_lane(s0, cv);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      for (uint32_t j = 0; j < 16; ++j) {
-        const uint32_t bin = s0 + 16 * q + j;
-        if (bin >= s1) break;
-        const uint32_t code = byte_code(byte_of(cv[q], j), esc + bin, p.R);
-        bits += v.cb_len[code];
-        nlo += code == 0;
+  if (tid == 0) flag_release(sw.ready_cb + f);
+}
+
+// Per-byte table of a frame's codebook: entry = codeword << 32 | length;
+// length 0 marks an escape byte (its code sits in the side array).
+__device__ void load_byte_table(const DevParams& p, const Scratch& s, uint32_t f, uint64_t* btab) {
+  for (uint32_t b = threadIdx.x; b < 256; b += kPT) {
+    uint64_t e = 0;
+    if (b != 255) {
+      const int32_t code = b == 0 ? 0 : (int32_t)b - 128 + p.R;
+      if (code >= 0 && code < (int32_t)p.nsym) {
+        const uint32_t L = __ldcg(s.cb_len + (size_t)f * kMaxSymbols + code);
+        const uint32_t cw = __ldcg(s.cb_code + (size_t)f * kMaxSymbols + code);
+        e = ((uint64_t)cw << 32) | L;
       }
     }
-    if (any_pq)
-      for (uint32_t i = s0; i < s1; ++i) npq += pq_bit(i);
-    for (int d = 16; d > 0; d >>= 1) {
-      bits += __shfl_xor_sync(0xffffffffu, bits, d);
-      nlo += __shfl_xor_sync(0xffffffffu, nlo, d);
-      npq += __shfl_xor_sync(0xffffffffu, npq, d);
-    }
-    if (lane == 0) {
-      v.cw[k] = (bits + 31) / 32;
-      v.clo[k] = nlo;
-      v.cpq[k] = npq;
+    btab[b] = e;
+  }
+}
+
+// (len, codeword) of the symbol stored as byte b at bin `bin` of frame f.
+__device__ __forceinline__ uint64_t symbol_entry(const DevParams& p, const Scratch& s, uint32_t f, const uint64_t* btab,
+                                                 uint32_t b, uint32_t bin) {
+  uint64_t e = btab[b];
+  if (b == 255) {  // escape: the code sits in the side array
+    const uint32_t code = __ldcg(s.codes + (size_t)f * p.M + bin);
+    e = ((uint64_t)__ldcg(s.cb_code + (size_t)f * kMaxSymbols + code) << 32) |
+        __ldcg(s.cb_len + (size_t)f * kMaxSymbols + code);
+  }
+  return e;
+}
+
+__device__ __forceinline__ uint32_t pq_bit_of(const DevParams& p, const Scratch& s, const FusedShape& sh, uint32_t f,
+                                              uint32_t bin) {
+  const uint32_t Mp = p.Hb * p.Wb;
+  const uint32_t pn = bin / Mp, lb = bin - pn * Mp;
+  return (__ldcg(s.pq_mask + ((size_t)f * p.P + pn) * sh.mask_words + (lb >> 5)) >> (lb & 31)) & 1u;
+}
+
+__device__ __forceinline__ uint32_t byte_of(const uint4& u, uint32_t j) {  // j < 16
+  const uint32_t w = (j >> 2) == 0 ? u.x : (j >> 2) == 1 ? u.y : (j >> 2) == 2 ? u.z : u.w;
+  return (w >> (8 * (j & 3))) & 0xFFu;
+}
+
+// Bits, Lorenzo outliers and prequantisation outliers of lane's 128 symbols.
+__device__ __forceinline__ void lane_counts(const DevParams& p, const Scratch& s, const FusedShape& sh, uint32_t f,
+                                            const uint64_t* btab, const uint4 (&cv)[8], uint32_t s0, uint32_t s1,
+                                            bool any_pq, uint32_t& bits, uint32_t& nlo, uint32_t& npq) {
+  bits = nlo = npq = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    for (uint32_t j = 0; j < 16; ++j) {
+      const uint32_t bin = s0 + 16 * q + j;
+      if (bin >= s1) break;
+      const uint32_t b = byte_of(cv[q], j);
+      bits += (uint32_t)symbol_entry(p, s, f, btab, b, bin);
+      nlo += b == 0;
     }
   }
-  if (tid < 3) v.ctl[CTL_CARRY0 + tid] = 0;
+  if (any_pq)
+    for (uint32_t i = s0; i < s1; ++i) npq += pq_bit_of(p, s, sh, f, i);
+}
+
+// (2) chunk sizes of one group of chunks of frame g.
+__device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                          unsigned char* sm, uint32_t g, uint32_t grp, const SyncWords& sw) {
+  const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
+  uint64_t* btab = reinterpret_cast<uint64_t*>(sm + sh.off_huff);
+  const bool ready = wait_flag(sw.ready_cb + g, ctl + CTL_WAIT);
+  if (!ready && tid == 0) atomicExch(reinterpret_cast<unsigned int*>(s.status + g), (unsigned int)ROIBIN_ERR_TIMEOUT);
+  const bool ok = ready && __ldcg(s.status + g) == ROIBIN_OK;
+  if (ok) {
+    load_byte_table(p, s, g, btab);
+    __syncthreads();
+    const bool any_pq = __ldcg(&s.plan[g].n_pq) != 0;
+    const uint8_t* codes = s.codes8 + (size_t)g * sh.codes_stride;
+    const uint32_t k_end = min(p.n_chunks, (grp + 1) * sh.group_chunks);
+    for (uint32_t k = grp * sh.group_chunks + warp; k < k_end; k += kPW) {
+      const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
+      uint4 cv[8];
+      const uint4* src = reinterpret_cast<const uint4*>(codes + s0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) cv[q] = __ldcg(src + q);
+      uint32_t bits, nlo, npq;
+      lane_counts(p, s, sh, g, btab, cv, s0, s1, any_pq, bits, nlo, npq);
+      for (int d = 16; d > 0; d >>= 1) {
+        bits += __shfl_xor_sync(0xffffffffu, bits, d);
+        nlo += __shfl_xor_sync(0xffffffffu, nlo, d);
+        npq += __shfl_xor_sync(0xffffffffu, npq, d);
+      }
+      if (lane == 0) {
+        const size_t o = (size_t)g * p.n_chunks + k;
+        s.chunk_words[o] = (bits + 31) / 32;
+        s.chunk_lo[o] = nlo;
+        s.chunk_pq[o] = npq;
+      }
+    }
+  }
+  __threadfence();
   __syncthreads();
+  if (tid == 0) ctl[CTL_LAST] = atomicAdd(sw.size_done + g, 1u) == sh.groups - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!ctl[CTL_LAST]) return;
+  __threadfence();
+  // the frame's plan: scan the chunks, lay the frame out, write its head
+  uint64_t* trace = (a.trace && g < a.trace_frames && tid == 0) ? a.trace + (size_t)g * kTracePoints : nullptr;
   if (trace) trace[3] = global_ns();
-  for (uint32_t k0 = 0; k0 < p.n_chunks; k0 += kPT) {
-    const uint32_t k = k0 + tid;
-    const uint32_t w = k < p.n_chunks ? v.cw[k] : 0u, l = k < p.n_chunks ? v.clo[k] : 0u,
-                   q = k < p.n_chunks ? v.cpq[k] : 0u;
-    uint32_t tw, tl, tq;
-    const uint32_t ew = block_excl_scan(w, v.ctl + CTL_TMP, &tw);
-    const uint32_t el = block_excl_scan(l, v.ctl + CTL_TMP, &tl);
-    const uint32_t eq = block_excl_scan(q, v.ctl + CTL_TMP, &tq);
-    if (k < p.n_chunks) {
-      v.cw[k] = v.ctl[CTL_CARRY0] + ew;
-      v.clo[k] = v.ctl[CTL_CARRY1] + el;
-      v.cpq[k] = v.ctl[CTL_CARRY2] + eq;
+  int32_t st = __ldcg(s.status + g);
+  uint32_t* cw = reinterpret_cast<uint32_t*>(sm + sh.off_cw);
+  uint32_t* clo = cw + p.n_chunks;
+  uint32_t* cpq = clo + p.n_chunks;
+  FramePlan pl{};
+  if (st == ROIBIN_OK) {
+    if (tid < 3) ctl[CTL_CARRY0 + tid] = 0;
+    for (uint32_t k = tid; k < p.n_chunks; k += kPT) {
+      const size_t o = (size_t)g * p.n_chunks + k;
+      cw[k] = __ldcg(s.chunk_words + o);
+      clo[k] = __ldcg(s.chunk_lo + o);
+      cpq[k] = __ldcg(s.chunk_pq + o);
     }
     __syncthreads();
-    if (tid == 0) {
-      v.ctl[CTL_CARRY0] += tw;
-      v.ctl[CTL_CARRY1] += tl;
-      v.ctl[CTL_CARRY2] += tq;
+    for (uint32_t k0 = 0; k0 < p.n_chunks; k0 += kPT) {
+      const uint32_t k = k0 + tid;
+      const uint32_t w = k < p.n_chunks ? cw[k] : 0u, l = k < p.n_chunks ? clo[k] : 0u,
+                     q = k < p.n_chunks ? cpq[k] : 0u;
+      uint32_t tw, tl, tq;
+      const uint32_t ew = block_excl_scan(w, ctl + CTL_TMP, &tw);
+      const uint32_t el = block_excl_scan(l, ctl + CTL_TMP, &tl);
+      const uint32_t eq = block_excl_scan(q, ctl + CTL_TMP, &tq);
+      if (k < p.n_chunks) {
+        cw[k] = ctl[CTL_CARRY0] + ew;
+        clo[k] = ctl[CTL_CARRY1] + el;
+        cpq[k] = ctl[CTL_CARRY2] + eq;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        ctl[CTL_CARRY0] += tw;
+        ctl[CTL_CARRY1] += tl;
+        ctl[CTL_CARRY2] += tq;
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    pl.n_peaks = __ldcg(a.peaks_count_out + g);
+    pl.n_words = ctl[CTL_CARRY0];
+    pl.n_lo = ctl[CTL_CARRY1];
+    pl.n_pq = ctl[CTL_CARRY2];
+    pl.off_peaks = kHeaderBytes;
+    pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
+    pl.off_len = pl.off_roi + align16((uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4);
+    pl.off_cidx = pl.off_len + align16(p.nsym);
+    pl.off_lo = pl.off_cidx + align16((uint64_t)p.n_chunks * 4);
+    pl.off_pq = pl.off_lo + align16((uint64_t)pl.n_lo * 8);
+    pl.off_bits = pl.off_pq + align16((uint64_t)pl.n_pq * 8);
+    pl.total = pl.off_bits + align16((uint64_t)pl.n_words * 4);
+    if (pl.total > a.out_stride) st = ROIBIN_ERR_CAPACITY;
   }
-  FramePlan pl;
-  pl.n_peaks = n_pk;
-  pl.n_words = v.ctl[CTL_CARRY0];
-  pl.n_lo = v.ctl[CTL_CARRY1];
-  pl.n_pq = v.ctl[CTL_CARRY2];
-  pl.off_peaks = kHeaderBytes;
-  pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
-  pl.off_len = pl.off_roi + align16((uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4);
-  pl.off_cidx = pl.off_len + align16(p.nsym);
-  pl.off_lo = pl.off_cidx + align16((uint64_t)p.n_chunks * 4);
-  pl.off_pq = pl.off_lo + align16((uint64_t)pl.n_lo * 8);
-  pl.off_bits = pl.off_pq + align16((uint64_t)pl.n_pq * 8);
-  pl.total = pl.off_bits + align16((uint64_t)pl.n_words * 4);
-  const bool fits = pl.total <= a.out_stride;
   if (tid == 0) {
-    a.frame_bytes[f] = pl.total;
-    a.frame_status[f] = fits ? ROIBIN_OK : ROIBIN_ERR_CAPACITY;
+    a.frame_bytes[g] = (st == ROIBIN_OK || st == ROIBIN_ERR_CAPACITY) ? pl.total : 0;
+    a.frame_status[g] = st;
+    s.status[g] = st;
   }
-  if (!fits) return;
-  write_frame_head(out, p, pl, v.keys, v.cb_len, v.cw);
+  if (st == ROIBIN_OK) {
+    for (uint32_t k = tid; k < p.n_chunks; k += kPT) {  // offsets for the write items
+      const size_t o = (size_t)g * p.n_chunks + k;
+      s.chunk_words[o] = cw[k];
+      s.chunk_lo[o] = clo[k];
+      s.chunk_pq[o] = cpq[k];
+    }
+    if (tid == 0) s.plan[g] = pl;
+    write_frame_head(a.out + (size_t)g * a.out_stride, p, pl, a.peaks_key_out + (size_t)g * p.max_peaks,
+                     s.cb_len + (size_t)g * kMaxSymbols, cw);
+  }
+  __syncthreads();
   if (trace) trace[4] = global_ns();
-  // a10 + a11: bit-packing and outliers, one warp per chunk
+  if (tid == 0) flag_release(sw.ready_plan + g);
+}
+
+// (3) bits, outliers and ROI windows of one group of chunks of frame g.
+__device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                           unsigned char* sm, uint32_t g, uint32_t grp, const SyncWords& sw) {
+  const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
+  uint64_t* btab = reinterpret_cast<uint64_t*>(sm + sh.off_huff);
+  const bool ready = wait_flag(sw.ready_plan + g, ctl + CTL_WAIT);
+  if (!ready) {
+    if (tid == 0) atomicExch(reinterpret_cast<unsigned int*>(a.frame_status + g), (unsigned int)ROIBIN_ERR_TIMEOUT);
+    return;
+  }
+  if (__ldcg(s.status + g) != ROIBIN_OK) return;
+  load_byte_table(p, s, g, btab);
+  FramePlan pl;
+  pl.n_peaks = __ldcg(&s.plan[g].n_peaks);
+  pl.n_pq = __ldcg(&s.plan[g].n_pq);
+  pl.n_words = __ldcg(&s.plan[g].n_words);
+  pl.off_roi = __ldcg(reinterpret_cast<const unsigned long long*>(&s.plan[g].off_roi));
+  pl.off_lo = __ldcg(reinterpret_cast<const unsigned long long*>(&s.plan[g].off_lo));
+  pl.off_pq = __ldcg(reinterpret_cast<const unsigned long long*>(&s.plan[g].off_pq));
+  pl.off_bits = __ldcg(reinterpret_cast<const unsigned long long*>(&s.plan[g].off_bits));
+  __syncthreads();
+  uint8_t* out = a.out + (size_t)g * a.out_stride;
   uint32_t* words = reinterpret_cast<uint32_t*>(out + pl.off_bits);
   uint2* lo_out = reinterpret_cast<uint2*>(out + pl.off_lo);
   uint2* pq_out = reinterpret_cast<uint2*>(out + pl.off_pq);
-  for (uint32_t k = warp; k < p.n_chunks; k += kPW) {
-    const uint32_t w0 = v.cw[k], nw = (k + 1 < p.n_chunks ? v.cw[k + 1] : pl.n_words) - w0;
-    for (uint32_t w = lane; w < nw; w += 32) words[w0 + w] = 0;
+  const bool any_pq = pl.n_pq != 0;
+  const uint8_t* codes = s.codes8 + (size_t)g * sh.codes_stride;
+  const int32_t* lo_delta = s.lo_delta + (size_t)g * p.M;
+  const uint32_t* pq_bits = s.pq_bits + (size_t)g * p.M;
+  const uint32_t k_begin = grp * sh.group_chunks, k_end = min(p.n_chunks, (grp + 1) * sh.group_chunks);
+  for (uint32_t k = k_begin + warp; k < k_end; k += kPW) {
+    const size_t o = (size_t)g * p.n_chunks + k;
+    const uint32_t w0 = __ldcg(s.chunk_words + o);
+    const uint32_t w1 = k + 1 < p.n_chunks ? __ldcg(s.chunk_words + o + 1) : pl.n_words;
+    for (uint32_t w = w0 + lane; w < w1; w += 32) words[w] = 0;
     __threadfence_block();
     __syncwarp();
-    // s0 stays 16-byte aligned and inside the frame's padded code slot even
-    // past the last bin; s1 bounds the symbols actually used
     const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
-    uint32_t bits = 0, nlo = 0, npq = 0;
     uint4 cv[8];
-    load_lane(s0, cv);
+    const uint4* src = reinterpret_cast<const uint4*>(codes + s0);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      for (uint32_t j = 0; j < 16; ++j) {
-        const uint32_t bin = s0 + 16 * q + j;
-        if (bin >= s1) break;
-        const uint32_t code = byte_code(byte_of(cv[q], j), esc + bin, p.R);
-        bits += v.cb_len[code];
-        nlo += code == 0;
-      }
-    }
-    if (any_pq)
-      for (uint32_t i = s0; i < s1; ++i) npq += pq_bit(i);
+    for (int q = 0; q < 8; ++q) cv[q] = __ldcg(src + q);
+    uint32_t bits, nlo, npq;
+    lane_counts(p, s, sh, g, btab, cv, s0, s1, any_pq, bits, nlo, npq);
     const uint32_t bit_incl = warp_incl_scan(bits), lo_incl = warp_incl_scan(nlo), pq_incl = warp_incl_scan(npq);
     const uint32_t start = bit_incl - bits;
     uint32_t wi = w0 + start / 32;
     uint64_t accb = 0;
     uint32_t nacc = start & 31u;
     bool first = nacc != 0;  // the first word is shared with the previous lane
-    uint32_t lo_pos = v.clo[k] + lo_incl - nlo, pq_pos = v.cpq[k] + pq_incl - npq;
+    uint32_t lo_pos = __ldcg(s.chunk_lo + o) + lo_incl - nlo;
+    uint32_t pq_pos = __ldcg(s.chunk_pq + o) + pq_incl - npq;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       for (uint32_t j = 0; j < 16; ++j) {
         const uint32_t bin = s0 + 16 * q + j;
         if (bin >= s1) break;
-        const uint32_t code = byte_code(byte_of(cv[q], j), esc + bin, p.R);
-        const uint32_t Lc = v.cb_len[code];
-        accb |= (uint64_t)v.cb_code[code] << (64 - nacc - Lc);
+        const uint32_t b = byte_of(cv[q], j);
+        const uint64_t e = symbol_entry(p, s, g, btab, b, bin);
+        const uint32_t Lc = (uint32_t)e;
+        accb |= (e >> 32) << (64 - nacc - Lc);
         nacc += Lc;
         if (nacc >= 32) {
           const uint32_t word = (uint32_t)(accb >> 32);
@@ -622,20 +771,21 @@ __device__ void finalize_frame(const DevParams& p, const Scratch& s, const Plain
           accb <<= 32;
           nacc -= 32;
         }
-        if (code == 0) lo_out[lo_pos++] = make_uint2(bin, (uint32_t)__ldcg(lo_delta + bin));
+        if (b == 0) lo_out[lo_pos++] = make_uint2(bin, (uint32_t)__ldcg(lo_delta + bin));
       }
     }
     if (nacc > 0) atomicOr(words + wi, (uint32_t)(accb >> 32));  // shared with the next lane
     if (npq)
       for (uint32_t i = s0; i < s1; ++i)
-        if (pq_bit(i)) pq_out[pq_pos++] = make_uint2(i, __ldcg(pq_bits + i));
+        if (pq_bit_of(p, s, sh, g, i)) pq_out[pq_pos++] = make_uint2(i, __ldcg(pq_bits + i));
   }
-  if (trace) trace[5] = global_ns();
-  // a3: ROI windows (one warp per peak)
+  // a3: ROI windows of peaks k = grp, grp + groups, ... (one warp per peak)
   float* roi = reinterpret_cast<float*>(out + pl.off_roi);
   const uint32_t win = (uint32_t)(p.roi_h * p.roi_w), plane = p.H * p.W;
-  for (uint32_t k = warp; k < n_pk; k += kPW) {
-    const uint32_t px = v.keys[k];
+  const float* frame = a.frames + (size_t)g * p.frame_px;
+  const uint32_t* keys = a.peaks_key_out + (size_t)g * p.max_peaks;
+  for (uint32_t k = grp + sh.groups * warp; k < pl.n_peaks; k += sh.groups * kPW) {
+    const uint32_t px = __ldcg(keys + k);
     const uint32_t pn = px / plane, rem = px - pn * plane;
     const int r = (int)(rem / p.W), c = (int)(rem % p.W);
     const float* panel = frame + (size_t)pn * plane;
@@ -646,11 +796,10 @@ __device__ void finalize_frame(const DevParams& p, const Scratch& s, const Plain
       roi[(size_t)k * win + e] = in ? __ldg(panel + (size_t)rr * p.W + cc) : 0.0f;
     }
   }
-  // the frame's code bytes are dead: drop them from L2 without a write-back
+  // this group's code bytes are dead: drop them from L2 without a write-back
   __syncthreads();
-  const uint32_t lines = ceil_div(p.M, 128);
-  for (uint32_t l = tid; l < lines; l += kPT) discard_line(codes + (size_t)l * 128);
-  if (trace) trace[6] = global_ns();
+  const uint32_t b0 = k_begin * kChunk, b1 = min(p.M, k_end * kChunk);
+  for (uint32_t l = b0 / 128 + tid; l < ceil_div(b1, 128); l += kPT) discard_line(codes + (size_t)l * 128);
 }
 
 // ---------------------------------------------------------------------------
@@ -659,23 +808,34 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
   const StreamView sv = stream_view(sm, sh);
   const FinView fv = fin_view(sm, sh);
   const uint64_t pol = evict_first_policy();
-  const uint32_t n_items = a.n_frames * p.P;
+  const SyncWords sw = sync_words(s, a.n_frames);
+  const uint32_t n = a.n_frames, lag = sh.lag, round = p.P + 2 * sh.groups;
+  const uint64_t total = (uint64_t)(n + 2 * lag) * round;
   for (;;) {
-    if (threadIdx.x == 0) sv.ctl[CTL_ITEM] = atomicAdd(s.work, 1u);
+    if (threadIdx.x == 0) sv.ctl[CTL_ITEM] = atomicAdd(sw.ticket, 1u);
     __syncthreads();
-    const uint32_t item = sv.ctl[CTL_ITEM];
+    const uint32_t t = sv.ctl[CTL_ITEM];
     __syncthreads();
-    if (item >= n_items) break;
-    const uint32_t f = item / p.P, pn = item - f * p.P;
-    process_panel(p, s, a, sh, sv, f, pn, pol);
-    // publish the panel; the CTA that completes the frame finalises it
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) sv.ctl[CTL_LAST] = atomicAdd(s.frame_done + f, 1u) == p.P - 1 ? 1u : 0u;
-    __syncthreads();
-    if (sv.ctl[CTL_LAST]) {
+    if (t >= total) break;
+    const uint32_t r = t / round, j = t - r * round;
+    if (j < p.P) {
+      if (r >= n) continue;
+      process_panel(p, s, a, sh, sv, r, j, pol);
+      // publish the panel; the CTA that completes the frame builds its codebook
       __threadfence();
-      finalize_frame(p, s, a, sh, fv, f);
+      __syncthreads();
+      if (threadIdx.x == 0) sv.ctl[CTL_LAST] = atomicAdd(sw.panel_done + r, 1u) == p.P - 1 ? 1u : 0u;
+      __syncthreads();
+      if (sv.ctl[CTL_LAST]) {
+        __threadfence();
+        frame_codebook(p, s, a, sh, fv, r, sw);
+      }
+    } else if (j < p.P + sh.groups) {
+      if (r < lag || r - lag >= n) continue;
+      size_item(p, s, a, sh, sm, r - lag, j - p.P, sw);
+    } else {
+      if (r < 2 * lag || r - 2 * lag >= n) continue;
+      write_item(p, s, a, sh, sm, r - 2 * lag, j - p.P - sh.groups, sw);
     }
     __syncthreads();
   }
@@ -700,6 +860,8 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, Fu
   sh.peak_cap = max(p.max_peaks, 1u);
   sh.n_chunks = p.n_chunks;
   sh.codes_stride = p.n_chunks * kChunk;
+  sh.group_chunks = 2 * kPW;
+  sh.groups = ceil_div(p.n_chunks, sh.group_chunks);
   uint64_t off = 0;
   auto take = [&](uint64_t bytes) {
     off = (off + 15) / 16 * 16;
@@ -707,9 +869,9 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, Fu
     off += bytes;
     return (uint32_t)o;
   };
-  sh.off_ctl = take((uint64_t)CTL_WORDS * 4);  // both roles use the control words
+  sh.off_ctl = take((uint64_t)CTL_WORDS * 4);  // every role uses the control words
   const uint64_t base = off;
-  // streaming role
+  // panel role
   sh.off_hist = take(kMaxSymbols * 4);
   sh.off_qbuf = take((uint64_t)sh.qrows * p.Wb * 4);
   sh.off_mask = take((uint64_t)sh.mask_words * 4);
@@ -717,13 +879,13 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, Fu
   sh.off_nb = take((uint64_t)kPW * sh.side * sh.side * 4);
   sh.off_acc = take((uint64_t)n2 * 4);
   const uint64_t stream_end = off;
-  // finalising role (overlaps the streaming role)
+  // codebook role / size, write and plan roles (overlap the panel role)
   off = base;
-  sh.off_huff = take(sizeof(HuffSmem));
+  sh.off_huff = take(sizeof(HuffSmem) > 2048 ? sizeof(HuffSmem) : 2048);  // Huffman scratch | byte table
   sh.off_total = take(kMaxSymbols * 4);
   sh.off_cblen = take(kMaxSymbols);
   sh.off_cbcode = take(kMaxSymbols * 4);
-  sh.off_keys = take((uint64_t)sh.peak_cap * 4);
+  sh.off_keys = take(16);
   sh.off_cw = take(3ull * p.n_chunks * 4);
   const uint64_t fin_end = off;
   sh.smem = (uint32_t)(stream_end > fin_end ? stream_end : fin_end);
@@ -762,15 +924,16 @@ bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out) {
 
 cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
                          cudaStream_t st) {
-  // per-frame completion counters and the work counter start at zero
-  cudaError_t e = cudaMemsetAsync(s.frame_done, 0, sizeof(uint32_t) * (a.n_frames + 1), st);
+  // stage counters, ready flags and the ticket counter start at zero
+  cudaError_t e = cudaMemsetAsync(s.frame_done, 0, sizeof(uint32_t) * (4ull * a.n_frames + 1), st);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
   if (e != cudaSuccess) return e;
-  Scratch s2 = s;
-  s2.work = s.frame_done + a.n_frames;
-  const uint32_t grid = min(sh.n_ctas, a.n_frames * p.P);
-  k_fused<<<grid, kPT, sh.smem, st>>>(p, s2, a, sh);
+  FusedShape s2 = sh;
+  s2.lag = a.n_frames < 16 ? a.n_frames : 16;  // frames between stages in the ticket order
+  const uint64_t tickets = (uint64_t)(a.n_frames + 2 * s2.lag) * (p.P + 2 * s2.groups);
+  const uint32_t grid = (uint32_t)(tickets < sh.n_ctas ? tickets : sh.n_ctas);
+  k_fused<<<grid, kPT, sh.smem, st>>>(p, s, a, s2);
   return cudaGetLastError();
 }
 

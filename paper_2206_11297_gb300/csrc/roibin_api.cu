@@ -179,7 +179,7 @@ uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s
   t.peak_part = c.take<uint32_t>((uint64_t)n * d.P * std::max<uint32_t>(d.max_peaks, 1));
   t.peak_part_count = c.take<uint32_t>((uint64_t)n * d.P);
   t.pq_part_count = c.take<uint32_t>((uint64_t)n * d.P);
-  t.frame_done = c.take<uint32_t>((uint64_t)n + 1);
+  t.frame_done = c.take<uint32_t>(4ull * n + 1);
   if (s) *s = t;
   return c.off + 256;
 }

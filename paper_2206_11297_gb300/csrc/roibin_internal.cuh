@@ -92,8 +92,7 @@ struct Scratch {
   uint32_t* peak_part;      // [n][P][max(max_peaks, 1)] per-panel sorted peaks
   uint32_t* peak_part_count;  // [n][P]
   uint32_t* pq_part_count;    // [n][P] prequantisation outliers per panel
-  uint32_t* frame_done;     // [n + 1] panels finished per frame; [n] = work counter
-  uint32_t* work;           // set per launch
+  uint32_t* frame_done;     // [4 n + 1] stage counters and flags, ticket counter
 };
 
 constexpr uint32_t kDecTableWords = 34 + 34 + 34 + kMaxSymbols;  // count, first, index, symbols
@@ -516,6 +515,8 @@ struct FusedShape {
   uint32_t peak_cap;             // max(max_peaks, 1)
   uint32_t n_chunks;
   uint32_t codes_stride;         // code bytes per frame slot (n_chunks * kChunk)
+  uint32_t group_chunks, groups; // chunks per size/write work item; items per frame
+  uint32_t lag;                  // frames between stages in the ticket order (per launch)
   uint32_t off_ctl, off_hist, off_qbuf, off_mask, off_thr, off_nb, off_acc;  // streaming role
   uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw;     // finalising role
   uint32_t smem;
