@@ -138,14 +138,16 @@ int roibin_ctx_resolved_path(const roibin_ctx* ctx);
 
 /* Tuning hook of the fused path: ctas_per_sm resident CTAs per SM (1..8,
  * capped by what fits) stream rows_per_step binned rows per step (0 = the
- * default for the geometry, else 1..16).  ROIBIN_ERR_INVALID_ARG when the
- * shape does not fit or the context has no fused path; the previous shape is
- * then kept.  Results are identical for every shape; only speed changes. */
-int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t rows_per_step);
-/* Current fused shape: CTAs per SM, rows per step, grid size, shared memory
- * bytes per CTA.  Any output pointer may be NULL. */
+ * default for the geometry, else 1..16) through a ring of `stages` TMA
+ * bulk-copy slots (1..8).  ROIBIN_ERR_INVALID_ARG when the shape does not fit
+ * or the context has no fused path; the previous shape is then kept.
+ * Results are identical for every shape; only speed changes. */
+int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t rows_per_step,
+                               uint32_t stages);
+/* Current fused shape: CTAs per SM, rows per step, ring stages, grid size,
+ * shared memory bytes per CTA.  Any output pointer may be NULL. */
 int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* rows_per_step,
-                           uint32_t* grid_ctas, uint32_t* smem_bytes);
+                           uint32_t* stages, uint32_t* grid_ctas, uint32_t* smem_bytes);
 
 /* Phase trace of the fused path: for frames f < n_frames of later calls, the
  * CTA that finalises frame f writes 10 globaltimer stamps (ns) to

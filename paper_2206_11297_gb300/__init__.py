@@ -63,9 +63,8 @@ _SIGNATURES = {
     "roibin_ctx_scratch_bytes": (_u64, [_P]),
     "roibin_ctx_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
     "roibin_ctx_resolved_path": (ctypes.c_int, [_P]),
-    "roibin_ctx_set_fused_shape": (ctypes.c_int, [_P, _u32, _u32]),
-    "roibin_ctx_fused_shape": (ctypes.c_int, [_P, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
-                                              ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    "roibin_ctx_set_fused_shape": (ctypes.c_int, [_P, _u32, _u32, _u32]),
+    "roibin_ctx_fused_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(_u32)] * 5),
     "roibin_ctx_set_trace": (ctypes.c_int, [_P, _P, _u32]),
     "roibin_compress": (ctypes.c_int, [_P, _P, _u32, _P, _P, _P, _u64, _P, _P, _P]),
     "roibin_decompress": (ctypes.c_int, [_P, _P, _u64, _P, _u32, _P, _P, _P]),
@@ -201,14 +200,14 @@ class Context:
     def set_path(self, path: int):
         _check("roibin_ctx_set_path", self.lib.roibin_ctx_set_path(self._h, int(path)))
 
-    def set_fused_shape(self, ctas_per_sm: int, rows_per_step: int = 0):
-        _check("roibin_ctx_set_fused_shape",
-               self.lib.roibin_ctx_set_fused_shape(self._h, int(ctas_per_sm), int(rows_per_step)))
+    def set_fused_shape(self, ctas_per_sm: int, rows_per_step: int = 0, stages: int = 2):
+        _check("roibin_ctx_set_fused_shape", self.lib.roibin_ctx_set_fused_shape(
+            self._h, int(ctas_per_sm), int(rows_per_step), int(stages)))
 
     @property
     def fused_shape(self):
-        """(CTAs per SM, rows per step, grid CTAs, shared memory bytes) or None."""
-        v = [_u32() for _ in range(4)]
+        """(CTAs per SM, rows per step, ring stages, grid CTAs, shared memory bytes) or None."""
+        v = [_u32() for _ in range(5)]
         if self.lib.roibin_ctx_fused_shape(self._h, *[ctypes.byref(x) for x in v]) != OK:
             return None
         return tuple(x.value for x in v)

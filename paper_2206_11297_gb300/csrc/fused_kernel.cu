@@ -28,6 +28,7 @@ constexpr int kPT = 256;       // threads per CTA
 constexpr int kPW = kPT / 32;  // warps per CTA
 constexpr int kItems = 2;      // bin-pair items per thread per step
 constexpr uint32_t kThrLocalCap = 512;
+constexpr uint32_t kPanelTimedOut = 0xFFFFFFFFu;  // per-panel peak count of a panel whose rows never arrived
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -52,6 +53,44 @@ __device__ __forceinline__ uint64_t evict_first_policy() {
 __device__ __forceinline__ void discard_line(const void* ptr) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(ptr) : "memory");
 }
+
+// mbarrier + TMA bulk-copy helpers (the streaming ring)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier wait
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// 1-D bulk copy global -> shared, completion counted on `bar`, L2 evict-first.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                            uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 // Symbol of a stored code byte.
 __device__ __forceinline__ uint32_t byte_code(uint32_t b, const uint16_t* esc_bin, int32_t R) {
@@ -121,9 +160,11 @@ struct StreamView {
   int32_t* qbuf;   // [qrows][Wb], circular by binned row
   uint32_t* mask;  // [mask_words] prequantisation-outlier bits of the panel
   uint32_t* thr;   // [kThrLocalCap] pixels >= amax_thr (panel-local index)
-  float* nb;       // [kPW][side^2] peak-test neighbourhoods
-  uint32_t* acc;   // [sort_n2] accepted peaks of the panel
+  float* nb;       // [kPW][side^2] peak-test neighbourhoods (aliases the ring)
+  uint32_t* acc;   // [sort_n2] accepted peaks of the panel (aliases the ring)
   uint32_t* ctl;
+  unsigned char* ring;  // [stages][stage_bytes] raw rows in flight
+  uint64_t* bars;       // [stages] one mbarrier per ring slot
 };
 struct FinView {
   HuffSmem* hs;
@@ -148,6 +189,7 @@ enum {
   CTL_CARRY2,
   CTL_PQ,
   CTL_WAIT,
+  CTL_TIMEOUT,
   CTL_TMP,
   CTL_OFFS = CTL_TMP + 33,  // per-panel peak offsets (first 1024 panels)
   CTL_WORDS = CTL_OFFS + 1024
@@ -162,6 +204,8 @@ __device__ __forceinline__ StreamView stream_view(unsigned char* sm, const Fused
   v.nb = reinterpret_cast<float*>(sm + sh.off_nb);
   v.acc = reinterpret_cast<uint32_t*>(sm + sh.off_acc);
   v.ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
+  v.ring = sm + sh.off_ring;
+  v.bars = reinterpret_cast<uint64_t*>(sm + sh.off_bar);
   return v;
 }
 __device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape& sh) {
@@ -181,7 +225,7 @@ __device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape&
 // ---------------------------------------------------------------------------
 // One panel: stream, code, list and evaluate candidates, flush.
 __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
-                              const StreamView& v, uint32_t f, uint32_t pn, uint64_t pol) {
+                              const StreamView& v, uint32_t f, uint32_t pn, uint64_t pol, uint32_t& ring_iter) {
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   const uint32_t NP = p.W >> 2, Mp = p.Hb * p.Wb;
   const float* panel = a.frames + (size_t)f * p.frame_px + (size_t)pn * p.H * p.W;
@@ -201,6 +245,7 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
     v.ctl[CTL_THR] = 0;
     v.ctl[CTL_PQ] = 0;
   }
+  if (a.user_peaks && tid == 0) s.peak_part_count[(size_t)f * p.P + pn] = 0;
 
   // the thread's items within a step (the same for every step)
   uint32_t il[kItems], pr[kItems];
@@ -211,34 +256,36 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
     pr[k] = it - il[k] * NP;
   }
   const uint32_t n_steps = ceil_div(p.Hb, sh.RB);
-  float4 va[kItems], vb[kItems];
-  auto load_step = [&](uint32_t i0) {
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      const uint32_t i = i0 + il[k];
-      va[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      vb[k] = va[k];
-      if (il[k] < sh.RB && i < p.Hb) {
-        const float* row = panel + (size_t)(2 * i) * p.W + 4 * pr[k];
-        va[k] = ld_stream(row, pol);
-        if (2 * i + 1 < p.H) vb[k] = ld_stream(row + p.W, pol);
-      }
-    }
+  // stage st = raw rows [2 st RB, min(H, 2 (st + 1) RB)) of the panel, one TMA bulk copy
+  auto issue = [&](uint32_t st) {  // thread 0 only
+    const uint32_t r0 = 2 * st * sh.RB, r1 = min(p.H, 2 * (st + 1) * sh.RB);
+    const uint32_t slot = (ring_iter + st) % sh.stages;
+    const uint32_t bytes = (r1 - r0) * p.W * 4;
+    fence_proxy_async();
+    mbar_expect_tx(v.bars + slot, bytes);
+    tma_load_1d(v.ring + (size_t)slot * sh.stage_bytes, panel + (size_t)r0 * p.W, bytes, v.bars + slot, pol);
   };
-  load_step(0);
+  if (tid == 0)
+    for (uint32_t st = 0; st < min(sh.stages, n_steps); ++st) issue(st);
   __syncthreads();  // hist, mask and counters are zero
   const bool find = a.user_peaks == nullptr;
+  bool timed_out = false;
   uint32_t n_common = 0;  // codes equal to R (zero residual), counted in a register
   for (uint32_t st = 0; st < n_steps; ++st) {
     const uint32_t i0 = st * sh.RB;
+    const uint32_t slot = (ring_iter + st) % sh.stages;
+    if (!mbar_wait(v.bars + slot, ((ring_iter + st) / sh.stages) & 1u)) timed_out = true;
+    const float4* ring = reinterpret_cast<const float4*>(v.ring + (size_t)slot * sh.stage_bytes);
     // phase A: q of the step's bins into the circular buffer
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
       const uint32_t i = i0 + il[k];
       if (il[k] >= sh.RB || i >= p.Hb) continue;
       const bool two = 2 * i + 1 < p.H;
+      const float4 va = ring[(size_t)(2 * il[k]) * NP + pr[k]];
+      const float4 vb = two ? ring[(size_t)(2 * il[k] + 1) * NP + pr[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
       float v0, v1;
-      bin_pair(va[k], vb[k], two, v0, v1);
+      bin_pair(va, vb, two, v0, v1);
       const Quant q0 = prequantize(v0, p), q1 = prequantize(v1, p);
       const uint32_t j0 = 2 * pr[k];
       *reinterpret_cast<int2*>(v.qbuf + (size_t)(i % sh.qrows) * p.Wb + j0) = make_int2(q0.q, q1.q);
@@ -249,22 +296,20 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
         if (q0.outlier) pq_bits[lb] = q0.outlier_bits;
         if (q1.outlier) pq_bits[lb + 1] = q1.outlier_bits;
       }
-      const float m = fmaxf(fmaxf(fmaxf(va[k].x, va[k].y), fmaxf(va[k].z, va[k].w)),
-                            fmaxf(fmaxf(vb[k].x, vb[k].y), fmaxf(vb[k].z, vb[k].w)));
+      const float m = fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)), fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
       if (find && m >= p.amax) {
-        const float px[8] = {va[k].x, va[k].y, va[k].z, va[k].w, vb[k].x, vb[k].y, vb[k].z, vb[k].w};
+        const float px[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
         const int npx = two ? 8 : 4;
         for (int e = 0; e < npx; ++e) {
           if (px[e] >= p.amax) {
-            const uint32_t slot = atomicAdd(v.ctl + CTL_THR, 1u);
-            if (slot < kThrLocalCap) v.thr[slot] = (2 * i + (e >> 2)) * p.W + 4 * pr[k] + (e & 3);
+            const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
+            if (slot_t < kThrLocalCap) v.thr[slot_t] = (2 * i + (e >> 2)) * p.W + 4 * pr[k] + (e & 3);
           }
         }
       }
     }
-    // the next step's loads fly while this step is coded
-    if (st + 1 < n_steps) load_step(i0 + sh.RB);
-    __syncthreads();
+    __syncthreads();  // the slot is consumed: refill it with the stage S steps ahead
+    if (tid == 0 && st + sh.stages < n_steps) issue(st + sh.stages);
     // phase B: residuals, code bytes, histogram, outliers.  The circular
     // buffer holds 2 RB + 1 rows, so the next phase A never overwrites a row
     // this phase B still reads: one barrier per step is enough.
@@ -310,6 +355,8 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       }
     }
   }
+  ring_iter += n_steps;
+  if (timed_out) v.ctl[CTL_TIMEOUT] = 1;
   // the zero residual's count: one add per warp
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) n_common += __shfl_xor_sync(0xffffffffu, n_common, d);
@@ -378,6 +425,11 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       for (uint32_t k = tid; k < n_acc; k += kPT) s.peak_part[fp * sh.peak_cap + k] = pn * p.H * p.W + v.acc[k];
     }
     if (tid == 0) s.peak_part_count[fp] = n_acc;
+  }
+  __syncthreads();
+  if (tid == 0 && v.ctl[CTL_TIMEOUT]) {  // a copy never arrived: the frame is marked, see frame_codebook
+    s.peak_part_count[fp] = kPanelTimedOut;
+    v.ctl[CTL_TIMEOUT] = 0;
   }
   if (trace) trace[2] = global_ns();
 }
@@ -463,7 +515,12 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
   uint32_t* keys = a.peaks_key_out + (size_t)f * p.max_peaks;
   if (a.user_peaks) {
     const uint32_t n = a.user_npeaks[f];
-    if (tid == 0) v.ctl[CTL_CARRY0] = n;
+    if (tid == 0) {
+      v.ctl[CTL_CARRY0] = n;
+      for (uint32_t pn = 0; pn < p.P; ++pn)
+        if (__ldcg(s.peak_part_count + (size_t)f * p.P + pn) == kPanelTimedOut)
+          v.ctl[CTL_BAD] = 2;
+    }
     if (n > p.max_peaks) {
       if (tid == 0) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_CAPACITY;
     } else {
@@ -478,14 +535,17 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
     if (tid == 0) {
       uint32_t n = 0;
       bool over = false;
+      bool timeout = false;
       for (uint32_t pn = 0; pn < p.P; ++pn) {
         const uint32_t c = __ldcg(s.peak_part_count + (size_t)f * p.P + pn);
-        if (c > p.max_peaks) over = true;
+        if (c == kPanelTimedOut) timeout = true;
+        else if (c > p.max_peaks) over = true;
         if (pn < 1024) v.ctl[CTL_OFFS + pn] = n;
         n += c;
       }
       if (over || n > p.max_peaks) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_CAPACITY;
-      v.ctl[CTL_CARRY0] = n;
+      if (timeout) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_TIMEOUT;
+      v.ctl[CTL_CARRY0] = timeout ? 0 : n;
     }
     __syncthreads();
     if (v.ctl[CTL_STATUS] == ROIBIN_OK) {
@@ -504,7 +564,8 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
   }
   __syncthreads();
   if (tid == 0) {
-    if (v.ctl[CTL_BAD] && v.ctl[CTL_STATUS] == ROIBIN_OK) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_INVALID_ARG;
+    if (v.ctl[CTL_BAD] == 2) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_TIMEOUT;
+    else if (v.ctl[CTL_BAD] && v.ctl[CTL_STATUS] == ROIBIN_OK) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_INVALID_ARG;
     a.peaks_count_out[f] = v.ctl[CTL_CARRY0];
   }
   if (trace) trace[1] = global_ns();
@@ -811,6 +872,13 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
   const SyncWords sw = sync_words(s, a.n_frames);
   const uint32_t n = a.n_frames, lag = sh.lag, round = p.P + 2 * sh.groups;
   const uint64_t total = (uint64_t)(n + 2 * lag) * round;
+  if (threadIdx.x == 0) {
+    for (uint32_t b = 0; b < sh.stages; ++b) mbar_init(sv.bars + b, 1);
+    fence_mbar_init();
+    sv.ctl[CTL_TIMEOUT] = 0;
+  }
+  __syncthreads();
+  uint32_t ring_iter = 0;  // ring stages consumed so far (the same in every thread)
   for (;;) {
     if (threadIdx.x == 0) sv.ctl[CTL_ITEM] = atomicAdd(sw.ticket, 1u);
     __syncthreads();
@@ -820,7 +888,7 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
     const uint32_t r = t / round, j = t - r * round;
     if (j < p.P) {
       if (r >= n) continue;
-      process_panel(p, s, a, sh, sv, r, j, pol);
+      process_panel(p, s, a, sh, sv, r, j, pol, ring_iter);
       // publish the panel; the CTA that completes the frame builds its codebook
       __threadfence();
       __syncthreads();
@@ -843,7 +911,7 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
 
 // ---------------------------------------------------------------------------
 // host side
-static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, FusedShape* out) {
+static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, uint32_t stages, FusedShape* out) {
   FusedShape sh{};
   const uint32_t NP = p.W / 4;
   uint32_t RB = rb ? rb : max(1u, (uint32_t)(kItems * kPT) / max(NP, 1u));
@@ -851,6 +919,8 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, Fu
   if (RB * NP > (uint32_t)(kItems * kPT)) return false;  // a step must fit the thread items
   sh.RB = RB;
   sh.qrows = 2 * RB + 1;
+  sh.stages = stages;
+  sh.stage_bytes = 2 * RB * p.W * 4;
   sh.ctas_per_sm = ctas_per_sm;
   sh.mask_words = ceil_div(p.Hb * p.Wb, 32) + 1;
   sh.side = 2 * (uint32_t)peak_reach(p) + 1;
@@ -870,15 +940,20 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, Fu
     return (uint32_t)o;
   };
   sh.off_ctl = take((uint64_t)CTL_WORDS * 4);  // every role uses the control words
+  sh.off_bar = take(8ull * stages);
   const uint64_t base = off;
-  // panel role
+  // panel role; the peak tests reuse the ring once the rows are consumed
   sh.off_hist = take(kMaxSymbols * 4);
   sh.off_qbuf = take((uint64_t)sh.qrows * p.Wb * 4);
   sh.off_mask = take((uint64_t)sh.mask_words * 4);
   sh.off_thr = take(kThrLocalCap * 4);
+  off = (off + 127) / 128 * 128;
+  sh.off_ring = take((uint64_t)stages * sh.stage_bytes);
+  const uint64_t ring_end = off;
+  off = sh.off_ring;
   sh.off_nb = take((uint64_t)kPW * sh.side * sh.side * 4);
   sh.off_acc = take((uint64_t)n2 * 4);
-  const uint64_t stream_end = off;
+  const uint64_t stream_end = off > ring_end ? off : ring_end;
   // codebook role / size, write and plan roles (overlap the panel role)
   off = base;
   sh.off_huff = take(sizeof(HuffSmem) > 2048 ? sizeof(HuffSmem) : 2048);  // Huffman scratch | byte table
@@ -893,11 +968,12 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, Fu
   return sh.smem <= 227 * 1024;
 }
 
-bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, FusedShape* out) {
+bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, uint32_t stages,
+                     FusedShape* out) {
   if (p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > (uint32_t)(kItems * kPT)) return false;
-  if (ctas_per_sm < 1 || ctas_per_sm > 8 || rows_per_step > 16) return false;
+  if (ctas_per_sm < 1 || ctas_per_sm > 8 || rows_per_step > 16 || stages < 1 || stages > 8) return false;
   FusedShape sh;
-  if (!make_shape(p, ctas_per_sm, rows_per_step, &sh)) return false;
+  if (!make_shape(p, ctas_per_sm, rows_per_step, stages, &sh)) return false;
   if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -919,7 +995,8 @@ bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per
 bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out) {
   (void)device;
   (void)num_sms;
-  return fused_shape_for(p, 4, 0, out);
+  return fused_shape_for(p, 4, 0, 2, out) || fused_shape_for(p, 3, 0, 2, out) || fused_shape_for(p, 2, 0, 2, out) ||
+         fused_shape_for(p, 1, 0, 1, out);
 }
 
 cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,

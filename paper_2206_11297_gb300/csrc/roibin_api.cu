@@ -369,20 +369,21 @@ int roibin_ctx_set_path(roibin_ctx* ctx, int path) {
   return ROIBIN_OK;
 }
 
-int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t rows_per_step) {
+int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t rows_per_step, uint32_t stages) {
   if (!ctx || !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
   FusedShape sh;
-  if (!fused_shape_for(ctx->dp, ctas_per_sm, rows_per_step, &sh)) return ROIBIN_ERR_INVALID_ARG;
+  if (!fused_shape_for(ctx->dp, ctas_per_sm, rows_per_step, stages, &sh)) return ROIBIN_ERR_INVALID_ARG;
   ctx->fshape = sh;
   return ROIBIN_OK;
 }
 
 int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* rows_per_step,
-                           uint32_t* grid_ctas, uint32_t* smem_bytes) {
+                           uint32_t* stages, uint32_t* grid_ctas, uint32_t* smem_bytes) {
   if (!ctx || !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
   if (ctas_per_sm) *ctas_per_sm = ctx->fshape.ctas_per_sm;
   if (rows_per_step) *rows_per_step = ctx->fshape.RB;
+  if (stages) *stages = ctx->fshape.stages;
   if (grid_ctas) *grid_ctas = ctx->fshape.n_ctas;
   if (smem_bytes) *smem_bytes = ctx->fshape.smem;
   return ROIBIN_OK;

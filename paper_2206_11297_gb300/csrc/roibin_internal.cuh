@@ -508,6 +508,7 @@ constexpr uint32_t kTracePoints = 10;
 struct FusedShape {
   uint32_t ctas_per_sm, n_ctas;  // resident CTAs per SM, grid size
   uint32_t RB;                   // binned rows per streaming step
+  uint32_t stages, stage_bytes;  // TMA ring: slots, bytes per slot (2 RB raw rows)
   uint32_t qrows;                // rows of the circular q buffer (2 RB + 1)
   uint32_t mask_words;           // prequantisation-outlier bitmask words per panel
   uint32_t side;                 // side of the peak-test neighbourhood
@@ -517,12 +518,13 @@ struct FusedShape {
   uint32_t codes_stride;         // code bytes per frame slot (n_chunks * kChunk)
   uint32_t group_chunks, groups; // chunks per size/write work item; items per frame
   uint32_t lag;                  // frames between stages in the ticket order (per launch)
-  uint32_t off_ctl, off_hist, off_qbuf, off_mask, off_thr, off_nb, off_acc;  // streaming role
+  uint32_t off_ctl, off_bar, off_hist, off_qbuf, off_mask, off_thr, off_ring, off_nb, off_acc;  // panel role
   uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw;     // finalising role
   uint32_t smem;
 };
 bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out);
-bool fused_shape_for(const DevParams& p, uint32_t C, uint32_t stages, FusedShape* out);
+bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, uint32_t stages,
+                     FusedShape* out);
 cudaError_t launch_fused(const DevParams& p, const Scratch& fs, const PlainArgs& a, const FusedShape& sh,
                          cudaStream_t st);
 
