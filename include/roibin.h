@@ -151,9 +151,11 @@ int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_
 
 /* Phase trace of the fused path: for frames f < n_frames of later calls, the
  * CTA that finalises frame f writes 10 globaltimer stamps (ns) to
- * d_trace[f * 10 + i]: 0 finalisation start, 1 peak list gathered, 2 codebook
- * built, 3 chunk sizes done, 4 header written, 5 bitstream written, 6 ROI
- * written (7..9 unused).  After those n_frames * 10 stamps, every panel item
+ * d_trace[f * 10 + i]: 0 codebook stage start, 1 peak list gathered, 2
+ * codebook built, 3 plan start, 4 plan done (head written); 5, 6: summed
+ * ns of the frame's chunk-size and chunk-write items; 7, 8: summed ns those
+ * items waited for their frame to be ready (9 unused).  The caller zeroes
+ * d_trace before the call.  After those n_frames * 10 stamps, every panel item
  * (f, p) of a traced frame writes 4 stamps at index n_frames * 10 + (f * P +
  * p) * 4: start, streaming done, peaks done (3 unused).  n_frames = 0
  * switches tracing off.  d_trace: device u64[n_frames * (10 + 4 P)], owned

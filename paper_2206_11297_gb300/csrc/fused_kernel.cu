@@ -248,12 +248,13 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
   if (a.user_peaks && tid == 0) s.peak_part_count[(size_t)f * p.P + pn] = 0;
 
   // the thread's items within a step (the same for every step)
-  uint32_t il[kItems], pr[kItems];
+  uint32_t il[kItems], pr[kItems], qs[kItems];  // qs: circular-buffer row of the item's bin row
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
     const uint32_t it = tid + k * kPT;
     il[k] = it / NP;
     pr[k] = it - il[k] * NP;
+    qs[k] = il[k] < sh.qrows ? il[k] : 0;
   }
   const uint32_t n_steps = ceil_div(p.Hb, sh.RB);
   // stage st = raw rows [2 st RB, min(H, 2 (st + 1) RB)) of the panel, one TMA bulk copy
@@ -288,7 +289,7 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       bin_pair(va, vb, two, v0, v1);
       const Quant q0 = prequantize(v0, p), q1 = prequantize(v1, p);
       const uint32_t j0 = 2 * pr[k];
-      *reinterpret_cast<int2*>(v.qbuf + (size_t)(i % sh.qrows) * p.Wb + j0) = make_int2(q0.q, q1.q);
+      *reinterpret_cast<int2*>(v.qbuf + (size_t)qs[k] * p.Wb + j0) = make_int2(q0.q, q1.q);
       if (q0.outlier | q1.outlier) {
         const uint32_t lb = i * p.Wb + j0;
         atomicAdd(v.ctl + CTL_PQ, (uint32_t)q0.outlier + (uint32_t)q1.outlier);
@@ -319,12 +320,12 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
       if (il[k] < sh.RB && i < p.Hb) {
         const uint32_t j0 = 2 * pr[k];
-        const int32_t* cur = v.qbuf + (size_t)(i % sh.qrows) * p.Wb;
+        const int32_t* cur = v.qbuf + (size_t)qs[k] * p.Wb;
         const int2 qc = *reinterpret_cast<const int2*>(cur + j0);
         int2 qu = make_int2(0, 0);
         int32_t ql = 0, qd = 0;
         if (i > 0) {
-          const int32_t* up = v.qbuf + (size_t)((i - 1) % sh.qrows) * p.Wb;
+          const int32_t* up = v.qbuf + (size_t)(qs[k] == 0 ? sh.qrows - 1 : qs[k] - 1) * p.Wb;
           qu = *reinterpret_cast<const int2*>(up + j0);
           if (j0 > 0) qd = up[j0 - 1];
         }
@@ -344,8 +345,7 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
           return 255u;
         };
         const uint32_t b0 = to_byte(d0, c0, lb), b1 = to_byte(d1, c1, lb + 1);
-        codes[lb] = (uint8_t)b0;
-        codes[lb + 1] = (uint8_t)b1;
+        *reinterpret_cast<uint16_t*>(codes + lb) = (uint16_t)(b0 | (b1 << 8));  // lb is even
       }
       n_common += (c0 == (uint32_t)p.R) + (c1 == (uint32_t)p.R);
       const bool r0 = c0 != 0xFFFFu && c0 != (uint32_t)p.R, r1 = c1 != 0xFFFFu && c1 != (uint32_t)p.R;
@@ -353,10 +353,13 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
         hist_add_warp(v.hist, r0 ? c0 : 0xFFFFu, 0xFFFFFFFFu);
         hist_add_warp(v.hist, r1 ? c1 : 0xFFFFu, 0xFFFFFFFFu);
       }
+      qs[k] += sh.RB;  // the same item's row in the next step
+      if (qs[k] >= sh.qrows) qs[k] -= sh.qrows;
     }
   }
   ring_iter += n_steps;
   if (timed_out) v.ctl[CTL_TIMEOUT] = 1;
+  (void)qs;
   // the zero residual's count: one add per warp
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) n_common += __shfl_xor_sync(0xffffffffu, n_common, d);
@@ -651,7 +654,12 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
   uint64_t* btab = reinterpret_cast<uint64_t*>(sm + sh.off_huff);
+  unsigned long long* acct = (a.trace && g < a.trace_frames && tid == 0)
+                                 ? reinterpret_cast<unsigned long long*>(a.trace + (size_t)g * kTracePoints)
+                                 : nullptr;
+  const uint64_t t_in = acct ? global_ns() : 0;
   const bool ready = wait_flag(sw.ready_cb + g, ctl + CTL_WAIT);
+  if (acct) atomicAdd(acct + 7, (unsigned long long)(global_ns() - t_in));
   if (!ready && tid == 0) atomicExch(reinterpret_cast<unsigned int*>(s.status + g), (unsigned int)ROIBIN_ERR_TIMEOUT);
   const bool ok = ready && __ldcg(s.status + g) == ROIBIN_OK;
   if (ok) {
@@ -681,6 +689,7 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
       }
     }
   }
+  if (acct) atomicAdd(acct + 5, (unsigned long long)(global_ns() - t_in));
   __threadfence();
   __syncthreads();
   if (tid == 0) ctl[CTL_LAST] = atomicAdd(sw.size_done + g, 1u) == sh.groups - 1 ? 1u : 0u;
@@ -766,7 +775,12 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
   uint64_t* btab = reinterpret_cast<uint64_t*>(sm + sh.off_huff);
+  unsigned long long* acct = (a.trace && g < a.trace_frames && tid == 0)
+                                 ? reinterpret_cast<unsigned long long*>(a.trace + (size_t)g * kTracePoints)
+                                 : nullptr;
+  const uint64_t t_in = acct ? global_ns() : 0;
   const bool ready = wait_flag(sw.ready_plan + g, ctl + CTL_WAIT);
+  if (acct) atomicAdd(acct + 8, (unsigned long long)(global_ns() - t_in));
   if (!ready) {
     if (tid == 0) atomicExch(reinterpret_cast<unsigned int*>(a.frame_status + g), (unsigned int)ROIBIN_ERR_TIMEOUT);
     return;
@@ -861,6 +875,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
   __syncthreads();
   const uint32_t b0 = k_begin * kChunk, b1 = min(p.M, k_end * kChunk);
   for (uint32_t l = b0 / 128 + tid; l < ceil_div(b1, 128); l += kPT) discard_line(codes + (size_t)l * 128);
+  if (acct) atomicAdd(acct + 6, (unsigned long long)(global_ns() - t_in));
 }
 
 // ---------------------------------------------------------------------------
@@ -1007,7 +1022,7 @@ cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& 
   e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
   if (e != cudaSuccess) return e;
   FusedShape s2 = sh;
-  s2.lag = a.n_frames < 16 ? a.n_frames : 16;  // frames between stages in the ticket order
+  s2.lag = a.n_frames < 48 ? a.n_frames : 48;  // frames between stages in the ticket order
   const uint64_t tickets = (uint64_t)(a.n_frames + 2 * s2.lag) * (p.P + 2 * s2.groups);
   const uint32_t grid = (uint32_t)(tickets < sh.n_ctas ? tickets : sh.n_ctas);
   k_fused<<<grid, kPT, sh.smem, st>>>(p, s, a, s2);

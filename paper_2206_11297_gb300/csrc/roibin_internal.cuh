@@ -183,8 +183,12 @@ __device__ __forceinline__ void bin_pair(const float4& a, const float4& b, bool 
     s1 = __fadd_rn(__fadd_rn(s1, b.z), b.w);
     c = 4.0f;
   }
-  b0 = __fdiv_rn(s0, c);
-  b1 = __fdiv_rn(s1, c);
+  // division by 2 or 4: the exact product with 0.5 or 0.25 is the correctly
+  // rounded quotient, bit for bit, so this is the same IEEE division
+  const float rc = two ? 0.25f : 0.5f;
+  (void)c;
+  b0 = __fmul_rn(s0, rc);
+  b1 = __fmul_rn(s1, rc);
 }
 
 // Histogram update by a whole warp (every lane calls; code 0xFFFF = no item).
