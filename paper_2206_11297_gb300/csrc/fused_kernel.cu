@@ -624,24 +624,45 @@ __device__ __forceinline__ uint32_t pq_bit_of(const DevParams& p, const Scratch&
   return (__ldcg(s.pq_mask + ((size_t)f * p.P + pn) * sh.mask_words + (lb >> 5)) >> (lb & 31)) & 1u;
 }
 
-__device__ __forceinline__ uint32_t byte_of(const uint4& u, uint32_t j) {  // j < 16
-  const uint32_t w = (j >> 2) == 0 ? u.x : (j >> 2) == 1 ? u.y : (j >> 2) == 2 ? u.z : u.w;
-  return (w >> (8 * (j & 3))) & 0xFFu;
+// A warp stages one chunk's 4096 code bytes in its shared buffer with
+// coalesced 16-byte loads; word w of the chunk sits at w + w / 32, so lane l
+// reading its words 32 l .. 32 l + 31 hits 32 different banks.
+constexpr uint32_t kStageWords = kChunk / 4 + kChunk / 128;  // 1056
+__device__ __forceinline__ void stage_chunk(const uint8_t* codes_frame, uint32_t k, uint32_t* wbuf) {
+  const uint4* src = reinterpret_cast<const uint4*>(codes_frame + (size_t)k * kChunk);
+  const uint32_t lane = lane_id();
+  uint4 u[8];
+#pragma unroll
+  for (int it = 0; it < 8; ++it) u[it] = __ldcg(src + it * 32 + lane);
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const uint32_t w = 4 * (it * 32 + lane);
+    uint32_t* d = wbuf + w + (w >> 5);
+    d[0] = u[it].x;
+    d[1] = u[it].y;
+    d[2] = u[it].z;
+    d[3] = u[it].w;
+  }
+  __syncwarp();
 }
 
-// Bits, Lorenzo outliers and prequantisation outliers of lane's 128 symbols.
+// Bits, Lorenzo outliers and prequantisation outliers of the lane's 128
+// symbols [s0, s1) of a staged chunk.
 __device__ __forceinline__ void lane_counts(const DevParams& p, const Scratch& s, const FusedShape& sh, uint32_t f,
-                                            const uint64_t* btab, const uint4 (&cv)[8], uint32_t s0, uint32_t s1,
+                                            const uint64_t* btab, const uint32_t* wbuf, uint32_t s0, uint32_t s1,
                                             bool any_pq, uint32_t& bits, uint32_t& nlo, uint32_t& npq) {
   bits = nlo = npq = 0;
+  const uint32_t* lw = wbuf + 33 * lane_id();
+  for (uint32_t w = 0; w < 32; ++w) {
+    const uint32_t word = lw[w];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    for (uint32_t j = 0; j < 16; ++j) {
-      const uint32_t bin = s0 + 16 * q + j;
-      if (bin >= s1) break;
-      const uint32_t b = byte_of(cv[q], j);
-      bits += (uint32_t)symbol_entry(p, s, f, btab, b, bin);
-      nlo += b == 0;
+    for (uint32_t t = 0; t < 4; ++t) {
+      const uint32_t bin = s0 + 4 * w + t;
+      if (bin < s1) {
+        const uint32_t b = (word >> (8 * t)) & 0xFFu;
+        bits += (uint32_t)symbol_entry(p, s, f, btab, b, bin);
+        nlo += b == 0;
+      }
     }
   }
   if (any_pq)
@@ -668,14 +689,13 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
     const bool any_pq = __ldcg(&s.plan[g].n_pq) != 0;
     const uint8_t* codes = s.codes8 + (size_t)g * sh.codes_stride;
     const uint32_t k_end = min(p.n_chunks, (grp + 1) * sh.group_chunks);
+    uint32_t* wbuf = reinterpret_cast<uint32_t*>(sm + sh.off_stage) + warp * kStageWords;
     for (uint32_t k = grp * sh.group_chunks + warp; k < k_end; k += kPW) {
       const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
-      uint4 cv[8];
-      const uint4* src = reinterpret_cast<const uint4*>(codes + s0);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) cv[q] = __ldcg(src + q);
+      stage_chunk(codes, k, wbuf);
       uint32_t bits, nlo, npq;
-      lane_counts(p, s, sh, g, btab, cv, s0, s1, any_pq, bits, nlo, npq);
+      lane_counts(p, s, sh, g, btab, wbuf, s0, s1, any_pq, bits, nlo, npq);
+      __syncwarp();
       for (int d = 16; d > 0; d >>= 1) {
         bits += __shfl_xor_sync(0xffffffffu, bits, d);
         nlo += __shfl_xor_sync(0xffffffffu, nlo, d);
@@ -805,6 +825,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
   const int32_t* lo_delta = s.lo_delta + (size_t)g * p.M;
   const uint32_t* pq_bits = s.pq_bits + (size_t)g * p.M;
   const uint32_t k_begin = grp * sh.group_chunks, k_end = min(p.n_chunks, (grp + 1) * sh.group_chunks);
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(sm + sh.off_stage) + warp * kStageWords;
   for (uint32_t k = k_begin + warp; k < k_end; k += kPW) {
     const size_t o = (size_t)g * p.n_chunks + k;
     const uint32_t w0 = __ldcg(s.chunk_words + o);
@@ -813,12 +834,9 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     __threadfence_block();
     __syncwarp();
     const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
-    uint4 cv[8];
-    const uint4* src = reinterpret_cast<const uint4*>(codes + s0);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) cv[q] = __ldcg(src + q);
+    stage_chunk(codes, k, wbuf);
     uint32_t bits, nlo, npq;
-    lane_counts(p, s, sh, g, btab, cv, s0, s1, any_pq, bits, nlo, npq);
+    lane_counts(p, s, sh, g, btab, wbuf, s0, s1, any_pq, bits, nlo, npq);
     const uint32_t bit_incl = warp_incl_scan(bits), lo_incl = warp_incl_scan(nlo), pq_incl = warp_incl_scan(npq);
     const uint32_t start = bit_incl - bits;
     uint32_t wi = w0 + start / 32;
@@ -827,12 +845,13 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     bool first = nacc != 0;  // the first word is shared with the previous lane
     uint32_t lo_pos = __ldcg(s.chunk_lo + o) + lo_incl - nlo;
     uint32_t pq_pos = __ldcg(s.chunk_pq + o) + pq_incl - npq;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      for (uint32_t j = 0; j < 16; ++j) {
-        const uint32_t bin = s0 + 16 * q + j;
+    const uint32_t* lw = wbuf + 33 * lane;
+    for (uint32_t w = 0; w < 32; ++w) {
+      const uint32_t word = lw[w];
+      for (uint32_t t = 0; t < 4; ++t) {
+        const uint32_t bin = s0 + 4 * w + t;
         if (bin >= s1) break;
-        const uint32_t b = byte_of(cv[q], j);
+        const uint32_t b = (word >> (8 * t)) & 0xFFu;
         const uint64_t e = symbol_entry(p, s, g, btab, b, bin);
         const uint32_t Lc = (uint32_t)e;
         accb |= (e >> 32) << (64 - nacc - Lc);
@@ -850,6 +869,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
       }
     }
     if (nacc > 0) atomicOr(words + wi, (uint32_t)(accb >> 32));  // shared with the next lane
+    __syncwarp();
     if (npq)
       for (uint32_t i = s0; i < s1; ++i)
         if (pq_bit_of(p, s, sh, g, i)) pq_out[pq_pos++] = make_uint2(i, __ldcg(pq_bits + i));
@@ -972,12 +992,17 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   // codebook role / size, write and plan roles (overlap the panel role)
   off = base;
   sh.off_huff = take(sizeof(HuffSmem) > 2048 ? sizeof(HuffSmem) : 2048);  // Huffman scratch | byte table
+  const uint64_t after_huff = off;
+  off = sh.off_huff + 2048;  // chunk staging of the size and write items (after the byte table)
+  sh.off_stage = take((uint64_t)kPW * kStageWords * 4);
+  const uint64_t stage_end = off;
+  off = after_huff;
   sh.off_total = take(kMaxSymbols * 4);
   sh.off_cblen = take(kMaxSymbols);
   sh.off_cbcode = take(kMaxSymbols * 4);
   sh.off_keys = take(16);
   sh.off_cw = take(3ull * p.n_chunks * 4);
-  const uint64_t fin_end = off;
+  const uint64_t fin_end = off > stage_end ? off : stage_end;
   sh.smem = (uint32_t)(stream_end > fin_end ? stream_end : fin_end);
   *out = sh;
   return sh.smem <= 227 * 1024;

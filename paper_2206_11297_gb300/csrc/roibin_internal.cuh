@@ -523,7 +523,8 @@ struct FusedShape {
   uint32_t group_chunks, groups; // chunks per size/write work item; items per frame
   uint32_t lag;                  // frames between stages in the ticket order (per launch)
   uint32_t off_ctl, off_bar, off_hist, off_qbuf, off_mask, off_thr, off_ring, off_nb, off_acc;  // panel role
-  uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw;     // finalising role
+  uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw;     // codebook / plan roles
+  uint32_t off_stage;                                                        // size / write roles
   uint32_t smem;
 };
 bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out);
