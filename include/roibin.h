@@ -149,17 +149,17 @@ int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t r
 int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* rows_per_step,
                            uint32_t* stages, uint32_t* grid_ctas, uint32_t* smem_bytes);
 
-/* Phase trace of the fused path: for frames f < n_frames of later calls, the
- * CTA that finalises frame f writes 10 globaltimer stamps (ns) to
- * d_trace[f * 10 + i]: 0 codebook stage start, 1 peak list gathered, 2
- * codebook built, 3 plan start, 4 plan done (head written); 5, 6: summed
- * ns of the frame's chunk-size and chunk-write items; 7, 8: summed ns those
- * items waited for their frame to be ready (9 unused).  The caller zeroes
- * d_trace before the call.  After those n_frames * 10 stamps, every panel item
- * (f, p) of a traced frame writes 4 stamps at index n_frames * 10 + (f * P +
- * p) * 4: start, streaming done, peaks done (3 unused).  n_frames = 0
- * switches tracing off.  d_trace: device u64[n_frames * (10 + 4 P)], owned
- * by the caller. */
+/* Phase trace of the fused path: for frames f < n_frames of later calls the
+ * kernel writes 16 u64 words at d_trace[f * 16 + i] (globaltimer ns):
+ * 0 codebook stage start, 1 peak list gathered, 2 codebook built, 3 plan
+ * start, 4 plan done (head written); summed over the frame's chunk items:
+ * 5 size items, 6 write items, 7 size waits, 8 write waits, 9 size chunk
+ * loops, 10 write chunk loops, 11 write ROI copies (12..15 unused).  After
+ * the n_frames * 16 words, every panel item (f, p) of a traced frame writes 4
+ * stamps at index n_frames * 16 + (f * P + p) * 4: start, streaming done,
+ * peaks done (3 unused).  The caller zeroes d_trace before the call and owns
+ * it (device u64[n_frames * (16 + 4 P)]); n_frames = 0 switches tracing off.
+ */
 int roibin_ctx_set_trace(roibin_ctx* ctx, uint64_t* d_trace, uint32_t n_frames);
 
 /* Compresses n_frames frames (1 <= n_frames <= max_frames_per_call).

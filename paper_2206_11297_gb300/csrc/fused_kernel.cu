@@ -588,9 +588,13 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
   if (tid == 0) flag_release(sw.ready_cb + f);
 }
 
-// Per-byte table of a frame's codebook: entry = codeword << 32 | length;
-// length 0 marks an escape byte (its code sits in the side array).
-__device__ void load_byte_table(const DevParams& p, const Scratch& s, uint32_t f, uint64_t* btab) {
+// Per-byte tables of a frame's codebook (byte = stored code byte):
+//   btab[b] = codeword << 32 | length  (0 for the escape byte 255)
+//   ctab[b] = length | (b == 0) << 21 | (b == 255) << 42, so that summing
+//             ctab over a lane's bytes counts bits, Lorenzo outliers and
+//             escapes in one 64-bit add per symbol.
+constexpr uint32_t kField = 21;
+__device__ void load_byte_tables(const DevParams& p, const Scratch& s, uint32_t f, uint64_t* btab, uint64_t* ctab) {
   for (uint32_t b = threadIdx.x; b < 256; b += kPT) {
     uint64_t e = 0;
     if (b != 255) {
@@ -602,10 +606,11 @@ __device__ void load_byte_table(const DevParams& p, const Scratch& s, uint32_t f
       }
     }
     btab[b] = e;
+    ctab[b] = (e & 0xFFu) | ((uint64_t)(b == 0) << kField) | ((uint64_t)(b == 255) << (2 * kField));
   }
 }
 
-// (len, codeword) of the symbol stored as byte b at bin `bin` of frame f.
+// (length, codeword) of the symbol stored as byte b at bin `bin` of frame f.
 __device__ __forceinline__ uint64_t symbol_entry(const DevParams& p, const Scratch& s, uint32_t f, const uint64_t* btab,
                                                  uint32_t b, uint32_t bin) {
   uint64_t e = btab[b];
@@ -647,24 +652,35 @@ __device__ __forceinline__ void stage_chunk(const uint8_t* codes_frame, uint32_t
 }
 
 // Bits, Lorenzo outliers and prequantisation outliers of the lane's 128
-// symbols [s0, s1) of a staged chunk.
+// symbols [s0, s1) of a staged chunk: one table add per symbol; escapes (rare)
+// are resolved afterwards.
 __device__ __forceinline__ void lane_counts(const DevParams& p, const Scratch& s, const FusedShape& sh, uint32_t f,
-                                            const uint64_t* btab, const uint32_t* wbuf, uint32_t s0, uint32_t s1,
-                                            bool any_pq, uint32_t& bits, uint32_t& nlo, uint32_t& npq) {
-  bits = nlo = npq = 0;
+                                            const uint64_t* btab, const uint64_t* ctab, const uint32_t* wbuf,
+                                            uint32_t s0, uint32_t s1, bool any_pq, uint32_t& bits, uint32_t& nlo,
+                                            uint32_t& npq) {
   const uint32_t* lw = wbuf + 33 * lane_id();
-  for (uint32_t w = 0; w < 32; ++w) {
+  const uint32_t n = s1 > s0 ? s1 - s0 : 0;  // symbols of this lane (<= 128)
+  const uint32_t full = n >> 2;
+  uint64_t acc = 0;
+  for (uint32_t w = 0; w < full; ++w) {
     const uint32_t word = lw[w];
-#pragma unroll
-    for (uint32_t t = 0; t < 4; ++t) {
-      const uint32_t bin = s0 + 4 * w + t;
-      if (bin < s1) {
-        const uint32_t b = (word >> (8 * t)) & 0xFFu;
-        bits += (uint32_t)symbol_entry(p, s, f, btab, b, bin);
-        nlo += b == 0;
-      }
+    acc += ctab[word & 0xFFu] + ctab[(word >> 8) & 0xFFu] + ctab[(word >> 16) & 0xFFu] + ctab[word >> 24];
+  }
+  if (n & 3u) {
+    const uint32_t word = lw[full];
+    for (uint32_t t = 0; t < (n & 3u); ++t) acc += ctab[(word >> (8 * t)) & 0xFFu];
+  }
+  const uint64_t mask = (1ull << kField) - 1;
+  bits = (uint32_t)(acc & mask);
+  nlo = (uint32_t)((acc >> kField) & mask);
+  const uint32_t nesc = (uint32_t)(acc >> (2 * kField));
+  if (nesc) {
+    for (uint32_t i = 0; i < n; ++i) {
+      const uint32_t b = (lw[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+      if (b == 255) bits += (uint32_t)symbol_entry(p, s, f, btab, b, s0 + i);
     }
   }
+  npq = 0;
   if (any_pq)
     for (uint32_t i = s0; i < s1; ++i) npq += pq_bit_of(p, s, sh, f, i);
 }
@@ -675,6 +691,7 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
   uint64_t* btab = reinterpret_cast<uint64_t*>(sm + sh.off_huff);
+  uint64_t* ctab = btab + 256;
   unsigned long long* acct = (a.trace && g < a.trace_frames && tid == 0)
                                  ? reinterpret_cast<unsigned long long*>(a.trace + (size_t)g * kTracePoints)
                                  : nullptr;
@@ -684,17 +701,18 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
   if (!ready && tid == 0) atomicExch(reinterpret_cast<unsigned int*>(s.status + g), (unsigned int)ROIBIN_ERR_TIMEOUT);
   const bool ok = ready && __ldcg(s.status + g) == ROIBIN_OK;
   if (ok) {
-    load_byte_table(p, s, g, btab);
+    load_byte_tables(p, s, g, btab, ctab);
     __syncthreads();
     const bool any_pq = __ldcg(&s.plan[g].n_pq) != 0;
     const uint8_t* codes = s.codes8 + (size_t)g * sh.codes_stride;
     const uint32_t k_end = min(p.n_chunks, (grp + 1) * sh.group_chunks);
     uint32_t* wbuf = reinterpret_cast<uint32_t*>(sm + sh.off_stage) + warp * kStageWords;
+    const uint64_t t_loop = acct ? global_ns() : 0;
     for (uint32_t k = grp * sh.group_chunks + warp; k < k_end; k += kPW) {
       const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
       stage_chunk(codes, k, wbuf);
       uint32_t bits, nlo, npq;
-      lane_counts(p, s, sh, g, btab, wbuf, s0, s1, any_pq, bits, nlo, npq);
+      lane_counts(p, s, sh, g, btab, ctab, wbuf, s0, s1, any_pq, bits, nlo, npq);
       __syncwarp();
       for (int d = 16; d > 0; d >>= 1) {
         bits += __shfl_xor_sync(0xffffffffu, bits, d);
@@ -708,6 +726,8 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
         s.chunk_pq[o] = npq;
       }
     }
+    __syncthreads();
+    if (acct) atomicAdd(acct + 9, (unsigned long long)(global_ns() - t_loop));
   }
   if (acct) atomicAdd(acct + 5, (unsigned long long)(global_ns() - t_in));
   __threadfence();
@@ -795,6 +815,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
   uint64_t* btab = reinterpret_cast<uint64_t*>(sm + sh.off_huff);
+  uint64_t* ctab = btab + 256;
   unsigned long long* acct = (a.trace && g < a.trace_frames && tid == 0)
                                  ? reinterpret_cast<unsigned long long*>(a.trace + (size_t)g * kTracePoints)
                                  : nullptr;
@@ -806,7 +827,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     return;
   }
   if (__ldcg(s.status + g) != ROIBIN_OK) return;
-  load_byte_table(p, s, g, btab);
+  load_byte_tables(p, s, g, btab, ctab);
   FramePlan pl;
   pl.n_peaks = __ldcg(&s.plan[g].n_peaks);
   pl.n_pq = __ldcg(&s.plan[g].n_pq);
@@ -826,6 +847,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
   const uint32_t* pq_bits = s.pq_bits + (size_t)g * p.M;
   const uint32_t k_begin = grp * sh.group_chunks, k_end = min(p.n_chunks, (grp + 1) * sh.group_chunks);
   uint32_t* wbuf = reinterpret_cast<uint32_t*>(sm + sh.off_stage) + warp * kStageWords;
+  const uint64_t t_loop = acct ? global_ns() : 0;
   for (uint32_t k = k_begin + warp; k < k_end; k += kPW) {
     const size_t o = (size_t)g * p.n_chunks + k;
     const uint32_t w0 = __ldcg(s.chunk_words + o);
@@ -836,7 +858,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
     stage_chunk(codes, k, wbuf);
     uint32_t bits, nlo, npq;
-    lane_counts(p, s, sh, g, btab, wbuf, s0, s1, any_pq, bits, nlo, npq);
+    lane_counts(p, s, sh, g, btab, ctab, wbuf, s0, s1, any_pq, bits, nlo, npq);
     const uint32_t bit_incl = warp_incl_scan(bits), lo_incl = warp_incl_scan(nlo), pq_incl = warp_incl_scan(npq);
     const uint32_t start = bit_incl - bits;
     uint32_t wi = w0 + start / 32;
@@ -845,26 +867,47 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     bool first = nacc != 0;  // the first word is shared with the previous lane
     uint32_t lo_pos = __ldcg(s.chunk_lo + o) + lo_incl - nlo;
     uint32_t pq_pos = __ldcg(s.chunk_pq + o) + pq_incl - npq;
+    // append `len` (<= 32) bits, emitting each completed 32-bit word
+    auto append = [&](uint32_t cw, uint32_t len) {
+      accb |= (uint64_t)cw << (64 - nacc - len);
+      nacc += len;
+      if (nacc >= 32) {
+        const uint32_t word = (uint32_t)(accb >> 32);
+        if (first) atomicOr(words + wi, word);
+        else words[wi] = word;
+        first = false;
+        ++wi;
+        accb <<= 32;
+        nacc -= 32;
+      }
+    };
     const uint32_t* lw = wbuf + 33 * lane;
-    for (uint32_t w = 0; w < 32; ++w) {
+    const uint32_t n = s1 > s0 ? s1 - s0 : 0;
+    for (uint32_t w = 0; w < (n + 3) / 4; ++w) {
       const uint32_t word = lw[w];
-      for (uint32_t t = 0; t < 4; ++t) {
+      const uint32_t cnt = min(4u, n - 4 * w);
+      // fast path: four ordinary bytes (no 0 = outlier, no 255 = escape) whose
+      // codewords fit 32 bits together are appended at once
+      const bool has0 = ((word - 0x01010101u) & ~word & 0x80808080u) != 0;
+      const bool has255 = ((~word - 0x01010101u) & word & 0x80808080u) != 0;
+      if (cnt == 4 && !has0 && !has255) {
+        const uint64_t e0 = btab[word & 0xFFu], e1 = btab[(word >> 8) & 0xFFu], e2 = btab[(word >> 16) & 0xFFu],
+                       e3 = btab[word >> 24];
+        const uint32_t L0 = (uint32_t)e0, L1 = (uint32_t)e1, L2 = (uint32_t)e2, L3 = (uint32_t)e3;
+        if (L0 + L1 + L2 + L3 <= 32) {
+          uint32_t combo = (uint32_t)(e0 >> 32);
+          combo = (combo << L1) | (uint32_t)(e1 >> 32);
+          combo = (combo << L2) | (uint32_t)(e2 >> 32);
+          combo = (combo << L3) | (uint32_t)(e3 >> 32);
+          append(combo, L0 + L1 + L2 + L3);
+          continue;
+        }
+      }
+      for (uint32_t t = 0; t < cnt; ++t) {
         const uint32_t bin = s0 + 4 * w + t;
-        if (bin >= s1) break;
         const uint32_t b = (word >> (8 * t)) & 0xFFu;
         const uint64_t e = symbol_entry(p, s, g, btab, b, bin);
-        const uint32_t Lc = (uint32_t)e;
-        accb |= (e >> 32) << (64 - nacc - Lc);
-        nacc += Lc;
-        if (nacc >= 32) {
-          const uint32_t word = (uint32_t)(accb >> 32);
-          if (first) atomicOr(words + wi, word);
-          else words[wi] = word;
-          first = false;
-          ++wi;
-          accb <<= 32;
-          nacc -= 32;
-        }
+        append((uint32_t)(e >> 32), (uint32_t)e);
         if (b == 0) lo_out[lo_pos++] = make_uint2(bin, (uint32_t)__ldcg(lo_delta + bin));
       }
     }
@@ -874,6 +917,9 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
       for (uint32_t i = s0; i < s1; ++i)
         if (pq_bit_of(p, s, sh, g, i)) pq_out[pq_pos++] = make_uint2(i, __ldcg(pq_bits + i));
   }
+  __syncthreads();
+  const uint64_t t_roi = acct ? global_ns() : 0;
+  if (acct) atomicAdd(acct + 10, (unsigned long long)(t_roi - t_loop));
   // a3: ROI windows of peaks k = grp, grp + groups, ... (one warp per peak)
   float* roi = reinterpret_cast<float*>(out + pl.off_roi);
   const uint32_t win = (uint32_t)(p.roi_h * p.roi_w), plane = p.H * p.W;
@@ -893,6 +939,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
   }
   // this group's code bytes are dead: drop them from L2 without a write-back
   __syncthreads();
+  if (acct) atomicAdd(acct + 11, (unsigned long long)(global_ns() - t_roi));
   const uint32_t b0 = k_begin * kChunk, b1 = min(p.M, k_end * kChunk);
   for (uint32_t l = b0 / 128 + tid; l < ceil_div(b1, 128); l += kPT) discard_line(codes + (size_t)l * 128);
   if (acct) atomicAdd(acct + 6, (unsigned long long)(global_ns() - t_in));
@@ -991,9 +1038,9 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   const uint64_t stream_end = off > ring_end ? off : ring_end;
   // codebook role / size, write and plan roles (overlap the panel role)
   off = base;
-  sh.off_huff = take(sizeof(HuffSmem) > 2048 ? sizeof(HuffSmem) : 2048);  // Huffman scratch | byte table
+  sh.off_huff = take(sizeof(HuffSmem) > 4096 ? sizeof(HuffSmem) : 4096);  // Huffman scratch | byte tables
   const uint64_t after_huff = off;
-  off = sh.off_huff + 2048;  // chunk staging of the size and write items (after the byte table)
+  off = sh.off_huff + 4096;  // chunk staging of the size and write items (after the byte tables)
   sh.off_stage = take((uint64_t)kPW * kStageWords * 4);
   const uint64_t stage_end = off;
   off = after_huff;

@@ -506,7 +506,7 @@ struct PlainArgs {
   uint64_t* trace;            // fused path: kTracePoints globaltimer stamps per traced frame
   uint32_t trace_frames;
 };
-constexpr uint32_t kTracePoints = 10;
+constexpr uint32_t kTracePoints = 16;
 
 // Shape of the persistent batched kernel, chosen on the host (fused_kernel.cu).
 struct FusedShape {
