@@ -299,10 +299,18 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       }
       const float m = fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)), fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
       if (find && m >= p.amax) {
+        // a pixel beaten inside its own 2x4 block (which lies inside its
+        // window) by the local-maximum rule can never be a candidate
         const float px[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
         const int npx = two ? 8 : 4;
         for (int e = 0; e < npx; ++e) {
-          if (px[e] >= p.amax) {
+          bool keep = px[e] >= p.amax;
+          for (int q = 0; q < npx && keep; ++q) {
+            const int dc = (q & 3) - (e & 3);
+            if (q == e || dc > p.rank || -dc > p.rank) continue;  // only pixels inside e's window
+            keep = q < e ? px[e] > px[q] : px[e] >= px[q];       // row-major order within the block
+          }
+          if (keep) {
             const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
             if (slot_t < kThrLocalCap) v.thr[slot_t] = (2 * i + (e >> 2)) * p.W + 4 * pr[k] + (e & 3);
           }
