@@ -287,16 +287,22 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       const float4 vb = two ? ring[(size_t)(2 * il[k] + 1) * NP + pr[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
       float v0, v1;
       bin_pair(va, vb, two, v0, v1);
-      const Quant q0 = prequantize(v0, p), q1 = prequantize(v1, p);
       const uint32_t j0 = 2 * pr[k];
-      *reinterpret_cast<int2*>(v.qbuf + (size_t)qs[k] * p.Wb + j0) = make_int2(q0.q, q1.q);
-      if (q0.outlier | q1.outlier) {
-        const uint32_t lb = i * p.Wb + j0;
-        atomicAdd(v.ctl + CTL_PQ, (uint32_t)q0.outlier + (uint32_t)q1.outlier);
-        atomicOr(v.mask + (lb >> 5), ((uint32_t)q0.outlier | ((uint32_t)q1.outlier << 1)) << (lb & 31));
-        if (q0.outlier) pq_bits[lb] = q0.outlier_bits;
-        if (q1.outlier) pq_bits[lb + 1] = q1.outlier_bits;
+      int32_t q0, q1;
+      const bool f0 = prequant_fast(v0, p, q0), f1 = prequant_fast(v1, p, q1);
+      if (!(f0 && f1)) {  // the screen could not decide: the full test (identical results)
+        const Quant Q0 = prequantize(v0, p), Q1 = prequantize(v1, p);
+        q0 = Q0.q;
+        q1 = Q1.q;
+        if (Q0.outlier | Q1.outlier) {
+          const uint32_t lb = i * p.Wb + j0;
+          atomicAdd(v.ctl + CTL_PQ, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
+          atomicOr(v.mask + (lb >> 5), ((uint32_t)Q0.outlier | ((uint32_t)Q1.outlier << 1)) << (lb & 31));
+          if (Q0.outlier) pq_bits[lb] = Q0.outlier_bits;
+          if (Q1.outlier) pq_bits[lb + 1] = Q1.outlier_bits;
+        }
       }
+      *reinterpret_cast<int2*>(v.qbuf + (size_t)qs[k] * p.Wb + j0) = make_int2(q0, q1);
       const float m = fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)), fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
       if (find && m >= p.amax) {
         // a pixel beaten inside its own 2x4 block (which lies inside its
@@ -340,19 +346,31 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
         if (j0 > 0) ql = cur[j0 - 1];
         const int32_t d0 = qc.x - qu.x - ql + qd;
         const int32_t d1 = qc.y - qu.y - qc.x + qu.x;
-        c0 = quant_code(d0, p.R);
-        c1 = quant_code(d1, p.R);
         const uint32_t lb = i * p.Wb + j0;
-        auto to_byte = [&](int32_t d, uint32_t c, uint32_t bin) -> uint32_t {
-          if (c == 0) {
-            lo_delta[bin] = d;
-            return 0u;
-          }
-          if (d >= -127 && d <= 126) return (uint32_t)(d + 128);
-          esc[bin] = (uint16_t)c;
-          return 255u;
-        };
-        const uint32_t b0 = to_byte(d0, c0, lb), b1 = to_byte(d1, c1, lb + 1);
+        // fast path: both residuals fit a code byte and the alphabet (one
+        // unsigned range test each): byte = residual + 128, code = residual + R
+        const bool fast = ((uint32_t)(d0 - p.d_lo) <= p.d_span) & ((uint32_t)(d1 - p.d_lo) <= p.d_span);
+        uint32_t b0, b1;
+        if (fast) {
+          c0 = (uint32_t)(d0 + p.R);
+          c1 = (uint32_t)(d1 + p.R);
+          b0 = (uint32_t)(d0 + 128);
+          b1 = (uint32_t)(d1 + 128);
+        } else {
+          c0 = quant_code(d0, p.R);
+          c1 = quant_code(d1, p.R);
+          auto to_byte = [&](int32_t d, uint32_t c, uint32_t bin) -> uint32_t {
+            if (c == 0) {
+              lo_delta[bin] = d;
+              return 0u;
+            }
+            if (d >= -127 && d <= 126) return (uint32_t)(d + 128);
+            esc[bin] = (uint16_t)c;
+            return 255u;
+          };
+          b0 = to_byte(d0, c0, lb);
+          b1 = to_byte(d1, c1, lb + 1);
+        }
         *reinterpret_cast<uint16_t*>(codes + lb) = (uint16_t)(b0 | (b1 << 8));  // lb is even
       }
       n_common += (c0 == (uint32_t)p.R) + (c1 == (uint32_t)p.R);

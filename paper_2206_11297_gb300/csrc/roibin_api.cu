@@ -117,6 +117,8 @@ DevParams make_dev_params(const roibin_geometry& g, const roibin_params& p) {
     d.eb_hi = INFINITY;
   }
   d.R = p.quant_radius;
+  d.d_lo = std::max(-127, -(p.quant_radius - 1));
+  d.d_span = (uint32_t)(std::min(126, p.quant_radius - 1) - d.d_lo);
   d.nsym = 2u * (uint32_t)p.quant_radius;
   d.max_peaks = (uint32_t)p.max_peaks;
   d.thr_cap = kThrCap;

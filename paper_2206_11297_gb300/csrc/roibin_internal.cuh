@@ -40,6 +40,8 @@ struct DevParams {
   int32_t roi_h, roi_w;
   float eb, two_eb, recip;  // two_eb = fl(2 eb), recip = fl(1 / two_eb)
   float eb_lo, eb_hi;       // screen of the bound test (see prequantize)
+  int32_t d_lo;             // residuals in [d_lo, d_lo + d_span] fit a code byte and the alphabet
+  uint32_t d_span;
   int32_t R;                // quant radius
   uint32_t nsym;            // 2R
   uint32_t max_peaks;
@@ -171,6 +173,15 @@ __device__ __forceinline__ Quant prequantize(float b, const DevParams& p) {
   r.q = out ? 0 : (int32_t)t;
   r.outlier_bits = isnan(b) ? kCanonicalNaN : __float_as_uint(b);
   return r;
+}
+
+// The common case of prequantize: true when the screen alone proves the bin
+// is not an outlier (then q is final); false sends the bin to prequantize.
+__device__ __forceinline__ bool prequant_fast(float b, const DevParams& p, int32_t& q) {
+  const float t = rintf(__fmul_rn(b, p.recip));
+  const float d = __fsub_rn(b, __fmul_rn(t, p.two_eb));
+  q = __float2int_rz(t);  // exact for the |t| < 2^28 the fast path accepts
+  return (fabsf(t) < kPqLimit) & (fabsf(d) < p.eb_lo);
 }
 
 // 2x2 bin pair from two float4 (4 pixels of raw row 2i and of row 2i+1):
