@@ -49,6 +49,20 @@ __device__ __forceinline__ uint64_t evict_first_policy() {
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
+__device__ __forceinline__ uint64_t evict_normal_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// 16-bit store that asks L2 to keep the line (code bytes wait there until packed)
+__device__ __forceinline__ void st_keep_u16(void* ptr, uint16_t v, uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(ptr), "h"(v), "l"(policy) : "memory");
+}
 // Drops a 128-byte line from L2 without writing it back (its contents are dead).
 __device__ __forceinline__ void discard_line(const void* ptr) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(ptr) : "memory");
@@ -225,7 +239,8 @@ __device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape&
 // ---------------------------------------------------------------------------
 // One panel: stream, code, list and evaluate candidates, flush.
 __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
-                              const StreamView& v, uint32_t f, uint32_t pn, uint64_t pol, uint32_t& ring_iter) {
+                              const StreamView& v, uint32_t f, uint32_t pn, uint64_t pol, uint64_t keep_pol,
+                              uint32_t& ring_iter) {
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   const uint32_t NP = p.W >> 2, Mp = p.Hb * p.Wb;
   const float* panel = a.frames + (size_t)f * p.frame_px + (size_t)pn * p.H * p.W;
@@ -371,7 +386,7 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
           b0 = to_byte(d0, c0, lb);
           b1 = to_byte(d1, c1, lb + 1);
         }
-        *reinterpret_cast<uint16_t*>(codes + lb) = (uint16_t)(b0 | (b1 << 8));  // lb is even
+        st_keep_u16(codes + lb, (uint16_t)(b0 | (b1 << 8)), keep_pol);  // lb is even
       }
       n_common += (c0 == (uint32_t)p.R) + (c1 == (uint32_t)p.R);
       const bool r0 = c0 != 0xFFFFu && c0 != (uint32_t)p.R, r1 = c1 != 0xFFFFu && c1 != (uint32_t)p.R;
@@ -740,16 +755,16 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
       uint32_t bits, nlo, npq;
       lane_counts(p, s, sh, g, btab, ctab, wbuf, s0, s1, any_pq, bits, nlo, npq);
       __syncwarp();
-      for (int d = 16; d > 0; d >>= 1) {
-        bits += __shfl_xor_sync(0xffffffffu, bits, d);
-        nlo += __shfl_xor_sync(0xffffffffu, nlo, d);
-        npq += __shfl_xor_sync(0xffffffffu, npq, d);
-      }
-      if (lane == 0) {
-        const size_t o = (size_t)g * p.n_chunks + k;
-        s.chunk_words[o] = (bits + 31) / 32;
-        s.chunk_lo[o] = nlo;
-        s.chunk_pq[o] = npq;
+      const uint32_t bit_incl = warp_incl_scan(bits), lo_incl = warp_incl_scan(nlo), pq_incl = warp_incl_scan(npq);
+      // where each lane's bits and outliers start inside the chunk, for the write items
+      const size_t o = (size_t)g * p.n_chunks + k;
+      s.lane_bit[o * 32 + lane] = bit_incl - bits;
+      s.lane_lo[o * 32 + lane] = lo_incl - nlo;
+      s.lane_pq[o * 32 + lane] = pq_incl - npq;
+      if (lane == 31) {
+        s.chunk_words[o] = (bit_incl + 31) / 32;
+        s.chunk_lo[o] = lo_incl;
+        s.chunk_pq[o] = pq_incl;
       }
     }
     __syncthreads();
@@ -883,16 +898,13 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     __syncwarp();
     const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
     stage_chunk(codes, k, wbuf);
-    uint32_t bits, nlo, npq;
-    lane_counts(p, s, sh, g, btab, ctab, wbuf, s0, s1, any_pq, bits, nlo, npq);
-    const uint32_t bit_incl = warp_incl_scan(bits), lo_incl = warp_incl_scan(nlo), pq_incl = warp_incl_scan(npq);
-    const uint32_t start = bit_incl - bits;
+    const uint32_t start = __ldcg(s.lane_bit + o * 32 + lane);
     uint32_t wi = w0 + start / 32;
     uint64_t accb = 0;
     uint32_t nacc = start & 31u;
     bool first = nacc != 0;  // the first word is shared with the previous lane
-    uint32_t lo_pos = __ldcg(s.chunk_lo + o) + lo_incl - nlo;
-    uint32_t pq_pos = __ldcg(s.chunk_pq + o) + pq_incl - npq;
+    uint32_t lo_pos = __ldcg(s.chunk_lo + o) + __ldcg(s.lane_lo + o * 32 + lane);
+    uint32_t pq_pos = __ldcg(s.chunk_pq + o) + __ldcg(s.lane_pq + o * 32 + lane);
     // append `len` (<= 32) bits, emitting each completed 32-bit word
     auto append = [&](uint32_t cw, uint32_t len) {
       accb |= (uint64_t)cw << (64 - nacc - len);
@@ -939,7 +951,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     }
     if (nacc > 0) atomicOr(words + wi, (uint32_t)(accb >> 32));  // shared with the next lane
     __syncwarp();
-    if (npq)
+    if (any_pq)
       for (uint32_t i = s0; i < s1; ++i)
         if (pq_bit_of(p, s, sh, g, i)) pq_out[pq_pos++] = make_uint2(i, __ldcg(pq_bits + i));
   }
@@ -955,13 +967,7 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     const uint32_t px = __ldcg(keys + k);
     const uint32_t pn = px / plane, rem = px - pn * plane;
     const int r = (int)(rem / p.W), c = (int)(rem % p.W);
-    const float* panel = frame + (size_t)pn * plane;
-    const int r0 = r - p.roi_h / 2, c0 = c - p.roi_w / 2;
-    for (uint32_t e = lane; e < win; e += 32) {
-      const int rr = r0 + (int)(e / p.roi_w), cc = c0 + (int)(e % p.roi_w);
-      const bool in = rr >= 0 && rr < (int)p.H && cc >= 0 && cc < (int)p.W;
-      roi[(size_t)k * win + e] = in ? __ldg(panel + (size_t)rr * p.W + cc) : 0.0f;
-    }
+    warp_copy_roi(frame + (size_t)pn * plane, p.H, p.W, r, c, p.roi_h, p.roi_w, roi + (size_t)k * win);
   }
   // this group's code bytes are dead: drop them from L2 without a write-back
   __syncthreads();
@@ -976,7 +982,10 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
   extern __shared__ __align__(128) unsigned char sm[];
   const StreamView sv = stream_view(sm, sh);
   const FinView fv = fin_view(sm, sh);
-  const uint64_t pol = evict_first_policy();
+  // input rows: normal L2 priority (the panel's peak tests re-read them soon);
+  // code bytes: evict-last until their chunk is packed (then discarded)
+  const uint64_t pol = sh.input_evict_first ? evict_first_policy() : evict_normal_policy();
+  const uint64_t keep_pol = evict_last_policy();
   const SyncWords sw = sync_words(s, a.n_frames);
   const uint32_t n = a.n_frames, lag = sh.lag, round = p.P + 2 * sh.groups;
   const uint64_t total = (uint64_t)(n + 2 * lag) * round;
@@ -996,7 +1005,7 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
     const uint32_t r = t / round, j = t - r * round;
     if (j < p.P) {
       if (r >= n) continue;
-      process_panel(p, s, a, sh, sv, r, j, pol, ring_iter);
+      process_panel(p, s, a, sh, sv, r, j, pol, keep_pol, ring_iter);
       // publish the panel; the CTA that completes the frame builds its codebook
       __threadfence();
       __syncthreads();

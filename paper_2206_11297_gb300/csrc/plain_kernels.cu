@@ -586,14 +586,7 @@ __global__ void __launch_bounds__(256) k_roi(DevParams p, Scratch s, PlainArgs a
   const float* panel = a.frames + (size_t)f * p.frame_px + (size_t)pn * p.H * p.W;
   float* dst = reinterpret_cast<float*>(a.out + (size_t)f * a.out_stride + pl.off_roi) +
                (size_t)k * p.roi_h * p.roi_w;
-  const int r0 = r - p.roi_h / 2, c0 = c - p.roi_w / 2;
-  const uint32_t win = (uint32_t)(p.roi_h * p.roi_w);
-  for (uint32_t e = lane_id(); e < win; e += 32) {
-    const int i = (int)(e / p.roi_w), j = (int)(e % p.roi_w);
-    const int rr = r0 + i, cc = c0 + j;
-    const bool in = rr >= 0 && rr < (int)p.H && cc >= 0 && cc < (int)p.W;
-    dst[e] = in ? __ldg(panel + (size_t)rr * p.W + cc) : 0.0f;
-  }
+  warp_copy_roi(panel, p.H, p.W, r, c, p.roi_h, p.roi_w, dst);
 }
 
 // last_peaks: peak lists of the last call as (panel, row, col) triples.

@@ -181,6 +181,9 @@ uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s
   t.peak_part = c.take<uint32_t>((uint64_t)n * d.P * std::max<uint32_t>(d.max_peaks, 1));
   t.peak_part_count = c.take<uint32_t>((uint64_t)n * d.P);
   t.pq_part_count = c.take<uint32_t>((uint64_t)n * d.P);
+  t.lane_bit = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
+  t.lane_lo = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
+  t.lane_pq = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
   t.frame_done = c.take<uint32_t>(4ull * n + 1);
   if (s) *s = t;
   return c.off + 256;

@@ -94,6 +94,9 @@ struct Scratch {
   uint32_t* peak_part;      // [n][P][max(max_peaks, 1)] per-panel sorted peaks
   uint32_t* peak_part_count;  // [n][P]
   uint32_t* pq_part_count;    // [n][P] prequantisation outliers per panel
+  uint32_t* lane_bit;         // [n][n_chunks][32] bit offset of each lane's symbols in its chunk
+  uint32_t* lane_lo;          // [n][n_chunks][32] Lorenzo outliers before the lane, in its chunk
+  uint32_t* lane_pq;          // [n][n_chunks][32] prequantisation outliers before the lane
   uint32_t* frame_done;     // [4 n + 1] stage counters and flags, ticket counter
 };
 
@@ -306,6 +309,28 @@ __device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int
                           H, W, r, c, p);
 }
 
+// One warp copies the roi_h x roi_w window centred on (r, c) of `panel` to
+// dst (fill 0 past the panel edge).  Loads are batched ahead of the stores.
+__device__ inline void warp_copy_roi(const float* __restrict__ panel, int H, int W, int r, int c, int roi_h,
+                                     int roi_w, float* dst) {
+  const int r0 = r - roi_h / 2, c0 = c - roi_w / 2, win = roi_h * roi_w;
+  const int lane = (int)lane_id();
+  for (int base = 0; base < win; base += 8 * 32) {
+    float vals[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * 32 + lane;
+      const int rr = r0 + e / roi_w, cc = c0 + e % roi_w;
+      vals[u] = (e < win && rr >= 0 && rr < H && cc >= 0 && cc < W) ? __ldg(panel + (size_t)rr * W + cc) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * 32 + lane;
+      if (e < win) dst[e] = vals[u];
+    }
+  }
+}
+
 // Reach of the neighbourhood a candidate needs: its window and its ring.
 __host__ __device__ inline int peak_reach(const DevParams& p) {
   const int ring = p.ring_r0 + p.ring_dr - 1;
@@ -323,9 +348,21 @@ __device__ inline bool warp_peak_test(const float* __restrict__ panel, int H, in
                                       const DevParams& p, float* nb, Load load) {
   const int reach = peak_reach(p), side = 2 * reach + 1, n = side * side;
   const uint32_t lane = lane_id();
-  for (int e = (int)lane; e < n; e += 32) {
-    const int rr = r + e / side - reach, cc = c + e % side - reach;
-    nb[e] = (rr >= 0 && rr < H && cc >= 0 && cc < W) ? load(panel + (size_t)rr * W + cc) : 0.0f;
+  // gather in batches: all loads of a batch are issued before any store, so
+  // the batch costs one memory latency instead of one per element
+  for (int base = 0; base < n; base += 8 * 32) {
+    float vals[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * 32 + (int)lane;
+      const int rr = r + e / side - reach, cc = c + e % side - reach;
+      vals[u] = (e < n && rr >= 0 && rr < H && cc >= 0 && cc < W) ? load(panel + (size_t)rr * W + cc) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * 32 + (int)lane;
+      if (e < n) nb[e] = vals[u];
+    }
   }
   __syncwarp();
   const float v = nb[reach * side + reach];
@@ -533,6 +570,7 @@ struct FusedShape {
   uint32_t codes_stride;         // code bytes per frame slot (n_chunks * kChunk)
   uint32_t group_chunks, groups; // chunks per size/write work item; items per frame
   uint32_t lag;                  // frames between stages in the ticket order (per launch)
+  uint32_t input_evict_first;    // L2 policy of the streamed rows (1 = evict first)
   uint32_t off_ctl, off_bar, off_hist, off_qbuf, off_mask, off_thr, off_ring, off_nb, off_acc;  // panel role
   uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw;     // codebook / plan roles
   uint32_t off_stage;                                                        // size / write roles
