@@ -892,17 +892,27 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
   for (uint32_t k = k_begin + warp; k < k_end; k += kPW) {
     const size_t o = (size_t)g * p.n_chunks + k;
     const uint32_t w0 = __ldcg(s.chunk_words + o);
-    const uint32_t w1 = k + 1 < p.n_chunks ? __ldcg(s.chunk_words + o + 1) : pl.n_words;
-    for (uint32_t w = w0 + lane; w < w1; w += 32) words[w] = 0;
-    __threadfence_block();
-    __syncwarp();
+    // In a full chunk every lane codes 128 symbols (>= 128 bits), so a word is
+    // shared by at most two neighbouring lanes: lane l keeps its first, partial
+    // word and ORs in lane l-1's last, partial word received by shuffle; every
+    // word is then written once.  The frame's last chunk may be partial: its
+    // words are zeroed and the shared ones merged with atomics.
+    const bool full = (k + 1) * kChunk <= p.M;
+    if (!full) {
+      const uint32_t w1 = pl.n_words;
+      for (uint32_t w = w0 + lane; w < w1; w += 32) words[w] = 0;
+      __threadfence_block();
+      __syncwarp();
+    }
     const uint32_t s0 = k * kChunk + lane * 128, s1 = min(p.M, s0 + 128);
     stage_chunk(codes, k, wbuf);
     const uint32_t start = __ldcg(s.lane_bit + o * 32 + lane);
-    uint32_t wi = w0 + start / 32;
+    const uint32_t first_idx = w0 + start / 32;
+    uint32_t wi = first_idx;
     uint64_t accb = 0;
     uint32_t nacc = start & 31u;
     bool first = nacc != 0;  // the first word is shared with the previous lane
+    uint32_t head = 0;       // full chunks: the shared first word, held back
     uint32_t lo_pos = __ldcg(s.chunk_lo + o) + __ldcg(s.lane_lo + o * 32 + lane);
     uint32_t pq_pos = __ldcg(s.chunk_pq + o) + __ldcg(s.lane_pq + o * 32 + lane);
     // append `len` (<= 32) bits, emitting each completed 32-bit word
@@ -911,8 +921,12 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
       nacc += len;
       if (nacc >= 32) {
         const uint32_t word = (uint32_t)(accb >> 32);
-        if (first) atomicOr(words + wi, word);
-        else words[wi] = word;
+        if (first) {
+          if (full) head = word;
+          else atomicOr(words + wi, word);
+        } else {
+          words[wi] = word;
+        }
         first = false;
         ++wi;
         accb <<= 32;
@@ -949,7 +963,14 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
         if (b == 0) lo_out[lo_pos++] = make_uint2(bin, (uint32_t)__ldcg(lo_delta + bin));
       }
     }
-    if (nacc > 0) atomicOr(words + wi, (uint32_t)(accb >> 32));  // shared with the next lane
+    if (full) {
+      const uint32_t tail = nacc > 0 ? (uint32_t)(accb >> 32) : 0u;  // shared with the next lane
+      const uint32_t prev_tail = __shfl_up_sync(0xffffffffu, tail, 1);
+      if ((start & 31u) != 0) words[first_idx] = head | prev_tail;
+      if (lane == 31 && nacc > 0) words[wi] = tail;  // the chunk's last word, zero padded
+    } else if (nacc > 0) {
+      atomicOr(words + wi, (uint32_t)(accb >> 32));  // shared with the next lane
+    }
     __syncwarp();
     if (any_pq)
       for (uint32_t i = s0; i < s1; ++i)
