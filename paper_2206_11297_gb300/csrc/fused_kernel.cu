@@ -173,7 +173,7 @@ struct StreamView {
   uint32_t* hist;  // [nsym]
   int32_t* qbuf;   // [qrows][Wb], circular by binned row
   uint32_t* mask;  // [mask_words] prequantisation-outlier bits of the panel
-  uint32_t* thr;   // [kThrLocalCap] pixels >= amax_thr (panel-local index)
+  uint32_t* thr;   // [kThrLocalCap] 2x4 blocks holding a pixel >= amax_thr (first pixel, panel-local)
   float* nb;       // [kPW][side^2] peak-test neighbourhoods (aliases the ring)
   uint32_t* acc;   // [sort_n2] accepted peaks of the panel (aliases the ring)
   uint32_t* ctl;
@@ -319,23 +319,9 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       }
       *reinterpret_cast<int2*>(v.qbuf + (size_t)qs[k] * p.Wb + j0) = make_int2(q0, q1);
       const float m = fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)), fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
-      if (find && m >= p.amax) {
-        // a pixel beaten inside its own 2x4 block (which lies inside its
-        // window) by the local-maximum rule can never be a candidate
-        const float px[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-        const int npx = two ? 8 : 4;
-        for (int e = 0; e < npx; ++e) {
-          bool keep = px[e] >= p.amax;
-          for (int q = 0; q < npx && keep; ++q) {
-            const int dc = (q & 3) - (e & 3);
-            if (q == e || dc > p.rank || -dc > p.rank) continue;  // only pixels inside e's window
-            keep = q < e ? px[e] > px[q] : px[e] >= px[q];       // row-major order within the block
-          }
-          if (keep) {
-            const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
-            if (slot_t < kThrLocalCap) v.thr[slot_t] = (2 * i + (e >> 2)) * p.W + 4 * pr[k] + (e & 3);
-          }
-        }
+      if (find && m >= p.amax) {  // rare: list the 2x4 block, its pixels are screened later
+        const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
+        if (slot_t < kThrLocalCap) v.thr[slot_t] = 2 * i * p.W + 4 * pr[k];
       }
     }
     __syncthreads();  // the slot is consumed: refill it with the stage S steps ahead
@@ -429,7 +415,28 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       }
     };
     if (cnt <= kThrLocalCap) {
-      for (uint32_t e = warp; e < cnt; e += kPW) test(v.thr[e]);
+      // each listed 2x4 block: a pixel beaten inside its own block (which lies
+      // inside its window) by the local-maximum rule can never be a candidate
+      for (uint32_t e = warp; e < cnt; e += kPW) {
+        const uint32_t key = v.thr[e], r0 = key / p.W, c0 = key - r0 * p.W;
+        const uint32_t npx = r0 + 1 < p.H ? 8u : 4u;
+        const uint32_t me = lane & 7u;
+        const float x = me < npx ? __ldg(panel + (size_t)(r0 + (me >> 2)) * p.W + c0 + (me & 3u)) : 0.0f;
+        bool keep = lane < npx && x >= p.amax;
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) {
+          const float y = __shfl_sync(0xffffffffu, x, q);
+          const int dc = (int)(q & 3u) - (int)(me & 3u);
+          if (q == me || q >= npx || dc > p.rank || -dc > p.rank) continue;
+          if (q < me ? !(x > y) : !(x >= y)) keep = false;
+        }
+        uint32_t m = __ballot_sync(0xffffffffu, keep);
+        while (m) {
+          const uint32_t l = __ffs(m) - 1;
+          m &= m - 1;
+          test(key + (l >> 2) * p.W + (l & 3u));
+        }
+      }
     } else {
       const uint32_t plane = p.H * p.W;
       for (uint32_t base = warp * 32; base < plane; base += kPW * 32) {

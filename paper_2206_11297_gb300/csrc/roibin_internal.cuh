@@ -337,16 +337,129 @@ __host__ __device__ inline int peak_reach(const DevParams& p) {
   return p.rank > ring ? p.rank : ring;
 }
 
-// One warp tests and evaluates the pixel (r, c) of `panel` (a1 + a2).  The
-// lanes stage its (2 reach + 1)^2 neighbourhood in `nb` (per-warp shared
-// memory) with one round of independent loads, test the local-maximum rule
-// in parallel (pure comparisons), and lane 0 runs the fp64 evaluation in its
-// fixed order.  `load(addr)` reads global memory (plain or L2-only).  Every
-// lane returns the same answer.
+// Sum of buf[0 .. n) in index order, one rounding per add.  Every lane runs
+// the same chain on broadcast shared-memory reads, eight loads ahead.
+__device__ __forceinline__ float ordered_sum(const float* buf, int n) {
+  float s = 0.0f;
+  for (int k0 = 0; k0 < n; k0 += 8) {
+    float t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = k0 + u < n ? buf[k0 + u] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u < n) s = __fadd_rn(s, t[u]);
+  }
+  return s;
+}
+// Sum of (buf[k] - m)^2 over k in [0, n), in index order.
+__device__ __forceinline__ float ordered_sq_dev(const float* buf, int n, float m) {
+  float s = 0.0f;
+  for (int k0 = 0; k0 < n; k0 += 8) {
+    float t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = k0 + u < n ? buf[k0 + u] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u < n) {
+        const float d = __fsub_rn(t[u], m);
+        s = __fadd_rn(s, __fmul_rn(d, d));
+      }
+  }
+  return s;
+}
+
+// One warp tests and evaluates the pixel (r, c) of `panel` (a1 + a2) when its
+// neighbourhood has at most 256 pixels (reach <= 7).  Lane l holds the pixels
+// l, l + 32, ... of the (2 reach + 1)^2 square in row-major order, loaded in
+// one round.  The local-maximum rule is checked on those registers.  The ring
+// pixels, then the window pixels above threshold, are compacted in row-major
+// order into `buf` (per-warp shared memory, (2 reach + 1)^2 floats) and summed
+// there in that order, so the float32 results equal evaluate_peak_at's.
+template <class Load>
+__device__ __noinline__ bool warp_peak_test_small(const float* __restrict__ panel, int H, int W, int r, int c,
+                                                  const DevParams& p, float* buf, Load load) {
+  const int reach = peak_reach(p), side = 2 * reach + 1, n = side * side;
+  const int lane = (int)lane_id();
+  const int in2 = p.ring_r0 * p.ring_r0, out2 = (p.ring_r0 + p.ring_dr) * (p.ring_r0 + p.ring_dr);
+  float x[8];
+  uint32_t ring = 0, win = 0, before = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int e = u * 32 + lane;
+    const int dr = e / side - reach, dc = e - (e / side) * side - reach;
+    const int rr = r + dr, cc = c + dc;
+    const bool in = e < n && rr >= 0 && rr < H && cc >= 0 && cc < W;
+    x[u] = in ? load(panel + (size_t)rr * W + cc) : 0.0f;
+    const int d2 = dr * dr + dc * dc;
+    ring |= (uint32_t)(in && d2 >= in2 && d2 < out2) << u;
+    win |= (uint32_t)(in && dr >= -p.rank && dr <= p.rank && dc >= -p.rank && dc <= p.rank) << u;
+    before |= (uint32_t)(dr < 0 || (dr == 0 && dc < 0)) << u;
+  }
+  // the centre pixel e = reach * side + reach
+  const int ec = reach * side + reach;
+  float mine = 0.0f;
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    if (u == (ec >> 5)) mine = x[u];
+  const float v = __shfl_sync(0xffffffffu, mine, ec & 31);
+  bool ok = v >= p.amax;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if (!((win >> u) & 1u) || u * 32 + lane == ec) continue;
+    if ((before >> u) & 1u ? !(v > x[u]) : !(v >= x[u])) ok = false;
+  }
+  if (!__all_sync(0xffffffffu, ok)) return false;
+  // ring pixels in row-major order
+  int nr = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const bool b = (ring >> u) & 1u;
+    const uint32_t m = __ballot_sync(0xffffffffu, b);
+    if (b) buf[nr + __popc(m & lanemask_lt())] = x[u];
+    nr += __popc(m);
+  }
+  __syncwarp();
+  float bkg = 0.0f, var = 0.0f;
+  if (nr > 0) {
+    bkg = __fdiv_rn(ordered_sum(buf, nr), (float)nr);
+    var = __fdiv_rn(ordered_sq_dev(buf, nr, bkg), (float)nr);
+  }
+  const float sigma = __fsqrt_rn(var);
+  const float thr = __fmul_rn(p.pix_nsigma, sigma);
+  __syncwarp();
+  // window pixels above threshold, in row-major order
+  int npix = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const float d = __fsub_rn(x[u], bkg);
+    const bool b = ((win >> u) & 1u) && d > thr;
+    const uint32_t m = __ballot_sync(0xffffffffu, b);
+    if (b) buf[npix + __popc(m & lanemask_lt())] = d;
+    npix += __popc(m);
+  }
+  __syncwarp();
+  bool keep = npix >= p.npix_min && npix <= p.npix_max;
+  if (keep) {
+    const float atot = ordered_sum(buf, npix);
+    const float noise = __fmul_rn(__fmul_rn(p.son_min, sigma), __fsqrt_rn((float)npix));
+    keep = atot > p.atot_thr && atot > noise;
+  }
+  __syncwarp();
+  return keep;
+}
+
+// One warp tests and evaluates the pixel (r, c) of `panel` (a1 + a2).  Small
+// neighbourhoods (the usual case) run warp_peak_test_small; larger ones are
+// staged in `nb` (per-warp shared memory, (2 reach + 1)^2 floats) with one
+// round of independent loads, the local-maximum rule is tested
+// in parallel, and lane 0 runs the evaluation in its fixed order.
+// `load(addr)` reads global memory (plain or L2-only).  Every lane returns
+// the same answer.
 template <class Load>
 __device__ inline bool warp_peak_test(const float* __restrict__ panel, int H, int W, int r, int c,
                                       const DevParams& p, float* nb, Load load) {
   const int reach = peak_reach(p), side = 2 * reach + 1, n = side * side;
+  if (n <= 256) return warp_peak_test_small(panel, H, W, r, c, p, nb, load);
   const uint32_t lane = lane_id();
   // gather in batches: all loads of a batch are issued before any store, so
   // the batch costs one memory latency instead of one per element
