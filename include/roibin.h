@@ -245,6 +245,44 @@ int roibin_ctx_kernel_times(roibin_ctx* ctx, const char** names, double* total_m
 /* Number of kernel launches the last compress call enqueued. */
 uint32_t roibin_ctx_last_launch_count(const roibin_ctx* ctx);
 
+/* Bytes of device memory the library sets aside, per device, for
+ * roibin_compress_frame_static (a fixed array in its device code). */
+#define ROIBIN_STATIC_SCRATCH_BYTES (16ull << 20)
+
+/* Compresses ONE frame with the per-stage kernels, taking its scratch from a
+ * fixed area in the library's static device memory: this call allocates
+ * nothing (no cudaMalloc, no allocating library routine).  It is for callers
+ * that cannot allocate at the point of the call: the allocator may
+ * synchronise the device and stall other streams, a process may run under a
+ * hard memory budget that was spent up front, or the caller holds no
+ * context object.  The paper has no counterpart of this call; it produces the
+ * same bytes as roibin_compress on a one-frame batch.
+ *   g, p            geometry and parameters (validated on every call).
+ *   d_frame         float32[P][H][W] on the current device, 16-byte aligned.
+ *   d_peaks,d_npeaks optional caller-supplied peak list as in roibin_compress
+ *                   (u16[max_peaks][3] and one u32), both or neither.
+ *   d_out           u8[out_capacity], 16-byte aligned; out_capacity a
+ *                   multiple of 16 (roibin_compress_bound is always enough).
+ *   d_frame_bytes   u64, d_frame_status i32: as roibin_compress for one frame.
+ *   stream          cudaStream_t (0 = legacy default stream).
+ * Limit: the frame's scratch (about 10 bytes per bin plus the peak and
+ * codebook tables) must fit ROIBIN_STATIC_SCRATCH_BYTES; otherwise the call
+ * returns ROIBIN_ERR_OUT_OF_BUDGET before touching the GPU.  A 32 x 185 x 388
+ * frame at bin 2x2 needs about 7.3 MB.
+ * Setup: the first call on each device looks the area's address up
+ * (cudaGetSymbolAddress) with that device current, which may load the
+ * library's device code; make one call per device before any stream capture
+ * or latency-critical section.  ROIBIN_ERR_CUDA if the lookup fails.
+ * Nothing has to start at zero: the call's first kernel clears the counters
+ * the later ones accumulate into.
+ * Overlap: every call on a device uses the same area, so two calls in flight
+ * at once on one device (other streams, other threads) corrupt each other's
+ * results.  The caller orders them (one stream, or events between streams). */
+int roibin_compress_frame_static(const roibin_geometry* g, const roibin_params* p, const float* d_frame,
+                                 const uint16_t* d_peaks, const uint32_t* d_npeaks, uint8_t* d_out,
+                                 uint64_t out_capacity, uint64_t* d_frame_bytes, int32_t* d_frame_status,
+                                 void* stream);
+
 /* Human-readable text for a status code (static string). */
 const char* roibin_status_string(int status);
 

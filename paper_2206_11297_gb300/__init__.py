@@ -14,7 +14,7 @@ from . import _build
 
 __all__ = ["Geometry", "Params", "Context", "library", "default_params", "validate",
            "compress_bound", "status_string", "GEOMETRIES", "PATH_AUTO", "PATH_PLAIN",
-           "PATH_FUSED", "EXPORTED_SYMBOLS"]
+           "PATH_FUSED", "EXPORTED_SYMBOLS", "compress_frame_static", "STATIC_SCRATCH_BYTES"]
 
 OK = 0
 ERR_INVALID_ARG = -1
@@ -79,6 +79,7 @@ _SIGNATURES = {
                                                ctypes.POINTER(ctypes.c_int)]),
     "roibin_ctx_last_launch_count": (_u32, [_P]),
     "roibin_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "roibin_compress_frame_static": (ctypes.c_int, [_G, _Pr, _P, _P, _P, _P, _u64, _P, _P, _P]),
 }
 EXPORTED_SYMBOLS = sorted(_SIGNATURES)
 
@@ -140,6 +141,20 @@ def validate(geometry, params: Params) -> int:
 def compress_bound(geometry, params: Params) -> int:
     g = Geometry(*geometry)
     return int(library().roibin_compress_bound(ctypes.byref(g), ctypes.byref(params)))
+
+
+STATIC_SCRATCH_BYTES = 16 << 20
+
+
+def compress_frame_static(geometry, params: Params, frame, out, frame_bytes, status, peaks=None,
+                          npeaks=None, stream=None):
+    """roibin_compress_frame_static: one CUDA float32 [P, H, W] frame into the caller's
+    buffers (out u8 [capacity], frame_bytes int64 [1], status int32 [1]) with the
+    library's static scratch; allocates nothing.  Asynchronous on `stream`."""
+    g = Geometry(*geometry)
+    _check("roibin_compress_frame_static", library().roibin_compress_frame_static(
+        ctypes.byref(g), ctypes.byref(params), _ptr(frame), _ptr(peaks), _ptr(npeaks), _ptr(out),
+        out.numel(), _ptr(frame_bytes), _ptr(status), _stream_handle(stream)))
 
 
 def _ptr(t):

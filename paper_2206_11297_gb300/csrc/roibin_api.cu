@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -273,6 +274,27 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
     return cuda_status(e);
   }
   return compress_plain(ctx, a, st);
+}
+
+// The fixed scratch area of roibin_compress_frame_static, one per device (a
+// module global exists once in every device context that loads the library).
+__device__ __align__(256) unsigned char g_static_scratch[ROIBIN_STATIC_SCRATCH_BYTES];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_base[kStaticMaxDevices] = {};
+
+// Address of the current device's area; looked up once per device.
+cudaError_t static_scratch_base(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_base[device]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_base[device] = ptr;
+  }
+  *out = g_static_base[device];
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -620,6 +642,56 @@ int roibin_ctx_kernel_times(roibin_ctx* ctx, const char** names, double* total_m
 }
 
 uint32_t roibin_ctx_last_launch_count(const roibin_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int roibin_compress_frame_static(const roibin_geometry* g, const roibin_params* p, const float* d_frame,
+                                 const uint16_t* d_peaks, const uint32_t* d_npeaks, uint8_t* d_out,
+                                 uint64_t out_capacity, uint64_t* d_frame_bytes, int32_t* d_frame_status,
+                                 void* stream) {
+  const int v = validate_impl(g, p);
+  if (v != ROIBIN_OK) return v;
+  if (!d_frame || !d_out || !d_frame_bytes || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
+  if ((d_peaks == nullptr) != (d_npeaks == nullptr)) return ROIBIN_ERR_INVALID_ARG;
+  if (out_capacity < 16 || out_capacity % 16 != 0) return ROIBIN_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_frame) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0)
+    return ROIBIN_ERR_INVALID_ARG;
+  const DevParams dp = make_dev_params(*g, *p);
+  if (carve_scratch(dp, 1, nullptr, nullptr) > ROIBIN_STATIC_SCRATCH_BYTES) return ROIBIN_ERR_OUT_OF_BUDGET;
+  int device = 0, sms = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kStaticMaxDevices) return ROIBIN_ERR_CUDA;
+  void* base = nullptr;
+  if (static_scratch_base(device, &base) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  Scratch s{};
+  carve_scratch(dp, 1, static_cast<uint8_t*>(base), &s);
+  PlainArgs a{};
+  a.frames = d_frame;
+  a.n_frames = 1;
+  a.user_peaks = d_peaks;
+  a.user_npeaks = d_npeaks;
+  a.out = d_out;
+  a.out_stride = out_capacity;
+  a.frame_bytes = d_frame_bytes;
+  a.frame_status = d_frame_status;
+  // one frame: split each panel into bands so that the grid covers the GPU
+  a.rows_per_step = std::max<uint32_t>(1, std::min<uint32_t>(16, 2048 / std::max<uint32_t>(dp.Wb, 1)));
+  const uint32_t target = 4u * (uint32_t)std::max(sms, 1);
+  a.bands_per_panel = std::min<uint32_t>(dp.P < target ? ceil_div(target, dp.P) : 1u,
+                                         std::max<uint32_t>(1, ceil_div(dp.Hb, 2)));
+  a.peaks_key_out = s.peak_key;
+  a.peaks_count_out = s.peak_count;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = launch_reset(dp, s, 1, st)) != cudaSuccess) return cuda_status(e);
+  if ((e = launch_stream(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
+  if (!a.user_peaks && (e = launch_peaks(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
+  if ((e = launch_peaks_final(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
+  if ((e = launch_huffman(dp, s, 1, st)) != cudaSuccess) return cuda_status(e);
+  if ((e = launch_chunks(dp, s, 1, st)) != cudaSuccess) return cuda_status(e);
+  if ((e = launch_plan(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
+  if ((e = launch_encode(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
+  if (dp.max_peaks > 0 && (e = launch_roi(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
+  return ROIBIN_OK;
+}
 
 const char* roibin_status_string(int status) {
   switch (status) {

@@ -1,0 +1,64 @@
+"""roibin_compress_frame_static, the one entry point that allocates nothing:
+it must give the same bytes as roibin_compress on a one-frame batch, call
+after call, and refuse frames whose scratch does not fit its fixed area."""
+import numpy as np
+import pytest
+
+import paper_2206_11297_gb300 as rb
+from synthetic import RECIPES, FrameRecipe, make_frame
+
+
+def test_oversized_frame_is_refused_before_any_gpu_work():
+    # 2 x 1024 x 1024 at bin 1x1: about 10 bytes per bin, well over the fixed area
+    p = rb.default_params(bin_h=1, bin_w=1)
+    g = rb.Geometry(2, 1024, 1024)
+    assert rb.validate((2, 1024, 1024), p) == rb.OK
+    lib = rb.library()
+    fake = 1 << 20  # never dereferenced: the size check comes first
+    code = lib.roibin_compress_frame_static(
+        rb.ctypes.byref(g), rb.ctypes.byref(p), rb.ctypes.c_void_p(fake), None, None,
+        rb.ctypes.c_void_p(fake), 1 << 20, rb.ctypes.c_void_p(fake), rb.ctypes.c_void_p(fake), None)
+    assert code == rb.ERR_OUT_OF_BUDGET
+
+
+def _static_vs_context(geometry, frame, params):
+    import torch
+    d = torch.from_numpy(np.ascontiguousarray(frame)).cuda()
+    with rb.Context(geometry, params, max_frames=1) as ctx:
+        ctx.set_path(rb.PATH_PLAIN)
+        ref, ref_n, ref_st = ctx.compress(d[None])
+        torch.cuda.synchronize()
+        cap = ctx.bound
+    ref_n, ref_st = int(ref_n.item()), int(ref_st.item())
+    assert ref_st == rb.OK
+    expect = ref[0, :ref_n].cpu().numpy()
+    out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    nb = torch.empty(1, dtype=torch.int64, device="cuda")
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    for call in range(2):  # two calls in a row reuse the same area
+        out.fill_(0xAA)
+        rb.compress_frame_static(geometry, params, d, out, nb, st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == rb.OK, f"call {call}"
+        assert int(nb.item()) == ref_n, f"call {call}"
+        assert np.array_equal(out[:ref_n].cpu().numpy(), expect), f"call {call}: bytes differ"
+
+
+@pytest.mark.gpu
+def test_static_scratch_matches_context_cspad():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    r = RECIPES["cspad_single"]
+    _static_vs_context(r.geometry, make_frame(r, 0), rb.default_params())
+
+
+@pytest.mark.gpu
+def test_static_scratch_matches_context_small_and_odd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    geom = (3, 45, 62)
+    r = FrameRecipe(geom, peaks=("uniform", 5, 20), seed=11)
+    p = rb.default_params(atot_thr=300.0, bin_h=3, bin_w=2)
+    _static_vs_context(geom, make_frame(r, 1), p)
