@@ -34,6 +34,11 @@ from synthetic import RECIPES, make_batch_threaded, make_frame  # noqa: E402
 
 WORKLOAD = "cspad_batch"
 N_FRAMES = 1000
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per frame of the
+# current k_fused, from one ncu capture of 100 frames of this workload; traffic
+# grows with the frame count, so a launch moves this many bytes per frame.
+# None whenever the kernel has changed since the capture.
+FUSED_DRAM_BYTES_PER_FRAME = 11.008e6
 
 
 def parse():
@@ -330,7 +335,9 @@ def run_ours(args, rank, local, world):
         "compression_ratio": {"vs_f32": n * frame_bytes / r["out_bytes"],
                               "vs_u16": n * frame_bytes / 2 / r["out_bytes"]},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": (FUSED_DRAM_BYTES_PER_FRAME * n
+                                 if kname == "fused" and FUSED_DRAM_BYTES_PER_FRAME else None),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in r["kernels"].items()},
         "gpu_launches": r["launches"],
