@@ -66,8 +66,8 @@ extern "C" {
 /* ---- execution paths for roibin_compress ----------------------------- */
 #define ROIBIN_PATH_AUTO 0  /* fused when the geometry allows it, else plain          */
 #define ROIBIN_PATH_PLAIN 1 /* one kernel per stage, intermediates in device memory  */
-#define ROIBIN_PATH_FUSED 2 /* one persistent kernel per batch: (frame, panel) work
-                               items, the last CTA of a frame finalises it          */
+#define ROIBIN_PATH_FUSED 2 /* one persistent kernel per batch: work items of a few
+                               panels each, then each frame's coding stages        */
 
 typedef struct roibin_ctx roibin_ctx;
 
@@ -131,14 +131,15 @@ uint64_t roibin_ctx_scratch_bytes(const roibin_ctx* ctx);
 
 /* Selects the kernel path for later roibin_compress calls (ROIBIN_PATH_*).
  * ROIBIN_ERR_INVALID_ARG when FUSED is asked for a shape it does not cover
- * (it needs bin 2x2 and cols % 4 == 0).  Both paths write identical bytes. */
+ * (it needs bin 2x2, cols % 4 == 0 and cols <= 1024).  Both paths write
+ * identical bytes. */
 int roibin_ctx_set_path(roibin_ctx* ctx, int path);
 /* The path AUTO resolves to for this context (PLAIN or FUSED). */
 int roibin_ctx_resolved_path(const roibin_ctx* ctx);
 
 /* Tuning hook of the fused path: ctas_per_sm resident CTAs per SM (1..8,
  * capped by what fits) stream rows_per_step binned rows per step (0 = the
- * default for the geometry, else 1..16) through a ring of `stages` TMA
+ * most that fits the shared memory, else 2 or 3) through a ring of `stages` TMA
  * bulk-copy slots (1..8).  ROIBIN_ERR_INVALID_ARG when the shape does not fit
  * or the context has no fused path; the previous shape is then kept.
  * Results are identical for every shape; only speed changes. */
@@ -155,9 +156,10 @@ int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_
  * start, 4 plan done (head written); summed over the frame's chunk items:
  * 5 size items, 6 write items, 7 size waits, 8 write waits, 9 size chunk
  * loops, 10 write chunk loops, 11 write ROI copies (12..15 unused).  After
- * the n_frames * 16 words, every panel item (f, p) of a traced frame writes 4
- * stamps at index n_frames * 16 + (f * P + p) * 4: start, streaming done,
- * peaks done (3 unused).  The caller zeroes d_trace before the call and owns
+ * the n_frames * 16 words, every streaming item u of a traced frame f (items
+ * are groups of consecutive panels, fewer than P per frame) writes 4 stamps
+ * at index n_frames * 16 + (f * P + u) * 4: start, streaming done, peaks done
+ * (3 unused; slots of items that do not exist stay zero).  The caller zeroes d_trace before the call and owns
  * it (device u64[n_frames * (16 + 4 P)]); n_frames = 0 switches tracing off.
  */
 int roibin_ctx_set_trace(roibin_ctx* ctx, uint64_t* d_trace, uint32_t n_frames);

@@ -1,18 +1,22 @@
 // fused_kernel.cu - the persistent batched kernel: the whole method for a
 // batch of frames in one launch.
 //
-// Work items are (frame, panel) pairs handed out in order by an atomic
-// counter to a grid of resident CTAs (several per SM).  For its panel a CTA:
-//   - streams the raw rows (16-byte loads, L2 evict-first, the next step's
-//     loads in flight while the current step is coded), bins them,
-//     prequantises, predicts with the 2-D Lorenzo rule and writes one byte per
-//     bin (byte = residual + 128 for residuals in [-127, 126], 0 = Lorenzo
+// Work items are handed out in order by an atomic ticket counter to a grid of
+// resident CTAs (several per SM).  A streaming item is a group of k panels of
+// one frame side by side (k NP <= 256 float4 columns, NP = cols / 4).  For it
+// a CTA:
+//   - streams the raw rows through a ring of 1-D TMA bulk copies (L2
+//     evict-first) while the previous rows are coded;
+//   - walks down the rows with one thread per float4 column (two bins per
+//     binned row): bins, prequantises, predicts with the 2-D Lorenzo rule from
+//     registers (row above) and shuffles (bin to the left) and writes one byte
+//     per bin (byte = residual + 128 for residuals in [-127, 126], 0 = Lorenzo
 //     outlier, 255 = escape whose code sits in a side array);
-//   - keeps the panel's histogram, prequantisation-outlier bits and pixels
-//     >= amax_thr in shared memory and flushes them to per-(frame, panel)
-//     slots with plain stores (no zeroing, no cross-CTA atomics);
-//   - tests and evaluates the panel's candidates right away, while its rows
-//     are still in L2, and stores its sorted peak list.
+//   - keeps the item's histogram, prequantisation-outlier bits and the 2x4
+//     blocks holding a pixel >= amax_thr in shared memory and flushes them to
+//     per-item and per-panel slots with plain stores;
+//   - screens the listed blocks, tests and evaluates the surviving candidates
+//     and stores its sorted peak list.
 // The rest of a frame's work (codebook, chunk sizes, layout, bit-packing)
 // runs as later work items of the same kernel (see the stages below), so the
 // latency-bound coding of earlier frames overlaps the HBM-bound streaming of
@@ -20,15 +24,20 @@
 // write-back.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "roibin_internal.cuh"
 
 namespace roibin {
 
 constexpr int kPT = 256;       // threads per CTA
 constexpr int kPW = kPT / 32;  // warps per CTA
-constexpr int kItems = 2;      // bin-pair items per thread per step
+constexpr uint32_t kMaxK = 8;   // panels per streaming item
+constexpr uint32_t kConsumerWarps = 7;  // warps that code rows (31 columns each)
+constexpr uint32_t kProducerWarp = 7;   // the warp whose lane 0 issues the row copies
 constexpr uint32_t kThrLocalCap = 512;
-constexpr uint32_t kPanelTimedOut = 0xFFFFFFFFu;  // per-panel peak count of a panel whose rows never arrived
+constexpr uint32_t kLagSize = 128, kLagWrite = 16;  // see launch_fused
+constexpr uint32_t kPanelTimedOut = 0xFFFFFFFFu;  // peak count of an item whose rows never arrived
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -63,6 +72,13 @@ __device__ __forceinline__ uint64_t evict_last_policy() {
 __device__ __forceinline__ void st_keep_u16(void* ptr, uint16_t v, uint64_t policy) {
   asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(ptr), "h"(v), "l"(policy) : "memory");
 }
+// The same, predicated on `pred` inside the instruction (no branch).
+__device__ __forceinline__ void st_keep_u16_if(void* ptr, uint16_t v, uint64_t policy, bool pred) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n @q st.global.L2::cache_hint.u16 [%0], %1, %2;\n}\n" ::"l"(ptr),
+      "h"(v), "l"(policy), "r"((uint32_t)pred)
+      : "memory");
+}
 // Drops a 128-byte line from L2 without writing it back (its contents are dead).
 __device__ __forceinline__ void discard_line(const void* ptr) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(ptr) : "memory");
@@ -78,6 +94,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
@@ -171,14 +190,13 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
 // one allocation; the control words sit in front of both.
 struct StreamView {
   uint32_t* hist;  // [nsym]
-  int32_t* qbuf;   // [qrows][Wb], circular by binned row
-  uint32_t* mask;  // [mask_words] prequantisation-outlier bits of the panel
-  uint32_t* thr;   // [kThrLocalCap] 2x4 blocks holding a pixel >= amax_thr (first pixel, panel-local)
+  uint32_t* mask;  // [k][mask_words] prequantisation-outlier bits of the item's panels
+  uint32_t* thr;   // [kThrLocalCap] 2x4 blocks holding a pixel >= amax_thr (first pixel, item-local)
   float* nb;       // [kPW][side^2] peak-test neighbourhoods (aliases the ring)
-  uint32_t* acc;   // [sort_n2] accepted peaks of the panel (aliases the ring)
+  uint32_t* acc;   // [sort_n2] accepted peaks of the item (aliases the ring)
   uint32_t* ctl;
   unsigned char* ring;  // [stages][stage_bytes] raw rows in flight
-  uint64_t* bars;       // [stages] one mbarrier per ring slot
+  uint64_t* bars;       // [2 stages] per ring slot: rows landed, slot released
 };
 struct FinView {
   HuffSmem* hs;
@@ -189,6 +207,7 @@ struct FinView {
   uint32_t* cw;    // [n_chunks] chunk words -> word offsets; then lo, pq
   uint32_t* clo;
   uint32_t* cpq;
+  uint32_t* offs;  // [U] offset of each item's peaks in the frame list
   uint32_t* ctl;
 };
 enum {
@@ -201,18 +220,17 @@ enum {
   CTL_CARRY0,
   CTL_CARRY1,
   CTL_CARRY2,
-  CTL_PQ,
   CTL_WAIT,
   CTL_TIMEOUT,
-  CTL_TMP,
-  CTL_OFFS = CTL_TMP + 33,  // per-panel peak offsets (first 1024 panels)
-  CTL_WORDS = CTL_OFFS + 1024
+  CTL_NZ,                       // codes other than the zero residual's in the item
+  CTL_PQ,                       // [kMaxK] prequantisation outliers per panel of the item
+  CTL_TMP = CTL_PQ + kMaxK,
+  CTL_WORDS = CTL_TMP + 33
 };
 
 __device__ __forceinline__ StreamView stream_view(unsigned char* sm, const FusedShape& sh) {
   StreamView v;
   v.hist = reinterpret_cast<uint32_t*>(sm + sh.off_hist);
-  v.qbuf = reinterpret_cast<int32_t*>(sm + sh.off_qbuf);
   v.mask = reinterpret_cast<uint32_t*>(sm + sh.off_mask);
   v.thr = reinterpret_cast<uint32_t*>(sm + sh.off_thr);
   v.nb = reinterpret_cast<float*>(sm + sh.off_nb);
@@ -232,184 +250,282 @@ __device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape&
   v.cw = reinterpret_cast<uint32_t*>(sm + sh.off_cw);
   v.clo = v.cw + sh.n_chunks;
   v.cpq = v.clo + sh.n_chunks;
+  v.offs = reinterpret_cast<uint32_t*>(sm + sh.off_offs);
   v.ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
   return v;
 }
 
 // ---------------------------------------------------------------------------
-// One panel: stream, code, list and evaluate candidates, flush.
-__device__ void process_panel(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
-                              const StreamView& v, uint32_t f, uint32_t pn, uint64_t pol, uint64_t keep_pol,
-                              uint32_t& ring_iter) {
+// One streaming item: panels pn0 .. pn0 + kp - 1 of frame f, side by side.
+//
+// Thread t < kp NP owns float4 column pc = t mod NP of panel slot pi = t / NP
+// (two bins per binned row) and walks down the rows.  The q values of the row
+// above stay in its registers; the bin to the left comes from the previous
+// lane by shuffle, and lane 0 reads the previous warp's last column from
+// shared memory.  A step covers RB binned rows: phase A bins and
+// prequantises them into registers, one barrier (it also frees the ring
+// slot), then phase B forms the Lorenzo residuals, code bytes and histogram.
+template <int RB>
+__device__ void process_item(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                             unsigned char* sm, uint32_t f, uint32_t u, uint32_t& ring_iter) {
+  const StreamView v = stream_view(sm, sh);
+  // input rows: evict-first (or normal) in L2; code bytes: evict-last until packed
+  const uint64_t pol = sh.input_evict_first ? evict_first_policy() : evict_normal_policy();
+  const uint64_t keep_pol = evict_last_policy();
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-  const uint32_t NP = p.W >> 2, Mp = p.Hb * p.Wb;
-  const float* panel = a.frames + (size_t)f * p.frame_px + (size_t)pn * p.H * p.W;
-  const size_t fbin = (size_t)f * p.M + (size_t)pn * Mp;  // first bin of the panel in the frame arrays
-  uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride + (size_t)pn * Mp;
+  const uint32_t NP = p.W >> 2, Mp = p.Hb * p.Wb, plane = p.H * p.W;
+  const uint32_t pn0 = u * sh.k, kp = min(sh.k, p.P - pn0);
+  // lane l >= 1 of warp w owns float4 column 31 w + l - 1 of the item; lane 0
+  // recomputes the column before (the previous warp's last) for its left
+  // neighbour, so warps never wait for one another
+  const uint32_t C = kp * NP;
+  const int gc = 31 * (int)warp + (int)lane - 1;
+  const bool col_ok = gc >= 0 && (uint32_t)gc < C;
+  const bool owned = col_ok && lane >= 1 && warp < kConsumerWarps;
+  const uint32_t gcol = col_ok ? (uint32_t)gc : 0u;
+  const uint32_t pi = gcol / NP, pc = gcol - pi * NP;
+  const float* item_px = a.frames + (size_t)f * p.frame_px + (size_t)pn0 * plane;
+  const size_t fbin = (size_t)f * p.M + (size_t)(pn0 + pi) * Mp;  // first bin of the lane's panel
+  uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride + (size_t)(pn0 + pi) * Mp + 2 * pc;
   uint16_t* esc = s.codes + fbin;
   int32_t* lo_delta = s.lo_delta + fbin;
   uint32_t* pq_bits = s.pq_bits + fbin;
+  uint32_t* mask = v.mask + pi * sh.mask_words;
+  const uint32_t slot_floats = 2 * RB * p.W;  // one panel's rows in a ring slot
+  const size_t fu = (size_t)f * p.P + u;
+  uint64_t* full_bar = v.bars;                 // [stages] rows landed (TMA transaction count)
+  uint64_t* empty_bar = v.bars + sh.stages;    // [stages] every consumer warp is done with the slot
 
   uint64_t* trace = (a.trace && f < a.trace_frames && tid == 0)
-                       ? a.trace + (size_t)a.trace_frames * kTracePoints + ((size_t)f * p.P + pn) * 4
+                       ? a.trace + (size_t)a.trace_frames * kTracePoints + fu * 4
                        : nullptr;
   if (trace) trace[0] = global_ns();
   for (uint32_t k = tid; k < p.nsym; k += kPT) v.hist[k] = 0;
-  for (uint32_t k = tid; k < sh.mask_words; k += kPT) v.mask[k] = 0;
+  for (uint32_t k = tid; k < kp * sh.mask_words; k += kPT) v.mask[k] = 0;
   if (tid == 0) {
     v.ctl[CTL_THR] = 0;
-    v.ctl[CTL_PQ] = 0;
+    v.ctl[CTL_NZ] = 0;
   }
-  if (a.user_peaks && tid == 0) s.peak_part_count[(size_t)f * p.P + pn] = 0;
+  if (tid < kMaxK) v.ctl[CTL_PQ + tid] = 0;
+  if (a.user_peaks && tid == 0) s.peak_part_count[fu] = 0;
+  __syncthreads();  // hist, masks and counters are zero
 
-  // the thread's items within a step (the same for every step)
-  uint32_t il[kItems], pr[kItems], qs[kItems];  // qs: circular-buffer row of the item's bin row
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    const uint32_t it = tid + k * kPT;
-    il[k] = it / NP;
-    pr[k] = it - il[k] * NP;
-    qs[k] = il[k] < sh.qrows ? il[k] : 0;
-  }
-  const uint32_t n_steps = ceil_div(p.Hb, sh.RB);
-  // stage st = raw rows [2 st RB, min(H, 2 (st + 1) RB)) of the panel, one TMA bulk copy
-  auto issue = [&](uint32_t st) {  // thread 0 only
-    const uint32_t r0 = 2 * st * sh.RB, r1 = min(p.H, 2 * (st + 1) * sh.RB);
-    const uint32_t slot = (ring_iter + st) % sh.stages;
-    const uint32_t bytes = (r1 - r0) * p.W * 4;
-    fence_proxy_async();
-    mbar_expect_tx(v.bars + slot, bytes);
-    tma_load_1d(v.ring + (size_t)slot * sh.stage_bytes, panel + (size_t)r0 * p.W, bytes, v.bars + slot, pol);
-  };
-  if (tid == 0)
-    for (uint32_t st = 0; st < min(sh.stages, n_steps); ++st) issue(st);
-  __syncthreads();  // hist, mask and counters are zero
+  const uint32_t n_steps = ceil_div(p.Hb, (uint32_t)RB);
   const bool find = a.user_peaks == nullptr;
   bool timed_out = false;
-  uint32_t n_common = 0;  // codes equal to R (zero residual), counted in a register
-  for (uint32_t st = 0; st < n_steps; ++st) {
-    const uint32_t i0 = st * sh.RB;
-    const uint32_t slot = (ring_iter + st) % sh.stages;
-    if (!mbar_wait(v.bars + slot, ((ring_iter + st) / sh.stages) & 1u)) timed_out = true;
-    const float4* ring = reinterpret_cast<const float4*>(v.ring + (size_t)slot * sh.stage_bytes);
-    // phase A: q of the step's bins into the circular buffer
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      const uint32_t i = i0 + il[k];
-      if (il[k] >= sh.RB || i >= p.Hb) continue;
-      const bool two = 2 * i + 1 < p.H;
-      const float4 va = ring[(size_t)(2 * il[k]) * NP + pr[k]];
-      const float4 vb = two ? ring[(size_t)(2 * il[k] + 1) * NP + pr[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
-      float v0, v1;
-      bin_pair(va, vb, two, v0, v1);
-      const uint32_t j0 = 2 * pr[k];
-      int32_t q0, q1;
-      const bool f0 = prequant_fast(v0, p, q0), f1 = prequant_fast(v1, p, q1);
-      if (!(f0 && f1)) {  // the screen could not decide: the full test (identical results)
-        const Quant Q0 = prequantize(v0, p), Q1 = prequantize(v1, p);
-        q0 = Q0.q;
-        q1 = Q1.q;
-        if (Q0.outlier | Q1.outlier) {
-          const uint32_t lb = i * p.Wb + j0;
-          atomicAdd(v.ctl + CTL_PQ, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
-          atomicOr(v.mask + (lb >> 5), ((uint32_t)Q0.outlier | ((uint32_t)Q1.outlier << 1)) << (lb & 31));
-          if (Q0.outlier) pq_bits[lb] = Q0.outlier_bits;
-          if (Q1.outlier) pq_bits[lb + 1] = Q1.outlier_bits;
-        }
-      }
-      *reinterpret_cast<int2*>(v.qbuf + (size_t)qs[k] * p.Wb + j0) = make_int2(q0, q1);
-      const float m = fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)), fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
-      if (find && m >= p.amax) {  // rare: list the 2x4 block, its pixels are screened later
-        const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
-        if (slot_t < kThrLocalCap) v.thr[slot_t] = 2 * i * p.W + 4 * pr[k];
+  uint32_t slot = ring_iter % sh.stages, phase = (ring_iter / sh.stages) & 1u;
+  auto advance = [&]() {
+    if (++slot == sh.stages) {
+      slot = 0;
+      phase ^= 1u;
+    }
+  };
+  if (warp == kProducerWarp) {
+    // producer: step st = raw rows [2 st RB, min(H, 2 (st + 1) RB)) of each
+    // panel, one bulk copy per panel, once every consumer has left the slot
+    if (lane == 0) {
+      for (uint32_t st = 0; st < n_steps; ++st) {
+        if (!mbar_wait(empty_bar + slot, phase ^ 1u)) timed_out = true;
+        const uint32_t r0 = 2 * st * RB, r1 = min(p.H, 2 * (st + 1) * RB);
+        const uint32_t bytes = (r1 - r0) * p.W * 4;
+        float* dst = reinterpret_cast<float*>(v.ring + (size_t)slot * sh.stage_bytes);
+        fence_proxy_async();
+        mbar_expect_tx(full_bar + slot, bytes * kp);
+        for (uint32_t j = 0; j < kp; ++j)
+          tma_load_1d(dst + (size_t)j * slot_floats, item_px + (size_t)j * plane + (size_t)r0 * p.W, bytes,
+                      full_bar + slot, pol);
+        advance();
       }
     }
-    __syncthreads();  // the slot is consumed: refill it with the stage S steps ahead
-    if (tid == 0 && st + sh.stages < n_steps) issue(st + sh.stages);
-    // phase B: residuals, code bytes, histogram, outliers.  The circular
-    // buffer holds 2 RB + 1 rows, so the next phase A never overwrites a row
-    // this phase B still reads: one barrier per step is enough.
+  } else if (31 * warp >= C) {
+    // a consumer warp without columns in this item still releases every slot
+    for (uint32_t st = 0; st < n_steps; ++st) {
+      if (!mbar_wait(full_bar + slot, phase)) timed_out = true;
+      if (lane == 0) mbar_arrive(empty_bar + slot);
+      advance();
+    }
+  } else {
+    int2 qu = make_int2(0, 0);  // q of the lane's two bins in the row above
+    int32_t qd = 0;             // q of the bin left of them in the row above
+    const bool first_col = pc == 0;  // the bin to the left lies outside the panel
+
+    // One step: RB binned rows.  FULL steps have RB rows of two raw rows each
+    // (every step but possibly the panel's last), so they need no row checks.
+    // Rare cases (prequantisation screen undecided, a block >= amax_thr, a
+    // non-zero residual) are flagged per row and handled after the rows by
+    // the whole warp, so the common path has no divergent branch.
+    auto step = [&](uint32_t st, auto full_tag) {
+      constexpr bool FULL = decltype(full_tag)::value;
+      const uint32_t i0 = st * RB;
+      const float4* rows =
+          reinterpret_cast<const float4*>(v.ring + (size_t)slot * sh.stage_bytes) + pi * (slot_floats / 4) + pc;
+      int2 qa[RB];
+      // phase A: q of the lane's bins in the step's rows
+      uint32_t redo = 0, hot = 0;  // bit ii: row ii needs the full test / holds a block >= amax_thr
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      const uint32_t i = i0 + il[k];
-      uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
-      if (il[k] < sh.RB && i < p.Hb) {
-        const uint32_t j0 = 2 * pr[k];
-        const int32_t* cur = v.qbuf + (size_t)qs[k] * p.Wb;
-        const int2 qc = *reinterpret_cast<const int2*>(cur + j0);
-        int2 qu = make_int2(0, 0);
-        int32_t ql = 0, qd = 0;
-        if (i > 0) {
-          const int32_t* up = v.qbuf + (size_t)(qs[k] == 0 ? sh.qrows - 1 : qs[k] - 1) * p.Wb;
-          qu = *reinterpret_cast<const int2*>(up + j0);
-          if (j0 > 0) qd = up[j0 - 1];
+      for (int ii = 0; ii < RB; ++ii) {
+        const uint32_t i = i0 + ii;
+        qa[ii] = make_int2(0, 0);
+        if (!FULL && i >= p.Hb) continue;
+        const bool two = FULL || 2 * i + 1 < p.H;
+        const float4 va = rows[(2 * ii) * NP];
+        const float4 vb = two ? rows[(2 * ii + 1) * NP] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float v0, v1;
+        bin_pair(va, vb, two, v0, v1);
+        int32_t q0, q1;
+        const bool ok = prequant_fast(v0, p, q0) & prequant_fast(v1, p, q1);
+        redo |= (uint32_t)!ok << ii;
+        qa[ii] = make_int2(q0, q1);
+        if (find) {
+          const float m =
+              fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)), fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
+          hot |= (uint32_t)(m >= p.amax) << ii;
         }
-        if (j0 > 0) ql = cur[j0 - 1];
-        const int32_t d0 = qc.x - qu.x - ql + qd;
-        const int32_t d1 = qc.y - qu.y - qc.x + qu.x;
-        const uint32_t lb = i * p.Wb + j0;
-        // fast path: both residuals fit a code byte and the alphabet (one
-        // unsigned range test each): byte = residual + 128, code = residual + R
-        const bool fast = ((uint32_t)(d0 - p.d_lo) <= p.d_span) & ((uint32_t)(d1 - p.d_lo) <= p.d_span);
-        uint32_t b0, b1;
-        if (fast) {
-          c0 = (uint32_t)(d0 + p.R);
-          c1 = (uint32_t)(d1 + p.R);
-          b0 = (uint32_t)(d0 + 128);
-          b1 = (uint32_t)(d1 + 128);
-        } else {
-          c0 = quant_code(d0, p.R);
-          c1 = quant_code(d1, p.R);
-          auto to_byte = [&](int32_t d, uint32_t c, uint32_t bin) -> uint32_t {
-            if (c == 0) {
-              lo_delta[bin] = d;
-              return 0u;
-            }
-            if (d >= -127 && d <= 126) return (uint32_t)(d + 128);
-            esc[bin] = (uint16_t)c;
-            return 255u;
-          };
-          b0 = to_byte(d0, c0, lb);
-          b1 = to_byte(d1, c1, lb + 1);
+      }
+      if (__any_sync(0xffffffffu, redo != 0)) {  // the screen could not decide: the full test
+#pragma unroll
+        for (int ii = 0; ii < RB; ++ii) {
+          if (!((redo >> ii) & 1u)) continue;
+          const uint32_t i = i0 + ii;
+          const bool two = 2 * i + 1 < p.H;
+          const float4 va = rows[(2 * ii) * NP];
+          const float4 vb = two ? rows[(2 * ii + 1) * NP] : make_float4(0.f, 0.f, 0.f, 0.f);
+          float v0, v1;
+          bin_pair(va, vb, two, v0, v1);
+          const Quant Q0 = prequantize(v0, p), Q1 = prequantize(v1, p);
+          qa[ii] = make_int2(Q0.q, Q1.q);
+          if (owned && (Q0.outlier | Q1.outlier)) {
+            const uint32_t lb = i * p.Wb + 2 * pc;
+            atomicAdd(v.ctl + CTL_PQ + pi, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
+            atomicOr(mask + (lb >> 5), ((uint32_t)Q0.outlier | ((uint32_t)Q1.outlier << 1)) << (lb & 31));
+            if (Q0.outlier) pq_bits[lb] = Q0.outlier_bits;
+            if (Q1.outlier) pq_bits[lb + 1] = Q1.outlier_bits;
+          }
         }
-        st_keep_u16(codes + lb, (uint16_t)(b0 | (b1 << 8)), keep_pol);  // lb is even
       }
-      n_common += (c0 == (uint32_t)p.R) + (c1 == (uint32_t)p.R);
-      const bool r0 = c0 != 0xFFFFu && c0 != (uint32_t)p.R, r1 = c1 != 0xFFFFu && c1 != (uint32_t)p.R;
-      if (__any_sync(0xffffffffu, r0 | r1)) {
-        hist_add_warp(v.hist, r0 ? c0 : 0xFFFFu, 0xFFFFFFFFu);
-        hist_add_warp(v.hist, r1 ? c1 : 0xFFFFu, 0xFFFFFFFFu);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty_bar + slot);  // this warp is done with the slot
+      advance();
+      if (!owned) hot = 0;
+      if (__any_sync(0xffffffffu, hot != 0)) {  // list the 2x4 blocks; their pixels are screened later
+#pragma unroll
+        for (int ii = 0; ii < RB; ++ii) {
+          if (!((hot >> ii) & 1u)) continue;
+          const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
+          if (slot_t < kThrLocalCap) v.thr[slot_t] = pi * plane + 2 * (i0 + ii) * p.W + 4 * pc;
+        }
       }
-      qs[k] += sh.RB;  // the same item's row in the next step
-      if (qs[k] >= sh.qrows) qs[k] -= sh.qrows;
+      // phase B: residuals and code bytes.  A pair of zero residuals (the
+      // common case) stores 0x8080 and is not counted: the zero residual's
+      // histogram count is derived from the bin count at the flush.
+      // Residuals in [-128, 127] store residual + 128 here; the rare pass
+      // below fixes the bytes of outliers and escapes and counts every
+      // non-zero residual.
+      uint32_t nz = 0;
+      const int2 qu_step = qu;  // the chain's start, replayed by the rare pass
+      const int32_t qd_step = qd;
+      auto left_of = [&](int ii) {  // q of the bin left of the lane's bins in row i0 + ii
+        const int32_t from_lane = __shfl_up_sync(0xffffffffu, qa[ii].y, 1);
+        return first_col ? 0 : from_lane;
+      };
+#pragma unroll
+      for (int ii = 0; ii < RB; ++ii) {
+        const uint32_t i = i0 + ii;
+        if (!FULL && i >= p.Hb) break;
+        const int32_t left = left_of(ii);
+        const int32_t d0 = qa[ii].x - qu.x - left + qd;
+        const int32_t d1 = qa[ii].y - qu.y - qa[ii].x + qu.x;
+        qu = qa[ii];
+        qd = left;
+        nz |= (uint32_t)((d0 | d1) != 0) << ii;
+        const uint32_t pair = (uint32_t)((d0 + 128) & 0xFF) | ((uint32_t)((d1 + 128) & 0xFF) << 8);
+        st_keep_u16_if(codes + (size_t)i * p.Wb, (uint16_t)pair, keep_pol, owned);  // 2 pc is even
+      }
+      if (!owned) nz = 0;
+      if (__any_sync(0xffffffffu, nz != 0)) {
+        int2 qu_r = qu_step;
+        int32_t qd_r = qd_step;
+#pragma unroll
+        for (int ii = 0; ii < RB; ++ii) {
+          const uint32_t i = i0 + ii;
+          if (!FULL && i >= p.Hb) break;
+          const int32_t left = left_of(ii);
+          const int32_t d0 = qa[ii].x - qu_r.x - left + qd_r;
+          const int32_t d1 = qa[ii].y - qu_r.y - qa[ii].x + qu_r.x;
+          qu_r = qa[ii];
+          qd_r = left;
+          const bool row_nz = (nz >> ii) & 1u;
+          if (!__any_sync(0xffffffffu, row_nz)) continue;
+          uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
+          if (row_nz) {
+            const uint32_t lb = i * p.Wb + 2 * pc;
+            c0 = quant_code(d0, p.R);
+            c1 = quant_code(d1, p.R);
+            // byte = residual + 128 for residuals in [-127, 126]; 0 = Lorenzo
+            // outlier (delta on the side); 255 = escape (code on the side)
+            auto to_byte = [&](int32_t d, uint32_t c, uint32_t bin) -> uint32_t {
+              if (c == 0) {
+                lo_delta[bin] = d;
+                return 0u;
+              }
+              if (d >= -127 && d <= 126) return (uint32_t)(d + 128);
+              esc[bin] = (uint16_t)c;
+              return 255u;
+            };
+            const uint32_t b0 = to_byte(d0, c0, lb), b1 = to_byte(d1, c1, lb + 1);
+            if (b0 != (uint32_t)((d0 + 128) & 0xFF) || b1 != (uint32_t)((d1 + 128) & 0xFF))
+              st_keep_u16_if(codes + (size_t)i * p.Wb, (uint16_t)(b0 | (b1 << 8)), keep_pol, true);
+          }
+          hist_add_warp(v.hist, c0 != (uint32_t)p.R ? c0 : 0xFFFFu, 0xFFFFFFFFu);
+          hist_add_warp(v.hist, c1 != (uint32_t)p.R ? c1 : 0xFFFFu, 0xFFFFFFFFu);
+        }
+      }
+    };
+    for (uint32_t st = 0; st < n_steps; ++st) {
+      if (!mbar_wait(full_bar + slot, phase)) timed_out = true;
+      const uint32_t i_end = (st + 1) * RB;
+      if (i_end <= p.Hb && 2 * i_end <= p.H) step(st, std::integral_constant<bool, true>{});
+      else step(st, std::integral_constant<bool, false>{});
     }
   }
-  ring_iter += n_steps;
   if (timed_out) v.ctl[CTL_TIMEOUT] = 1;
-  (void)qs;
-  // the zero residual's count: one add per warp
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) n_common += __shfl_xor_sync(0xffffffffu, n_common, d);
-  if (lane == 0 && n_common) atomicAdd(v.hist + p.R, n_common);
+  ring_iter += n_steps;
   __syncthreads();
+  // the zero residual's count: every bin of the item not counted elsewhere
+  {
+    uint32_t part = 0;
+    for (uint32_t k = tid; k < p.nsym; k += kPT) part += k != (uint32_t)p.R ? v.hist[k] : 0u;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+    if (lane == 0 && part) atomicAdd(v.ctl + CTL_NZ, part);
+    __syncthreads();
+    if (tid == 0) v.hist[p.R] = kp * Mp - v.ctl[CTL_NZ];
+    __syncthreads();
+  }
   if (trace) trace[1] = global_ns();
-  // flush the panel's histogram and outlier bits (disjoint per-panel slots)
-  const size_t fp = (size_t)f * p.P + pn;
-  for (uint32_t k = tid; k < p.nsym; k += kPT) s.hist_part[fp * kMaxSymbols + k] = v.hist[k];
-  const uint32_t n_pq = v.ctl[CTL_PQ];
-  if (n_pq)
-    for (uint32_t k = tid; k < sh.mask_words; k += kPT) s.pq_mask[fp * sh.mask_words + k] = v.mask[k];
-  if (tid == 0) s.pq_part_count[fp] = n_pq;
+  // flush the item's histogram and its panels' outlier bits (disjoint slots)
+  for (uint32_t k = tid; k < p.nsym; k += kPT) s.hist_part[fu * kMaxSymbols + k] = v.hist[k];
+  for (uint32_t j = 0; j < kp; ++j) {
+    const uint32_t n_pq = v.ctl[CTL_PQ + j];
+    const size_t fp = (size_t)f * p.P + pn0 + j;
+    if (n_pq)
+      for (uint32_t k = tid; k < sh.mask_words; k += kPT)
+        s.pq_mask[fp * sh.mask_words + k] = v.mask[j * sh.mask_words + k];
+    if (tid == 0) s.pq_part_count[fp] = n_pq;
+  }
 
-  // a1 + a2 on the panel's listed pixels (on every pixel >= amax_thr if the list overflowed)
+  // a1 + a2 on the listed blocks (on every pixel >= amax_thr if the list overflowed)
   if (find) {
     if (tid == 0) v.ctl[CTL_ACC] = 0;
     __syncthreads();
     const uint32_t cnt = v.ctl[CTL_THR];
     float* nb = v.nb + warp * sh.side * sh.side;
-    auto test = [&](uint32_t lp) {  // lp: pixel index within the panel
-      const uint32_t r = lp / p.W, c = lp - r * p.W;
-      if (warp_peak_test(panel, p.H, p.W, r, c, p, nb, [](const float* q) { return __ldg(q); }) && lane == 0) {
+    auto test = [&](uint32_t lp) {  // lp: pixel index within the item
+      const uint32_t pj = lp / plane, rem = lp - pj * plane;
+      const uint32_t r = rem / p.W, c = rem - r * p.W;
+      if (warp_peak_test(item_px + (size_t)pj * plane, p.H, p.W, r, c, p, nb,
+                         [](const float* q) { return __ldg(q); }) &&
+          lane == 0) {
         const uint32_t slot = atomicAdd(v.ctl + CTL_ACC, 1u);
         if (slot < sh.sort_n2) v.acc[slot] = lp;
       }
@@ -418,10 +534,11 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
       // each listed 2x4 block: a pixel beaten inside its own block (which lies
       // inside its window) by the local-maximum rule can never be a candidate
       for (uint32_t e = warp; e < cnt; e += kPW) {
-        const uint32_t key = v.thr[e], r0 = key / p.W, c0 = key - r0 * p.W;
+        const uint32_t key = v.thr[e], pj = key / plane, rem = key - pj * plane;
+        const uint32_t r0 = rem / p.W;
         const uint32_t npx = r0 + 1 < p.H ? 8u : 4u;
         const uint32_t me = lane & 7u;
-        const float x = me < npx ? __ldg(panel + (size_t)(r0 + (me >> 2)) * p.W + c0 + (me & 3u)) : 0.0f;
+        const float x = me < npx ? __ldg(item_px + key + (me >> 2) * p.W + (me & 3u)) : 0.0f;
         bool keep = lane < npx && x >= p.amax;
 #pragma unroll
         for (uint32_t q = 0; q < 8; ++q) {
@@ -438,10 +555,10 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
         }
       }
     } else {
-      const uint32_t plane = p.H * p.W;
-      for (uint32_t base = warp * 32; base < plane; base += kPW * 32) {
+      const uint32_t n_px = kp * plane;
+      for (uint32_t base = warp * 32; base < n_px; base += kPW * 32) {
         const uint32_t lp = base + lane;
-        const bool hot = lp < plane && __ldg(panel + lp) >= p.amax;
+        const bool hot = lp < n_px && __ldg(item_px + lp) >= p.amax;
         uint32_t m = __ballot_sync(0xffffffffu, hot);
         while (m) {
           const uint32_t l = __ffs(m) - 1;
@@ -452,7 +569,7 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
     }
     __syncthreads();
     const uint32_t n_acc = v.ctl[CTL_ACC];
-    if (n_acc <= p.max_peaks) {  // sort the panel's peaks (row-major order)
+    if (n_acc <= p.max_peaks) {  // sort the item's peaks: (panel, row, col) order
       uint32_t n2 = 1;
       while (n2 < n_acc) n2 <<= 1;
       for (uint32_t k = n_acc + tid; k < n2; k += kPT) v.acc[k] = 0xFFFFFFFFu;
@@ -473,13 +590,13 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
           __syncthreads();
         }
       }
-      for (uint32_t k = tid; k < n_acc; k += kPT) s.peak_part[fp * sh.peak_cap + k] = pn * p.H * p.W + v.acc[k];
+      for (uint32_t k = tid; k < n_acc; k += kPT) s.peak_part[fu * sh.peak_cap + k] = pn0 * plane + v.acc[k];
     }
-    if (tid == 0) s.peak_part_count[fp] = n_acc;
+    if (tid == 0) s.peak_part_count[fu] = n_acc;
   }
   __syncthreads();
   if (tid == 0 && v.ctl[CTL_TIMEOUT]) {  // a copy never arrived: the frame is marked, see frame_codebook
-    s.peak_part_count[fp] = kPanelTimedOut;
+    s.peak_part_count[fu] = kPanelTimedOut;
     v.ctl[CTL_TIMEOUT] = 0;
   }
   if (trace) trace[2] = global_ns();
@@ -494,8 +611,8 @@ __device__ void process_panel(const DevParams& p, const Scratch& s, const PlainA
 //   (3) chunk-write items pack the bits, write the outliers and the ROI
 //       windows, and drop their code bytes from L2.
 // One atomic ticket counter orders all work: round r holds the panels of
-// frame r, the size items of frame r - lag and the write items of frame
-// r - 2 lag.  Stages hand over through release/acquire flags.  A CTA only
+// frame r, the size items of frame r - lag1 and the write items of frame
+// r - lag1 - lag2.  Stages hand over through release/acquire flags.  A CTA only
 // ever waits for work handed out to an earlier ticket, which is running or
 // done, so every wait ends; waits are bounded anyway (ROIBIN_ERR_TIMEOUT).
 constexpr uint32_t kWaitLimit = 1u << 22;
@@ -541,16 +658,17 @@ __device__ bool wait_flag(const uint32_t* f, uint32_t* slot) {
   return ok;
 }
 
-// (1) peak list + codebook of frame f, by the CTA that completed its last panel.
+// (1) peak list + codebook of frame f, by the CTA that completed its last streaming item.
 __device__ void frame_codebook(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
-                               const FinView& v, uint32_t f, const SyncWords& sw) {
+                               unsigned char* sm, uint32_t f, const SyncWords& sw) {
+  const FinView v = fin_view(sm, sh);
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   uint64_t* trace = (a.trace && f < a.trace_frames && tid == 0) ? a.trace + (size_t)f * kTracePoints : nullptr;
   if (trace) trace[0] = global_ns();
   // a8: the frame's histogram; prequantisation outliers in the frame
   for (uint32_t k = tid; k < p.nsym; k += kPT) {
     uint32_t t = 0;
-    for (uint32_t pn = 0; pn < p.P; ++pn) t += __ldcg(s.hist_part + ((size_t)f * p.P + pn) * kMaxSymbols + k);
+    for (uint32_t u = 0; u < sh.U; ++u) t += __ldcg(s.hist_part + ((size_t)f * p.P + u) * kMaxSymbols + k);
     v.total[k] = t;
   }
   if (tid == 0) {
@@ -562,14 +680,14 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
     v.ctl[CTL_CARRY0] = 0;
   }
   __syncthreads();
-  // the peak list: per-panel sorted lists concatenated in panel order, or the user's
+  // the peak list: per-item sorted lists concatenated in item (= panel) order, or the user's
   uint32_t* keys = a.peaks_key_out + (size_t)f * p.max_peaks;
   if (a.user_peaks) {
     const uint32_t n = a.user_npeaks[f];
     if (tid == 0) {
       v.ctl[CTL_CARRY0] = n;
-      for (uint32_t pn = 0; pn < p.P; ++pn)
-        if (__ldcg(s.peak_part_count + (size_t)f * p.P + pn) == kPanelTimedOut)
+      for (uint32_t u = 0; u < sh.U; ++u)
+        if (__ldcg(s.peak_part_count + (size_t)f * p.P + u) == kPanelTimedOut)
           v.ctl[CTL_BAD] = 2;
     }
     if (n > p.max_peaks) {
@@ -587,12 +705,12 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
       uint32_t n = 0;
       bool over = false;
       bool timeout = false;
-      for (uint32_t pn = 0; pn < p.P; ++pn) {
-        const uint32_t c = __ldcg(s.peak_part_count + (size_t)f * p.P + pn);
+      for (uint32_t u = 0; u < sh.U; ++u) {
+        const uint32_t c = __ldcg(s.peak_part_count + (size_t)f * p.P + u);
         if (c == kPanelTimedOut) timeout = true;
         else if (c > p.max_peaks) over = true;
-        if (pn < 1024) v.ctl[CTL_OFFS + pn] = n;
-        n += c;
+        v.offs[u] = n;
+        if (c != kPanelTimedOut) n += c;
       }
       if (over || n > p.max_peaks) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_CAPACITY;
       if (timeout) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_TIMEOUT;
@@ -600,16 +718,10 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
     }
     __syncthreads();
     if (v.ctl[CTL_STATUS] == ROIBIN_OK) {
-      for (uint32_t pn = warp; pn < p.P; pn += kPW) {
-        const uint32_t c = __ldcg(s.peak_part_count + (size_t)f * p.P + pn);
-        uint32_t off = 0;
-        if (pn < 1024) {
-          off = v.ctl[CTL_OFFS + pn];
-        } else {
-          for (uint32_t q = 0; q < pn; ++q) off += __ldcg(s.peak_part_count + (size_t)f * p.P + q);
-        }
+      for (uint32_t u = warp; u < sh.U; u += kPW) {
+        const uint32_t c = __ldcg(s.peak_part_count + (size_t)f * p.P + u), off = v.offs[u];
         for (uint32_t k = lane; k < c; k += 32)
-          keys[off + k] = __ldcg(s.peak_part + ((size_t)f * p.P + pn) * sh.peak_cap + k);
+          keys[off + k] = __ldcg(s.peak_part + ((size_t)f * p.P + u) * sh.peak_cap + k);
       }
     }
   }
@@ -674,6 +786,8 @@ __device__ __forceinline__ uint32_t pq_bit_of(const DevParams& p, const Scratch&
                                               uint32_t bin) {
   const uint32_t Mp = p.Hb * p.Wb;
   const uint32_t pn = bin / Mp, lb = bin - pn * Mp;
+  // a panel without prequantisation outliers never wrote its mask words
+  if (__ldcg(s.pq_part_count + (size_t)f * p.P + pn) == 0) return 0u;
   return (__ldcg(s.pq_mask + ((size_t)f * p.P + pn) * sh.mask_words + (lb >> 5)) >> (lb & 31)) & 1u;
 }
 
@@ -1008,47 +1122,47 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainArgs a, FusedShape sh) {
   extern __shared__ __align__(128) unsigned char sm[];
-  const StreamView sv = stream_view(sm, sh);
-  const FinView fv = fin_view(sm, sh);
-  // input rows: normal L2 priority (the panel's peak tests re-read them soon);
-  // code bytes: evict-last until their chunk is packed (then discarded)
-  const uint64_t pol = sh.input_evict_first ? evict_first_policy() : evict_normal_policy();
-  const uint64_t keep_pol = evict_last_policy();
+  uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
   const SyncWords sw = sync_words(s, a.n_frames);
-  const uint32_t n = a.n_frames, lag = sh.lag, round = p.P + 2 * sh.groups;
-  const uint64_t total = (uint64_t)(n + 2 * lag) * round;
+  const uint32_t n = a.n_frames, lag1 = sh.lag1, lag2 = lag1 + sh.lag2, round = sh.U + 2 * sh.groups;
+  const uint64_t total = (uint64_t)(n + lag2) * round;
   if (threadIdx.x == 0) {
-    for (uint32_t b = 0; b < sh.stages; ++b) mbar_init(sv.bars + b, 1);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + sh.off_bar);
+    for (uint32_t b = 0; b < sh.stages; ++b) {
+      mbar_init(bars + b, 1);                            // full: the producer's expect_tx
+      mbar_init(bars + sh.stages + b, kConsumerWarps);   // empty: one arrival per consumer warp
+    }
     fence_mbar_init();
-    sv.ctl[CTL_TIMEOUT] = 0;
+    ctl[CTL_TIMEOUT] = 0;
   }
   __syncthreads();
   uint32_t ring_iter = 0;  // ring stages consumed so far (the same in every thread)
   for (;;) {
-    if (threadIdx.x == 0) sv.ctl[CTL_ITEM] = atomicAdd(sw.ticket, 1u);
+    if (threadIdx.x == 0) ctl[CTL_ITEM] = atomicAdd(sw.ticket, 1u);
     __syncthreads();
-    const uint32_t t = sv.ctl[CTL_ITEM];
+    const uint32_t t = ctl[CTL_ITEM];
     __syncthreads();
     if (t >= total) break;
     const uint32_t r = t / round, j = t - r * round;
-    if (j < p.P) {
+    if (j < sh.U) {
       if (r >= n) continue;
-      process_panel(p, s, a, sh, sv, r, j, pol, keep_pol, ring_iter);
-      // publish the panel; the CTA that completes the frame builds its codebook
+      if (sh.RB == 2) process_item<2>(p, s, a, sh, sm, r, j, ring_iter);
+      else process_item<3>(p, s, a, sh, sm, r, j, ring_iter);
+      // publish the item; the CTA that completes the frame builds its codebook
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) sv.ctl[CTL_LAST] = atomicAdd(sw.panel_done + r, 1u) == p.P - 1 ? 1u : 0u;
+      if (threadIdx.x == 0) ctl[CTL_LAST] = atomicAdd(sw.panel_done + r, 1u) == sh.U - 1 ? 1u : 0u;
       __syncthreads();
-      if (sv.ctl[CTL_LAST]) {
+      if (ctl[CTL_LAST]) {
         __threadfence();
-        frame_codebook(p, s, a, sh, fv, r, sw);
+        frame_codebook(p, s, a, sh, sm, r, sw);
       }
-    } else if (j < p.P + sh.groups) {
-      if (r < lag || r - lag >= n) continue;
-      size_item(p, s, a, sh, sm, r - lag, j - p.P, sw);
+    } else if (j < sh.U + sh.groups) {
+      if (r < lag1 || r - lag1 >= n) continue;
+      size_item(p, s, a, sh, sm, r - lag1, j - sh.U, sw);
     } else {
-      if (r < 2 * lag || r - 2 * lag >= n) continue;
-      write_item(p, s, a, sh, sm, r - 2 * lag, j - p.P - sh.groups, sw);
+      if (r < lag2 || r - lag2 >= n) continue;
+      write_item(p, s, a, sh, sm, r - lag2, j - sh.U - sh.groups, sw);
     }
     __syncthreads();
   }
@@ -1056,16 +1170,16 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
 
 // ---------------------------------------------------------------------------
 // host side
+// Shared memory a CTA of this shape needs (0 if the shape is impossible).
 static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, uint32_t stages, FusedShape* out) {
   FusedShape sh{};
   const uint32_t NP = p.W / 4;
-  uint32_t RB = rb ? rb : max(1u, (uint32_t)(kItems * kPT) / max(NP, 1u));
-  RB = min(RB, min(16u, p.Hb));
-  if (RB * NP > (uint32_t)(kItems * kPT)) return false;  // a step must fit the thread items
-  sh.RB = RB;
-  sh.qrows = 2 * RB + 1;
+  if (NP < 1 || NP > kConsumerWarps * 31 || rb < 2 || rb > 3) return false;
+  sh.k = min(kMaxK, kConsumerWarps * 31 / NP);
+  sh.U = ceil_div(p.P, sh.k);
+  sh.RB = rb;
   sh.stages = stages;
-  sh.stage_bytes = 2 * RB * p.W * 4;
+  sh.stage_bytes = sh.k * 2 * rb * p.W * 4;
   sh.ctas_per_sm = ctas_per_sm;
   sh.mask_words = ceil_div(p.Hb * p.Wb, 32) + 1;
   sh.side = 2 * (uint32_t)peak_reach(p) + 1;
@@ -1085,12 +1199,11 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
     return (uint32_t)o;
   };
   sh.off_ctl = take((uint64_t)CTL_WORDS * 4);  // every role uses the control words
-  sh.off_bar = take(8ull * stages);
+  sh.off_bar = take(16ull * stages);
   const uint64_t base = off;
-  // panel role; the peak tests reuse the ring once the rows are consumed
+  // streaming role; the peak tests reuse the ring once the rows are consumed
   sh.off_hist = take(kMaxSymbols * 4);
-  sh.off_qbuf = take((uint64_t)sh.qrows * p.Wb * 4);
-  sh.off_mask = take((uint64_t)sh.mask_words * 4);
+  sh.off_mask = take((uint64_t)sh.k * sh.mask_words * 4);
   sh.off_thr = take(kThrLocalCap * 4);
   off = (off + 127) / 128 * 128;
   sh.off_ring = take((uint64_t)stages * sh.stage_bytes);
@@ -1099,7 +1212,7 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   sh.off_nb = take((uint64_t)kPW * sh.side * sh.side * 4);
   sh.off_acc = take((uint64_t)n2 * 4);
   const uint64_t stream_end = off > ring_end ? off : ring_end;
-  // codebook role / size, write and plan roles (overlap the panel role)
+  // codebook role / size, write and plan roles (overlap the streaming role)
   off = base;
   sh.off_huff = take(sizeof(HuffSmem) > 4096 ? sizeof(HuffSmem) : 4096);  // Huffman scratch | byte tables
   const uint64_t after_huff = off;
@@ -1112,6 +1225,7 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   sh.off_cbcode = take(kMaxSymbols * 4);
   sh.off_keys = take(16);
   sh.off_cw = take(3ull * p.n_chunks * 4);
+  sh.off_offs = take((uint64_t)sh.U * 4);
   const uint64_t fin_end = off > stage_end ? off : stage_end;
   sh.smem = (uint32_t)(stream_end > fin_end ? stream_end : fin_end);
   *out = sh;
@@ -1120,10 +1234,19 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
 
 bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, uint32_t stages,
                      FusedShape* out) {
-  if (p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > (uint32_t)(kItems * kPT)) return false;
-  if (ctas_per_sm < 1 || ctas_per_sm > 8 || rows_per_step > 16 || stages < 1 || stages > 8) return false;
+  if (p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > kConsumerWarps * 31) return false;
+  if (ctas_per_sm < 1 || ctas_per_sm > 8 || stages < 1 || stages > 8) return false;
+  if (rows_per_step != 0 && (rows_per_step < 2 || rows_per_step > 3)) return false;
   FusedShape sh;
-  if (!make_shape(p, ctas_per_sm, rows_per_step, stages, &sh)) return false;
+  bool ok = false;
+  if (rows_per_step) {
+    ok = make_shape(p, ctas_per_sm, rows_per_step, stages, &sh);
+  } else {
+    // the most rows per step whose shared memory lets ctas_per_sm CTAs share an SM
+    const uint32_t budget = 233472u / ctas_per_sm - 1024u;
+    for (uint32_t rb = 3; rb >= 2 && !ok; --rb) ok = make_shape(p, ctas_per_sm, rb, stages, &sh) && sh.smem <= budget;
+  }
+  if (!ok) return false;
   if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -1157,8 +1280,12 @@ cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& 
   e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
   if (e != cudaSuccess) return e;
   FusedShape s2 = sh;
-  s2.lag = a.n_frames < 48 ? a.n_frames : 48;  // frames between stages in the ticket order
-  const uint64_t tickets = (uint64_t)(a.n_frames + 2 * s2.lag) * (p.P + 2 * s2.groups);
+  // frames between the stages in the ticket order: streaming -> chunk sizes
+  // (long enough that the frame's codebook is usually ready), chunk sizes ->
+  // writing (short: the plan is ready soon after its frame's size items)
+  s2.lag1 = a.n_frames < kLagSize ? a.n_frames : kLagSize;
+  s2.lag2 = a.n_frames < kLagWrite ? a.n_frames : kLagWrite;
+  const uint64_t tickets = (uint64_t)(a.n_frames + s2.lag1 + s2.lag2) * (s2.U + 2 * s2.groups);
   const uint32_t grid = (uint32_t)(tickets < sh.n_ctas ? tickets : sh.n_ctas);
   k_fused<<<grid, kPT, sh.smem, st>>>(p, s, a, s2);
   return cudaGetLastError();

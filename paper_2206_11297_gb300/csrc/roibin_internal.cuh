@@ -672,9 +672,9 @@ constexpr uint32_t kTracePoints = 16;
 // Shape of the persistent batched kernel, chosen on the host (fused_kernel.cu).
 struct FusedShape {
   uint32_t ctas_per_sm, n_ctas;  // resident CTAs per SM, grid size
-  uint32_t RB;                   // binned rows per streaming step
-  uint32_t stages, stage_bytes;  // TMA ring: slots, bytes per slot (2 RB raw rows)
-  uint32_t qrows;                // rows of the circular q buffer (2 RB + 1)
+  uint32_t k, U;                 // panels per streaming item; streaming items per frame
+  uint32_t RB;                   // binned rows per streaming step (2 or 3)
+  uint32_t stages, stage_bytes;  // TMA ring: slots, bytes per slot (2 RB raw rows of k panels)
   uint32_t mask_words;           // prequantisation-outlier bitmask words per panel
   uint32_t side;                 // side of the peak-test neighbourhood
   uint32_t sort_n2;              // power of two >= max_peaks
@@ -682,10 +682,10 @@ struct FusedShape {
   uint32_t n_chunks;
   uint32_t codes_stride;         // code bytes per frame slot (n_chunks * kChunk)
   uint32_t group_chunks, groups; // chunks per size/write work item; items per frame
-  uint32_t lag;                  // frames between stages in the ticket order (per launch)
+  uint32_t lag1, lag2;           // frames between stages in the ticket order (per launch)
   uint32_t input_evict_first;    // L2 policy of the streamed rows (1 = evict first)
-  uint32_t off_ctl, off_bar, off_hist, off_qbuf, off_mask, off_thr, off_ring, off_nb, off_acc;  // panel role
-  uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw;     // codebook / plan roles
+  uint32_t off_ctl, off_bar, off_hist, off_mask, off_thr, off_ring, off_nb, off_acc;  // streaming role
+  uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw, off_offs;  // codebook / plan roles
   uint32_t off_stage;                                                        // size / write roles
   uint32_t smem;
 };

@@ -41,7 +41,8 @@ def fused_or_skip(geom, params, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
-@pytest.mark.parametrize("geom", [(2, 12, 13), (1, 7, 8), (3, 21, 27), (4, 37, 52), (2, 64, 100), (1, 3, 1)])
+@pytest.mark.parametrize("geom", [(2, 12, 13), (1, 7, 8), (3, 21, 27), (4, 37, 52), (2, 64, 100), (1, 3, 1),
+                                  (5, 33, 400), (2, 21, 1024), (9, 10, 4), (3, 5, 96)])
 def test_small_geometries(geom, path):
     f = small_batch(geom, 3, seed=sum(geom))
     assert_parity(f, rb.default_params(atot_thr=300.0), path)
@@ -216,3 +217,28 @@ def test_batch_composition_invariance(path):
     for k in (0, 3):
         _, _, alone = gpu_compress(f[k:k + 1], p, path=path)
         assert np.array_equal(alone[0], together[k])
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_context_reuse_with_outliers_in_other_panels(path):
+    """Prequantisation outliers in different panels on successive calls of one
+    context: nothing left over from the first call may leak into the second."""
+    import torch
+    geom = (3, 40, 44)
+    p = rb.default_params(atot_thr=300.0)
+    fused_or_skip(geom, p, path)
+    a = small_batch(geom, 2, 31)
+    b = a.copy()
+    a[:, 0, 5, 6] = np.nan       # outliers in panel 0 on the first call
+    a[:, 0, 20:22, 8:12] = 1e30
+    b[:, 2, 7, 9] = np.inf       # and only in panel 2 on the second
+    with rb.Context(geom, p, max_frames=2) as ctx:
+        ctx.set_path(path)
+        for frames in (a, b):
+            out, nb, st = ctx.compress(torch.from_numpy(frames).cuda())
+            torch.cuda.synchronize()
+            out, nb, st = out.cpu().numpy(), nb.cpu().numpy(), st.cpu().numpy()
+            for k in range(2):
+                ost, ref = oracle.compress_frame(frames[k], oparams(p))
+                assert st[k] == ost == 0
+                assert np.array_equal(out[k, :nb[k]], ref)
