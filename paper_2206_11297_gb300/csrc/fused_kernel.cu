@@ -35,7 +35,8 @@ constexpr int kPW = kPT / 32;  // warps per CTA
 constexpr uint32_t kMaxK = 8;   // panels per streaming item
 constexpr uint32_t kConsumerWarps = 7;  // warps that code rows (31 columns each)
 constexpr uint32_t kProducerWarp = 7;   // the warp whose lane 0 issues the row copies
-constexpr uint32_t kThrLocalCap = 512;
+constexpr uint32_t kThrLocalCap = 256;
+constexpr uint32_t kPqList = 128;  // prequantisation outliers an item lists before rescanning
 constexpr uint32_t kLagSize = 128, kLagWrite = 16;  // see launch_fused
 constexpr uint32_t kPanelTimedOut = 0xFFFFFFFFu;  // peak count of an item whose rows never arrived
 
@@ -98,16 +99,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// A waiting thread is suspended (up to kSuspendNs per try) until the phase
+// completes instead of spinning on the barrier.
+constexpr uint32_t kSuspendNs = 1000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
-constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier wait
+constexpr uint32_t kSpinLimit = 1u << 21;  // bounded mbarrier wait (about 2 s at most)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   for (uint32_t i = 0; i < kSpinLimit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
@@ -190,7 +194,7 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
 // one allocation; the control words sit in front of both.
 struct StreamView {
   uint32_t* hist;  // [nsym]
-  uint32_t* mask;  // [k][mask_words] prequantisation-outlier bits of the item's panels
+  uint32_t* pql;   // [kPqList] prequantisation outliers of the item (item-local bin index)
   uint32_t* thr;   // [kThrLocalCap] 2x4 blocks holding a pixel >= amax_thr (first pixel, item-local)
   float* nb;       // [kPW][side^2] peak-test neighbourhoods (aliases the ring)
   uint32_t* acc;   // [sort_n2] accepted peaks of the item (aliases the ring)
@@ -223,6 +227,7 @@ enum {
   CTL_WAIT,
   CTL_TIMEOUT,
   CTL_NZ,                       // codes other than the zero residual's in the item
+  CTL_PQN,                      // prequantisation outliers in the item
   CTL_PQ,                       // [kMaxK] prequantisation outliers per panel of the item
   CTL_TMP = CTL_PQ + kMaxK,
   CTL_WORDS = CTL_TMP + 33
@@ -231,7 +236,7 @@ enum {
 __device__ __forceinline__ StreamView stream_view(unsigned char* sm, const FusedShape& sh) {
   StreamView v;
   v.hist = reinterpret_cast<uint32_t*>(sm + sh.off_hist);
-  v.mask = reinterpret_cast<uint32_t*>(sm + sh.off_mask);
+  v.pql = reinterpret_cast<uint32_t*>(sm + sh.off_pql);
   v.thr = reinterpret_cast<uint32_t*>(sm + sh.off_thr);
   v.nb = reinterpret_cast<float*>(sm + sh.off_nb);
   v.acc = reinterpret_cast<uint32_t*>(sm + sh.off_acc);
@@ -290,7 +295,6 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
   uint16_t* esc = s.codes + fbin;
   int32_t* lo_delta = s.lo_delta + fbin;
   uint32_t* pq_bits = s.pq_bits + fbin;
-  uint32_t* mask = v.mask + pi * sh.mask_words;
   const uint32_t slot_floats = 2 * RB * p.W;  // one panel's rows in a ring slot
   const size_t fu = (size_t)f * p.P + u;
   uint64_t* full_bar = v.bars;                 // [stages] rows landed (TMA transaction count)
@@ -301,10 +305,10 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
                        : nullptr;
   if (trace) trace[0] = global_ns();
   for (uint32_t k = tid; k < p.nsym; k += kPT) v.hist[k] = 0;
-  for (uint32_t k = tid; k < kp * sh.mask_words; k += kPT) v.mask[k] = 0;
   if (tid == 0) {
     v.ctl[CTL_THR] = 0;
     v.ctl[CTL_NZ] = 0;
+    v.ctl[CTL_PQN] = 0;
   }
   if (tid < kMaxK) v.ctl[CTL_PQ + tid] = 0;
   if (a.user_peaks && tid == 0) s.peak_part_count[fu] = 0;
@@ -397,9 +401,17 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
           if (owned && (Q0.outlier | Q1.outlier)) {
             const uint32_t lb = i * p.Wb + 2 * pc;
             atomicAdd(v.ctl + CTL_PQ + pi, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
-            atomicOr(mask + (lb >> 5), ((uint32_t)Q0.outlier | ((uint32_t)Q1.outlier << 1)) << (lb & 31));
-            if (Q0.outlier) pq_bits[lb] = Q0.outlier_bits;
-            if (Q1.outlier) pq_bits[lb + 1] = Q1.outlier_bits;
+            const uint32_t at = atomicAdd(v.ctl + CTL_PQN, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
+            uint32_t e = at;
+            if (Q0.outlier) {
+              pq_bits[lb] = Q0.outlier_bits;
+              if (e < kPqList) v.pql[e] = pi * Mp + lb;
+              ++e;
+            }
+            if (Q1.outlier) {
+              pq_bits[lb + 1] = Q1.outlier_bits;
+              if (e < kPqList) v.pql[e] = pi * Mp + lb + 1;
+            }
           }
         }
       }
@@ -505,13 +517,36 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
   if (trace) trace[1] = global_ns();
   // flush the item's histogram and its panels' outlier bits (disjoint slots)
   for (uint32_t k = tid; k < p.nsym; k += kPT) s.hist_part[fu * kMaxSymbols + k] = v.hist[k];
+  const uint32_t n_pq_item = v.ctl[CTL_PQN];
   for (uint32_t j = 0; j < kp; ++j) {
     const uint32_t n_pq = v.ctl[CTL_PQ + j];
     const size_t fp = (size_t)f * p.P + pn0 + j;
-    if (n_pq)
-      for (uint32_t k = tid; k < sh.mask_words; k += kPT)
-        s.pq_mask[fp * sh.mask_words + k] = v.mask[j * sh.mask_words + k];
+    if (n_pq)  // the panel's bitmask, set below
+      for (uint32_t k = tid; k < sh.mask_words; k += kPT) s.pq_mask[fp * sh.mask_words + k] = 0;
     if (tid == 0) s.pq_part_count[fp] = n_pq;
+  }
+  if (n_pq_item) {
+    __syncthreads();  // the masks are zero
+    uint32_t* gmask = s.pq_mask + ((size_t)f * p.P + pn0) * sh.mask_words;
+    if (n_pq_item <= kPqList) {
+      for (uint32_t e = tid; e < n_pq_item; e += kPT) {
+        const uint32_t b = v.pql[e], pj = b / Mp, lb = b - pj * Mp;
+        atomicOr(gmask + pj * sh.mask_words + (lb >> 5), 1u << (lb & 31));
+      }
+    } else {
+      // more outliers than the list holds: find them again from the input
+      for (uint32_t b = tid; b < kp * Mp; b += kPT) {
+        const uint32_t pj = b / Mp, lb = b - pj * Mp, i = lb / p.Wb, jb = lb - i * p.Wb;
+        const float* px = item_px + (size_t)pj * plane + (size_t)(2 * i) * p.W + 2 * jb;
+        const bool two = 2 * i + 1 < p.H;
+        const float4 va = make_float4(__ldg(px), __ldg(px + 1), 0.f, 0.f);
+        const float4 vb = two ? make_float4(__ldg(px + p.W), __ldg(px + p.W + 1), 0.f, 0.f)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        float v0, v1;
+        bin_pair(va, vb, two, v0, v1);
+        if (prequantize(v0, p).outlier) atomicOr(gmask + pj * sh.mask_words + (lb >> 5), 1u << (lb & 31));
+      }
+    }
   }
 
   // a1 + a2 on the listed blocks (on every pixel >= amax_thr if the list overflowed)
@@ -824,9 +859,14 @@ __device__ __forceinline__ void lane_counts(const DevParams& p, const Scratch& s
   const uint32_t n = s1 > s0 ? s1 - s0 : 0;  // symbols of this lane (<= 128)
   const uint32_t full = n >> 2;
   uint64_t acc = 0;
+  const uint64_t c4 = 4 * ctab[0x80];  // four zero residuals
+#pragma unroll 4
   for (uint32_t w = 0; w < full; ++w) {
     const uint32_t word = lw[w];
-    acc += ctab[word & 0xFFu] + ctab[(word >> 8) & 0xFFu] + ctab[(word >> 16) & 0xFFu] + ctab[word >> 24];
+    if (word == 0x80808080u)
+      acc += c4;
+    else
+      acc += ctab[word & 0xFFu] + ctab[(word >> 8) & 0xFFu] + ctab[(word >> 16) & 0xFFu] + ctab[word >> 24];
   }
   if (n & 3u) {
     const uint32_t word = lw[full];
@@ -1009,6 +1049,14 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
   const uint32_t* pq_bits = s.pq_bits + (size_t)g * p.M;
   const uint32_t k_begin = grp * sh.group_chunks, k_end = min(p.n_chunks, (grp + 1) * sh.group_chunks);
   uint32_t* wbuf = reinterpret_cast<uint32_t*>(sm + sh.off_stage) + warp * kStageWords;
+  // eight zero-residual symbols at once (their codeword repeated), when they fit 32 bits
+  const uint64_t zero_entry = btab[0x80];
+  const uint32_t len1 = (uint32_t)zero_entry, cw1 = (uint32_t)(zero_entry >> 32);
+  const bool run8 = len1 >= 1 && len1 <= 4;
+  const uint32_t len8 = 8 * len1;
+  uint32_t cw8 = 0;
+  if (run8)
+    for (int t = 0; t < 8; ++t) cw8 = (cw8 << len1) | cw1;
   const uint64_t t_loop = acct ? global_ns() : 0;
   for (uint32_t k = k_begin + warp; k < k_end; k += kPW) {
     const size_t o = (size_t)g * p.n_chunks + k;
@@ -1059,6 +1107,12 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
     for (uint32_t w = 0; w < (n + 3) / 4; ++w) {
       const uint32_t word = lw[w];
       const uint32_t cnt = min(4u, n - 4 * w);
+      // fastest path: eight zero residuals (bytes 0x80) in a row, one append
+      if (run8 && 4 * w + 8 <= n && (word & lw[w + 1]) == 0x80808080u && (word | lw[w + 1]) == 0x80808080u) {
+        append(cw8, len8);
+        ++w;
+        continue;
+      }
       // fast path: four ordinary bytes (no 0 = outlier, no 255 = escape) whose
       // codewords fit 32 bits together are appended at once
       const bool has0 = ((word - 0x01010101u) & ~word & 0x80808080u) != 0;
@@ -1203,7 +1257,7 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   const uint64_t base = off;
   // streaming role; the peak tests reuse the ring once the rows are consumed
   sh.off_hist = take(kMaxSymbols * 4);
-  sh.off_mask = take((uint64_t)sh.k * sh.mask_words * 4);
+  sh.off_pql = take(kPqList * 4);
   sh.off_thr = take(kThrLocalCap * 4);
   off = (off + 127) / 128 * 128;
   sh.off_ring = take((uint64_t)stages * sh.stage_bytes);
@@ -1268,8 +1322,10 @@ bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per
 bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out) {
   (void)device;
   (void)num_sms;
-  return fused_shape_for(p, 4, 0, 2, out) || fused_shape_for(p, 3, 0, 2, out) || fused_shape_for(p, 2, 0, 2, out) ||
-         fused_shape_for(p, 1, 0, 1, out);
+  // measured on CSPAD-like frames: 2 binned rows per step through a 3-slot
+  // ring, 4 CTAs per SM, is the fastest shape that fits
+  return fused_shape_for(p, 4, 2, 3, out) || fused_shape_for(p, 4, 2, 2, out) || fused_shape_for(p, 3, 2, 3, out) ||
+         fused_shape_for(p, 2, 2, 2, out) || fused_shape_for(p, 1, 2, 1, out);
 }
 
 cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,

@@ -242,3 +242,17 @@ def test_context_reuse_with_outliers_in_other_panels(path):
                 ost, ref = oracle.compress_frame(frames[k], oparams(p))
                 assert st[k] == ost == 0
                 assert np.array_equal(out[k, :nb[k]], ref)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_many_prequant_outliers(path):
+    """More prequantisation outliers in one work item than any per-item list
+    holds (the fused path then finds them again from the input)."""
+    geom = (3, 40, 44)
+    p = rb.default_params(atot_thr=300.0)
+    fused_or_skip(geom, p, path)
+    f = small_batch(geom, 2, 41)
+    f[0, :, 4:24, 6:26] = np.nan          # 100 NaN bins in every panel
+    f[1, 1, 10:30, 10:40] = 1e30          # 150 huge bins in one panel
+    f[1, 2, 0:2, :] = -np.inf
+    assert_parity(f, p, path)
