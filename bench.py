@@ -38,13 +38,13 @@ N_FRAMES = 1000
 # current k_fused, from one ncu capture of 100 frames of this workload; traffic
 # grows with the frame count, so a launch moves this many bytes per frame.
 # None whenever the kernel has changed since the capture.
-FUSED_DRAM_BYTES_PER_FRAME = 11.008e6
+FUSED_DRAM_BYTES_PER_FRAME = 10.468e6
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=N_FRAMES)
@@ -113,7 +113,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
