@@ -36,6 +36,7 @@ constexpr uint32_t kMaxK = 8;   // panels per streaming item
 constexpr uint32_t kConsumerWarps = 7;  // warps that code rows (31 columns each)
 constexpr uint32_t kProducerWarp = 7;   // the warp whose lane 0 issues the row copies
 constexpr uint32_t kThrLocalCap = 256;
+constexpr uint32_t kBlockKey = 1u << 31;  // a listed 2x4 block (else a listed candidate pixel)
 constexpr uint32_t kPqList = 128;  // prequantisation outliers an item lists before rescanning
 constexpr uint32_t kLagSize = 128, kLagWrite = 16;  // see launch_fused
 constexpr uint32_t kPanelTimedOut = 0xFFFFFFFFu;  // peak count of an item whose rows never arrived
@@ -195,9 +196,11 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
 struct StreamView {
   uint32_t* hist;  // [nsym]
   uint32_t* pql;   // [kPqList] prequantisation outliers of the item (item-local bin index)
-  uint32_t* thr;   // [kThrLocalCap] 2x4 blocks holding a pixel >= amax_thr (first pixel, item-local)
+  uint32_t* thr;   // [kThrLocalCap] listed candidates (item-local pixel) or 2x4 blocks (kBlockKey set)
+  float* thrv;     // [kThrLocalCap] value of each listed candidate
   float* nb;       // [kPW][side^2] peak-test neighbourhoods (aliases the ring)
   uint32_t* acc;   // [sort_n2] accepted peaks of the item (aliases the ring)
+  uint32_t* cand;  // [kThrLocalCap] listed candidates left after pruning (aliases the ring)
   uint32_t* ctl;
   unsigned char* ring;  // [stages][stage_bytes] raw rows in flight
   uint64_t* bars;       // [2 stages] per ring slot: rows landed, slot released
@@ -228,6 +231,7 @@ enum {
   CTL_TIMEOUT,
   CTL_NZ,                       // codes other than the zero residual's in the item
   CTL_PQN,                      // prequantisation outliers in the item
+  CTL_NCAND,                    // listed candidates left after pruning
   CTL_PQ,                       // [kMaxK] prequantisation outliers per panel of the item
   CTL_TMP = CTL_PQ + kMaxK,
   CTL_WORDS = CTL_TMP + 33
@@ -238,8 +242,10 @@ __device__ __forceinline__ StreamView stream_view(unsigned char* sm, const Fused
   v.hist = reinterpret_cast<uint32_t*>(sm + sh.off_hist);
   v.pql = reinterpret_cast<uint32_t*>(sm + sh.off_pql);
   v.thr = reinterpret_cast<uint32_t*>(sm + sh.off_thr);
+  v.thrv = reinterpret_cast<float*>(sm + sh.off_thr + kThrLocalCap * 4);
   v.nb = reinterpret_cast<float*>(sm + sh.off_nb);
   v.acc = reinterpret_cast<uint32_t*>(sm + sh.off_acc);
+  v.cand = reinterpret_cast<uint32_t*>(sm + sh.off_cand);
   v.ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
   v.ring = sm + sh.off_ring;
   v.bars = reinterpret_cast<uint64_t*>(sm + sh.off_bar);
@@ -415,18 +421,43 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
           }
         }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(empty_bar + slot);  // this warp is done with the slot
-      advance();
       if (!owned) hot = 0;
-      if (__any_sync(0xffffffffu, hot != 0)) {  // list the 2x4 blocks; their pixels are screened later
+      if (__any_sync(0xffffffffu, hot != 0)) {
+        // a 2x4 block holding a pixel >= amax_thr.  With rank >= 3 the block
+        // lies inside the window of each of its pixels, so only its first
+        // maximum can be a candidate: that pixel and its value are listed.
+        // With a smaller rank the block itself is listed.
 #pragma unroll
         for (int ii = 0; ii < RB; ++ii) {
           if (!((hot >> ii) & 1u)) continue;
+          const uint32_t i = i0 + ii;
+          uint32_t key = kBlockKey | (pi * plane + 2 * i * p.W + 4 * pc);
+          float best = 0.0f;
+          if (p.rank >= 3) {
+            const bool two = 2 * i + 1 < p.H;
+            const float4 va = rows[(2 * ii) * NP];
+            const float4 vb = rows[(2 * ii + 1) * NP];  // inside the slot; used only when two
+            const float px[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+            uint32_t at = 0;
+            best = px[0];
+#pragma unroll
+            for (int e = 1; e < 8; ++e)
+              if ((e < 4 || two) && (px[e] > best || best != best)) {
+                best = px[e];
+                at = e;
+              }
+            key = pi * plane + (2 * i + (at >> 2)) * p.W + 4 * pc + (at & 3u);
+          }
           const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
-          if (slot_t < kThrLocalCap) v.thr[slot_t] = pi * plane + 2 * (i0 + ii) * p.W + 4 * pc;
+          if (slot_t < kThrLocalCap) {
+            v.thr[slot_t] = key;
+            v.thrv[slot_t] = best;
+          }
         }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty_bar + slot);  // this warp is done with the slot
+      advance();
       // phase B: residuals and code bytes.  A pair of zero residuals (the
       // common case) stores 0x8080 and is not counted: the zero residual's
       // histogram count is derived from the bin count at the flush.
@@ -566,10 +597,42 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
       }
     };
     if (cnt <= kThrLocalCap) {
-      // each listed 2x4 block: a pixel beaten inside its own block (which lies
-      // inside its window) by the local-maximum rule can never be a candidate
-      for (uint32_t e = warp; e < cnt; e += kPW) {
-        const uint32_t key = v.thr[e], pj = key / plane, rem = key - pj * plane;
+      // a listed candidate beaten by another listed candidate inside its
+      // window (larger, or equal and earlier in row-major order) fails the
+      // local-maximum rule; the others are tested in full
+      if (tid == 0) v.ctl[CTL_NCAND] = 0;
+      __syncthreads();
+      for (uint32_t e = tid; e < cnt; e += kPT) {
+        const uint32_t key = v.thr[e];
+        bool keep = true;
+        if (!(key & kBlockKey)) {
+          const float x = v.thrv[e];
+          const uint32_t pj = key / plane, rem = key - pj * plane;
+          const int r = (int)(rem / p.W), c = (int)(rem % p.W);
+          keep = x >= p.amax;
+          for (uint32_t o = 0; o < cnt && keep; ++o) {
+            const uint32_t k2 = v.thr[o];
+            if (o == e || (k2 & kBlockKey) || k2 / plane != pj) continue;
+            const uint32_t rem2 = k2 - pj * plane;
+            const int dr = (int)(rem2 / p.W) - r, dc = (int)(rem2 % p.W) - c;
+            if (dr > p.rank || -dr > p.rank || dc > p.rank || -dc > p.rank) continue;
+            const float y = v.thrv[o];
+            if (y > x || (y == x && k2 < key)) keep = false;
+          }
+        }
+        if (keep) v.cand[atomicAdd(v.ctl + CTL_NCAND, 1u)] = key;
+      }
+      __syncthreads();
+      // survivors: a listed pixel is tested; a listed 2x4 block is screened
+      // first (a pixel beaten inside its own block, which lies inside its
+      // window, by the local-maximum rule can never be a candidate)
+      const uint32_t n_cand = v.ctl[CTL_NCAND];
+      for (uint32_t e = warp; e < n_cand; e += kPW) {
+        if (!(v.cand[e] & kBlockKey)) {
+          test(v.cand[e]);
+          continue;
+        }
+        const uint32_t key = v.cand[e] & ~kBlockKey, pj = key / plane, rem = key - pj * plane;
         const uint32_t r0 = rem / p.W;
         const uint32_t npx = r0 + 1 < p.H ? 8u : 4u;
         const uint32_t me = lane & 7u;
@@ -1230,6 +1293,7 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   const uint32_t NP = p.W / 4;
   if (NP < 1 || NP > kConsumerWarps * 31 || rb < 2 || rb > 3) return false;
   sh.k = min(kMaxK, kConsumerWarps * 31 / NP);
+  if ((uint64_t)sh.k * p.H * p.W >= kBlockKey) return false;  // item-local keys stay below the flag
   sh.U = ceil_div(p.P, sh.k);
   sh.RB = rb;
   sh.stages = stages;
@@ -1258,13 +1322,14 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   // streaming role; the peak tests reuse the ring once the rows are consumed
   sh.off_hist = take(kMaxSymbols * 4);
   sh.off_pql = take(kPqList * 4);
-  sh.off_thr = take(kThrLocalCap * 4);
+  sh.off_thr = take(kThrLocalCap * 8);  // keys, then values
   off = (off + 127) / 128 * 128;
   sh.off_ring = take((uint64_t)stages * sh.stage_bytes);
   const uint64_t ring_end = off;
   off = sh.off_ring;
   sh.off_nb = take((uint64_t)kPW * sh.side * sh.side * 4);
   sh.off_acc = take((uint64_t)n2 * 4);
+  sh.off_cand = take(kThrLocalCap * 4);
   const uint64_t stream_end = off > ring_end ? off : ring_end;
   // codebook role / size, write and plan roles (overlap the streaming role)
   off = base;

@@ -684,7 +684,7 @@ struct FusedShape {
   uint32_t group_chunks, groups; // chunks per size/write work item; items per frame
   uint32_t lag1, lag2;           // frames between stages in the ticket order (per launch)
   uint32_t input_evict_first;    // L2 policy of the streamed rows (1 = evict first)
-  uint32_t off_ctl, off_bar, off_hist, off_pql, off_thr, off_ring, off_nb, off_acc;  // streaming role
+  uint32_t off_ctl, off_bar, off_hist, off_pql, off_thr, off_ring, off_nb, off_acc, off_cand;  // streaming role
   uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw, off_offs;  // codebook / plan roles
   uint32_t off_stage;                                                        // size / write roles
   uint32_t smem;
