@@ -38,7 +38,7 @@ N_FRAMES = 1000
 # current k_fused, from one ncu capture of 100 frames of this workload; traffic
 # grows with the frame count, so a launch moves this many bytes per frame.
 # None whenever the kernel has changed since the capture.
-FUSED_DRAM_BYTES_PER_FRAME = 10.468e6
+FUSED_DRAM_BYTES_PER_FRAME = 10.419e6
 
 
 def parse():

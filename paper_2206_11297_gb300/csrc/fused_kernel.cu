@@ -38,7 +38,7 @@ constexpr uint32_t kProducerWarp = 7;   // the warp whose lane 0 issues the row 
 constexpr uint32_t kThrLocalCap = 256;
 constexpr uint32_t kBlockKey = 1u << 31;  // a listed 2x4 block (else a listed candidate pixel)
 constexpr uint32_t kPqList = 128;  // prequantisation outliers an item lists before rescanning
-constexpr uint32_t kLagSize = 128, kLagWrite = 16;  // see launch_fused
+constexpr uint32_t kLagSize = 256, kLagWrite = 16;  // see launch_fused
 constexpr uint32_t kPanelTimedOut = 0xFFFFFFFFu;  // peak count of an item whose rows never arrived
 
 __device__ __forceinline__ uint64_t global_ns() {
