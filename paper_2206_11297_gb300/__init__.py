@@ -80,6 +80,7 @@ _SIGNATURES = {
     "roibin_ctx_last_launch_count": (_u32, [_P]),
     "roibin_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "roibin_compress_frame_static": (ctypes.c_int, [_G, _Pr, _P, _P, _P, _P, _u64, _P, _P, _P]),
+    "roibin_ctx_autotune": (ctypes.c_int, [_P, _P, _u32, _P, _u64, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
 }
 EXPORTED_SYMBOLS = sorted(_SIGNATURES)
 
@@ -227,8 +228,27 @@ class Context:
             return None
         return tuple(x.value for x in v)
 
+    def autotune(self, frames, out=None, out_stride=None, frame_bytes=None, status=None, stream=None):
+        """roibin_ctx_autotune on a CUDA float32 [n, P, H, W] batch: times every fused shape that
+        fits and keeps the fastest.  Returns (best fused_shape, best ms per call)."""
+        import torch
+        n = frames.shape[0]
+        stride = int(out_stride or self.bound)
+        dev = frames.device
+        if out is None:
+            out = torch.empty((n, stride), dtype=torch.uint8, device=dev)
+        if frame_bytes is None:
+            frame_bytes = torch.empty(n, dtype=torch.int64, device=dev)
+        if status is None:
+            status = torch.empty(n, dtype=torch.int32, device=dev)
+        ms = ctypes.c_float(-1.0)
+        _check("roibin_ctx_autotune", self.lib.roibin_ctx_autotune(
+            self._h, _ptr(frames), n, _ptr(out), stride, _ptr(frame_bytes), _ptr(status),
+            _stream_handle(stream), ctypes.byref(ms)))
+        return self.fused_shape, ms.value
+
     def set_trace(self, trace=None, n_frames: int = 0):
-        """trace: CUDA int64 tensor of n_frames * 10 entries (None switches tracing off)."""
+        """trace: CUDA int64 tensor of n_frames * (16 + 4 P) entries (None switches tracing off)."""
         _check("roibin_ctx_set_trace", self.lib.roibin_ctx_set_trace(self._h, _ptr(trace), int(n_frames)))
 
     @property

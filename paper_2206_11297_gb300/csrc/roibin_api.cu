@@ -416,6 +416,57 @@ int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_
   return ROIBIN_OK;
 }
 
+int roibin_ctx_autotune(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, uint8_t* d_out,
+                        uint64_t out_stride, uint64_t* d_frame_bytes, int32_t* d_frame_status, void* stream,
+                        float* best_ms) {
+  if (!ctx || !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
+  if (!d_frames || !d_out || !d_frame_bytes || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
+  if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
+  if (out_stride < 16 || out_stride % 16 != 0) return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return ROIBIN_ERR_CUDA;
+  }
+  const int path_was = ctx->path_req;
+  const FusedShape keep = ctx->fshape;
+  ctx->path_req = ROIBIN_PATH_FUSED;
+  FusedShape best = keep;
+  float best_t = -1.0f;
+  int status = ROIBIN_OK;
+  for (uint32_t cps = 4; cps >= 2 && status == ROIBIN_OK; --cps) {
+    for (uint32_t rb = 2; rb <= 3 && status == ROIBIN_OK; ++rb) {
+      for (uint32_t stages = 2; stages <= 4 && status == ROIBIN_OK; ++stages) {
+        FusedShape sh;
+        if (!fused_shape_for(ctx->dp, cps, rb, stages, &sh) || sh.ctas_per_sm != cps) continue;
+        ctx->fshape = sh;
+        status = compress_device(ctx, d_frames, n_frames, nullptr, nullptr, d_out, out_stride, d_frame_bytes,
+                                 d_frame_status, st);  // warm-up
+        if (status != ROIBIN_OK) break;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2 && status == ROIBIN_OK; ++rep)
+          status = compress_device(ctx, d_frames, n_frames, nullptr, nullptr, d_out, out_stride, d_frame_bytes,
+                                   d_frame_status, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) status = ROIBIN_ERR_CUDA;
+        float ms = 0.0f;
+        if (status == ROIBIN_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best_t < 0 || ms < best_t)) {
+          best_t = ms;
+          best = sh;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->path_req = path_was;
+  ctx->fshape = status == ROIBIN_OK && best_t >= 0 ? best : keep;
+  if (best_ms && best_t >= 0) *best_ms = best_t / 2.0f;
+  return status;
+}
+
 int roibin_ctx_set_trace(roibin_ctx* ctx, uint64_t* d_trace, uint32_t n_frames) {
   if (!ctx || (n_frames > 0 && !d_trace)) return ROIBIN_ERR_INVALID_ARG;
   ctx->trace = n_frames ? d_trace : nullptr;

@@ -256,3 +256,23 @@ def test_many_prequant_outliers(path):
     f[1, 1, 10:30, 10:40] = 1e30          # 150 huge bins in one panel
     f[1, 2, 0:2, :] = -np.inf
     assert_parity(f, p, path)
+
+
+def test_autotuned_shape_writes_the_same_bytes():
+    """The autotuner keeps one of the fused shapes; every shape writes the oracle's bytes."""
+    import torch
+    geom = (4, 37, 52)
+    f = small_batch(geom, 3, seed=77)
+    p = rb.default_params(atot_thr=300.0)
+    with rb.Context(geom, p, max_frames=3) as ctx:
+        if ctx.resolved_path != rb.PATH_FUSED:
+            pytest.skip("no fused path for this shape")
+        shape, ms = ctx.autotune(torch.from_numpy(f).cuda())
+        assert shape is not None and ms > 0
+        ctx.set_path(rb.PATH_FUSED)
+        out, nb, st = ctx.compress(torch.from_numpy(f).cuda())
+        torch.cuda.synchronize()
+        out, nb, st = out.cpu().numpy(), nb.cpu().numpy(), st.cpu().numpy()
+    for k in range(3):
+        ost, ref = oracle.compress_frame(f[k], oparams(p))
+        assert st[k] == ost == 0 and np.array_equal(out[k, :nb[k]], ref)

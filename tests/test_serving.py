@@ -1,0 +1,98 @@
+"""The serving loop: continuous batching across geometries, HBM-budget
+admission, and each request's bytes equal to compressing it alone."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2206_11297_gb300 as rb
+from paper_2206_11297_gb300 import serving
+from synthetic import FrameRecipe, make_frame
+
+
+def test_poisson_schedule_is_seeded_and_bounded():
+    pools = {(2, 8, 8): np.zeros((10, 2, 8, 8), np.float32), (1, 4, 4): np.zeros((5, 1, 4, 4), np.float32)}
+    a = serving.poisson_requests(pools, rate_hz=500, seconds=0.2, max_frames=4, seed=3)
+    b = serving.poisson_requests(pools, rate_hz=500, seconds=0.2, max_frames=4, seed=3)
+    assert a == b and 40 < len(a) < 200
+    for t, g, n, first in a:
+        assert 0 < t <= 0.2 and 1 <= n <= 4 and 0 <= first <= pools[g].shape[0] - n
+    assert [x[0] for x in a] == sorted(x[0] for x in a)
+
+
+def _pools(geoms, n=24):
+    import torch
+    pools = {}
+    for i, g in enumerate(geoms):
+        r = FrameRecipe(g, peaks=("uniform", 2, 10), seed=50 + i)
+        pools[g] = torch.from_numpy(np.stack([make_frame(r, k) for k in range(n)])).pin_memory()
+    return pools
+
+
+def _alone(pools, req, params):
+    import torch
+    g = req.geometry
+    with rb.Context(g, params, max_frames=req.frames.shape[0]) as ctx:
+        out, nb, st = ctx.compress(req.frames.cuda())
+        torch.cuda.synchronize()
+        out, nb, st = out.cpu().numpy(), nb.cpu().numpy(), st.cpu().numpy()
+    return [out[k, :nb[k]] if st[k] == 0 else None for k in range(len(nb))]
+
+
+def _check_mixed(server, pools, schedule, params):
+    reqs = serving.run(pools, schedule, server)
+    assert len(reqs) == len(schedule)
+    for r in reqs:
+        assert r.done is not None and r.latency >= 0
+        assert all(s == 0 for s in r.status)
+        alone = _alone(pools, r, params)
+        for mine, ref in zip(r.streams, alone):
+            assert np.array_equal(mine, ref)
+    # and against the oracle for one frame of each geometry
+    seen = set()
+    for r in reqs:
+        if r.geometry in seen:
+            continue
+        seen.add(r.geometry)
+        st, ref = oracle.compress_frame(r.frames[0].numpy(), oracle.make_params(**params.as_dict()))
+        assert st == 0 and np.array_equal(r.streams[0], ref)
+    return reqs
+
+
+@pytest.mark.gpu
+def test_mixed_geometries_same_bytes_alone_and_in_the_mix():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    geoms = [(3, 40, 44), (4, 37, 52), (2, 21, 27)]   # two fused shapes and one plain-path shape
+    pools = _pools(geoms)
+    params = rb.default_params(atot_thr=300.0)
+    schedule = serving.poisson_requests(pools, rate_hz=2000, seconds=0.05, max_frames=8, seed=7)
+    server = serving.Server(params, hbm_budget=4 << 30, lane_frames=16, lanes_per_geometry=2)
+    try:
+        reqs = _check_mixed(server, pools, schedule, params)
+        assert {r.geometry for r in reqs} == set(geoms)
+    finally:
+        server.close()
+
+
+@pytest.mark.gpu
+def test_budget_admission_releases_idle_lanes():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    geoms = [(3, 40, 44), (4, 37, 52)]
+    pools = _pools(geoms)
+    params = rb.default_params(atot_thr=300.0)
+    # room for one lane at a time: the other geometry waits until the first lane is released
+    one = serving.Server(params, hbm_budget=1 << 40, lane_frames=16)
+    for g in geoms:
+        one._lane_for(g)
+    lane_bytes = max(l.bytes for l in one.lanes)
+    one.close()
+    schedule = [(0.0, geoms[k % 2], 4, 4 * (k // 2)) for k in range(8)]
+    server = serving.Server(params, hbm_budget=int(lane_bytes * 1.5), lane_frames=16, lanes_per_geometry=1)
+    try:
+        _check_mixed(server, pools, schedule, params)
+        assert len(server.lanes) == 1 and server.held_bytes <= server.budget
+    finally:
+        server.close()
