@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=N_FRAMES)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-decompress", action="store_true", help="skip the decompression timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--min-load-seconds", type=float, default=2.0,
                     help="keep the GPU busy at least this long before timing (clock sampling)")
@@ -344,6 +345,51 @@ def run_ours(args, rank, local, world):
         "clocks": clocks,
         "e2e": e2e,
     }
+    # decompression of the same batch (a13): the streams in their slots, decoded
+    # back to float32 frames on the device, by each decompression path
+    if not args.no_decompress:
+        ctx.set_path(main)
+        ctx.compress(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
+        flat = out.view(-1)
+        offsets = torch.arange(n, dtype=torch.int64, device=dev) * stride
+        recon = torch.empty_like(frames)
+        dstat = torch.empty(n, dtype=torch.int32, device=dev)
+        n_bins = ctx.n_bins
+        dec = {}
+        for dpath, dname in ((rb.DEC_PANEL, "panel"), (rb.DEC_MULTIPASS, "multipass")):
+            try:
+                ctx.set_decompress_path(dpath)
+            except rb.RoibinError:
+                continue
+            for _ in range(max(3, args.warmup // 2)):
+                ctx.decompress(flat, offsets, n, out=recon, status=dstat)
+            torch.cuda.synchronize()
+            ctx.enable_timing(True)
+            ctx.kernel_times()
+            d_steps = max(3, min(args.steps, 10))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(d_steps):
+                ctx.decompress(flat, offsets, n, out=recon, status=dstat)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dk = ctx.kernel_times()
+            ctx.enable_timing(False)
+            assert (dstat.cpu() == 0).all()
+            d_ms = e0.elapsed_time(e1) / d_steps
+            dec[dname] = {"value": n * frame_bytes / 1e9 / (d_ms / 1e3), "unit": "GB/s of float32 frames out",
+                          "ms_per_step": d_ms, "launches_per_step": ctx.last_launch_count,
+                          "kernels_ms_per_step": {k: v[0] / d_steps for k, v in dk.items()}}
+            pk = dk.get("dec_panel")
+            if pk:
+                # algorithmic bytes of the panel kernel: the u16 symbols in, the
+                # float32 frames out
+                algo_b = n * (2 * n_bins + frame_bytes)
+                ach = algo_b / 1e9 / (pk[0] / 1e3 / pk[1])
+                dec[dname]["roofline"] = {"bound": "hbm", "kernel": "dec_panel", "achieved": ach,
+                                          "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
+        ctx.set_decompress_path(rb.DEC_AUTO)
+        line["decompress"] = dec
     if rb.PATH_PLAIN in res and main != rb.PATH_PLAIN:
         pr = res[rb.PATH_PLAIN]
         line["plain"] = {"value": args.steps * n * frame_bytes / 1e9 / (pr["total_ms"] / 1e3), "unit": "GB/s",

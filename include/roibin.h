@@ -69,6 +69,15 @@ extern "C" {
 #define ROIBIN_PATH_FUSED 2 /* one persistent kernel per batch: work items of a few
                                panels each, then each frame's coding stages        */
 
+/* Decompression paths (roibin_ctx_set_decompress_path). */
+#define ROIBIN_DEC_AUTO 0      /* PANEL when the geometry allows it, else MULTIPASS      */
+#define ROIBIN_DEC_PANEL 1     /* prefix-table decode to symbols, then one block per
+                                  (frame, panel) rebuilds the panel in shared memory
+                                  and writes its pixels once; needs bins per panel row
+                                  (cols / bin_w rounded up) <= 4096                     */
+#define ROIBIN_DEC_MULTIPASS 2 /* one kernel per step of the inverse, intermediates in
+                                  device memory                                         */
+
 typedef struct roibin_ctx roibin_ctx;
 
 /* Detector geometry: every frame is n_panels panels of rows x cols pixels
@@ -131,7 +140,7 @@ uint64_t roibin_ctx_scratch_bytes(const roibin_ctx* ctx);
 
 /* Selects the kernel path for later roibin_compress calls (ROIBIN_PATH_*).
  * ROIBIN_ERR_INVALID_ARG when FUSED is asked for a shape it does not cover
- * (it needs bin 2x2, cols % 4 == 0 and cols <= 1024).  Both paths write
+ * (it needs bin 2x2, cols % 4 == 0 and cols <= 868).  Both paths write
  * identical bytes. */
 int roibin_ctx_set_path(roibin_ctx* ctx, int path);
 /* The path AUTO resolves to for this context (PLAIN or FUSED). */
@@ -210,6 +219,13 @@ int roibin_compress(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames,
 int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes,
                       const uint64_t* d_frame_offsets, uint32_t n_frames, float* d_frames_out,
                       int32_t* d_frame_status, void* stream);
+
+/* Selects the kernel path for later roibin_decompress calls (ROIBIN_DEC_*).
+ * ROIBIN_ERR_INVALID_ARG for an unknown path or PANEL on a geometry it does
+ * not cover.  Both paths write identical frames and statuses. */
+int roibin_ctx_set_decompress_path(roibin_ctx* ctx, int path);
+/* The decompression path AUTO resolves to (PANEL or MULTIPASS). */
+int roibin_ctx_resolved_decompress_path(const roibin_ctx* ctx);
 
 /* Reserves the device staging area that roibin_compress_host needs:
  * max_frames_per_call input frames, the same number of output slots of

@@ -26,6 +26,7 @@ ERR_TIMEOUT = -6
 ERR_CODE_LENGTH = -7
 
 PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
+DEC_AUTO, DEC_PANEL, DEC_MULTIPASS = 0, 1, 2
 
 GEOMETRIES = {"cspad": (32, 185, 388), "epix10k": (16, 352, 384), "jungfrau": (8, 512, 1024)}
 
@@ -63,6 +64,8 @@ _SIGNATURES = {
     "roibin_ctx_scratch_bytes": (_u64, [_P]),
     "roibin_ctx_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
     "roibin_ctx_resolved_path": (ctypes.c_int, [_P]),
+    "roibin_ctx_set_decompress_path": (ctypes.c_int, [_P, ctypes.c_int]),
+    "roibin_ctx_resolved_decompress_path": (ctypes.c_int, [_P]),
     "roibin_ctx_set_fused_shape": (ctypes.c_int, [_P, _u32, _u32, _u32]),
     "roibin_ctx_fused_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(_u32)] * 5),
     "roibin_ctx_set_trace": (ctypes.c_int, [_P, _P, _u32]),
@@ -186,6 +189,13 @@ class Context:
             int(hbm_budget), self.device))
         self._h = h
 
+    @property
+    def n_bins(self) -> int:
+        """Bins per frame: P * ceil(rows / bin_h) * ceil(cols / bin_w)."""
+        P, H, W = self.geometry
+        bh, bw = int(self.params.bin_h), int(self.params.bin_w)
+        return P * (-(-H // bh)) * (-(-W // bw))
+
     # -- lifetime
     def close(self):
         if getattr(self, "_h", None):
@@ -215,6 +225,13 @@ class Context:
 
     def set_path(self, path: int):
         _check("roibin_ctx_set_path", self.lib.roibin_ctx_set_path(self._h, int(path)))
+
+    def set_decompress_path(self, path: int):
+        _check("roibin_ctx_set_decompress_path", self.lib.roibin_ctx_set_decompress_path(self._h, int(path)))
+
+    @property
+    def resolved_decompress_path(self) -> int:
+        return int(self.lib.roibin_ctx_resolved_decompress_path(self._h))
 
     def set_fused_shape(self, ctas_per_sm: int, rows_per_step: int = 0, stages: int = 2):
         _check("roibin_ctx_set_fused_shape", self.lib.roibin_ctx_set_fused_shape(

@@ -15,7 +15,7 @@ const char* kernel_name(int id) {
   static const char* names[K_COUNT] = {
       "reset", "stream", "peaks", "peaks_final", "huffman", "chunks", "plan", "encode", "roi",
       "fused", "dec_parse", "dec_decode", "dec_lorenzo", "dec_rows", "dec_cols", "dec_pq",
-      "dec_upsample", "dec_roi", "roi_mask", "pack"};
+      "dec_upsample", "dec_roi", "dec_panel", "roi_mask", "pack"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 

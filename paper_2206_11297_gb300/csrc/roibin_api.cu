@@ -33,6 +33,7 @@ struct roibin_ctx {
   uint64_t budget = 0;
   uint32_t max_frames = 0;
   int path_req = ROIBIN_PATH_AUTO;
+  int dec_path_req = ROIBIN_DEC_AUTO;
   bool fused_ok = false;
   FusedShape fshape{};
   uint64_t* trace = nullptr;
@@ -243,6 +244,11 @@ int compress_plain(roibin_ctx* ctx, const PlainArgs& a, cudaStream_t st) {
   if (p.max_peaks > 0)
     if ((e = timed(ctx, K_ROI, st, [&] { return launch_roi(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   return ROIBIN_OK;
+}
+
+int resolved_dec_path(const roibin_ctx* ctx) {
+  if (ctx->dec_path_req == ROIBIN_DEC_MULTIPASS) return ROIBIN_DEC_MULTIPASS;
+  return dec_panel_rows(ctx->dp) ? ROIBIN_DEC_PANEL : ROIBIN_DEC_MULTIPASS;
 }
 
 int resolved_path(const roibin_ctx* ctx) {
@@ -507,6 +513,14 @@ int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes, c
   ctx->last_launches = 0;
   cudaError_t e;
   if ((e = timed(ctx, K_DEC_PARSE, st, [&] { return launch_dec_parse(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  if (resolved_dec_path(ctx) == ROIBIN_DEC_PANEL) {
+    if ((e = timed(ctx, K_DEC_DECODE, st, [&] { return launch_dec_decode_lut(p, s, a, st); })) != cudaSuccess)
+      return cuda_status(e);
+    if ((e = timed(ctx, K_DEC_PANEL, st, [&] { return launch_dec_panel(p, s, a, st); })) != cudaSuccess)
+      return cuda_status(e);
+    ctx->last_launches++;  // the status copy that ends the panel launch
+    return ROIBIN_OK;
+  }
   if ((e = timed(ctx, K_DEC_DECODE, st, [&] { return launch_dec_decode(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_LORENZO, st, [&] { return launch_dec_lorenzo(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_ROWS, st, [&] { return launch_dec_rows(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
@@ -514,7 +528,22 @@ int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes, c
   if ((e = timed(ctx, K_DEC_PQ, st, [&] { return launch_dec_pq(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_UPSAMPLE, st, [&] { return launch_dec_upsample(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_ROI, st, [&] { return launch_dec_roi(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  ctx->last_launches++;  // the status copy that ends the ROI launch
   return ROIBIN_OK;
+}
+
+int roibin_ctx_set_decompress_path(roibin_ctx* ctx, int path) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  if (path != ROIBIN_DEC_AUTO && path != ROIBIN_DEC_PANEL && path != ROIBIN_DEC_MULTIPASS)
+    return ROIBIN_ERR_INVALID_ARG;
+  if (path == ROIBIN_DEC_PANEL && dec_panel_rows(ctx->dp) == 0) return ROIBIN_ERR_INVALID_ARG;
+  ctx->dec_path_req = path;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_resolved_decompress_path(const roibin_ctx* ctx) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  return resolved_dec_path(ctx);
 }
 
 int roibin_ctx_reserve_host_path(roibin_ctx* ctx) {

@@ -61,6 +61,7 @@ struct DecInfo {
   float eb, two_eb;
   int32_t R, roi_h, roi_w;
   uint32_t nsym;
+  uint32_t sparse;    // 1: a length-1 code, and few other symbols in every chunk
 };
 
 // Per-frame scratch owned by the context (indexed by frame slot).
@@ -82,8 +83,10 @@ struct Scratch {
   FramePlan* plan;        // [n]
   int32_t* status;        // [n]
   // decompression (aliases lo_delta / pq_bits: a context runs one call at a time)
-  int32_t* dq;            // [n][M] delta, then q
-  float* bhat;            // [n][M]
+  int32_t* dq;            // [n][M] delta, then q (multi-pass); the panel path keeps
+                          // [n][P] first Lorenzo outlier of each panel at dq + f * M
+  float* bhat;            // [n][M] (multi-pass); the panel path keeps [n][P] first
+                          // prequantisation outlier of each panel at bhat + f * M
   uint32_t* dec_table;    // [n][kDecTableWords] canonical decoding tables
   uint32_t* dec_zero;     // [n] code-0 symbols decoded
   DecInfo* dec_info;      // [n]
@@ -100,7 +103,13 @@ struct Scratch {
   uint32_t* frame_done;     // [4 n + 1] stage counters and flags, ticket counter
 };
 
-constexpr uint32_t kDecTableWords = 34 + 34 + 34 + kMaxSymbols;  // count, first, index, symbols
+// count, first, index (34 words each), symbols; padded to 16 bytes
+constexpr uint32_t kDecCanonWords = (34 + 34 + 34 + kMaxSymbols + 3) & ~3u;
+// prefix table: entry for the next kDecLutBits bits = (length << 10) | symbol for
+// codes of at most kDecLutBits bits, 0 for a longer code (u16 entries, two a word)
+constexpr uint32_t kDecLutBits = 12;
+constexpr uint32_t kDecLutWords = (1u << kDecLutBits) / 2;
+constexpr uint32_t kDecTableWords = kDecCanonWords + kDecLutWords;
 
 // ---- small helpers -------------------------------------------------------
 __host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15u) & ~uint64_t(15u); }
@@ -722,6 +731,7 @@ enum KernelId {
   K_DEC_PQ,
   K_DEC_UPSAMPLE,
   K_DEC_ROI,
+  K_DEC_PANEL,
   K_ROI_MASK,
   K_PACK,
   K_COUNT
@@ -756,9 +766,67 @@ cudaError_t launch_dec_cols(const DevParams& p, const Scratch& s, const DecArgs&
 cudaError_t launch_dec_pq(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_upsample(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_roi(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+// the panel path: decode through the prefix table into symbols, then one block
+// per (frame, panel) rebuilds the panel strip by strip
+uint32_t dec_panel_rows(const DevParams& p);  // binned rows per strip; 0: panel path unavailable
+cudaError_t launch_dec_decode_lut(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_panel(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_roi_mask(const DevParams& p, const uint16_t* peaks, const uint32_t* npeaks,
                             uint32_t n, uint8_t* mask, cudaStream_t st);
 cudaError_t launch_pack(const uint8_t* src, uint64_t stride, const uint64_t* sizes, const uint64_t* offsets,
                         uint32_t n, uint8_t* dst, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// mbarrier + TMA bulk-copy helpers (the fused streaming ring, the decompressor's
+// symbol strips)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// A waiting thread is suspended (up to kSuspendNs per try) until the phase
+// completes instead of spinning on the barrier.
+constexpr uint32_t kSuspendNs = 1000;
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+constexpr uint32_t kSpinLimit = 1u << 21;  // bounded mbarrier wait (about 2 s at most)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// 1-D bulk copy global -> shared, completion counted on `bar`, L2 evict-first.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                            uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// L2 policy for data read once.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 
 }  // namespace roibin

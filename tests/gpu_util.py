@@ -44,7 +44,7 @@ def gpu_compress(frames: np.ndarray, params: rb.Params, path: int = rb.PATH_AUTO
     return st, nb, streams
 
 
-def gpu_decompress(streams, geometry, params: rb.Params, ctx=None):
+def gpu_decompress(streams, geometry, params: rb.Params, ctx=None, dec_path=rb.DEC_AUTO):
     """Packs the streams (16-byte aligned) and decompresses them on the GPU."""
     import torch
     n = len(streams)
@@ -61,12 +61,23 @@ def gpu_decompress(streams, geometry, params: rb.Params, ctx=None):
     try:
         data = torch.from_numpy(buf).cuda()
         off = torch.tensor(offs, dtype=torch.int64, device="cuda")
+        ctx.set_decompress_path(dec_path)
         rec, st = ctx.decompress(data, off, n)
         torch.cuda.synchronize()
         return rec.cpu().numpy(), st.cpu().numpy()
     finally:
         if own:
             ctx.close()
+
+
+def dec_paths(geometry, params):
+    """Every decompression path the geometry has: the panel path when it fits, and multi-pass."""
+    ctx = rb.Context(geometry, params, max_frames=1)
+    try:
+        panel = ctx.resolved_decompress_path == rb.DEC_PANEL
+    finally:
+        ctx.close()
+    return ([rb.DEC_PANEL] if panel else []) + [rb.DEC_MULTIPASS]
 
 
 def assert_parity(frames, params, path=rb.PATH_AUTO, peaks=None, npeaks=None, check_decompress=True):
@@ -94,11 +105,15 @@ def assert_parity(frames, params, path=rb.PATH_AUTO, peaks=None, npeaks=None, ch
     if check_decompress:
         ok = [k for k in range(len(refs)) if refs[k] is not None]
         if ok:
-            rec, dst = gpu_decompress([refs[k] for k in ok], frames.shape[1:], params)
-            for i, k in enumerate(ok):
-                assert dst[i] == 0, f"frame {k}: decompress status {dst[i]}"
+            orecs = []
+            for k in ok:
                 ost, orec = oracle.decompress_frame(refs[k], frames.shape[1:])
                 assert ost == 0
-                assert np.array_equal(rec[i].view(np.uint32), orec.view(np.uint32)), \
-                    f"frame {k}: reconstruction differs"
+                orecs.append(orec)
+            for dp in dec_paths(frames.shape[1:], params):
+                rec, dst = gpu_decompress([refs[k] for k in ok], frames.shape[1:], params, dec_path=dp)
+                for i, k in enumerate(ok):
+                    assert dst[i] == 0, f"frame {k}: decompress path {dp} status {dst[i]}"
+                    assert np.array_equal(rec[i].view(np.uint32), orecs[i].view(np.uint32)), \
+                        f"frame {k}: decompress path {dp}: reconstruction differs"
     return st, nb, streams

@@ -92,6 +92,18 @@ def test_epix_hot_pixels(eb, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("eb", [1.0, 10.0, 50.0])
+def test_epix_hot_pixels_round_trip(eb, path):
+    """With room for their ~3,600 peaks the hot-pixel frames compress, and their
+    streams decode on the dense decoder: no length-1 code at eb 1 and 10, and
+    chunks too full of other symbols for the sparse way at eb 50."""
+    r = RECIPES["epix_hot"]
+    f = np.stack([make_frame(r, k) for k in range(2)])
+    st, _, _ = assert_parity(f, rb.default_params(abs_eb=eb, max_peaks=8192), path)
+    assert (st == 0).all()
+
+
+@pytest.mark.parametrize("path", PATHS)
 def test_jungfrau(path):
     r = RECIPES["jungfrau_mixed"]
     f = np.stack([make_frame(r, k) for k in range(2)])
@@ -183,8 +195,77 @@ def test_corrupt_streams_are_rejected():
     bad_len[o["lengths"]:o["lengths"] + 2 * h["quant_radius"]] = 0
     bad_bits = ref.copy()
     bad_bits[o["bitstream"]:o["end"]] = 0xFF
-    rec, dst = gpu_decompress([bad_magic, bad_total, bad_len, bad_bits, ref], geom, p)
-    assert dst.tolist()[:4] == [rb.ERR_CORRUPT_STREAM] * 4 and dst[4] == 0
+    for dp in (rb.DEC_PANEL, rb.DEC_MULTIPASS):
+        rec, dst = gpu_decompress([bad_magic, bad_total, bad_len, bad_bits, ref], geom, p, dec_path=dp)
+        assert dst.tolist()[:4] == [rb.ERR_CORRUPT_STREAM] * 4 and dst[4] == 0
+
+
+def test_wide_rows_decompress_through_multipass():
+    """Panels wider than 4096 bins per row have no panel decompression path:
+    AUTO resolves to multi-pass and the round trip still matches the oracle."""
+    geom = (1, 5, 8200)
+    p = rb.default_params(atot_thr=300.0)
+    with rb.Context(geom, p, max_frames=1) as ctx:
+        assert ctx.resolved_decompress_path == rb.DEC_MULTIPASS
+        with pytest.raises(rb.RoibinError):
+            ctx.set_decompress_path(rb.DEC_PANEL)
+    assert_parity(small_batch(geom, 2, 5), p, rb.PATH_PLAIN)
+
+
+def test_wide_rows_decompress_one_bin_row_per_strip():
+    """3100 bins per row: the panel path takes one binned row per strip."""
+    geom = (2, 5, 6200)
+    p = rb.default_params(atot_thr=300.0)
+    with rb.Context(geom, p, max_frames=1) as ctx:
+        assert ctx.resolved_decompress_path == rb.DEC_PANEL
+    assert_parity(small_batch(geom, 2, 6), p, rb.PATH_PLAIN)
+
+
+@pytest.mark.parametrize("dec_path", [rb.DEC_PANEL, rb.DEC_MULTIPASS])
+def test_corrupt_outlier_lists_and_peaks_are_rejected(dec_path):
+    """Outlier lists out of order, off their code-0 bins or past the frame, and a
+    peak outside the frame: the oracle and both decompression paths reject each."""
+    geom = (3, 24, 28)
+    f = small_batch(geom, 1, 17)
+    f[0, 0, 8:12, 8:12] = 60000.0   # Lorenzo outliers around a bright block
+    f[0, 2, 4:8, 4:8] = -60000.0
+    f[0, 1, 3, 3] = np.nan           # prequantisation outliers
+    f[0, 2, 20, 20] = np.inf
+    p = rb.default_params(atot_thr=300.0)
+    st, ref = oracle.compress_frame(f[0], oparams(p))
+    assert st == 0
+    h = oracle.parse_header(ref)
+    o = oracle.section_offsets(h)
+    assert h["n_lorenzo"] >= 2 and h["n_prequant"] >= 2 and h["n_peaks"] >= 1
+    u32 = lambda b, off: b[off:off + 4].view(np.uint32)
+    bad = {}
+    b = ref.copy()   # first two Lorenzo outliers swapped
+    b[o["lorenzo"]:o["lorenzo"] + 16] = np.concatenate([ref[o["lorenzo"] + 8:o["lorenzo"] + 16],
+                                                        ref[o["lorenzo"]:o["lorenzo"] + 8]])
+    bad["lo_order"] = b
+    b = ref.copy()   # first Lorenzo outlier moved to bin 0 (not a code-0 bin)
+    u32(b, o["lorenzo"])[0] = 0
+    bad["lo_place"] = b
+    b = ref.copy()   # last Lorenzo outlier past the frame
+    u32(b, o["lorenzo"] + 8 * (h["n_lorenzo"] - 1))[0] = 0xFFFFFFF0
+    bad["lo_range"] = b
+    b = ref.copy()   # prequantisation outliers out of order
+    u32(b, o["prequant"] + 8)[0] = u32(ref, o["prequant"])[0]
+    bad["pq_order"] = b
+    b = ref.copy()   # last prequantisation outlier past the frame
+    u32(b, o["prequant"] + 8 * (h["n_prequant"] - 1))[0] = 0xFFFFFFF0
+    bad["pq_range"] = b
+    b = ref.copy()   # first peak on a panel that does not exist
+    b[o["peaks"]:o["peaks"] + 2].view(np.uint16)[0] = 7
+    bad["peak_panel"] = b
+    names = list(bad)
+    for k in names:
+        assert oracle.decompress_frame(bad[k], geom)[0] == oracle.ERR_CORRUPT_STREAM, k
+    rec, dst = gpu_decompress([bad[k] for k in names] + [ref], geom, p, dec_path=dec_path)
+    assert dict(zip(names, dst.tolist())) == {k: rb.ERR_CORRUPT_STREAM for k in names}
+    assert dst[-1] == 0
+    ost, orec = oracle.decompress_frame(ref, geom)
+    assert np.array_equal(rec[-1].view(np.uint32), orec.view(np.uint32))
 
 
 @pytest.mark.parametrize("path", PATHS)
