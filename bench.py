@@ -328,11 +328,12 @@ def run_ours(args, rank, local, world):
         "config": {"workload": f"{n} CSPAD-like frames 32x185x388 f32 per GPU, 20-100 peaks, ROI 17x17, "
                                "bin 2x2, eb 10, batched",
                    "frames_per_step": n, "path": {1: "plain", 2: "fused"}[main],
-                   "l2": "inputs (9.19 GB per step) larger than L2; no flush"},
+                   "l2": f"inputs ({n * frame_bytes / 1e9:.2f} GB per step) "
+                         + ("larger than L2; no flush" if n * frame_bytes > 129e6 else "not larger than L2")},
         "frames_per_s": gbs * 1e9 / frame_bytes,
         "latency_ms": {"p50": steps_ms[len(steps_ms) // 2],
                        "p99": steps_ms[min(len(steps_ms) - 1, int(0.99 * len(steps_ms)))],
-                       "unit": "per 1,000-frame batch"},
+                       "unit": f"per {n:,}-frame batch"},
         "compression_ratio": {"vs_f32": n * frame_bytes / r["out_bytes"],
                               "vs_u16": n * frame_bytes / 2 / r["out_bytes"]},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
