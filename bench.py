@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=N_FRAMES)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-decompress", action="store_true", help="skip the decompression timing")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-geometry graph timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--min-load-seconds", type=float, default=2.0,
                     help="keep the GPU busy at least this long before timing (clock sampling)")
@@ -215,6 +216,69 @@ def run_reference(args, rank, world):
                              "sample": f"{sample} frames per step, one frame per worker thread"},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- mixed batch
+# Uneven batching: three detector geometries with 0-500 peaks per frame (the
+# epix10k-like frames also carry 1% hot pixels), each on its own context.
+MIXED = (("cspad_mixed", 300), ("epix_mixed", 300), ("jungfrau_mixed", 150))
+
+
+def mixed_graph(args, dev, local, stream):
+    """The mixed batch as branches of one CUDA graph (roibin_graph_*), each fused
+    context on the shape its autotuner picked, timed against the same three
+    compress calls issued one after another on one stream."""
+    import torch
+    import paper_2206_11297_gb300 as rb
+    params = rb.default_params(max_peaks=8192)
+    jobs, total, frames_of, paths, shapes = [], 0, {}, {}, {}
+    for name, n in MIXED:
+        r = RECIPES[name]
+        ctx = rb.Context(r.geometry, params, max_frames=n, device=local)
+        host = np.empty((n, *r.geometry), np.float32)
+        make_batch_threaded(r, n, first=0, out=host)
+        frames = torch.from_numpy(host).to(dev)
+        out = torch.empty((n, ctx.bound), dtype=torch.uint8, device=dev)
+        nb = torch.empty(n, dtype=torch.int64, device=dev)
+        st = torch.empty(n, dtype=torch.int32, device=dev)
+        if ctx.resolved_path == rb.PATH_FUSED:
+            shape, _ = ctx.autotune(frames, out=out, frame_bytes=nb, status=st)
+            shapes[name] = {"ctas_per_sm": shape[0], "rows_per_step": shape[1], "stages": shape[2]}
+        paths[name] = {rb.PATH_PLAIN: "plain", rb.PATH_FUSED: "fused"}[ctx.resolved_path]
+        jobs.append(dict(ctx=ctx, frames=frames, out=out, frame_bytes=nb, status=st))
+        frames_of[name] = n
+        total += frames.numel() * 4
+    graph = rb.Graph(jobs)
+
+    def sequential():
+        for j in jobs:
+            j["ctx"].compress(j["frames"], out=j["out"], frame_bytes=j["frame_bytes"], status=j["status"])
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for j in jobs:
+            assert (j["status"].cpu() == 0).all()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, min(args.steps, 10))
+    t_graph = timed(lambda: graph.launch(stream), reps)
+    t_seq = timed(sequential, reps)
+    res = {"unit": "GB/s", "bytes_per_step": total, "frames": frames_of, "paths": paths, "fused_shapes": shapes,
+           "graph": {"value": total / 1e9 / (t_graph / 1e3), "ms_per_step": t_graph,
+                     "launches_per_step": graph.launch_count},
+           "sequential": {"value": total / 1e9 / (t_seq / 1e3), "ms_per_step": t_seq}}
+    graph.close()
+    for j in jobs:
+        j["ctx"].close()
+    return res
 
 
 # ----------------------------------------------------------------- our arm
@@ -395,6 +459,8 @@ def run_ours(args, rank, local, world):
         pr = res[rb.PATH_PLAIN]
         line["plain"] = {"value": args.steps * n * frame_bytes / 1e9 / (pr["total_ms"] / 1e3), "unit": "GB/s",
                          "kernels_ms_per_step": {k: v[0] / args.steps for k, v in pr["kernels"].items()}}
+    if not args.no_mixed:
+        line["mixed_graph"] = mixed_graph(args, dev, local, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host.numpy(), params.as_dict())
     if rank == 0:

@@ -312,6 +312,47 @@ int roibin_compress_frame_static(const roibin_geometry* g, const roibin_params* 
                                  uint64_t out_capacity, uint64_t* d_frame_bytes, int32_t* d_frame_status,
                                  void* stream);
 
+/* ---- Mixed batches under one CUDA graph ---------------------------------
+ * One compression job: the arguments of roibin_compress, with its context.
+ * Jobs of one graph may have different geometries and parameters (one
+ * context each). */
+typedef struct {
+  roibin_ctx* ctx;
+  const float* d_frames;
+  uint32_t n_frames;
+  const uint16_t* d_peaks;   /* optional, as in roibin_compress */
+  const uint32_t* d_npeaks;  /* optional, as in roibin_compress */
+  uint8_t* d_out;
+  uint64_t out_stride;
+  uint64_t* d_frame_bytes;
+  int32_t* d_frame_status;
+} roibin_job;
+
+typedef struct roibin_graph roibin_graph;
+
+/* Captures the jobs' compression launches, each job on its own branch, into
+ * one CUDA graph and instantiates it.  A launch of the graph runs every job
+ * once: the branches are independent, so the GPU runs them concurrently (a
+ * persistent fused kernel only ever waits for work handed out at an earlier
+ * ticket of its own launch, so concurrent branches cannot block one another).
+ * Each context compiles into the graph with its path and fused shape at
+ * capture time (tune them first, e.g. with roibin_ctx_autotune).
+ * The graph keeps the job pointers: the caller refills d_frames (and the
+ * peak lists) between launches, keeps every buffer alive, and does not use a
+ * job's context for anything else while a launch may be in flight.
+ * Contexts must be distinct and on one device; ROIBIN_ERR_INVALID_ARG
+ * otherwise or for any job roibin_compress would reject; ROIBIN_ERR_CUDA if
+ * capture or instantiation fails.  Allocates (the graph), so call it at
+ * setup, not per batch. */
+int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_jobs);
+/* Launches the graph on `stream`; asynchronous; per-frame results as
+ * roibin_compress writes them. */
+int roibin_graph_launch(roibin_graph* g, void* stream);
+/* Kernel launches (and memsets) one graph launch performs. */
+int roibin_graph_launch_count(const roibin_graph* g);
+/* Frees the graph.  Synchronises the device first.  NULL ok. */
+int roibin_graph_destroy(roibin_graph* g);
+
 /* Human-readable text for a status code (static string). */
 const char* roibin_status_string(int status);
 

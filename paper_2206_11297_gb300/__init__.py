@@ -14,7 +14,8 @@ from . import _build
 
 __all__ = ["Geometry", "Params", "Context", "library", "default_params", "validate",
            "compress_bound", "status_string", "GEOMETRIES", "PATH_AUTO", "PATH_PLAIN",
-           "PATH_FUSED", "EXPORTED_SYMBOLS", "compress_frame_static", "STATIC_SCRATCH_BYTES"]
+           "PATH_FUSED", "DEC_AUTO", "DEC_PANEL", "DEC_MULTIPASS", "EXPORTED_SYMBOLS",
+           "compress_frame_static", "STATIC_SCRATCH_BYTES", "Job", "Graph"]
 
 OK = 0
 ERR_INVALID_ARG = -1
@@ -54,6 +55,15 @@ _P = ctypes.c_void_p
 _u32, _i32, _u64 = ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64
 _G, _Pr = ctypes.POINTER(Geometry), ctypes.POINTER(Params)
 
+
+class Job(ctypes.Structure):
+    """One job of a graph (roibin_job): a context and the arguments of its compress call."""
+    _fields_ = [("ctx", ctypes.c_void_p), ("d_frames", ctypes.c_void_p), ("n_frames", ctypes.c_uint32),
+                ("d_peaks", ctypes.c_void_p), ("d_npeaks", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("out_stride", ctypes.c_uint64), ("d_frame_bytes", ctypes.c_void_p),
+                ("d_frame_status", ctypes.c_void_p)]
+
+
 # name -> (restype, argtypes); every symbol include/roibin.h declares
 _SIGNATURES = {
     "roibin_default_params": (ctypes.c_int, [_Pr]),
@@ -65,6 +75,10 @@ _SIGNATURES = {
     "roibin_ctx_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
     "roibin_ctx_resolved_path": (ctypes.c_int, [_P]),
     "roibin_ctx_set_decompress_path": (ctypes.c_int, [_P, ctypes.c_int]),
+    "roibin_graph_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Job), _u32]),
+    "roibin_graph_launch": (ctypes.c_int, [_P, _P]),
+    "roibin_graph_launch_count": (ctypes.c_int, [_P]),
+    "roibin_graph_destroy": (ctypes.c_int, [_P]),
     "roibin_ctx_resolved_decompress_path": (ctypes.c_int, [_P]),
     "roibin_ctx_set_fused_shape": (ctypes.c_int, [_P, _u32, _u32, _u32]),
     "roibin_ctx_fused_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(_u32)] * 5),
@@ -352,3 +366,50 @@ class Context:
         _check("roibin_ctx_kernel_times", self.lib.roibin_ctx_kernel_times(
             self._h, names, ms, cnt, maxk, ctypes.byref(nk)))
         return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(nk.value, maxk))}
+
+
+class Graph:
+    """Several contexts' compress calls captured as parallel branches of one
+    CUDA graph (roibin_graph_create).  `jobs` is a list of dicts with the keys
+    ctx, frames, out, frame_bytes, status and optionally out_stride, peaks,
+    npeaks (CUDA tensors, as Context.compress takes them).  The graph keeps the
+    tensors' addresses: refill `frames` in place between launches."""
+
+    def __init__(self, jobs):
+        self.lib = library()
+        self._keep = []
+        arr = (Job * len(jobs))()
+        for i, j in enumerate(jobs):
+            ctx, frames, out = j["ctx"], j["frames"], j["out"]
+            assert tuple(frames.shape[1:]) == ctx.geometry and frames.is_contiguous()
+            stride = int(j.get("out_stride") or out.shape[-1])
+            arr[i] = Job(ctx._h, _ptr(frames), frames.shape[0], _ptr(j.get("peaks")), _ptr(j.get("npeaks")),
+                         _ptr(out), stride, _ptr(j["frame_bytes"]), _ptr(j["status"]))
+            self._keep.append(j)
+        h = ctypes.c_void_p()
+        _check("roibin_graph_create", self.lib.roibin_graph_create(ctypes.byref(h), arr, len(jobs)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check("roibin_graph_launch", self.lib.roibin_graph_launch(self._h, _stream_handle(stream)))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.roibin_graph_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.roibin_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -21,6 +21,13 @@ struct TimedLaunch {
   cudaEvent_t start, stop;
 };
 
+struct roibin_graph {
+  int device = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint32_t launches = 0;
+};
+
 struct roibin_ctx {
   int device = 0;
   int num_sms = 0;
@@ -257,6 +264,17 @@ int resolved_path(const roibin_ctx* ctx) {
   return ctx->fused_ok ? ROIBIN_PATH_FUSED : ROIBIN_PATH_PLAIN;
 }
 
+// The checks roibin_compress makes on its arguments.
+bool compress_args_ok(const roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, const uint16_t* d_peaks,
+                      const uint32_t* d_npeaks, const uint8_t* d_out, uint64_t out_stride,
+                      const uint64_t* d_frame_bytes, const int32_t* d_frame_status) {
+  if (!ctx || !d_frames || !d_out || !d_frame_bytes || !d_frame_status) return false;
+  if (n_frames < 1 || n_frames > ctx->max_frames) return false;
+  if ((d_peaks == nullptr) != (d_npeaks == nullptr)) return false;
+  if (out_stride < 16 || out_stride % 16 != 0) return false;
+  if (reinterpret_cast<uintptr_t>(d_frames) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0) return false;
+  return true;
+}
 int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, const uint16_t* d_peaks,
                     const uint32_t* d_npeaks, uint8_t* d_out, uint64_t out_stride, uint64_t* d_frame_bytes,
                     int32_t* d_frame_status, cudaStream_t st) {
@@ -488,11 +506,8 @@ int roibin_ctx_resolved_path(const roibin_ctx* ctx) {
 int roibin_compress(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, const uint16_t* d_peaks,
                     const uint32_t* d_npeaks, uint8_t* d_out, uint64_t out_stride, uint64_t* d_frame_bytes,
                     int32_t* d_frame_status, void* stream) {
-  if (!ctx || !d_frames || !d_out || !d_frame_bytes || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
-  if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
-  if ((d_peaks == nullptr) != (d_npeaks == nullptr)) return ROIBIN_ERR_INVALID_ARG;
-  if (out_stride < 16 || out_stride % 16 != 0) return ROIBIN_ERR_INVALID_ARG;
-  if (reinterpret_cast<uintptr_t>(d_frames) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0)
+  if (!compress_args_ok(ctx, d_frames, n_frames, d_peaks, d_npeaks, d_out, out_stride, d_frame_bytes,
+                        d_frame_status))
     return ROIBIN_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
   ctx->last_launches = 0;
@@ -544,6 +559,100 @@ int roibin_ctx_set_decompress_path(roibin_ctx* ctx, int path) {
 int roibin_ctx_resolved_decompress_path(const roibin_ctx* ctx) {
   if (!ctx) return ROIBIN_ERR_INVALID_ARG;
   return resolved_dec_path(ctx);
+}
+
+int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_jobs) {
+  if (!out) return ROIBIN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!jobs || n_jobs == 0) return ROIBIN_ERR_INVALID_ARG;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    const roibin_job& b = jobs[j];
+    if (!compress_args_ok(b.ctx, b.d_frames, b.n_frames, b.d_peaks, b.d_npeaks, b.d_out, b.out_stride,
+                          b.d_frame_bytes, b.d_frame_status))
+      return ROIBIN_ERR_INVALID_ARG;
+    if (b.ctx->device != jobs[0].ctx->device) return ROIBIN_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < j; ++i)
+      if (jobs[i].ctx == b.ctx) return ROIBIN_ERR_INVALID_ARG;
+  }
+  const int device = jobs[0].ctx->device;
+  if (cudaSetDevice(device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaStream_t> side(n_jobs, nullptr);
+  std::vector<cudaEvent_t> ev(n_jobs + 1, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+  for (uint32_t j = 0; ok && j < n_jobs; ++j) ok = cudaStreamCreateWithFlags(&side[j], cudaStreamNonBlocking) == cudaSuccess;
+  for (uint32_t j = 0; ok && j <= n_jobs; ++j) ok = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming) == cudaSuccess;
+  int status = ok ? ROIBIN_OK : ROIBIN_ERR_CUDA;
+  uint32_t launches = 0;
+  cudaGraph_t graph = nullptr;
+  // relaxed mode: the fused launcher sets a kernel attribute while capturing
+  if (status == ROIBIN_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    status = ROIBIN_ERR_CUDA;
+  if (status == ROIBIN_OK) {
+    if (cudaEventRecord(ev[n_jobs], cs) != cudaSuccess) status = ROIBIN_ERR_CUDA;  // the fork
+    for (uint32_t j = 0; status == ROIBIN_OK && j < n_jobs; ++j) {
+      const roibin_job& b = jobs[j];
+      if (cudaStreamWaitEvent(side[j], ev[n_jobs], 0) != cudaSuccess) {
+        status = ROIBIN_ERR_CUDA;
+        break;
+      }
+      const bool timing = b.ctx->timing;  // no timing events inside a graph
+      b.ctx->timing = false;
+      b.ctx->last_launches = 0;
+      status = compress_device(b.ctx, b.d_frames, b.n_frames, b.d_peaks, b.d_npeaks, b.d_out, b.out_stride,
+                               b.d_frame_bytes, b.d_frame_status, side[j]);
+      b.ctx->timing = timing;
+      launches += b.ctx->last_launches;
+      if (status == ROIBIN_OK && (cudaEventRecord(ev[j], side[j]) != cudaSuccess ||
+                                  cudaStreamWaitEvent(cs, ev[j], 0) != cudaSuccess))  // the join
+        status = ROIBIN_ERR_CUDA;
+    }
+    // capture always ends, so that the streams leave capture mode
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess && status == ROIBIN_OK) status = ROIBIN_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (status == ROIBIN_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) status = ROIBIN_ERR_CUDA;
+  for (auto e : ev)
+    if (e) cudaEventDestroy(e);
+  for (auto st : side)
+    if (st) cudaStreamDestroy(st);
+  if (cs) cudaStreamDestroy(cs);
+  if (status != ROIBIN_OK) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return status;
+  }
+  roibin_graph* g = new (std::nothrow) roibin_graph;
+  if (!g) {
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return ROIBIN_ERR_OUT_OF_BUDGET;
+  }
+  g->device = device;
+  g->graph = graph;
+  g->exec = exec;
+  g->launches = launches;
+  *out = g;
+  return ROIBIN_OK;
+}
+
+int roibin_graph_launch(roibin_graph* g, void* stream) {
+  if (!g || !g->exec) return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(g->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  return cuda_status(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+}
+
+int roibin_graph_launch_count(const roibin_graph* g) { return g ? (int)g->launches : ROIBIN_ERR_INVALID_ARG; }
+
+int roibin_graph_destroy(roibin_graph* g) {
+  if (!g) return ROIBIN_OK;
+  cudaSetDevice(g->device);
+  cudaDeviceSynchronize();
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return ROIBIN_OK;
 }
 
 int roibin_ctx_reserve_host_path(roibin_ctx* ctx) {
