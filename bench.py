@@ -241,9 +241,11 @@ def mixed_graph(args, dev, local, stream):
         out = torch.empty((n, ctx.bound), dtype=torch.uint8, device=dev)
         nb = torch.empty(n, dtype=torch.int64, device=dev)
         st = torch.empty(n, dtype=torch.int32, device=dev)
+        shape, _ = ctx.autotune(frames, out=out, frame_bytes=nb, status=st)
         if ctx.resolved_path == rb.PATH_FUSED:
-            shape, _ = ctx.autotune(frames, out=out, frame_bytes=nb, status=st)
             shapes[name] = {"ctas_per_sm": shape[0], "rows_per_step": shape[1], "stages": shape[2]}
+        else:
+            shapes[name] = {"rows_per_step": shape[0], "bands_per_panel": shape[1]}
         paths[name] = {rb.PATH_PLAIN: "plain", rb.PATH_FUSED: "fused"}[ctx.resolved_path]
         jobs.append(dict(ctx=ctx, frames=frames, out=out, frame_bytes=nb, status=st))
         frames_of[name] = n
@@ -271,7 +273,7 @@ def mixed_graph(args, dev, local, stream):
     reps = max(3, min(args.steps, 10))
     t_graph = timed(lambda: graph.launch(stream), reps)
     t_seq = timed(sequential, reps)
-    res = {"unit": "GB/s", "bytes_per_step": total, "frames": frames_of, "paths": paths, "fused_shapes": shapes,
+    res = {"unit": "GB/s", "bytes_per_step": total, "frames": frames_of, "paths": paths, "autotuned_shapes": shapes,
            "graph": {"value": total / 1e9 / (t_graph / 1e3), "ms_per_step": t_graph,
                      "launches_per_step": graph.launch_count},
            "sequential": {"value": total / 1e9 / (t_seq / 1e3), "ms_per_step": t_seq}}

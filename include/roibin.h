@@ -154,16 +154,28 @@ int roibin_ctx_resolved_path(const roibin_ctx* ctx);
  * Results are identical for every shape; only speed changes. */
 int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t rows_per_step,
                                uint32_t stages);
-/* Autotuner of the fused path: times every fused shape that fits this GPU
- * (CTAs per SM 2..4, rows per step 2..3, ring slots 2..4) on the caller's
- * batch (arguments as roibin_compress, which it calls three times per shape)
- * with CUDA events on `stream`, and keeps the fastest shape for later calls.
+/* Autotuner of the path the context resolves to, on the caller's batch
+ * (arguments as roibin_compress, which it calls three times per shape), with
+ * CUDA events on `stream`; keeps the fastest shape for later calls.
+ *   fused: every fused shape that fits this GPU (CTAs per SM 2..4, rows per
+ *          step 2..3, ring slots 2..4);
+ *   plain: rows per step 1, 2, 4, 8, 16 (those that fit) times bands per
+ *          panel 1, 2, 4, 8, 16 (up to half the binned rows).
  * Synchronous.  *best_ms (optional) receives the best time per call.  Every
- * shape writes identical bytes, so the choice only changes speed.
- * ROIBIN_ERR_INVALID_ARG when the context has no fused path. */
+ * shape writes identical bytes, so the choice only changes speed. */
 int roibin_ctx_autotune(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, uint8_t* d_out,
                         uint64_t out_stride, uint64_t* d_frame_bytes, int32_t* d_frame_status, void* stream,
                         float* best_ms);
+
+/* Shape of the plain path: binned rows per step of its streaming kernel
+ * (1..16, as fit its shared memory) and bands per panel (1 .. ceil(rows /
+ * bin_h / 2)); 0 for either leaves that choice to each call (rows from the
+ * panel width, bands from the batch size).  ROIBIN_ERR_INVALID_ARG for a
+ * value out of range.  Results are identical for every shape. */
+int roibin_ctx_set_plain_shape(roibin_ctx* ctx, uint32_t rows_per_step, uint32_t bands_per_panel);
+/* The plain-path shape set on the context (0: chosen per call).  Either
+ * output pointer may be NULL. */
+int roibin_ctx_plain_shape(const roibin_ctx* ctx, uint32_t* rows_per_step, uint32_t* bands_per_panel);
 
 /* Current fused shape: CTAs per SM, rows per step, ring stages, grid size,
  * shared memory bytes per CTA.  Any output pointer may be NULL. */

@@ -75,6 +75,8 @@ _SIGNATURES = {
     "roibin_ctx_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
     "roibin_ctx_resolved_path": (ctypes.c_int, [_P]),
     "roibin_ctx_set_decompress_path": (ctypes.c_int, [_P, ctypes.c_int]),
+    "roibin_ctx_set_plain_shape": (ctypes.c_int, [_P, _u32, _u32]),
+    "roibin_ctx_plain_shape": (ctypes.c_int, [_P, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     "roibin_graph_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Job), _u32]),
     "roibin_graph_launch": (ctypes.c_int, [_P, _P]),
     "roibin_graph_launch_count": (ctypes.c_int, [_P]),
@@ -240,6 +242,17 @@ class Context:
     def set_path(self, path: int):
         _check("roibin_ctx_set_path", self.lib.roibin_ctx_set_path(self._h, int(path)))
 
+    def set_plain_shape(self, rows_per_step: int = 0, bands_per_panel: int = 0):
+        _check("roibin_ctx_set_plain_shape", self.lib.roibin_ctx_set_plain_shape(
+            self._h, int(rows_per_step), int(bands_per_panel)))
+
+    @property
+    def plain_shape(self):
+        """(rows per step, bands per panel) set on the context; 0 = chosen per call."""
+        r, b = _u32(), _u32()
+        _check("roibin_ctx_plain_shape", self.lib.roibin_ctx_plain_shape(self._h, ctypes.byref(r), ctypes.byref(b)))
+        return r.value, b.value
+
     def set_decompress_path(self, path: int):
         _check("roibin_ctx_set_decompress_path", self.lib.roibin_ctx_set_decompress_path(self._h, int(path)))
 
@@ -260,8 +273,9 @@ class Context:
         return tuple(x.value for x in v)
 
     def autotune(self, frames, out=None, out_stride=None, frame_bytes=None, status=None, stream=None):
-        """roibin_ctx_autotune on a CUDA float32 [n, P, H, W] batch: times every fused shape that
-        fits and keeps the fastest.  Returns (best fused_shape, best ms per call)."""
+        """roibin_ctx_autotune on a CUDA float32 [n, P, H, W] batch: times every shape of the
+        path the context resolves to and keeps the fastest.  Returns (the kept shape: fused_shape
+        or plain_shape, best ms per call)."""
         import torch
         n = frames.shape[0]
         stride = int(out_stride or self.bound)
@@ -276,7 +290,7 @@ class Context:
         _check("roibin_ctx_autotune", self.lib.roibin_ctx_autotune(
             self._h, _ptr(frames), n, _ptr(out), stride, _ptr(frame_bytes), _ptr(status),
             _stream_handle(stream), ctypes.byref(ms)))
-        return self.fused_shape, ms.value
+        return (self.fused_shape if self.resolved_path == PATH_FUSED else self.plain_shape), ms.value
 
     def set_trace(self, trace=None, n_frames: int = 0):
         """trace: CUDA int64 tensor of n_frames * (16 + 4 P) entries (None switches tracing off)."""

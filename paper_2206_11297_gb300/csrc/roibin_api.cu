@@ -41,6 +41,7 @@ struct roibin_ctx {
   uint32_t max_frames = 0;
   int path_req = ROIBIN_PATH_AUTO;
   int dec_path_req = ROIBIN_DEC_AUTO;
+  uint32_t plain_rows = 0, plain_bands = 0;  // plain-path shape; 0: chosen per call
   bool fused_ok = false;
   FusedShape fshape{};
   uint64_t* trace = nullptr;
@@ -159,6 +160,13 @@ struct Carver {
   }
 };
 
+// Bands per panel of the plain path: each band takes at least two binned rows.
+uint32_t max_plain_bands(const DevParams& d) { return std::max<uint32_t>(1, ceil_div(d.Hb, 2)); }
+// Rows per step of the plain path that fit its shared memory.
+bool plain_rows_ok(const DevParams& d, uint32_t rows) {
+  return rows >= 1 && rows <= 16 && (uint64_t)(rows + 1) * d.Wb * 4 + (uint64_t)rows * d.Wb + 4096 <= 200 * 1024;
+}
+
 // Lays out the per-frame scratch for n frames; with base == nullptr only sizes it.
 uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s) {
   Carver c{base};
@@ -231,8 +239,11 @@ void choose_shape(const roibin_ctx* ctx, uint32_t n_frames, PlainArgs* a) {
   const uint32_t base = d.P * n_frames;
   uint32_t bands = 1;
   if (base < target) bands = ceil_div(target, base);
-  bands = std::min<uint32_t>(bands, std::max<uint32_t>(1, ceil_div(d.Hb, 2)));
+  bands = std::min<uint32_t>(bands, max_plain_bands(d));
   a->bands_per_panel = bands;
+  // a shape set by roibin_ctx_set_plain_shape (or the autotuner) wins
+  if (ctx->plain_rows) a->rows_per_step = ctx->plain_rows;
+  if (ctx->plain_bands) a->bands_per_panel = ctx->plain_bands;
 }
 
 int compress_plain(roibin_ctx* ctx, const PlainArgs& a, cudaStream_t st) {
@@ -319,6 +330,63 @@ cudaError_t static_scratch_base(int device, void** out) {
   }
   *out = g_static_base[device];
   return cudaSuccess;
+}
+
+// Times `calls` compress calls (after one warm-up) with CUDA events; < 0 on error.
+float time_compress(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, uint8_t* d_out, uint64_t out_stride,
+                    uint64_t* d_frame_bytes, int32_t* d_frame_status, cudaStream_t st, cudaEvent_t e0,
+                    cudaEvent_t e1, int* status) {
+  *status = compress_device(ctx, d_frames, n_frames, nullptr, nullptr, d_out, out_stride, d_frame_bytes,
+                            d_frame_status, st);  // warm-up
+  if (*status != ROIBIN_OK) return -1.0f;
+  cudaEventRecord(e0, st);
+  for (int rep = 0; rep < 2 && *status == ROIBIN_OK; ++rep)
+    *status = compress_device(ctx, d_frames, n_frames, nullptr, nullptr, d_out, out_stride, d_frame_bytes,
+                              d_frame_status, st);
+  cudaEventRecord(e1, st);
+  if (cudaEventSynchronize(e1) != cudaSuccess) *status = ROIBIN_ERR_CUDA;
+  float ms = 0.0f;
+  if (*status != ROIBIN_OK || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0f;
+  return ms;
+}
+
+// The plain path's autotuner: rows per step 1..16 (powers of two that fit)
+// times bands per panel 1..16 (powers of two up to the panel's limit).
+int autotune_plain(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, uint8_t* d_out, uint64_t out_stride,
+                   uint64_t* d_frame_bytes, int32_t* d_frame_status, cudaStream_t st, float* best_ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return ROIBIN_ERR_CUDA;
+  }
+  const int path_was = ctx->path_req;
+  const uint32_t keep_rows = ctx->plain_rows, keep_bands = ctx->plain_bands;
+  ctx->path_req = ROIBIN_PATH_PLAIN;
+  uint32_t best_rows = keep_rows, best_bands = keep_bands;
+  float best_t = -1.0f;
+  int status = ROIBIN_OK;
+  for (uint32_t rows = 1; rows <= 16 && status == ROIBIN_OK; rows *= 2) {
+    if (!plain_rows_ok(ctx->dp, rows) || rows > ctx->dp.Hb) continue;
+    for (uint32_t bands = 1; bands <= 16 && bands <= max_plain_bands(ctx->dp) && status == ROIBIN_OK; bands *= 2) {
+      ctx->plain_rows = rows;
+      ctx->plain_bands = bands;
+      const float ms = time_compress(ctx, d_frames, n_frames, d_out, out_stride, d_frame_bytes, d_frame_status,
+                                     st, e0, e1, &status);
+      if (ms >= 0 && (best_t < 0 || ms < best_t)) {
+        best_t = ms;
+        best_rows = rows;
+        best_bands = bands;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->path_req = path_was;
+  const bool ok = status == ROIBIN_OK && best_t >= 0;
+  ctx->plain_rows = ok ? best_rows : keep_rows;
+  ctx->plain_bands = ok ? best_bands : keep_bands;
+  if (best_ms && ok) *best_ms = best_t / 2.0f;
+  return status;
 }
 
 }  // namespace
@@ -440,10 +508,35 @@ int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_
   return ROIBIN_OK;
 }
 
+int roibin_ctx_set_plain_shape(roibin_ctx* ctx, uint32_t rows_per_step, uint32_t bands_per_panel) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  if (rows_per_step && !plain_rows_ok(ctx->dp, rows_per_step)) return ROIBIN_ERR_INVALID_ARG;
+  if (bands_per_panel > max_plain_bands(ctx->dp)) return ROIBIN_ERR_INVALID_ARG;
+  ctx->plain_rows = rows_per_step;
+  ctx->plain_bands = bands_per_panel;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_plain_shape(const roibin_ctx* ctx, uint32_t* rows_per_step, uint32_t* bands_per_panel) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  if (rows_per_step) *rows_per_step = ctx->plain_rows;
+  if (bands_per_panel) *bands_per_panel = ctx->plain_bands;
+  return ROIBIN_OK;
+}
+
+
 int roibin_ctx_autotune(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, uint8_t* d_out,
                         uint64_t out_stride, uint64_t* d_frame_bytes, int32_t* d_frame_status, void* stream,
                         float* best_ms) {
-  if (!ctx || !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  if (!ctx->fused_ok || resolved_path(ctx) == ROIBIN_PATH_PLAIN) {
+    if (!d_frames || !d_out || !d_frame_bytes || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
+    if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
+    if (out_stride < 16 || out_stride % 16 != 0) return ROIBIN_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+    return autotune_plain(ctx, d_frames, n_frames, d_out, out_stride, d_frame_bytes, d_frame_status,
+                          static_cast<cudaStream_t>(stream), best_ms);
+  }
   if (!d_frames || !d_out || !d_frame_bytes || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
   if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
   if (out_stride < 16 || out_stride % 16 != 0) return ROIBIN_ERR_INVALID_ARG;

@@ -339,6 +339,36 @@ def test_many_prequant_outliers(path):
     assert_parity(f, p, path)
 
 
+def test_plain_autotuner_and_shapes_write_the_same_bytes():
+    """The plain path's autotuner keeps one of its shapes; a few fixed shapes,
+    and the kept one, all write the oracle's bytes."""
+    import torch
+    geom = (2, 21, 1024)   # wider than the fused path takes
+    f = small_batch(geom, 2, seed=91)
+    p = rb.default_params(atot_thr=300.0)
+    refs = [oracle.compress_frame(f[k], oparams(p)) for k in range(2)]
+    with rb.Context(geom, p, max_frames=2) as ctx:
+        assert ctx.resolved_path == rb.PATH_PLAIN
+        ft = torch.from_numpy(f).cuda()
+        for rows, bands in [(1, 1), (4, 5), (16, 2), (0, 0)]:
+            ctx.set_plain_shape(rows, bands)
+            out, nb, st = ctx.compress(ft)
+            torch.cuda.synchronize()
+            for k in range(2):
+                assert int(st[k]) == refs[k][0] == 0
+                assert np.array_equal(out[k, :int(nb[k])].cpu().numpy(), refs[k][1]), (rows, bands, k)
+        with pytest.raises(rb.RoibinError):
+            ctx.set_plain_shape(17, 0)
+        with pytest.raises(rb.RoibinError):
+            ctx.set_plain_shape(0, 7)    # 11 binned rows: at most 6 bands
+        shape, ms = ctx.autotune(ft)
+        assert shape[0] >= 1 and shape[1] >= 1 and ms > 0
+        out, nb, st = ctx.compress(ft)
+        torch.cuda.synchronize()
+        for k in range(2):
+            assert np.array_equal(out[k, :int(nb[k])].cpu().numpy(), refs[k][1])
+
+
 def test_autotuned_shape_writes_the_same_bytes():
     """The autotuner keeps one of the fused shapes; every shape writes the oracle's bytes."""
     import torch

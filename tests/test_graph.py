@@ -37,7 +37,7 @@ def _jobs(torch, params, first, tune):
         out = torch.zeros((n, ctx.bound), dtype=torch.uint8, device="cuda")
         nb = torch.zeros(n, dtype=torch.int64, device="cuda")
         st = torch.zeros(n, dtype=torch.int32, device="cuda")
-        if tune and ctx.resolved_path == rb.PATH_FUSED:
+        if tune:
             ctx.autotune(frames)
         jobs.append(dict(ctx=ctx, frames=frames, out=out, frame_bytes=nb, status=st, name=name))
     return jobs
