@@ -351,6 +351,15 @@ def run_ours(args, rank, local, world):
     paths = [rb.PATH_PLAIN]
     if ctx.resolved_path == rb.PATH_FUSED:
         paths.append(rb.PATH_FUSED)
+    # each path on the shape the project's autotuner keeps for this batch
+    tuned = {}
+    for path in paths:
+        ctx.set_path(path)
+        shape, _ = ctx.autotune(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
+        tuned[{rb.PATH_PLAIN: "plain", rb.PATH_FUSED: "fused"}[path]] = (
+            {"rows_per_step": shape[0], "bands_per_panel": shape[1]} if path == rb.PATH_PLAIN else
+            {"ctas_per_sm": shape[0], "rows_per_step": shape[1], "stages": shape[2], "grid_ctas": shape[3]})
+    torch.cuda.synchronize()
     for path in paths:
         res[path] = timed_path(path)
     main = paths[-1]
@@ -399,7 +408,7 @@ def run_ours(args, rank, local, world):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{n} CSPAD-like frames 32x185x388 f32 per GPU, 20-100 peaks, ROI 17x17, "
                                "bin 2x2, eb 10, batched",
-                   "frames_per_step": n, "path": {1: "plain", 2: "fused"}[main],
+                   "frames_per_step": n, "path": {1: "plain", 2: "fused"}[main], "autotuned_shapes": tuned,
                    "l2": f"inputs ({n * frame_bytes / 1e9:.2f} GB per step) "
                          + ("larger than L2; no flush" if n * frame_bytes > 129e6 else "not larger than L2")},
         "frames_per_s": gbs * 1e9 / frame_bytes,
