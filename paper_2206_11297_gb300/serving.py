@@ -19,6 +19,7 @@ its compressed frames are on the host.
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
 import time
 
@@ -48,9 +49,10 @@ class Request:
 class _Lane:
     """One context, its batch buffers and its stream."""
 
-    HOST_SLOT = 1 << 20
+    PACKED_START = 64 << 20  # pinned bytes for a batch's streams at first; grown on demand
 
-    def __init__(self, geometry, params: Params, max_frames: int, device, budget: int):
+    def __init__(self, geometry, params: Params, max_frames: int, device, budget: int, pool,
+                 keep_streams: bool = True):
         """Raises RoibinError(ERR_OUT_OF_BUDGET) when the lane does not fit `budget` bytes."""
         import torch
         self.geometry = geometry
@@ -69,13 +71,18 @@ class _Lane:
         self.d_st = torch.empty(max_frames, dtype=torch.int32, device=device)
         self.h_nb = torch.empty(max_frames, dtype=torch.int64).pin_memory()
         self.h_st = torch.empty(max_frames, dtype=torch.int32).pin_memory()
-        # host copies of the streams: a compressed frame is far below the bound;
-        # one above host_slot bytes is fetched on its own
-        self.host_slot = min(self.stride, self.HOST_SLOT)
-        self.h_out = torch.empty((max_frames, self.host_slot), dtype=torch.uint8).pin_memory()
+        # the batch's streams come back packed, back to back, into one pinned
+        # buffer; host copies out of it run on the server's thread pool
+        self.h_packed = torch.empty(self.PACKED_START, dtype=torch.uint8).pin_memory()
+        self.pool = pool
+        self.keep_streams = keep_streams
+        self.offsets: list = []
+        self.futures: list = []
         self.batch: list[Request] = []
         self.n = 0
-        self.phase = "idle"   # idle -> sizes (kernel + sizes copy in flight) -> bytes (bytes copy in flight)
+        # idle -> sizes (kernel + sizes copy in flight) -> bytes (streams copy in flight)
+        #      -> host (copies out of the pinned buffer running) -> idle
+        self.phase = "idle"
         self.event = None
         self.last_used = 0.0
         self.bytes = self.ctx.scratch_bytes + buffers
@@ -101,37 +108,62 @@ class _Lane:
     def advance(self):
         """Moves a running batch on when its copies are done; returns finished requests."""
         import torch
-        if self.phase == "idle" or not self.event.query():
+        if self.phase == "idle":
+            return []
+        if self.phase in ("sizes", "bytes") and not self.event.query():
             return []
         if self.phase == "sizes":
-            nb = self.h_nb[:self.n].numpy()
+            nb, st = self.h_nb[:self.n].numpy(), self.h_st[:self.n].numpy()
+            self.offsets, total = [], 0
+            for k in range(self.n):
+                m = int(nb[k]) if st[k] == 0 else 0
+                self.offsets.append((total, m))
+                total += m
+            if total > self.h_packed.numel():
+                self.h_packed = torch.empty(max(total, 2 * self.h_packed.numel()), dtype=torch.uint8).pin_memory()
             with torch.cuda.stream(self.stream):
-                for k in range(self.n):
-                    m = int(nb[k]) if self.h_st[k] == 0 else 0
-                    if 0 < m <= self.host_slot:
-                        self.h_out[k, :m].copy_(self.d_out[k, :m], non_blocking=True)
+                for k, (o, m) in enumerate(self.offsets):
+                    if m:
+                        self.h_packed[o:o + m].copy_(self.d_out[k, :m], non_blocking=True)
                 self.event = torch.cuda.Event()
                 self.event.record(self.stream)
             self.phase = "bytes"
             return []
+        if self.phase == "bytes":
+            if not self.keep_streams:  # the bytes are on the host: done
+                now = time.perf_counter()
+                st = self.h_st[:self.n].numpy()
+                k = 0
+                for r in self.batch:
+                    m = r.frames.shape[0]
+                    r.status = [int(x) for x in st[k:k + m]]
+                    r.done = now
+                    k += m
+                finished, self.batch, self.phase = self.batch, [], "idle"
+                self.last_used = now
+                return finished
+            # each request's streams are copied out of the pinned buffer in parallel
+            packed = self.h_packed.numpy()
+            st = self.h_st[:self.n].numpy().copy()
+            k = 0
+            self.futures = []
+            for r in self.batch:
+                m = r.frames.shape[0]
+                spans = self.offsets[k:k + m]
+                stats = [int(x) for x in st[k:k + m]]
+                self.futures.append(self.pool.submit(
+                    lambda spans=spans, stats=stats: (stats, [packed[o:o + n].copy() if s == 0 else None
+                                                              for (o, n), s in zip(spans, stats)])))
+                k += m
+            self.phase = "host"
+            return []
+        if not all(f.done() for f in self.futures):
+            return []
         now = time.perf_counter()
-        nb, st, out = self.h_nb[:self.n].numpy(), self.h_st[:self.n].numpy(), self.h_out.numpy()
-        k = 0
-        for r in self.batch:
-            m = r.frames.shape[0]
-            r.status = [int(x) for x in st[k:k + m]]
-            r.streams = []
-            for i in range(m):
-                size = int(nb[k + i])
-                if st[k + i] != 0:
-                    r.streams.append(None)
-                elif size <= self.host_slot:
-                    r.streams.append(out[k + i, :size].copy())
-                else:
-                    r.streams.append(self.d_out[k + i, :size].cpu().numpy())
+        for r, f in zip(self.batch, self.futures):
+            r.status, r.streams = f.result()
             r.done = now
-            k += m
-        finished, self.batch, self.phase = self.batch, [], "idle"
+        finished, self.batch, self.futures, self.phase = self.batch, [], [], "idle"
         self.last_used = now
         return finished
 
@@ -145,10 +177,16 @@ class Server:
     hbm_budget: bytes of device memory the lanes may hold together;
     lane_frames: frames per batch of a lane; lanes_per_geometry: lanes a
     geometry may hold at once (more than one lets a batch start while the
-    previous one of the same geometry is still copying back)."""
+    previous one of the same geometry is still copying back);
+    max_queued_frames: frames that may wait (submit refuses a request beyond
+    that, so an offered load above capacity is shed instead of queued without
+    bound); keep_streams: hand each request a copy of its streams (False: a
+    request is done once its bytes are in the lane's pinned host buffer, where
+    a consumer would write them out)."""
 
     def __init__(self, params: Params | None = None, hbm_budget: int = 40 << 30, lane_frames: int = 128,
-                 lanes_per_geometry: int = 2, device=None):
+                 lanes_per_geometry: int = 2, device=None, host_threads: int = 8,
+                 max_queued_frames: int = 1 << 20, keep_streams: bool = True):
         import torch
         self.params = params or default_params()
         self.budget = int(hbm_budget)
@@ -158,15 +196,28 @@ class Server:
         self.queues: dict = collections.defaultdict(collections.deque)
         self.lanes: list[_Lane] = []
         self.finished: list[Request] = []
+        self.pool = concurrent.futures.ThreadPoolExecutor(host_threads)
+        self.max_queued_frames = int(max_queued_frames)
+        self.keep_streams = bool(keep_streams)
+        self.queued_frames = 0
+        self.rejected = 0
 
     @property
     def held_bytes(self):
         return sum(lane.bytes for lane in self.lanes)
 
-    def submit(self, req: Request):
-        if req.frames.shape[0] > self.lane_frames:
-            raise ValueError(f"request of {req.frames.shape[0]} frames exceeds lane_frames={self.lane_frames}")
+    def submit(self, req: Request) -> bool:
+        """Queues the request; False (and counted in `rejected`) when the waiting
+        frames would exceed max_queued_frames."""
+        n = req.frames.shape[0]
+        if n > self.lane_frames:
+            raise ValueError(f"request of {n} frames exceeds lane_frames={self.lane_frames}")
+        if self.queued_frames + n > self.max_queued_frames:
+            self.rejected += 1
+            return False
+        self.queued_frames += n
         self.queues[req.geometry].append(req)
+        return True
 
     def _lane_for(self, geometry):
         idle = [l for l in self.lanes if l.geometry == geometry and l.phase == "idle"]
@@ -177,7 +228,7 @@ class Server:
         while True:
             try:
                 lane = _Lane(geometry, self.params, self.lane_frames, self.device,
-                             self.budget - self.held_bytes)
+                             self.budget - self.held_bytes, self.pool, self.keep_streams)
                 self.lanes.append(lane)
                 return lane
             except RoibinError as e:
@@ -211,6 +262,7 @@ class Server:
                     r = q.popleft()
                     batch.append(r)
                     n += r.frames.shape[0]
+                self.queued_frames -= n
                 lane.start(batch)
                 moved = True
         return moved
@@ -227,6 +279,7 @@ class Server:
         for lane in self.lanes:
             lane.close()
         self.lanes = []
+        self.pool.shutdown(wait=True)
 
 
 def poisson_requests(pools: dict, rate_hz: float, seconds: float, max_frames: int = 64, seed: int = 0):
@@ -245,7 +298,8 @@ def poisson_requests(pools: dict, rate_hz: float, seconds: float, max_frames: in
 
 
 def run(pools: dict, schedule, server: Server):
-    """Replays a request schedule in real time against the server; returns the finished requests."""
+    """Replays a request schedule in real time against the server; returns the accepted (and
+    finished) requests; refused ones are counted in server.rejected."""
     t0 = time.perf_counter()
     pending = collections.deque(schedule)
     reqs = []
@@ -256,8 +310,8 @@ def run(pools: dict, schedule, server: Server):
             at, g, n, first = pending.popleft()
             r = Request(rid, pools[g][first:first + n], t0 + at)
             rid += 1
-            reqs.append(r)
-            server.submit(r)
+            if server.submit(r):
+                reqs.append(r)
         if not server.step():
             time.sleep(20e-6)
     return reqs
@@ -276,6 +330,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--pool-frames", type=int, default=96)
     ap.add_argument("--max-peaks", type=int, default=8192)
+    ap.add_argument("--max-queued-frames", type=int, default=8192)
     args = ap.parse_args()
     pools = {}
     for name in ("cspad_batch", "epix_hot", "jungfrau_mixed"):
@@ -284,11 +339,13 @@ def main():
     # epix-like frames with 1% hot pixels hold about 3,600 accepted peaks (pairs of hot pixels pass
     # the tests), above the default list size: allow the largest
     params = default_params(max_peaks=args.max_peaks)
-    server = Server(params, hbm_budget=int(args.budget_gb * 1e9), lane_frames=args.lane_frames)
+    server = Server(params, hbm_budget=int(args.budget_gb * 1e9), lane_frames=args.lane_frames,
+                    max_queued_frames=args.max_queued_frames, keep_streams=False)
     warm = poisson_requests(pools, args.rate, 0.5, args.max_request_frames, seed=1)
     run(pools, warm, server)
     sched = poisson_requests(pools, args.rate, args.seconds, args.max_request_frames, seed=2)
     t0 = time.perf_counter()
+    server.rejected = 0
     reqs = run(pools, sched, server)
     wall = time.perf_counter() - t0
     lat = np.array([r.latency for r in reqs]) * 1e3
@@ -301,6 +358,7 @@ def main():
                       "frames_per_s": frames / wall,
                       "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                      "max": float(lat.max())},
+                      "offered_requests": len(sched), "rejected_requests": server.rejected,
                       "lanes": len(server.lanes), "held_gb": server.held_bytes / 1e9, "all_ok": ok,
                       "errors": {f"{g} status {s}": c for (g, s), c in bad.items()}}))
     server.close()

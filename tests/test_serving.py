@@ -96,3 +96,57 @@ def test_budget_admission_releases_idle_lanes():
         assert len(server.lanes) == 1 and server.held_bytes <= server.budget
     finally:
         server.close()
+
+
+def test_queue_is_bounded():
+    """Requests beyond max_queued_frames waiting frames are refused and counted;
+    starting a batch frees their room (no GPU needed: nothing is scheduled)."""
+    server = serving.Server(rb.default_params(), lane_frames=8, max_queued_frames=10)
+    try:
+        g = (1, 4, 4)
+        mk = lambda rid, n: serving.Request(rid, np.zeros((n, *g), np.float32), 0.0)
+        assert server.submit(mk(0, 6)) and server.submit(mk(1, 4))
+        assert not server.submit(mk(2, 1)) and server.rejected == 1
+        assert server.queued_frames == 10 and len(server.queues[g]) == 2
+        with pytest.raises(ValueError):
+            server.submit(mk(3, 9))   # larger than a lane's batch
+    finally:
+        server.close()
+
+
+@pytest.mark.gpu
+def test_packed_buffer_grows_and_streams_stay_exact(monkeypatch):
+    """A lane's pinned buffer starts small here, so batches outgrow it and it is
+    reallocated; every request's bytes still equal compressing it alone."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    monkeypatch.setattr(serving._Lane, "PACKED_START", 4096)
+    geoms = [(3, 40, 44), (2, 21, 27)]
+    pools = _pools(geoms)
+    params = rb.default_params(atot_thr=300.0)
+    schedule = serving.poisson_requests(pools, rate_hz=1000, seconds=0.05, max_frames=8, seed=11)
+    server = serving.Server(params, hbm_budget=4 << 30, lane_frames=16)
+    try:
+        _check_mixed(server, pools, schedule, params)
+        assert all(l.h_packed.numel() > 4096 for l in server.lanes)
+    finally:
+        server.close()
+
+
+@pytest.mark.gpu
+def test_requests_done_without_keeping_streams():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    geoms = [(3, 40, 44)]
+    pools = _pools(geoms)
+    params = rb.default_params(atot_thr=300.0)
+    schedule = serving.poisson_requests(pools, rate_hz=1000, seconds=0.05, max_frames=8, seed=12)
+    server = serving.Server(params, hbm_budget=4 << 30, lane_frames=16, keep_streams=False)
+    try:
+        reqs = serving.run(pools, schedule, server)
+        assert len(reqs) == len(schedule) and server.rejected == 0
+        assert all(r.done is not None and r.streams is None and all(s == 0 for s in r.status) for r in reqs)
+    finally:
+        server.close()
