@@ -224,8 +224,16 @@ int roibin_compress(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames,
  *                    (16-byte aligned).
  *   d_frames_out     float32[n_frames][P][H][W].
  *   d_frame_status   i32[n_frames] out: ROIBIN_OK or ROIBIN_ERR_CORRUPT_STREAM
- *                    (header, geometry, size, index or code mismatch).  A
- *                    corrupt frame's output is unspecified.
+ *                    (header, geometry, size, index or code mismatch; outlier
+ *                    lists out of order, past the frame or off their code-0
+ *                    bins; a peak outside the frame).  The panel path may also
+ *                    report ROIBIN_ERR_TIMEOUT (a bulk copy of symbols that did
+ *                    not land within its bounded wait).  A frame's output is
+ *                    unspecified unless its status is ROIBIN_OK.
+ * Paths (roibin_ctx_set_decompress_path): the panel path decodes through a
+ * prefix table into symbols and rebuilds each panel in shared memory, writing
+ * every pixel once; the multi-pass path runs one kernel per step.  Both write
+ * the same frames and statuses.
  * Streams must come from a context of the same geometry (other parameters are
  * read from each header). */
 int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes,
