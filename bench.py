@@ -436,7 +436,6 @@ def run_ours(args, rank, local, world):
         offsets = torch.arange(n, dtype=torch.int64, device=dev) * stride
         recon = torch.empty_like(frames)
         dstat = torch.empty(n, dtype=torch.int32, device=dev)
-        n_bins = ctx.n_bins
         dec = {}
         for dpath, dname in ((rb.DEC_PANEL, "panel"), (rb.DEC_MULTIPASS, "multipass")):
             try:
@@ -464,9 +463,11 @@ def run_ours(args, rank, local, world):
                           "kernels_ms_per_step": {k: v[0] / d_steps for k, v in dk.items()}}
             pk = dk.get("dec_panel")
             if pk:
-                # algorithmic bytes of the panel kernel: the u16 symbols in, the
-                # float32 frames out
-                algo_b = n * (2 * n_bins + frame_bytes)
+                # algorithmic bytes of the panel kernel: the float32 frames out.
+                # These frames are all sparse (their symbols reach it as short
+                # per-chunk lists, a few KB per frame); a dense frame would add
+                # its 2 B per bin of symbols in.
+                algo_b = n * frame_bytes
                 ach = algo_b / 1e9 / (pk[0] / 1e3 / pk[1])
                 dec[dname]["roofline"] = {"bound": "hbm", "kernel": "dec_panel", "achieved": ach,
                                           "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}

@@ -405,14 +405,15 @@ __global__ void k_dec_roi(DevParams p, Scratch s, DecArgs a) {
 //     bits is z copies of its symbol, taken in one step (count of leading zeros).
 //   - Other codes: the next 12 bits index the prefix table (codes of up to 12
 //     bits resolve in one lookup; longer ones continue bit by bit from length 13).
-// The symbols go to the [n][n_chunks * kChunk] u16 symbol array.  A frame the
-// parse step marked sparse (a length-1 code, and each chunk's bit count leaves
-// room for at most kDecSparseMax other symbols) takes k_dec_decode_sparse: the
-// block fills its chunks with the length-1 code's symbol in coalesced stores,
-// then each thread stores only its other symbols.  Other frames take
-// k_dec_decode_dense, which stages kDecRound symbols per thread in shared memory
-// and has the warp store its 32 slots together, instead of each thread storing
-// into its own cache lines.  Corrupt-stream checks are those of k_dec_decode.
+// A frame the parse step marked sparse (a length-1 code, and each chunk's bit
+// count leaves room for at most kDecSparseMax other symbols) takes
+// k_dec_decode_sparse, which lists only each chunk's other symbols (dec_list):
+// the panel kernel fills the rest with the length-1 code's symbol, so the
+// frame's symbols never go through device memory.  Other frames take
+// k_dec_decode_dense, which writes every symbol to the [n][n_chunks * kChunk]
+// u16 symbol array: it stages kDecRound symbols per thread in shared memory and
+// has the warp store its 32 slots together, instead of each thread storing into
+// its own cache lines.  Corrupt-stream checks are those of k_dec_decode.
 constexpr uint32_t kDecRound = 32;                     // symbols per thread and round (dense)
 constexpr uint32_t kDecSlotWords = kDecRound / 2 + 4;  // 64 bytes + 16 bytes of bank skew
 constexpr uint32_t kDecMaxThreads = 256;
@@ -468,6 +469,19 @@ __device__ __forceinline__ uint32_t decode_one(const uint32_t* tab, const uint16
   return 0;
 }
 
+// A sparse frame's symbols, as the decoder leaves them for the panel kernel:
+// chunk k lists its symbols other than the length-1 code's, in order, as
+// (position in the chunk << 16) | symbol, in the first half of the chunk's slot
+// of the symbol array; the count per chunk goes to the [n][n_chunks] array the
+// compressor uses for its per-chunk outlier offsets (free while decompressing).
+__device__ __forceinline__ uint32_t* dec_list(const Scratch& s, const DevParams& p, uint32_t f, uint32_t k) {
+  return reinterpret_cast<uint32_t*>(s.codes + ((size_t)f * p.n_chunks + k) * kChunk);
+}
+__device__ __forceinline__ uint32_t* dec_list_count(const Scratch& s, const DevParams& p, uint32_t f) {
+  return s.chunk_lo + (size_t)f * p.n_chunks;
+}
+static_assert(kDecSparseMax * 4 <= kChunk * 2, "a chunk's list fits its slot of the symbol array");
+
 // The frame's decoding tables into shared memory; false when the frame is not
 // this kernel's (or not OK).  Read once by thread 0 and shared, since other
 // blocks of the frame may mark it corrupt meanwhile.
@@ -492,18 +506,6 @@ __global__ void __launch_bounds__(kDecMaxThreads) k_dec_decode_sparse(DevParams 
   const uint16_t* lut = reinterpret_cast<const uint16_t*>(tab + kDecCanonWords);
   // the length-1 code is code 0: its symbol comes first in the (length, symbol) order
   const uint32_t zsym = tab[102];
-  uint16_t* out = s.codes + (size_t)f * p.n_chunks * kChunk;
-  {  // the block's chunks are contiguous and start 16-byte aligned
-    const uint32_t k0 = blockIdx.x * blockDim.x;
-    const uint32_t s_begin = k0 * kChunk, s_end = min(p.M, min(p.n_chunks, k0 + blockDim.x) * kChunk);
-    const uint32_t rep32 = zsym | (zsym << 16);
-    const uint4 rep = make_uint4(rep32, rep32, rep32, rep32);
-    const uint32_t n8 = (s_end - s_begin) / 8;
-    uint4* region = reinterpret_cast<uint4*>(out + s_begin);
-    for (uint32_t e = threadIdx.x; e < n8; e += blockDim.x) region[e] = rep;
-    for (uint32_t e = s_begin + n8 * 8 + threadIdx.x; e < s_end; e += blockDim.x) out[e] = (uint16_t)zsym;
-  }
-  __syncthreads();
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= p.n_chunks) return;
   const DecInfo& di = s.dec_info[f];
@@ -513,17 +515,19 @@ __global__ void __launch_bounds__(kDecMaxThreads) k_dec_decode_sparse(DevParams 
   const uint32_t* words = reinterpret_cast<const uint32_t*>(base + di.pl.off_bits);
   const uint32_t w0 = cidx[k];
   const uint32_t w1 = k + 1 < p.n_chunks ? cidx[k + 1] : n_words;
+  uint32_t* count = dec_list_count(s, p, f) + k;
   if (w0 > w1 || w1 > n_words) {
+    *count = 0;
     mark_corrupt(s, f);
     return;
   }
   const uint64_t bit_end = (uint64_t)(w1 - w0) * 32;
   const uint32_t n_sym = min(p.M, k * kChunk + kChunk) - k * kChunk;
-  uint16_t* mine = out + (size_t)k * kChunk;
+  uint32_t* list = dec_list(s, p, f, k);
   WordReader rd;
   rd.init(words, w0, w1);
   uint64_t buf = 0;  // next bits, MSB first; nbuf of them are valid
-  uint32_t nbuf = 0, pos = 0, zeros = 0;
+  uint32_t nbuf = 0, pos = 0, zeros = 0, n_list = 0;
   uint64_t bit = 0;
   bool bad = false;
   while (pos < n_sym) {
@@ -541,11 +545,12 @@ __global__ void __launch_bounds__(kDecMaxThreads) k_dec_decode_sparse(DevParams 
     } else {
       uint32_t sym;
       const uint32_t L = decode_one(tab, lut, buf, sym);
-      if (L == 0) {
+      if (L == 0 || n_list == kDecSparseMax) {
         bad = true;
         break;
       }
-      mine[pos++] = (uint16_t)sym;
+      list[n_list++] = (pos << 16) | sym;
+      ++pos;
       buf <<= L;
       nbuf -= L;
       bit += L;
@@ -556,6 +561,7 @@ __global__ void __launch_bounds__(kDecMaxThreads) k_dec_decode_sparse(DevParams 
       break;
     }
   }
+  *count = bad ? 0u : n_list;
   if (bad || (bit + 31) / 32 != (uint64_t)(w1 - w0)) mark_corrupt(s, f);
   if (zeros) atomicAdd(s.dec_zero + f, zeros);
 }
@@ -790,7 +796,13 @@ __global__ void __launch_bounds__(kPanelThreads, 8) k_dec_panel(DevParams p, Scr
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) fetch(0);
+  // a sparse frame's strips are filled with the length-1 code's delta and its
+  // listed symbols scattered in; a dense frame's symbols come by bulk copy
+  const bool sparse = di.sparse != 0;
+  const uint32_t zsym = s.dec_table[(size_t)f * kDecTableWords + 102];
+  const uint32_t fillv = zsym ? (uint32_t)((int32_t)zsym - R) : (uint32_t)kSentinel;
+  const uint32_t* counts = dec_list_count(s, p, f);
+  if (threadIdx.x == 0 && !sparse) fetch(0);
   uint32_t phase = 0;
   bool timed_out = false;  // uniform: set after a barrier
   float* panel = a.out + (size_t)f * p.frame_px + (size_t)pn * H * W;
@@ -807,23 +819,38 @@ __global__ void __launch_bounds__(kPanelThreads, 8) k_dec_panel(DevParams p, Scr
     const uint32_t nr = min(sb, Hb - r0), nb = nr * Wb;
     const uint32_t sb0 = pb + r0 * Wb, sb1 = sb0 + nb;
     // symbols -> deltas (code 0: sentinel until its outlier arrives)
-    const bool late = !mbar_wait(bar, phase);
-    phase ^= 1u;
-    if (!late) {
-      const uint16_t* u16 = reinterpret_cast<const uint16_t*>(symbuf) + ((2 * (pb + r0 * Wb)) & 15u) / 2;
-      for (uint32_t e = threadIdx.x; e < nb; e += blockDim.x) {
-        const uint32_t u = u16[e];
-        tile[e] = u ? (uint32_t)((int32_t)u - R) : (uint32_t)kSentinel;
+    if (sparse) {
+      for (uint32_t e = threadIdx.x; e < nb; e += blockDim.x) tile[e] = fillv;
+      __syncthreads();
+      // the strip's bins lie in chunks sb0 / kChunk .. (sb1 - 1) / kChunk
+      for (uint32_t k = sb0 / kChunk; k <= (sb1 - 1) / kChunk; ++k) {
+        const uint32_t* list = dec_list(s, p, f, k);
+        const uint32_t cnt = min(counts[k], kDecSparseMax), kb = k * kChunk;
+        for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+          const uint32_t v = list[e], x = kb + (v >> 16), u = v & 0xFFFFu;
+          if (x >= sb0 && x < sb1) tile[x - sb0] = u ? (uint32_t)((int32_t)u - R) : (uint32_t)kSentinel;
+        }
       }
+      __syncthreads();
+    } else {
+      const bool late = !mbar_wait(bar, phase);
+      phase ^= 1u;
+      if (!late) {
+        const uint16_t* u16 = reinterpret_cast<const uint16_t*>(symbuf) + ((2 * (pb + r0 * Wb)) & 15u) / 2;
+        for (uint32_t e = threadIdx.x; e < nb; e += blockDim.x) {
+          const uint32_t u = u16[e];
+          tile[e] = u ? (uint32_t)((int32_t)u - R) : (uint32_t)kSentinel;
+        }
+      }
+      if (__syncthreads_or(late)) {
+        // a copy that did not land in time: wait for it once more (bounded), then stop
+        if (threadIdx.x == 0) mbar_wait(bar, phase ^ 1u);
+        timed_out = true;
+        break;
+      }
+      // the buffer is free: the next strip's symbols come in behind this one
+      if (threadIdx.x == 0 && r0 + sb < Hb) fetch(r0 + sb);
     }
-    if (__syncthreads_or(late)) {
-      // a copy that did not land in time: wait for it once more (bounded), then stop
-      if (threadIdx.x == 0) mbar_wait(bar, phase ^ 1u);
-      timed_out = true;
-      break;
-    }
-    // the buffer is free: the next strip's symbols come in behind this one
-    if (threadIdx.x == 0 && r0 + sb < Hb) fetch(r0 + sb);
     lo_cur = place_strip_outliers(lo, lo_cur, lo_end, sb1, [&](uint32_t x, uint32_t y) {
       if (x < sb0 || tile[x - sb0] != (uint32_t)kSentinel) return false;
       tile[x - sb0] = y;
