@@ -895,6 +895,7 @@ __global__ void __launch_bounds__(kPanelThreads, 8) k_dec_panel(DevParams p, Scr
       return true;
     }, bad);
     // output rows of the strip: bin row i covers pixel rows (r0 + i) * bh ...
+    // (streaming stores: the kernel never reads these pixels back)
     if (vec4) {  // bin width 2, W % 4 == 0: one float4 = 2 bins, stored on each of its rows
       const uint32_t n2 = nr * W4;
       uint32_t i = threadIdx.x / W4, c4 = threadIdx.x - i * W4;
@@ -902,7 +903,7 @@ __global__ void __launch_bounds__(kPanelThreads, 8) k_dec_panel(DevParams p, Scr
         const float2 v = *reinterpret_cast<const float2*>(tilef + i * Wb + 2 * c4);
         const float4 o = make_float4(v.x, v.x, v.y, v.y);
         const uint32_t pr0 = (r0 + i) * bh, pr1 = min(H, pr0 + bh);
-        for (uint32_t pr = pr0; pr < pr1; ++pr) reinterpret_cast<float4*>(panel + (size_t)pr * W)[c4] = o;
+        for (uint32_t pr = pr0; pr < pr1; ++pr) __stcs(reinterpret_cast<float4*>(panel + (size_t)pr * W) + c4, o);
         i += dr;
         c4 += dc;
         if (c4 >= W4) {
@@ -915,7 +916,7 @@ __global__ void __launch_bounds__(kPanelThreads, 8) k_dec_panel(DevParams p, Scr
       const uint32_t n1 = (ro1 - ro0) * W;
       for (uint32_t e = threadIdx.x; e < n1; e += blockDim.x) {
         const uint32_t rr = e / W, c = e - rr * W;
-        panel[(size_t)ro0 * W + e] = tilef[((ro0 + rr) / bh - r0) * Wb + c / p.bw];
+        __stcs(panel + (size_t)ro0 * W + e, tilef[((ro0 + rr) / bh - r0) * Wb + c / p.bw]);
       }
     }
     __syncthreads();
