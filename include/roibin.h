@@ -143,7 +143,8 @@ uint64_t roibin_ctx_scratch_bytes(const roibin_ctx* ctx);
  * (it needs bin 2x2, cols % 4 == 0 and cols <= 868).  Both paths write
  * identical bytes. */
 int roibin_ctx_set_path(roibin_ctx* ctx, int path);
-/* The path AUTO resolves to for this context (PLAIN or FUSED). */
+/* The path AUTO resolves to for this context (PLAIN or FUSED): FUSED when the
+ * shape allows it, unless the autotuner found PLAIN faster on this context. */
 int roibin_ctx_resolved_path(const roibin_ctx* ctx);
 
 /* Tuning hook of the fused path: ctas_per_sm resident CTAs per SM (1..8,
@@ -161,8 +162,11 @@ int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t r
  *          step 2..3, ring slots 2..4);
  *   plain: rows per step 1, 2, 4, 8, 16 (those that fit) times bands per
  *          panel 1, 2, 4, 8, 16 (up to half the binned rows).
+ * A context left on ROIBIN_PATH_AUTO that has both paths gets both tuned, and
+ * AUTO then takes the faster one for later calls (roibin_ctx_resolved_path
+ * reports it; roibin_ctx_set_path still overrides it).
  * Synchronous.  *best_ms (optional) receives the best time per call.  Every
- * shape writes identical bytes, so the choice only changes speed. */
+ * shape and path writes identical bytes, so the choice only changes speed. */
 int roibin_ctx_autotune(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, uint8_t* d_out,
                         uint64_t out_stride, uint64_t* d_frame_bytes, int32_t* d_frame_status, void* stream,
                         float* best_ms);

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kPeakWarps * 32) k_peaks(DevParams p, Scratch 
     const uint32_t pn = px / plane, rem = px - pn * plane;
     const uint32_t r = rem / p.W, c = rem - r * p.W;
     const float* panel = frame + (size_t)pn * plane;
-    if (warp_peak_test(panel, p.H, p.W, r, c, p, nb, [](const float* q) { return __ldg(q); })) {
+    if (warp_peak_test<true>(panel, p.H, p.W, r, c, p, nb, [](const float* q) { return __ldg(q); })) {
       if (lane_id() == 0) {
         const uint32_t slot = atomicAdd(s.peak_count + f, 1u);
         if (slot < p.max_peaks) s.peak_key[(size_t)f * p.max_peaks + slot] = px;
@@ -242,7 +242,38 @@ __global__ void __launch_bounds__(kPeakWarps * 32) k_peaks(DevParams p, Scratch 
     for (uint32_t e = warp; e < count; e += nwarps) test(s.thr_idx[(size_t)f * p.thr_cap + e]);
     return;
   }
-  // dense: the warp takes 32 pixels at a time and tests those >= amax_thr
+  // dense: the warp reads 512 pixels per round with four independent float4
+  // loads per lane (frames start 16-byte aligned; a frame of fewer than a
+  // multiple of 4 pixels takes the scalar loop), then tests those >= amax_thr
+  if (p.frame_px % 4 == 0 && (reinterpret_cast<uintptr_t>(frame) & 15u) == 0) {
+    const uint64_t n4 = p.frame_px / 4;
+    const float4* f4 = reinterpret_cast<const float4*>(frame);
+    for (uint64_t b4 = (uint64_t)warp * 128; b4 < n4; b4 += (uint64_t)nwarps * 128) {
+      float4 q[4];
+      uint32_t valid = 0;  // bit u: the lane's u-th float4 lies inside the frame
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint64_t i4 = b4 + u * 32 + lane_id();
+        valid |= (uint32_t)(i4 < n4) << u;
+        q[u] = i4 < n4 ? __ldg(f4 + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      uint32_t hot = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if ((valid >> u) & 1u)
+          hot |= (uint32_t)(q[u].x >= p.amax) << (4 * u) | (uint32_t)(q[u].y >= p.amax) << (4 * u + 1) |
+                 (uint32_t)(q[u].z >= p.amax) << (4 * u + 2) | (uint32_t)(q[u].w >= p.amax) << (4 * u + 3);
+      for (uint32_t j = 0; j < 16; ++j) {
+        uint32_t m = __ballot_sync(0xffffffffu, (hot >> j) & 1u);
+        while (m) {
+          const uint32_t l = __ffs(m) - 1;
+          m &= m - 1;
+          test((uint32_t)(4 * (b4 + (j >> 2) * 32 + l) + (j & 3u)));
+        }
+      }
+    }
+    return;
+  }
   for (uint64_t base = (uint64_t)warp * 32; base < p.frame_px; base += (uint64_t)nwarps * 32) {
     const uint64_t px = base + lane_id();
     const bool hot = px < p.frame_px && __ldg(frame + px) >= p.amax;

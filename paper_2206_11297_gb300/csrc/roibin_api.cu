@@ -40,6 +40,7 @@ struct roibin_ctx {
   uint64_t budget = 0;
   uint32_t max_frames = 0;
   int path_req = ROIBIN_PATH_AUTO;
+  int auto_path = 0;  // the path AUTO takes once the autotuner has timed both (0: not yet)
   int dec_path_req = ROIBIN_DEC_AUTO;
   uint32_t plain_rows = 0, plain_bands = 0;  // plain-path shape; 0: chosen per call
   bool fused_ok = false;
@@ -272,7 +273,8 @@ int resolved_dec_path(const roibin_ctx* ctx) {
 int resolved_path(const roibin_ctx* ctx) {
   if (ctx->path_req == ROIBIN_PATH_PLAIN) return ROIBIN_PATH_PLAIN;
   if (ctx->path_req == ROIBIN_PATH_FUSED) return ROIBIN_PATH_FUSED;
-  return ctx->fused_ok ? ROIBIN_PATH_FUSED : ROIBIN_PATH_PLAIN;
+  if (!ctx->fused_ok) return ROIBIN_PATH_PLAIN;
+  return ctx->auto_path ? ctx->auto_path : ROIBIN_PATH_FUSED;
 }
 
 // The checks roibin_compress makes on its arguments.
@@ -388,6 +390,55 @@ int autotune_plain(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, ui
   if (best_ms && ok) *best_ms = best_t / 2.0f;
   return status;
 }
+
+// The fused path's autotuner: every fused shape that fits (CTAs per SM 2..4,
+// rows per step 2..3, ring slots 2..4).
+int autotune_fused(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, uint8_t* d_out,
+                   uint64_t out_stride, uint64_t* d_frame_bytes, int32_t* d_frame_status, void* stream,
+                   float* best_ms) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return ROIBIN_ERR_CUDA;
+  }
+  const int path_was = ctx->path_req;
+  const FusedShape keep = ctx->fshape;
+  ctx->path_req = ROIBIN_PATH_FUSED;
+  FusedShape best = keep;
+  float best_t = -1.0f;
+  int status = ROIBIN_OK;
+  for (uint32_t cps = 4; cps >= 2 && status == ROIBIN_OK; --cps) {
+    for (uint32_t rb = 2; rb <= 3 && status == ROIBIN_OK; ++rb) {
+      for (uint32_t stages = 2; stages <= 4 && status == ROIBIN_OK; ++stages) {
+        FusedShape sh;
+        if (!fused_shape_for(ctx->dp, cps, rb, stages, &sh) || sh.ctas_per_sm != cps) continue;
+        ctx->fshape = sh;
+        status = compress_device(ctx, d_frames, n_frames, nullptr, nullptr, d_out, out_stride, d_frame_bytes,
+                                 d_frame_status, st);  // warm-up
+        if (status != ROIBIN_OK) break;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2 && status == ROIBIN_OK; ++rep)
+          status = compress_device(ctx, d_frames, n_frames, nullptr, nullptr, d_out, out_stride, d_frame_bytes,
+                                   d_frame_status, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) status = ROIBIN_ERR_CUDA;
+        float ms = 0.0f;
+        if (status == ROIBIN_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best_t < 0 || ms < best_t)) {
+          best_t = ms;
+          best = sh;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->path_req = path_was;
+  ctx->fshape = status == ROIBIN_OK && best_t >= 0 ? best : keep;
+  if (best_ms && best_t >= 0) *best_ms = best_t / 2.0f;
+  return status;
+}
+
 
 }  // namespace
 
@@ -529,59 +580,26 @@ int roibin_ctx_autotune(roibin_ctx* ctx, const float* d_frames, uint32_t n_frame
                         uint64_t out_stride, uint64_t* d_frame_bytes, int32_t* d_frame_status, void* stream,
                         float* best_ms) {
   if (!ctx) return ROIBIN_ERR_INVALID_ARG;
-  if (!ctx->fused_ok || resolved_path(ctx) == ROIBIN_PATH_PLAIN) {
-    if (!d_frames || !d_out || !d_frame_bytes || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
-    if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
-    if (out_stride < 16 || out_stride % 16 != 0) return ROIBIN_ERR_INVALID_ARG;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
-    return autotune_plain(ctx, d_frames, n_frames, d_out, out_stride, d_frame_bytes, d_frame_status,
-                          static_cast<cudaStream_t>(stream), best_ms);
-  }
   if (!d_frames || !d_out || !d_frame_bytes || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
   if (n_frames < 1 || n_frames > ctx->max_frames) return ROIBIN_ERR_INVALID_ARG;
   if (out_stride < 16 || out_stride % 16 != 0) return ROIBIN_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-    if (e0) cudaEventDestroy(e0);
-    return ROIBIN_ERR_CUDA;
-  }
-  const int path_was = ctx->path_req;
-  const FusedShape keep = ctx->fshape;
-  ctx->path_req = ROIBIN_PATH_FUSED;
-  FusedShape best = keep;
-  float best_t = -1.0f;
-  int status = ROIBIN_OK;
-  for (uint32_t cps = 4; cps >= 2 && status == ROIBIN_OK; --cps) {
-    for (uint32_t rb = 2; rb <= 3 && status == ROIBIN_OK; ++rb) {
-      for (uint32_t stages = 2; stages <= 4 && status == ROIBIN_OK; ++stages) {
-        FusedShape sh;
-        if (!fused_shape_for(ctx->dp, cps, rb, stages, &sh) || sh.ctas_per_sm != cps) continue;
-        ctx->fshape = sh;
-        status = compress_device(ctx, d_frames, n_frames, nullptr, nullptr, d_out, out_stride, d_frame_bytes,
-                                 d_frame_status, st);  // warm-up
-        if (status != ROIBIN_OK) break;
-        cudaEventRecord(e0, st);
-        for (int rep = 0; rep < 2 && status == ROIBIN_OK; ++rep)
-          status = compress_device(ctx, d_frames, n_frames, nullptr, nullptr, d_out, out_stride, d_frame_bytes,
-                                   d_frame_status, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) status = ROIBIN_ERR_CUDA;
-        float ms = 0.0f;
-        if (status == ROIBIN_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best_t < 0 || ms < best_t)) {
-          best_t = ms;
-          best = sh;
-        }
-      }
-    }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  ctx->path_req = path_was;
-  ctx->fshape = status == ROIBIN_OK && best_t >= 0 ? best : keep;
-  if (best_ms && best_t >= 0) *best_ms = best_t / 2.0f;
-  return status;
+  if (!ctx->fused_ok || ctx->path_req == ROIBIN_PATH_PLAIN)
+    return autotune_plain(ctx, d_frames, n_frames, d_out, out_stride, d_frame_bytes, d_frame_status, st, best_ms);
+  if (ctx->path_req == ROIBIN_PATH_FUSED)
+    return autotune_fused(ctx, d_frames, n_frames, d_out, out_stride, d_frame_bytes, d_frame_status, stream,
+                          best_ms);
+  // AUTO with both paths: tune each, and let AUTO take the faster one
+  float t_fused = -1.0f, t_plain = -1.0f;
+  int status = autotune_fused(ctx, d_frames, n_frames, d_out, out_stride, d_frame_bytes, d_frame_status, stream,
+                              &t_fused);
+  if (status != ROIBIN_OK) return status;
+  status = autotune_plain(ctx, d_frames, n_frames, d_out, out_stride, d_frame_bytes, d_frame_status, st, &t_plain);
+  if (status != ROIBIN_OK) return status;
+  ctx->auto_path = (t_plain >= 0.0f && t_fused >= 0.0f && t_plain < t_fused) ? ROIBIN_PATH_PLAIN : ROIBIN_PATH_FUSED;
+  if (best_ms) *best_ms = ctx->auto_path == ROIBIN_PATH_PLAIN ? t_plain : t_fused;
+  return ROIBIN_OK;
 }
 
 int roibin_ctx_set_trace(roibin_ctx* ctx, uint64_t* d_trace, uint32_t n_frames) {

@@ -377,6 +377,79 @@ __device__ __forceinline__ float ordered_sq_dev(const float* buf, int n, float m
   return s;
 }
 
+// A certain rejection for the evaluation below, without its ordered sums.
+// The evaluation keeps a candidate only if at least npix_min window pixels have
+// RN(x - bkg) > thr, where bkg = RN(S / nr) with S the ordered float32 sum of
+// the ring, and thr = RN(pix_nsigma * RN(sqrt(RN(Q / nr)))) with Q the ordered
+// sum of RN(RN(x - bkg)^2).  Here the warp bounds those values instead:
+//   - a tree sum t of the ring and a tree sum of |x|: the ordered sum S_f lies
+//     within (gamma_{nr-1} + gamma_12) * sum|x| of t (recursive summation
+//     bounds; each lane adds at most 8 terms, then 5 shuffle levels), so
+//     bkg lies in [RN(S_lo / nr), RN(S_hi / nr)] (RN is monotone);
+//   - each squared deviation lies between the squares of the nearest and the
+//     farthest rounded deviation over that interval; sums of those bounds
+//     rounded down and up, widened by gamma_{nr-1}, enclose Q (a sum of
+//     non-negative terms under RN is monotone in each term), so thr is at least
+//     RN(pix_nsigma * RN(sqrt(RN(Q_lo / nr)))).
+// A window pixel can pass only if RN(x - bkg_lo) exceeds that lowest threshold.
+// If fewer than npix_min could, the evaluation would reject the candidate too.
+// Non-finite values, an empty ring or an overflowing bound skip the screen.
+__device__ __forceinline__ bool screen_rejects(const float (&x)[8], uint32_t ring, uint32_t win, const DevParams& p) {
+  if (p.npix_min < 1) return false;
+  float t = 0.0f, aabs = 0.0f;
+  int nr = 0;
+  bool finite = true;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const bool in_ring = (ring >> u) & 1u, in_win = (win >> u) & 1u;
+    if (in_ring) {
+      t = __fadd_rn(t, x[u]);
+      aabs = __fadd_rn(aabs, fabsf(x[u]));
+      ++nr;
+    }
+    if ((in_ring || in_win) && !isfinite(x[u])) finite = false;
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, d));
+    aabs = __fadd_rn(aabs, __shfl_xor_sync(0xffffffffu, aabs, d));
+    nr += __shfl_xor_sync(0xffffffffu, nr, d);
+  }
+  if (!__all_sync(0xffffffffu, finite) || nr == 0) return false;
+  // gamma_k <= 1.0001 k u for k <= 300 (u = 2^-24 < 5.97e-8): this covers
+  // gamma_{nr-1} + gamma_12 with room, and the error of the tree sum of |x|
+  const float g = __fmul_ru((float)(nr + 13), 6.0e-8f);
+  const float err = __fmul_ru(aabs, __fmul_ru(g, 1.001f));
+  const float s_lo = __fsub_rd(t, err), s_hi = __fadd_ru(t, err);
+  if (!isfinite(s_lo) || !isfinite(s_hi)) return false;
+  const float bl = __fdiv_rn(s_lo, (float)nr), bh = __fdiv_rn(s_hi, (float)nr);
+  float ql = 0.0f, qh = 0.0f;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if (!((ring >> u) & 1u)) continue;
+    const float dl = __fsub_rn(x[u], bh), dh = __fsub_rn(x[u], bl);  // dl <= dh
+    const float near = (dl <= 0.0f && dh >= 0.0f) ? 0.0f : fminf(fabsf(dl), fabsf(dh));
+    const float far = fmaxf(fabsf(dl), fabsf(dh));
+    ql = __fadd_rd(ql, __fmul_rn(near, near));
+    qh = __fadd_ru(qh, __fmul_rn(far, far));
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    ql = __fadd_rd(ql, __shfl_xor_sync(0xffffffffu, ql, d));
+    qh = __fadd_ru(qh, __shfl_xor_sync(0xffffffffu, qh, d));
+  }
+  if (!isfinite(qh)) return false;
+  const float q_lo = __fmul_rd(ql, __fsub_rd(1.0f, g));
+  const float thr_lo = __fmul_rn(p.pix_nsigma, __fsqrt_rn(__fdiv_rn(q_lo, (float)nr)));
+  int possible = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const bool b = ((win >> u) & 1u) && __fsub_rn(x[u], bl) > thr_lo;
+    possible += __popc(__ballot_sync(0xffffffffu, b));
+  }
+  return possible < p.npix_min;
+}
+
 // One warp tests and evaluates the pixel (r, c) of `panel` (a1 + a2) when its
 // neighbourhood has at most 256 pixels (reach <= 7).  Lane l holds the pixels
 // l, l + 32, ... of the (2 reach + 1)^2 square in row-major order, loaded in
@@ -384,7 +457,7 @@ __device__ __forceinline__ float ordered_sq_dev(const float* buf, int n, float m
 // pixels, then the window pixels above threshold, are compacted in row-major
 // order into `buf` (per-warp shared memory, (2 reach + 1)^2 floats) and summed
 // there in that order, so the float32 results equal evaluate_peak_at's.
-template <class Load>
+template <class Load, bool kScreen = false>
 __device__ __noinline__ bool warp_peak_test_small(const float* __restrict__ panel, int H, int W, int r, int c,
                                                   const DevParams& p, float* buf, Load load) {
   const int reach = peak_reach(p), side = 2 * reach + 1, n = side * side;
@@ -418,6 +491,9 @@ __device__ __noinline__ bool warp_peak_test_small(const float* __restrict__ pane
     if ((before >> u) & 1u ? !(v > x[u]) : !(v >= x[u])) ok = false;
   }
   if (!__all_sync(0xffffffffu, ok)) return false;
+  if constexpr (kScreen) {
+    if (screen_rejects(x, ring, win, p)) return false;
+  }
   // ring pixels in row-major order
   int nr = 0;
 #pragma unroll
@@ -464,11 +540,12 @@ __device__ __noinline__ bool warp_peak_test_small(const float* __restrict__ pane
 // in parallel, and lane 0 runs the evaluation in its fixed order.
 // `load(addr)` reads global memory (plain or L2-only).  Every lane returns
 // the same answer.
-template <class Load>
+// kScreen: run screen_rejects before the ordered sums of the small path.
+template <bool kScreen = false, class Load>
 __device__ inline bool warp_peak_test(const float* __restrict__ panel, int H, int W, int r, int c,
                                       const DevParams& p, float* nb, Load load) {
   const int reach = peak_reach(p), side = 2 * reach + 1, n = side * side;
-  if (n <= 256) return warp_peak_test_small(panel, H, W, r, c, p, nb, load);
+  if (n <= 256) return warp_peak_test_small<Load, kScreen>(panel, H, W, r, c, p, nb, load);
   const uint32_t lane = lane_id();
   // gather in batches: all loads of a batch are issued before any store, so
   // the batch costs one memory latency instead of one per element

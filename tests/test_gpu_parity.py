@@ -339,6 +339,26 @@ def test_many_prequant_outliers(path):
     assert_parity(f, p, path)
 
 
+def test_autotuner_picks_a_path_for_auto_and_keeps_the_bytes():
+    """On AUTO with both paths the autotuner times both and AUTO takes the
+    faster; the bytes are the oracle's whichever it is."""
+    import torch
+    geom = (4, 37, 52)
+    f = small_batch(geom, 3, seed=78)
+    p = rb.default_params(atot_thr=300.0)
+    with rb.Context(geom, p, max_frames=3) as ctx:
+        assert ctx.resolved_path == rb.PATH_FUSED
+        shape, ms = ctx.autotune(torch.from_numpy(f).cuda())
+        assert ms > 0 and ctx.resolved_path in (rb.PATH_FUSED, rb.PATH_PLAIN)
+        out, nb, st = ctx.compress(torch.from_numpy(f).cuda())
+        torch.cuda.synchronize()
+        for k in range(3):
+            ost, ref = oracle.compress_frame(f[k], oparams(p))
+            assert int(st[k]) == ost == 0 and np.array_equal(out[k, :int(nb[k])].cpu().numpy(), ref)
+        ctx.set_path(rb.PATH_FUSED)            # an explicit path still wins
+        assert ctx.resolved_path == rb.PATH_FUSED
+
+
 def test_plain_autotuner_and_shapes_write_the_same_bytes():
     """The plain path's autotuner keeps one of its shapes; a few fixed shapes,
     and the kept one, all write the oracle's bytes."""
