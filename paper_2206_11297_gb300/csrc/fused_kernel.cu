@@ -227,7 +227,7 @@ __device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape&
 // shared memory.  A step covers RB binned rows: phase A bins and
 // prequantises them into registers, one barrier (it also frees the ring
 // slot), then phase B forms the Lorenzo residuals, code bytes and histogram.
-template <int RB>
+template <int RB, bool kScreen>
 __device__ void process_item(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
                              unsigned char* sm, uint32_t f, uint32_t u, uint32_t& ring_iter) {
   const StreamView v = stream_view(sm, sh);
@@ -540,7 +540,7 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
     auto test = [&](uint32_t lp) {  // lp: pixel index within the item
       const uint32_t pj = lp / plane, rem = lp - pj * plane;
       const uint32_t r = rem / p.W, c = rem - r * p.W;
-      if (warp_peak_test(item_px + (size_t)pj * plane, p.H, p.W, r, c, p, nb,
+      if (warp_peak_test<kScreen>(item_px + (size_t)pj * plane, p.H, p.W, r, c, p, nb,
                          [](const float* q) { return __ldg(q); }) &&
           lane == 0) {
         const uint32_t slot = atomicAdd(v.ctl + CTL_ACC, 1u);
@@ -1188,6 +1188,10 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
 }
 
 // ---------------------------------------------------------------------------
+// kScreen: the peak tests first try the exact rejection screen (screen_rejects),
+// which pays on frames with many candidates (hot pixels); both variants write
+// the same bytes.
+template <bool kScreen>
 __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainArgs a, FusedShape sh) {
   extern __shared__ __align__(128) unsigned char sm[];
   uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
@@ -1214,8 +1218,8 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
     const uint32_t r = t / round, j = t - r * round;
     if (j < sh.U) {
       if (r >= n) continue;
-      if (sh.RB == 2) process_item<2>(p, s, a, sh, sm, r, j, ring_iter);
-      else process_item<3>(p, s, a, sh, sm, r, j, ring_iter);
+      if (sh.RB == 2) process_item<2, kScreen>(p, s, a, sh, sm, r, j, ring_iter);
+      else process_item<3, kScreen>(p, s, a, sh, sm, r, j, ring_iter);
       // publish the item; the CTA that completes the frame builds its codebook
       __threadfence();
       __syncthreads();
@@ -1317,12 +1321,12 @@ bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per
     for (uint32_t rb = 3; rb >= 2 && !ok; --rb) ok = make_shape(p, ctas_per_sm, rb, stages, &sh) && sh.smem <= budget;
   }
   if (!ok) return false;
-  if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, kPT, sh.smem) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, kPT, sh.smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return false;
   }
@@ -1345,11 +1349,12 @@ bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out) {
 }
 
 cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
-                         cudaStream_t st) {
+                         bool screen, cudaStream_t st) {
   // stage counters, ready flags and the ticket counter start at zero
   cudaError_t e = cudaMemsetAsync(s.frame_done, 0, sizeof(uint32_t) * (4ull * a.n_frames + 1), st);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+  e = cudaFuncSetAttribute(screen ? k_fused<true> : k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sh.smem);
   if (e != cudaSuccess) return e;
   FusedShape s2 = sh;
   // frames between the stages in the ticket order: streaming -> chunk sizes
@@ -1359,7 +1364,8 @@ cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& 
   s2.lag2 = a.n_frames < kLagWrite ? a.n_frames : kLagWrite;
   const uint64_t tickets = (uint64_t)(a.n_frames + s2.lag1 + s2.lag2) * (s2.U + 2 * s2.groups);
   const uint32_t grid = (uint32_t)(tickets < sh.n_ctas ? tickets : sh.n_ctas);
-  k_fused<<<grid, kPT, sh.smem, st>>>(p, s, a, s2);
+  if (screen) k_fused<true><<<grid, kPT, sh.smem, st>>>(p, s, a, s2);
+  else k_fused<false><<<grid, kPT, sh.smem, st>>>(p, s, a, s2);
   return cudaGetLastError();
 }
 

@@ -779,7 +779,7 @@ bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out);
 bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, uint32_t stages,
                      FusedShape* out);
 cudaError_t launch_fused(const DevParams& p, const Scratch& fs, const PlainArgs& a, const FusedShape& sh,
-                         cudaStream_t st);
+                         bool screen, cudaStream_t st);
 
 // Each launcher enqueues one kernel and returns cudaGetLastError().
 // `timer` may be null; when set, it brackets the launch with events.

@@ -9,6 +9,10 @@ import oracle
 import paper_2206_11297_gb300 as rb
 
 
+# a path token for the tests: the fused path with its peak screen on
+FUSED_SCREEN = 1002
+
+
 def oparams(params: rb.Params):
     return oracle.make_params(**params.as_dict())
 
@@ -22,6 +26,9 @@ def gpu_compress(frames: np.ndarray, params: rb.Params, path: int = rb.PATH_AUTO
     own = ctx is None
     if own:
         ctx = rb.Context(frames.shape[1:], params, max_frames=n)
+    screen = path == FUSED_SCREEN
+    if screen:
+        path = rb.PATH_FUSED
     try:
         try:
             ctx.set_path(path)
@@ -29,6 +36,8 @@ def gpu_compress(frames: np.ndarray, params: rb.Params, path: int = rb.PATH_AUTO
             if path == rb.PATH_FUSED and e.code == rb.ERR_INVALID_ARG:
                 pytest.skip("the fused path does not cover this shape (bin 2x2, cols % 4 == 0 only)")
             raise
+        if screen:
+            ctx.set_fused_screen(True)
         d = torch.from_numpy(frames).cuda()
         dp = dn = None
         if peaks is not None:

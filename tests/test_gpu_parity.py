@@ -8,12 +8,13 @@ import pytest
 import oracle
 import oracle_pins
 import paper_2206_11297_gb300 as rb
-from gpu_util import assert_parity, gpu_compress, gpu_decompress, oparams
+from gpu_util import FUSED_SCREEN, assert_parity, gpu_compress, gpu_decompress, oparams
 from synthetic import RECIPES, FrameRecipe, make_frame
 
 pytestmark = pytest.mark.gpu
 
-PATHS = [rb.PATH_PLAIN, rb.PATH_FUSED]
+PATHS2 = [rb.PATH_PLAIN, rb.PATH_FUSED]
+PATHS = PATHS2 + [FUSED_SCREEN]   # and the fused kernel's screened variant
 
 
 def small_batch(geom, n, seed, peaks=("uniform", 2, 12), **kw):
@@ -32,7 +33,7 @@ def _cuda():
 
 def fused_or_skip(geom, params, path):
     """The fused path covers bin 2x2 with cols % 4 == 0; other shapes run the plain path."""
-    if path != rb.PATH_FUSED:
+    if path not in (rb.PATH_FUSED, FUSED_SCREEN):
         return
     with rb.Context(geom, params, max_frames=1) as ctx:
         ctx.set_path(rb.PATH_AUTO)
@@ -268,7 +269,7 @@ def test_corrupt_outlier_lists_and_peaks_are_rejected(dec_path):
     assert np.array_equal(rec[-1].view(np.uint32), orec.view(np.uint32))
 
 
-@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("path", PATHS2)
 def test_roi_mask_and_peaks_match_oracle(path):
     import torch
     geom = (3, 50, 60)
@@ -300,7 +301,7 @@ def test_batch_composition_invariance(path):
         assert np.array_equal(alone[0], together[k])
 
 
-@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("path", PATHS2)
 def test_context_reuse_with_outliers_in_other_panels(path):
     """Prequantisation outliers in different panels on successive calls of one
     context: nothing left over from the first call may leak into the second."""
