@@ -1033,7 +1033,7 @@ uint32_t dec_panel_rows(const DevParams& p) {
   const uint32_t strips = ceil_div(p.Hb, most);
   return ceil_div(p.Hb, strips);
 }
-cudaError_t launch_dec_decode_lut(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st) {
+cudaError_t launch_dec_decoders(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st) {
   // a thread per chunk, in whole warps; a frame's chunks in as few blocks as fit
   const uint32_t threads = std::min<uint32_t>(kDecMaxThreads, ceil_div(p.n_chunks, 32) * 32);
   dim3 grid(ceil_div(p.n_chunks, threads), a.n_frames);

@@ -669,8 +669,9 @@ int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes, c
   cudaError_t e;
   if ((e = timed(ctx, K_DEC_PARSE, st, [&] { return launch_dec_parse(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if (resolved_dec_path(ctx) == ROIBIN_DEC_PANEL) {
-    if ((e = timed(ctx, K_DEC_DECODE, st, [&] { return launch_dec_decode_lut(p, s, a, st); })) != cudaSuccess)
+    if ((e = timed(ctx, K_DEC_DECODE, st, [&] { return launch_dec_decoders(p, s, a, st); })) != cudaSuccess)
       return cuda_status(e);
+    ctx->last_launches++;  // the decode step is two kernels: sparse frames, then dense ones
     if ((e = timed(ctx, K_DEC_PANEL, st, [&] { return launch_dec_panel(p, s, a, st); })) != cudaSuccess)
       return cuda_status(e);
     ctx->last_launches++;  // the status copy that ends the panel launch

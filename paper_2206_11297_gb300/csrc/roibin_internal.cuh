@@ -846,7 +846,8 @@ cudaError_t launch_dec_roi(const DevParams& p, const Scratch& s, const DecArgs& 
 // the panel path: decode through the prefix table into symbols, then one block
 // per (frame, panel) rebuilds the panel strip by strip
 uint32_t dec_panel_rows(const DevParams& p);  // binned rows per strip; 0: panel path unavailable
-cudaError_t launch_dec_decode_lut(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+// the decoders of the panel path: k_dec_decode_sparse, then k_dec_decode_dense
+cudaError_t launch_dec_decoders(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_panel(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_roi_mask(const DevParams& p, const uint16_t* peaks, const uint32_t* npeaks,
                             uint32_t n, uint8_t* mask, cudaStream_t st);
