@@ -306,7 +306,8 @@ int roibin_ctx_enable_timing(roibin_ctx* ctx, int enable);
 int roibin_ctx_kernel_times(roibin_ctx* ctx, const char** names, double* total_ms,
                             uint32_t* launches, int max_kernels, int* n_kernels);
 
-/* Number of kernel launches the last compress call enqueued. */
+/* Number of kernels the last compress or decompress call launched (memsets
+ * not counted). */
 uint32_t roibin_ctx_last_launch_count(const roibin_ctx* ctx);
 
 /* Bytes of device memory the library sets aside, per device, for
@@ -383,7 +384,7 @@ int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_j
 /* Launches the graph on `stream`; asynchronous; per-frame results as
  * roibin_compress writes them. */
 int roibin_graph_launch(roibin_graph* g, void* stream);
-/* Kernel launches (and memsets) one graph launch performs. */
+/* Kernel launches one graph launch performs (memset nodes not counted). */
 int roibin_graph_launch_count(const roibin_graph* g);
 /* Frees the graph.  Synchronises the device first.  NULL ok. */
 int roibin_graph_destroy(roibin_graph* g);

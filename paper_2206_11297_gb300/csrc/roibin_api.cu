@@ -307,7 +307,6 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
   a.trace = ctx->trace;
   a.trace_frames = ctx->trace_frames;
   if (resolved_path(ctx) == ROIBIN_PATH_FUSED && (uint64_t)n_frames * ctx->dp.P < (1ull << 31)) {
-    ctx->last_launches++;  // the counter reset
     cudaError_t e = timed(ctx, K_FUSED, st,
                           [&] { return launch_fused(ctx->dp, ctx->s, a, ctx->fshape, ctx->fused_screen, st); });
     return cuda_status(e);
