@@ -408,3 +408,30 @@ def test_autotuned_shape_writes_the_same_bytes():
     for k in range(3):
         ost, ref = oracle.compress_frame(f[k], oparams(p))
         assert st[k] == ost == 0 and np.array_equal(out[k, :nb[k]], ref)
+
+
+def test_new_entry_points_reject_bad_arguments():
+    """The screen switch needs a fused path; decompression paths and plain
+    shapes out of range are refused; the context keeps its settings."""
+    import torch
+    wide = (2, 21, 1024)   # no fused path
+    p = rb.default_params(atot_thr=300.0)
+    with rb.Context(wide, p, max_frames=1) as ctx:
+        with pytest.raises(rb.RoibinError):
+            ctx.set_fused_screen(True)
+        assert not ctx.fused_screen
+        with pytest.raises(rb.RoibinError):
+            ctx.set_decompress_path(7)
+        assert ctx.resolved_decompress_path == rb.DEC_PANEL
+        with pytest.raises(rb.RoibinError):
+            ctx.set_plain_shape(0, 100)
+        assert ctx.plain_shape == (0, 0)
+        f = torch.zeros((2, *wide), dtype=torch.float32, device="cuda")
+        with pytest.raises(rb.RoibinError):
+            ctx.autotune(f)                # more frames than the context takes
+    with rb.Context((2, 12, 16), p, max_frames=1) as ctx:
+        assert ctx.resolved_path == rb.PATH_FUSED
+        ctx.set_fused_screen(True)
+        assert ctx.fused_screen
+        ctx.set_fused_screen(False)
+        assert not ctx.fused_screen
