@@ -603,6 +603,51 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
           test(key + (l >> 2) * p.W + (l & 3u));
         }
       }
+    } else if constexpr (kScreen) {
+      // many candidates (hot pixels): one lane per candidate.  The warp gathers
+      // the pixels >= amax_thr of its slices, 32 at a time, and each lane runs
+      // the local-maximum rule and the evaluation on its own candidate in the
+      // sequential order the warp tests reproduce (is_local_max_at,
+      // evaluate_peak_at), so a warp instruction serves 32 candidates
+      const uint32_t n_px = kp * plane;
+      uint32_t mine = 0, nq = 0;  // nq: candidates held by lanes 0 .. nq - 1 (the same in every lane)
+      auto flush = [&]() {
+        if (lane < nq) {
+          const uint32_t pj = mine / plane, rem = mine - pj * plane;
+          const int r = (int)(rem / p.W), c = (int)(rem - (uint32_t)r * p.W);
+          const float* pan = item_px + (size_t)pj * plane;
+          auto px = [&](int dr, int dc) { return __ldg(pan + (size_t)(r + dr) * p.W + (c + dc)); };
+          if (is_local_max_at(px, (int)p.H, (int)p.W, r, c, p) &&
+              evaluate_peak_at(px, (int)p.H, (int)p.W, r, c, p)) {
+            const uint32_t slot = atomicAdd(v.ctl + CTL_ACC, 1u);
+            if (slot < sh.sort_n2) v.acc[slot] = mine;
+          }
+        }
+        __syncwarp();
+        nq = 0;
+      };
+      for (uint32_t base = warp * 32; base < n_px; base += kPW * 32) {
+        const uint32_t lp = base + lane;
+        const bool hot = lp < n_px && __ldg(item_px + lp) >= p.amax;
+        uint32_t m = __ballot_sync(0xffffffffu, hot);
+        while (m) {
+          // the first `take` hot lanes hand their pixels to lanes nq .. nq + take - 1
+          // through the warp's 32 slots of the candidate list (unused on this path)
+          static_assert(kThrLocalCap >= kPW * 32, "32 candidate slots per warp");
+          uint32_t* q = v.cand + warp * 32;
+          const uint32_t take = min((uint32_t)__popc(m), 32u - nq);
+          const uint32_t k = __popc(m & lanemask_lt());
+          const bool go = ((m >> lane) & 1u) && k < take;
+          if (go) q[nq + k] = base + lane;
+          m &= ~__ballot_sync(0xffffffffu, go);
+          __syncwarp();
+          if (lane >= nq && lane < nq + take) mine = q[lane];
+          __syncwarp();
+          nq += take;
+          if (nq == 32) flush();
+        }
+      }
+      if (nq) flush();
     } else {
       const uint32_t n_px = kp * plane;
       for (uint32_t base = warp * 32; base < n_px; base += kPW * 32) {

@@ -312,6 +312,24 @@ __device__ inline bool evaluate_peak_at(Px px, int H, int W, int r, int c, const
   return atot > noise;
 }
 
+// a1 for one thread: (r, c) is >= amax_thr, >= every in-panel window pixel and
+// > every window pixel before it in row-major order (the warp tests' rule).
+template <class Px>
+__device__ inline bool is_local_max_at(Px px, int H, int W, int r, int c, const DevParams& p) {
+  const float v = px(0, 0);
+  if (!(v >= p.amax)) return false;
+  for (int dr = -p.rank; dr <= p.rank; ++dr) {
+    for (int dc = -p.rank; dc <= p.rank; ++dc) {
+      const int rr = r + dr, cc = c + dc;
+      if ((dr == 0 && dc == 0) || rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+      const float u = px(dr, dc);
+      const bool before = dr < 0 || (dr == 0 && dc < 0);
+      if (before ? !(v > u) : !(v >= u)) return false;
+    }
+  }
+  return true;
+}
+
 __device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int W, int r, int c,
                                      const DevParams& p) {
   return evaluate_peak_at([&](int dr, int dc) { return __ldg(panel + (size_t)(r + dr) * W + (c + dc)); },
