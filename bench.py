@@ -250,7 +250,7 @@ def mixed_graph(args, dev, local, stream):
         shape, _ = ctx.autotune(frames, out=out, frame_bytes=nb, status=st)
         if ctx.resolved_path == rb.PATH_FUSED:
             shapes[name] = {"ctas_per_sm": shape[0], "rows_per_step": shape[1], "stages": shape[2],
-                            "peak_screen": ctx.fused_screen}
+                            "dense_peaks": ctx.fused_dense_peaks}
         else:
             shapes[name] = {"rows_per_step": shape[0], "bands_per_panel": shape[1]}
         paths[name] = {rb.PATH_PLAIN: "plain", rb.PATH_FUSED: "fused"}[ctx.resolved_path]
@@ -360,7 +360,7 @@ def run_ours(args, rank, local, world):
         tuned[{rb.PATH_PLAIN: "plain", rb.PATH_FUSED: "fused"}[path]] = (
             {"rows_per_step": shape[0], "bands_per_panel": shape[1]} if path == rb.PATH_PLAIN else
             {"ctas_per_sm": shape[0], "rows_per_step": shape[1], "stages": shape[2], "grid_ctas": shape[3],
-             "peak_screen": ctx.fused_screen})
+             "dense_peaks": ctx.fused_dense_peaks})
     torch.cuda.synchronize()
     for path in paths:
         res[path] = timed_path(path)

@@ -159,8 +159,8 @@ int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t r
  * (arguments as roibin_compress, which it calls three times per shape), with
  * CUDA events on `stream`; keeps the fastest shape for later calls.
  *   fused: every fused shape that fits this GPU (CTAs per SM 2..4, rows per
- *          step 2..3, ring slots 2..4), then the best one with and without
- *          the peak screen (roibin_ctx_set_fused_screen);
+ *          step 2..3, ring slots 2..4), then the best one in both peak
+ *          variants (roibin_ctx_set_fused_dense_peaks);
  *   plain: rows per step 1, 2, 4, 8, 16 (those that fit) times bands per
  *          panel 1, 2, 4, 8, 16 (up to half the binned rows).
  * A context left on ROIBIN_PATH_AUTO that has both paths gets both tuned, and
@@ -172,15 +172,17 @@ int roibin_ctx_autotune(roibin_ctx* ctx, const float* d_frames, uint32_t n_frame
                         uint64_t out_stride, uint64_t* d_frame_bytes, int32_t* d_frame_status, void* stream,
                         float* best_ms);
 
-/* Variant of the fused kernel whose peak tests first try an exact rejection
- * screen (interval bounds on the ring statistics; a candidate that could pass
- * still gets the full evaluation).  It pays on frames with many candidates
- * (hot pixels) and costs a little elsewhere; both variants write the same
- * bytes.  Off by default; the autotuner tries both on its best fused shape.
- * ROIBIN_ERR_INVALID_ARG when the context has no fused path. */
-int roibin_ctx_set_fused_screen(roibin_ctx* ctx, int on);
-/* 1 if the fused kernel's screened variant is selected, else 0. */
-int roibin_ctx_fused_screen(const roibin_ctx* ctx);
+/* Variant of the fused kernel for frames with many peak candidates (hot
+ * pixels).  Its warp tests first try an exact rejection screen (interval
+ * bounds on the ring statistics; a candidate that could pass still gets the
+ * full evaluation), and a work item whose candidates overflow its list
+ * evaluates them one per lane instead of one per warp.  It pays on such frames
+ * and costs a little on frames with few candidates; both variants write the
+ * same bytes.  Off by default; the autotuner tries both on its best fused
+ * shape.  ROIBIN_ERR_INVALID_ARG when the context has no fused path. */
+int roibin_ctx_set_fused_dense_peaks(roibin_ctx* ctx, int on);
+/* 1 if the fused kernel's dense-peaks variant is selected, else 0. */
+int roibin_ctx_fused_dense_peaks(const roibin_ctx* ctx);
 
 /* Shape of the plain path: binned rows per step of its streaming kernel
  * (1..16, as fit its shared memory) and bands per panel (1 .. ceil(rows /

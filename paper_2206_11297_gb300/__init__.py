@@ -76,8 +76,8 @@ _SIGNATURES = {
     "roibin_ctx_resolved_path": (ctypes.c_int, [_P]),
     "roibin_ctx_set_decompress_path": (ctypes.c_int, [_P, ctypes.c_int]),
     "roibin_ctx_set_plain_shape": (ctypes.c_int, [_P, _u32, _u32]),
-    "roibin_ctx_set_fused_screen": (ctypes.c_int, [_P, ctypes.c_int]),
-    "roibin_ctx_fused_screen": (ctypes.c_int, [_P]),
+    "roibin_ctx_set_fused_dense_peaks": (ctypes.c_int, [_P, ctypes.c_int]),
+    "roibin_ctx_fused_dense_peaks": (ctypes.c_int, [_P]),
     "roibin_ctx_plain_shape": (ctypes.c_int, [_P, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     "roibin_graph_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Job), _u32]),
     "roibin_graph_launch": (ctypes.c_int, [_P, _P]),
@@ -244,12 +244,12 @@ class Context:
     def set_path(self, path: int):
         _check("roibin_ctx_set_path", self.lib.roibin_ctx_set_path(self._h, int(path)))
 
-    def set_fused_screen(self, on: bool):
-        _check("roibin_ctx_set_fused_screen", self.lib.roibin_ctx_set_fused_screen(self._h, 1 if on else 0))
+    def set_fused_dense_peaks(self, on: bool):
+        _check("roibin_ctx_set_fused_dense_peaks", self.lib.roibin_ctx_set_fused_dense_peaks(self._h, 1 if on else 0))
 
     @property
-    def fused_screen(self) -> bool:
-        return self.lib.roibin_ctx_fused_screen(self._h) == 1
+    def fused_dense_peaks(self) -> bool:
+        return self.lib.roibin_ctx_fused_dense_peaks(self._h) == 1
 
     def set_plain_shape(self, rows_per_step: int = 0, bands_per_panel: int = 0):
         _check("roibin_ctx_set_plain_shape", self.lib.roibin_ctx_set_plain_shape(

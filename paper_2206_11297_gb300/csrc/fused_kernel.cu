@@ -227,7 +227,7 @@ __device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape&
 // shared memory.  A step covers RB binned rows: phase A bins and
 // prequantises them into registers, one barrier (it also frees the ring
 // slot), then phase B forms the Lorenzo residuals, code bytes and histogram.
-template <int RB, bool kScreen>
+template <int RB, bool kDense>
 __device__ void process_item(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
                              unsigned char* sm, uint32_t f, uint32_t u, uint32_t& ring_iter) {
   const StreamView v = stream_view(sm, sh);
@@ -540,7 +540,7 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
     auto test = [&](uint32_t lp) {  // lp: pixel index within the item
       const uint32_t pj = lp / plane, rem = lp - pj * plane;
       const uint32_t r = rem / p.W, c = rem - r * p.W;
-      if (warp_peak_test<kScreen>(item_px + (size_t)pj * plane, p.H, p.W, r, c, p, nb,
+      if (warp_peak_test<kDense>(item_px + (size_t)pj * plane, p.H, p.W, r, c, p, nb,
                          [](const float* q) { return __ldg(q); }) &&
           lane == 0) {
         const uint32_t slot = atomicAdd(v.ctl + CTL_ACC, 1u);
@@ -603,7 +603,7 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
           test(key + (l >> 2) * p.W + (l & 3u));
         }
       }
-    } else if constexpr (kScreen) {
+    } else if constexpr (kDense) {
       // many candidates (hot pixels): one lane per candidate.  The warp gathers
       // the pixels >= amax_thr of its slices, 32 at a time, and each lane runs
       // the local-maximum rule and the evaluation on its own candidate in the
@@ -1233,10 +1233,11 @@ __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs
 }
 
 // ---------------------------------------------------------------------------
-// kScreen: the peak tests first try the exact rejection screen (screen_rejects),
-// which pays on frames with many candidates (hot pixels); both variants write
-// the same bytes.
-template <bool kScreen>
+// kDense: the variant for frames with many peak candidates (hot pixels).  Its
+// warp tests of listed candidates first try the exact rejection screen
+// (screen_rejects), and an item whose candidates overflow the list evaluates
+// them one per lane.  Both variants write the same bytes.
+template <bool kDense>
 __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainArgs a, FusedShape sh) {
   extern __shared__ __align__(128) unsigned char sm[];
   uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
@@ -1263,8 +1264,8 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
     const uint32_t r = t / round, j = t - r * round;
     if (j < sh.U) {
       if (r >= n) continue;
-      if (sh.RB == 2) process_item<2, kScreen>(p, s, a, sh, sm, r, j, ring_iter);
-      else process_item<3, kScreen>(p, s, a, sh, sm, r, j, ring_iter);
+      if (sh.RB == 2) process_item<2, kDense>(p, s, a, sh, sm, r, j, ring_iter);
+      else process_item<3, kDense>(p, s, a, sh, sm, r, j, ring_iter);
       // publish the item; the CTA that completes the frame builds its codebook
       __threadfence();
       __syncthreads();

@@ -44,7 +44,7 @@ struct roibin_ctx {
   int dec_path_req = ROIBIN_DEC_AUTO;
   uint32_t plain_rows = 0, plain_bands = 0;  // plain-path shape; 0: chosen per call
   bool fused_ok = false;
-  bool fused_screen = false;  // the fused kernel's variant with the exact peak screen
+  bool fused_dense_peaks = false;  // the fused kernel's variant for many peak candidates
   FusedShape fshape{};
   uint64_t* trace = nullptr;
   uint32_t trace_frames = 0;
@@ -308,7 +308,7 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
   a.trace_frames = ctx->trace_frames;
   if (resolved_path(ctx) == ROIBIN_PATH_FUSED && (uint64_t)n_frames * ctx->dp.P < (1ull << 31)) {
     cudaError_t e = timed(ctx, K_FUSED, st,
-                          [&] { return launch_fused(ctx->dp, ctx->s, a, ctx->fshape, ctx->fused_screen, st); });
+                          [&] { return launch_fused(ctx->dp, ctx->s, a, ctx->fshape, ctx->fused_dense_peaks, st); });
     return cuda_status(e);
   }
   return compress_plain(ctx, a, st);
@@ -432,18 +432,18 @@ int autotune_fused(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, ui
       }
     }
   }
-  // the variant with the exact peak screen, on the best shape
-  const bool screen_was = ctx->fused_screen;
-  bool best_screen = screen_was;
+  // the dense-peaks variant, on the best shape
+  const bool dense_was = ctx->fused_dense_peaks;
+  bool best_dense = dense_was;
   if (status == ROIBIN_OK && best_t >= 0) {
     ctx->fshape = best;
     for (int scr = 0; scr < 2 && status == ROIBIN_OK; ++scr) {
-      ctx->fused_screen = scr != 0;
+      ctx->fused_dense_peaks = scr != 0;
       const float ms = time_compress(ctx, d_frames, n_frames, d_out, out_stride, d_frame_bytes, d_frame_status,
                                      st, e0, e1, &status);
       if (ms >= 0 && (scr == 0 || ms < best_t)) {
         best_t = ms;
-        best_screen = scr != 0;
+        best_dense = scr != 0;
       }
     }
   }
@@ -451,7 +451,7 @@ int autotune_fused(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, ui
   cudaEventDestroy(e1);
   ctx->path_req = path_was;
   ctx->fshape = status == ROIBIN_OK && best_t >= 0 ? best : keep;
-  ctx->fused_screen = status == ROIBIN_OK && best_t >= 0 ? best_screen : screen_was;
+  ctx->fused_dense_peaks = status == ROIBIN_OK && best_t >= 0 ? best_dense : dense_was;
   if (best_ms && best_t >= 0) *best_ms = best_t / 2.0f;
   return status;
 }
@@ -576,15 +576,15 @@ int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_
   return ROIBIN_OK;
 }
 
-int roibin_ctx_set_fused_screen(roibin_ctx* ctx, int on) {
+int roibin_ctx_set_fused_dense_peaks(roibin_ctx* ctx, int on) {
   if (!ctx || !ctx->fused_ok) return ROIBIN_ERR_INVALID_ARG;
-  ctx->fused_screen = on != 0;
+  ctx->fused_dense_peaks = on != 0;
   return ROIBIN_OK;
 }
 
-int roibin_ctx_fused_screen(const roibin_ctx* ctx) {
+int roibin_ctx_fused_dense_peaks(const roibin_ctx* ctx) {
   if (!ctx) return ROIBIN_ERR_INVALID_ARG;
-  return ctx->fused_screen ? 1 : 0;
+  return ctx->fused_dense_peaks ? 1 : 0;
 }
 
 int roibin_ctx_set_plain_shape(roibin_ctx* ctx, uint32_t rows_per_step, uint32_t bands_per_panel) {

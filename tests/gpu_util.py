@@ -9,8 +9,8 @@ import oracle
 import paper_2206_11297_gb300 as rb
 
 
-# a path token for the tests: the fused path with its peak screen on
-FUSED_SCREEN = 1002
+# a path token for the tests: the fused path in its dense-peaks variant
+FUSED_DENSE = 1002
 
 
 def oparams(params: rb.Params):
@@ -26,8 +26,8 @@ def gpu_compress(frames: np.ndarray, params: rb.Params, path: int = rb.PATH_AUTO
     own = ctx is None
     if own:
         ctx = rb.Context(frames.shape[1:], params, max_frames=n)
-    screen = path == FUSED_SCREEN
-    if screen:
+    dense = path == FUSED_DENSE
+    if dense:
         path = rb.PATH_FUSED
     try:
         try:
@@ -36,8 +36,8 @@ def gpu_compress(frames: np.ndarray, params: rb.Params, path: int = rb.PATH_AUTO
             if path == rb.PATH_FUSED and e.code == rb.ERR_INVALID_ARG:
                 pytest.skip("the fused path does not cover this shape (bin 2x2, cols % 4 == 0 only)")
             raise
-        if screen:
-            ctx.set_fused_screen(True)
+        if dense:
+            ctx.set_fused_dense_peaks(True)
         d = torch.from_numpy(frames).cuda()
         dp = dn = None
         if peaks is not None:

@@ -8,13 +8,13 @@ import pytest
 import oracle
 import oracle_pins
 import paper_2206_11297_gb300 as rb
-from gpu_util import FUSED_SCREEN, assert_parity, gpu_compress, gpu_decompress, oparams
+from gpu_util import FUSED_DENSE, assert_parity, gpu_compress, gpu_decompress, oparams
 from synthetic import RECIPES, FrameRecipe, make_frame
 
 pytestmark = pytest.mark.gpu
 
 PATHS2 = [rb.PATH_PLAIN, rb.PATH_FUSED]
-PATHS = PATHS2 + [FUSED_SCREEN]   # and the fused kernel's screened variant
+PATHS = PATHS2 + [FUSED_DENSE]   # and the fused kernel's dense-peaks variant
 
 
 def small_batch(geom, n, seed, peaks=("uniform", 2, 12), **kw):
@@ -33,7 +33,7 @@ def _cuda():
 
 def fused_or_skip(geom, params, path):
     """The fused path covers bin 2x2 with cols % 4 == 0; other shapes run the plain path."""
-    if path not in (rb.PATH_FUSED, FUSED_SCREEN):
+    if path not in (rb.PATH_FUSED, FUSED_DENSE):
         return
     with rb.Context(geom, params, max_frames=1) as ctx:
         ctx.set_path(rb.PATH_AUTO)
@@ -411,15 +411,15 @@ def test_autotuned_shape_writes_the_same_bytes():
 
 
 def test_new_entry_points_reject_bad_arguments():
-    """The screen switch needs a fused path; decompression paths and plain
+    """The dense-peaks switch needs a fused path; decompression paths and plain
     shapes out of range are refused; the context keeps its settings."""
     import torch
     wide = (2, 21, 1024)   # no fused path
     p = rb.default_params(atot_thr=300.0)
     with rb.Context(wide, p, max_frames=1) as ctx:
         with pytest.raises(rb.RoibinError):
-            ctx.set_fused_screen(True)
-        assert not ctx.fused_screen
+            ctx.set_fused_dense_peaks(True)
+        assert not ctx.fused_dense_peaks
         with pytest.raises(rb.RoibinError):
             ctx.set_decompress_path(7)
         assert ctx.resolved_decompress_path == rb.DEC_PANEL
@@ -431,7 +431,7 @@ def test_new_entry_points_reject_bad_arguments():
             ctx.autotune(f)                # more frames than the context takes
     with rb.Context((2, 12, 16), p, max_frames=1) as ctx:
         assert ctx.resolved_path == rb.PATH_FUSED
-        ctx.set_fused_screen(True)
-        assert ctx.fused_screen
-        ctx.set_fused_screen(False)
-        assert not ctx.fused_screen
+        ctx.set_fused_dense_peaks(True)
+        assert ctx.fused_dense_peaks
+        ctx.set_fused_dense_peaks(False)
+        assert not ctx.fused_dense_peaks
