@@ -219,6 +219,7 @@ constexpr int kPeakWarps = 8;
 
 __global__ void __launch_bounds__(kPeakWarps * 32) k_peaks(DevParams p, Scratch s, PlainArgs a) {
   extern __shared__ float nb_all[];
+  __shared__ uint32_t q_all[kPeakWarps * 32];  // 32 candidate slots per warp (dense frames)
   const int side = 2 * peak_reach(p) + 1;
   float* nb = nb_all + (threadIdx.x >> 5) * side * side;
   const uint32_t f = blockIdx.y;
@@ -246,6 +247,27 @@ __global__ void __launch_bounds__(kPeakWarps * 32) k_peaks(DevParams p, Scratch 
   // loads per lane (frames start 16-byte aligned; a frame of fewer than a
   // multiple of 4 pixels takes the scalar loop), then tests those >= amax_thr
   if (p.frame_px % 4 == 0 && (reinterpret_cast<uintptr_t>(frame) & 15u) == 0) {
+    // many candidates: one lane per candidate.  Pixels >= amax_thr are gathered
+    // 32 at a time and each lane runs the local-maximum rule and the evaluation
+    // on its own, in the sequential order the warp tests reproduce
+    // (is_local_max_at, evaluate_peak_at), so a warp instruction serves 32
+    const uint32_t lane = lane_id();
+    uint32_t* slots = q_all + (threadIdx.x >> 5) * 32;
+    uint32_t mine = 0, nq = 0;  // nq: candidates held by lanes 0 .. nq - 1 (the same in every lane)
+    auto flush = [&]() {
+      if (lane < nq) {
+        const uint32_t pn = mine / plane, rem = mine - pn * plane;
+        const int r = (int)(rem / p.W), c = (int)(rem - (uint32_t)r * p.W);
+        const float* pan = frame + (size_t)pn * plane;
+        auto px = [&](int dr, int dc) { return __ldg(pan + (size_t)(r + dr) * p.W + (c + dc)); };
+        if (is_local_max_at(px, (int)p.H, (int)p.W, r, c, p) && evaluate_peak_at(px, (int)p.H, (int)p.W, r, c, p)) {
+          const uint32_t slot = atomicAdd(s.peak_count + f, 1u);
+          if (slot < p.max_peaks) s.peak_key[(size_t)f * p.max_peaks + slot] = mine;
+        }
+      }
+      __syncwarp();
+      nq = 0;
+    };
     const uint64_t n4 = p.frame_px / 4;
     const float4* f4 = reinterpret_cast<const float4*>(frame);
     for (uint64_t b4 = (uint64_t)warp * 128; b4 < n4; b4 += (uint64_t)nwarps * 128) {
@@ -265,13 +287,23 @@ __global__ void __launch_bounds__(kPeakWarps * 32) k_peaks(DevParams p, Scratch 
                  (uint32_t)(q[u].z >= p.amax) << (4 * u + 2) | (uint32_t)(q[u].w >= p.amax) << (4 * u + 3);
       for (uint32_t j = 0; j < 16; ++j) {
         uint32_t m = __ballot_sync(0xffffffffu, (hot >> j) & 1u);
+        const uint32_t px0 = (uint32_t)(4 * (b4 + (j >> 2) * 32)) + (j & 3u);  // pixel of lane 0
         while (m) {
-          const uint32_t l = __ffs(m) - 1;
-          m &= m - 1;
-          test((uint32_t)(4 * (b4 + (j >> 2) * 32 + l) + (j & 3u)));
+          // the first `take` hot lanes hand their pixels to lanes nq .. nq + take - 1
+          const uint32_t take = min((uint32_t)__popc(m), 32u - nq);
+          const uint32_t k = __popc(m & lanemask_lt());
+          const bool go = ((m >> lane) & 1u) && k < take;
+          if (go) slots[nq + k] = px0 + 4 * lane;
+          m &= ~__ballot_sync(0xffffffffu, go);
+          __syncwarp();
+          if (lane >= nq && lane < nq + take) mine = slots[lane];
+          __syncwarp();
+          nq += take;
+          if (nq == 32) flush();
         }
       }
     }
+    if (nq) flush();
     return;
   }
   for (uint64_t base = (uint64_t)warp * 32; base < p.frame_px; base += (uint64_t)nwarps * 32) {
