@@ -163,9 +163,11 @@ int roibin_ctx_set_fused_shape(roibin_ctx* ctx, uint32_t ctas_per_sm, uint32_t r
  *          variants (roibin_ctx_set_fused_dense_peaks);
  *   plain: rows per step 1, 2, 4, 8, 16 (those that fit) times bands per
  *          panel 1, 2, 4, 8, 16 (up to half the binned rows).
- * A context left on ROIBIN_PATH_AUTO that has both paths gets both tuned, and
- * AUTO then takes the faster one for later calls (roibin_ctx_resolved_path
- * reports it; roibin_ctx_set_path still overrides it).
+ * A context left on ROIBIN_PATH_AUTO that has both paths gets both tuned;
+ * the two winners are then timed again three times in alternation (so that
+ * clocks still ramping during the first search favour neither), and AUTO
+ * takes the faster one for later calls (roibin_ctx_resolved_path reports it;
+ * roibin_ctx_set_path still overrides it).
  * Synchronous.  *best_ms (optional) receives the best time per call.  Every
  * shape and path writes identical bytes, so the choice only changes speed. */
 int roibin_ctx_autotune(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, uint8_t* d_out,
@@ -368,11 +370,17 @@ typedef struct {
 
 typedef struct roibin_graph roibin_graph;
 
-/* Captures the jobs' compression launches, each job on its own branch, into
- * one CUDA graph and instantiates it.  A launch of the graph runs every job
- * once: the branches are independent, so the GPU runs them concurrently (a
- * persistent fused kernel only ever waits for work handed out at an earlier
- * ticket of its own launch, so concurrent branches cannot block one another).
+#define ROIBIN_GRAPH_SERIAL 0     /* the jobs run one after another (a chain)        */
+#define ROIBIN_GRAPH_CONCURRENT 1 /* each job on its own branch, free to overlap     */
+
+/* Captures the jobs' compression launches into one CUDA graph and
+ * instantiates it.  A launch of the graph runs every job once, in the order
+ * given (ROIBIN_GRAPH_SERIAL) or on independent branches the GPU may run
+ * concurrently (ROIBIN_GRAPH_CONCURRENT; a persistent fused kernel only ever
+ * waits for work handed out at an earlier ticket of its own launch, so
+ * concurrent branches cannot block one another).  Which is faster depends on
+ * the mix: a persistent kernel that fills the GPU leaves little for a
+ * concurrent branch to overlap with.
  * Each context compiles into the graph with its path and fused shape at
  * capture time (tune them first, e.g. with roibin_ctx_autotune).
  * The graph keeps the job pointers: the caller refills d_frames (and the
@@ -382,7 +390,7 @@ typedef struct roibin_graph roibin_graph;
  * otherwise or for any job roibin_compress would reject; ROIBIN_ERR_CUDA if
  * capture or instantiation fails.  Allocates (the graph), so call it at
  * setup, not per batch. */
-int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_jobs);
+int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_jobs, int flags);
 /* Launches the graph on `stream`; asynchronous; per-frame results as
  * roibin_compress writes them. */
 int roibin_graph_launch(roibin_graph* g, void* stream);

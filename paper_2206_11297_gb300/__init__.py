@@ -28,6 +28,7 @@ ERR_CODE_LENGTH = -7
 
 PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
 DEC_AUTO, DEC_PANEL, DEC_MULTIPASS = 0, 1, 2
+GRAPH_SERIAL, GRAPH_CONCURRENT = 0, 1
 
 GEOMETRIES = {"cspad": (32, 185, 388), "epix10k": (16, 352, 384), "jungfrau": (8, 512, 1024)}
 
@@ -79,7 +80,7 @@ _SIGNATURES = {
     "roibin_ctx_set_fused_dense_peaks": (ctypes.c_int, [_P, ctypes.c_int]),
     "roibin_ctx_fused_dense_peaks": (ctypes.c_int, [_P]),
     "roibin_ctx_plain_shape": (ctypes.c_int, [_P, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
-    "roibin_graph_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Job), _u32]),
+    "roibin_graph_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Job), _u32, ctypes.c_int]),
     "roibin_graph_launch": (ctypes.c_int, [_P, _P]),
     "roibin_graph_launch_count": (ctypes.c_int, [_P]),
     "roibin_graph_destroy": (ctypes.c_int, [_P]),
@@ -392,13 +393,14 @@ class Context:
 
 
 class Graph:
-    """Several contexts' compress calls captured as parallel branches of one
-    CUDA graph (roibin_graph_create).  `jobs` is a list of dicts with the keys
-    ctx, frames, out, frame_bytes, status and optionally out_stride, peaks,
-    npeaks (CUDA tensors, as Context.compress takes them).  The graph keeps the
-    tensors' addresses: refill `frames` in place between launches."""
+    """Several contexts' compress calls captured into one CUDA graph
+    (roibin_graph_create): one after another, or with `concurrent` on branches
+    the GPU may overlap.  `jobs` is a list of dicts with the keys ctx, frames,
+    out, frame_bytes, status and optionally out_stride, peaks, npeaks (CUDA
+    tensors, as Context.compress takes them).  The graph keeps the tensors'
+    addresses: refill `frames` in place between launches."""
 
-    def __init__(self, jobs):
+    def __init__(self, jobs, concurrent: bool = False):
         self.lib = library()
         self._keep = []
         arr = (Job * len(jobs))()
@@ -410,7 +412,8 @@ class Graph:
                          _ptr(out), stride, _ptr(j["frame_bytes"]), _ptr(j["status"]))
             self._keep.append(j)
         h = ctypes.c_void_p()
-        _check("roibin_graph_create", self.lib.roibin_graph_create(ctypes.byref(h), arr, len(jobs)))
+        _check("roibin_graph_create", self.lib.roibin_graph_create(
+            ctypes.byref(h), arr, len(jobs), GRAPH_CONCURRENT if concurrent else GRAPH_SERIAL))
         self._h = h
 
     def launch(self, stream=None):

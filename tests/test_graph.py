@@ -1,6 +1,8 @@
-"""Mixed-geometry batches under one CUDA graph (roibin_graph_*): every job's
-bytes equal those of its own compress call, on every launch, after the inputs
-are refilled in place."""
+"""Mixed-geometry batches under one CUDA graph (roibin_graph_*), with the jobs
+chained or on concurrent branches: every job's bytes equal those of its own
+compress call, on every launch, after the inputs are refilled in place."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -60,13 +62,14 @@ def _check_against_alone(torch, jobs):
             assert np.array_equal(g_out[k, :g_nb[k]], a_out[k, :a_nb[k]]), (j["name"], k)
 
 
-def test_graph_matches_separate_calls_and_refills():
+@pytest.mark.parametrize("concurrent", [False, True], ids=["serial", "concurrent"])
+def test_graph_matches_separate_calls_and_refills(concurrent):
     import torch
     params = rb.default_params(max_peaks=8192)
     jobs = _jobs(torch, params, first=0, tune=True)
     paths = {j["name"]: j["ctx"].resolved_path for j in jobs}
     assert paths["jungfrau_mixed"] == rb.PATH_PLAIN and paths["cspad_mixed"] == rb.PATH_FUSED
-    with rb.Graph(jobs) as g:
+    with rb.Graph(jobs, concurrent=concurrent) as g:
         assert g.launch_count >= len(jobs)
         g.launch()
         _check_against_alone(torch, jobs)
@@ -100,6 +103,11 @@ def test_graph_rejects_shared_contexts_and_bad_jobs():
             rb.Graph([job, job])
         with pytest.raises(rb.RoibinError):
             rb.Graph([dict(job, out_stride=ctx.bound + 8)])
+        # an unknown mode is refused through the C ABI
+        lib, h = rb.library(), ctypes.c_void_p()
+        arr = (rb.Job * 1)(rb.Job(ctx._h, f.data_ptr(), 1, None, None, out.data_ptr(), ctx.bound,
+                                   nb.data_ptr(), st.data_ptr()))
+        assert lib.roibin_graph_create(ctypes.byref(h), arr, 1, 7) == rb.ERR_INVALID_ARG and not h.value
         with rb.Graph([job]) as g:   # one job is a graph too
             g.launch()
             torch.cuda.synchronize()
