@@ -45,12 +45,13 @@ class Params(ctypes.Structure):
         ("roi_h", ctypes.c_int32), ("roi_w", ctypes.c_int32),
         ("bin_h", ctypes.c_int32), ("bin_w", ctypes.c_int32),
         ("abs_eb", ctypes.c_float), ("quant_radius", ctypes.c_int32), ("max_peaks", ctypes.c_int32),
+        ("lorenzo_dims", ctypes.c_int32),
     ]
 
 
 DEFAULTS = dict(amax_thr=300.0, atot_thr=600.0, son_min=10.0, pix_nsigma=3.0, rank=3,
                 ring_r0=5, ring_dr=2, npix_min=2, npix_max=30, roi_h=17, roi_w=17,
-                bin_h=2, bin_w=2, abs_eb=10.0, quant_radius=512, max_peaks=2048)
+                bin_h=2, bin_w=2, abs_eb=10.0, quant_radius=512, max_peaks=2048, lorenzo_dims=2)
 
 
 def make_params(**kw) -> Params:
@@ -94,6 +95,7 @@ def _bind(path: str):
         "orc_bin": (None, [P, G, i32, i32, P]),
         "orc_prequantize": (None, [P, u64, ctypes.c_float, P, P]),
         "orc_lorenzo": (None, [P, u32, u32, u32, P]),
+        "orc_lorenzo_nd": (None, [P, u32, u32, u32, ctypes.c_int32, P]),
         "orc_quant_codes": (None, [P, u64, i32, P]),
         "orc_histogram": (None, [P, u64, u32, P]),
         "orc_huffman_lengths": (ctypes.c_int, [P, u32, P]),
@@ -217,11 +219,14 @@ def prequantize(binned: np.ndarray, abs_eb: float):
     return q, pq
 
 
-def lorenzo(q: np.ndarray) -> np.ndarray:
+def lorenzo(q: np.ndarray, dims: int = 2) -> np.ndarray:
     q = np.ascontiguousarray(q, dtype=np.int32)
     P, hb, wb = q.shape
     d = np.zeros_like(q)
-    lib().orc_lorenzo(_ptr(q), P, hb, wb, _ptr(d))
+    if dims == 2:
+        lib().orc_lorenzo(_ptr(q), P, hb, wb, _ptr(d))
+    else:
+        lib().orc_lorenzo_nd(_ptr(q), P, hb, wb, dims, _ptr(d))
     return d
 
 
@@ -308,7 +313,8 @@ def parse_header(stream: np.ndarray) -> dict:
                 quant_radius=int(u32[8]), n_peaks=int(u32[9]), n_lorenzo=int(u32[10]),
                 n_prequant=int(u32[11]), n_symbols=int(u32[12]), chunk_symbols=int(u32[13]),
                 n_chunks=int(u32[14]), n_words=int(u32[15]),
-                total_bytes=int(b[64:72].view(np.uint64)[0]))
+                total_bytes=int(b[64:72].view(np.uint64)[0]),
+                lorenzo_dims={0: 2}.get(int(b[72:76].view(np.uint32)[0]), int(b[72:76].view(np.uint32)[0])))
 
 
 def section_offsets(h: dict) -> dict:

@@ -276,6 +276,48 @@ void orc_lorenzo(const int32_t* q, uint32_t n_panels, uint32_t hb, uint32_t wb,
   }
 }
 
+/* a6 in the dimension §6 names as a parameter of the method ("dimension": the
+ * row of pixels, the entire panel, or the stack of panels).  Reading: the SZ
+ * Lorenzo predictor of that order on the binned array [n_panels][hb][wb]
+ *   dims 1: the whole frame as one row-major run, delta_k = q_k - q_(k-1);
+ *   dims 2: each panel on its own (orc_lorenzo);
+ *   dims 3: the panels as a volume, delta = q - (the seven-neighbour 3-D
+ *           Lorenzo prediction from the previous panel, row and column);
+ * neighbours outside the array taken as 0. */
+void orc_lorenzo_nd(const int32_t* q, uint32_t n_panels, uint32_t hb, uint32_t wb, int32_t dims,
+                    int32_t* delta_out) {
+  const uint64_t m = (uint64_t)n_panels * hb * wb;
+  if (dims == 1) {
+    for (uint64_t k = 0; k < m; ++k) {
+      const int64_t prev = k > 0 ? q[k - 1] : 0;
+      delta_out[k] = (int32_t)((int64_t)q[k] - prev);
+    }
+    return;
+  }
+  if (dims == 2) {
+    orc_lorenzo(q, n_panels, hb, wb, delta_out);
+    return;
+  }
+  const size_t plane = (size_t)hb * wb;
+  for (uint32_t pn = 0; pn < n_panels; ++pn) {
+    for (uint32_t i = 0; i < hb; ++i) {
+      for (uint32_t j = 0; j < wb; ++j) {
+        /* the eight corners of the unit cube ending at (pn, i, j) */
+        int64_t corner[2][2][2];
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) {
+              const int inside = (a == 0 || pn > 0) && (b == 0 || i > 0) && (c == 0 || j > 0);
+              corner[a][b][c] = inside ? q[(size_t)(pn - a) * plane + (size_t)(i - b) * wb + (j - c)] : 0;
+            }
+        const int64_t prediction = corner[1][0][0] + corner[0][1][0] + corner[0][0][1] - corner[1][1][0] -
+                                   corner[1][0][1] - corner[0][1][1] + corner[1][1][1];
+        delta_out[(size_t)pn * plane + (size_t)i * wb + j] = (int32_t)(corner[0][0][0] - prediction);
+      }
+    }
+  }
+}
+
 /* a7. Linear-quantisation codes: code = delta + R when |delta| < R, else 0
  * (a Lorenzo outlier whose delta is stored on the side). */
 void orc_quant_codes(const int32_t* delta, uint64_t m, int32_t radius, uint16_t* codes_out) {
@@ -464,6 +506,7 @@ static int params_valid(const orc_geometry* g, const orc_params* p) {
   if (p->ring_r0 < 1 || p->ring_dr < 1 || p->ring_r0 + p->ring_dr > 16) return 0;
   if (p->quant_radius < 2 || p->quant_radius > 512) return 0;
   if (p->max_peaks < 0 || p->max_peaks > 65535) return 0;
+  if (p->lorenzo_dims < 1 || p->lorenzo_dims > 3) return 0;
   if (!(p->pix_nsigma >= 0.0f)) return 0;
   if (!(p->abs_eb > 0.0f) || !isfinite(2.0f * p->abs_eb) || !isfinite(1.0f / (2.0f * p->abs_eb)))
     return 0;
@@ -535,7 +578,7 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
 
   orc_bin(frame, g, p->bin_h, p->bin_w, binned);
   orc_prequantize(binned, m, p->abs_eb, q, pq);
-  orc_lorenzo(q, g->n_panels, hb, wb, delta);
+  orc_lorenzo_nd(q, g->n_panels, hb, wb, p->lorenzo_dims, delta);
   orc_quant_codes(delta, m, p->quant_radius, codes);
   orc_histogram(codes, m, n_symbols, hist);
   int status = orc_huffman_lengths(hist, n_symbols, len);
@@ -577,6 +620,9 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
     put_u32(out + 56, n_chunks);
     put_u32(out + 60, n_words);
     put_u64(out + 64, L.total);
+    /* Lorenzo dimension: 0 stands for the default 2, so that 2-D streams keep
+     * the 24 zero bytes that end the header */
+    put_u32(out + 72, p->lorenzo_dims == 2 ? 0u : (uint32_t)p->lorenzo_dims);
 
     for (uint32_t k = 0; k < n_peaks; ++k)
       for (int t = 0; t < 3; ++t) put_u16(out + L.peaks + 6 * k + 2 * t, peaks[3 * k + t]);
@@ -640,6 +686,9 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
   const uint32_t m_hdr = get_u32(in + 48), chunk = get_u32(in + 52), n_chunks = get_u32(in + 56);
   const uint32_t n_words = get_u32(in + 60);
   const uint64_t total = get_u64(in + 64);
+  const uint32_t dims_code = get_u32(in + 72);
+  if (dims_code != 0 && dims_code != 1 && dims_code != 3) return ORC_ERR_CORRUPT_STREAM;
+  const int dims = dims_code == 0 ? 2 : (int)dims_code;
   if (p.bin_h < 1 || p.bin_w < 1 || p.roi_h < 1 || p.roi_w < 1 || p.quant_radius < 2 ||
       p.quant_radius > 512 || chunk != ORC_CHUNK_SYMBOLS)
     return ORC_ERR_CORRUPT_STREAM;
@@ -726,18 +775,39 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
 
   float* bhat = (float*)malloc(sizeof(float) * m);
   if (status == ORC_OK) {
-    /* q = 2-D inclusive prefix sum of delta within each panel */
+    /* q = delta + the predictor's value from the q already rebuilt, in the
+     * order of the array: the inverse of a6 in the stream's dimension */
     const float two_eb = 2.0f * p.abs_eb;
     int64_t* q = (int64_t*)malloc(sizeof(int64_t) * m);
-    for (uint32_t pn = 0; pn < g->n_panels; ++pn) {
-      const size_t base = (size_t)pn * hb * wb;
-      for (uint32_t i = 0; i < hb; ++i)
-        for (uint32_t j = 0; j < wb; ++j) {
-          const int64_t up = i > 0 ? q[base + (size_t)(i - 1) * wb + j] : 0;
-          const int64_t left = j > 0 ? q[base + (size_t)i * wb + j - 1] : 0;
-          const int64_t diag = (i > 0 && j > 0) ? q[base + (size_t)(i - 1) * wb + j - 1] : 0;
-          q[base + (size_t)i * wb + j] = delta[base + (size_t)i * wb + j] + up + left - diag;
-        }
+    if (dims == 1) {
+      for (uint64_t k = 0; k < m; ++k) q[k] = delta[k] + (k > 0 ? q[k - 1] : 0);
+    } else if (dims == 2) {
+      for (uint32_t pn = 0; pn < g->n_panels; ++pn) {
+        const size_t base = (size_t)pn * hb * wb;
+        for (uint32_t i = 0; i < hb; ++i)
+          for (uint32_t j = 0; j < wb; ++j) {
+            const int64_t up = i > 0 ? q[base + (size_t)(i - 1) * wb + j] : 0;
+            const int64_t left = j > 0 ? q[base + (size_t)i * wb + j - 1] : 0;
+            const int64_t diag = (i > 0 && j > 0) ? q[base + (size_t)(i - 1) * wb + j - 1] : 0;
+            q[base + (size_t)i * wb + j] = delta[base + (size_t)i * wb + j] + up + left - diag;
+          }
+      }
+    } else {
+      const size_t plane = (size_t)hb * wb;
+      for (uint32_t pn = 0; pn < g->n_panels; ++pn)
+        for (uint32_t i = 0; i < hb; ++i)
+          for (uint32_t j = 0; j < wb; ++j) {
+            int64_t corner[2][2][2];
+            for (int a = 0; a < 2; ++a)
+              for (int b = 0; b < 2; ++b)
+                for (int c = 0; c < 2; ++c) {
+                  const int inside = (a == 0 || pn > 0) && (b == 0 || i > 0) && (c == 0 || j > 0);
+                  corner[a][b][c] = (inside && (a | b | c)) ? q[(size_t)(pn - a) * plane + (size_t)(i - b) * wb + (j - c)] : 0;
+                }
+            const int64_t prediction = corner[1][0][0] + corner[0][1][0] + corner[0][0][1] - corner[1][1][0] -
+                                       corner[1][0][1] - corner[0][1][1] + corner[1][1][1];
+            q[(size_t)pn * plane + (size_t)i * wb + j] = delta[(size_t)pn * plane + (size_t)i * wb + j] + prediction;
+          }
     }
     for (uint64_t i = 0; i < m; ++i) bhat[i] = (float)(int32_t)q[i] * two_eb;
     free(q);

@@ -56,6 +56,7 @@ typedef struct {
   float abs_eb;     /* absolute error bound on binned values */
   int32_t quant_radius; /* R: codes 1..2R-1 hold |delta| < R, code 0 = outlier */
   int32_t max_peaks;    /* 2048 */
+  int32_t lorenzo_dims; /* 1: the frame as one row-major run; 2: each panel (default); 3: the panel stack */
 } orc_params;
 
 /* ---- step-level entry points (each is one row of the method) ---- */
@@ -75,6 +76,10 @@ void orc_prequantize(const float* binned, uint64_t m, float abs_eb, int32_t* q_o
                      uint8_t* outlier_out);
 void orc_lorenzo(const int32_t* q, uint32_t n_panels, uint32_t hb, uint32_t wb,
                  int32_t* delta_out);
+/* a6 in dimension 1, 2 or 3 (§6: along the row of pixels, the panel, the
+ * stack of panels); 2 is orc_lorenzo. */
+void orc_lorenzo_nd(const int32_t* q, uint32_t n_panels, uint32_t hb, uint32_t wb, int32_t dims,
+                    int32_t* delta_out);
 void orc_quant_codes(const int32_t* delta, uint64_t m, int32_t radius, uint16_t* codes_out);
 void orc_histogram(const uint16_t* codes, uint64_t m, uint32_t n_symbols, uint64_t* hist_out);
 int orc_huffman_lengths(const uint64_t* hist, uint32_t n_symbols, uint8_t* len_out);

@@ -343,6 +343,79 @@ def pin_lorenzo():
     assert np.all(d[:, 0, 0] == 9) and np.count_nonzero(d) == 2, "per-panel, no cross-panel neighbour"
 
 
+def pin_lorenzo_dims():
+    """Dimension 1, 2 and 3 (the row of pixels, the panel, the panel stack):
+    each is the zero-padded backward difference along its axes, a separable
+    form the oracle does not use, and a prefix sum along the same axes
+    inverts it."""
+    rng = np.random.default_rng(14)
+    q = rng.integers(-2 ** 27, 2 ** 27, (4, 7, 9)).astype(np.int32)
+    q64 = q.astype(np.int64)
+    d1 = O.lorenzo(q, dims=1)
+    assert np.array_equal(d1.ravel(), np.diff(q64.ravel(), prepend=0)), "1-D: one run over the frame"
+    d3 = O.lorenzo(q, dims=3)
+    want = q64
+    for ax in range(3):
+        want = np.diff(want, axis=ax, prepend=0)
+    assert np.array_equal(d3, want), "3-D: backward differences along panel, row and column"
+    assert np.array_equal(O.lorenzo(q[:1], dims=3), O.lorenzo(q[:1], dims=2)), "one panel: 3-D is 2-D"
+    rebuilt = d3.astype(np.int64)
+    for ax in range(3):
+        rebuilt = np.cumsum(rebuilt, axis=ax)
+    assert np.array_equal(rebuilt, q64)
+    # the 3-D predictor is exact on any sum of terms that each skip one axis
+    P, H, W = 5, 6, 8
+    g = rng.integers(-1000, 1000, (1, H, W))
+    h = rng.integers(-1000, 1000, (P, 1, W))
+    k = rng.integers(-1000, 1000, (P, H, 1))
+    field = (g + h + k).astype(np.int32)
+    d = O.lorenzo(field, dims=3)
+    assert np.all(d[1:, 1:, 1:] == 0) and np.any(d[0] != 0)
+    const = np.full((2, 3, 4), 7, np.int32)
+    assert np.count_nonzero(O.lorenzo(const, dims=1)) == 1, "1-D: a constant frame is one delta"
+    assert np.count_nonzero(O.lorenzo(const, dims=3)) == 1, "3-D: a constant stack is one delta"
+
+
+def pin_lorenzo_dims_roundtrip():
+    """Streams in dimension 1 and 3 decode within eb, name their dimension in
+    the header, and carry the codes of that predictor."""
+    f = tiny_frame(6, shape=(3, 21, 27))
+    streams = {}
+    for dims in (1, 2, 3):
+        p = O.make_params(atot_thr=300.0, lorenzo_dims=dims)
+        s, dec, rec = _roundtrip(f, p)
+        streams[dims] = s
+        assert dec["header"]["lorenzo_dims"] == dims
+        assert int(s[72:76].view(np.uint32)[0]) == (0 if dims == 2 else dims)
+        b = O.bin_frame(f, 2, 2)
+        up = np.repeat(np.repeat(b, 2, axis=1), 2, axis=2)[:, :f.shape[1], :f.shape[2]]
+        mask = O.roi_mask(f.shape, p, dec["peaks"])
+        err = np.abs(rec.astype(np.float64) - up.astype(np.float64))
+        assert np.all(err[mask == 0] <= p.abs_eb), dims
+        assert np.array_equal(rec[mask == 1], f[mask == 1])
+        q, pq = O.prequantize(b, p.abs_eb)
+        dq = q.astype(np.int64)
+        axes = {1: None, 2: (1, 2), 3: (0, 1, 2)}[dims]
+        if axes is None:
+            d = np.diff(dq.ravel(), prepend=0)
+        else:
+            d = dq
+            for ax in axes:
+                d = np.diff(d, axis=ax, prepend=0)
+        d = d.astype(np.int32).ravel()
+        codes = np.where(np.abs(d) < p.quant_radius, d + p.quant_radius, 0)
+        assert np.array_equal(dec["codes"], codes), dims
+        lo_idx = np.flatnonzero(codes == 0)
+        assert np.array_equal(dec["lorenzo"][:, 1].view(np.int32), d[lo_idx])
+    assert len({bytes(v) for v in streams.values()}) == 3
+    for code in (2, 4):
+        bad = streams[3].copy()
+        bad[72:76] = np.array([code], np.uint32).view(np.uint8)
+        assert O.decompress_frame(bad, f.shape)[0] == O.ERR_CORRUPT_STREAM, code
+    st, _ = O.compress_frame(f, O.make_params(lorenzo_dims=4))
+    assert st == O.ERR_INVALID_ARG
+
+
 def pin_codes_histogram():
     R = 512
     d = np.array([0, 1, -1, R - 1, -(R - 1), R, -R, 10 ** 6, -(10 ** 6)], np.int32)
@@ -530,5 +603,5 @@ ALL_PINS = [
     pin_evaluation_brute_force, pin_find_peaks_frame, pin_roi, pin_binning, pin_prequantize,
     pin_lorenzo, pin_codes_histogram, pin_huffman_small, pin_huffman_optimal, pin_pack_decode,
     pin_frame_roundtrip, pin_identity_binning_bound, pin_user_peaks_and_corruption,
-    pin_nonsquare_bins_roundtrip,
+    pin_nonsquare_bins_roundtrip, pin_lorenzo_dims, pin_lorenzo_dims_roundtrip,
 ]

@@ -46,6 +46,11 @@ MUTANTS = {
     "lorenzo_diag_sign": ("- up - left + diag);", "- up - left - diag);"),
     "lorenzo_crosses_panels": ("const int64_t up = i > 0 ? qp[(size_t)(i - 1) * wb + j] : 0;",
                                "const int64_t up = (i > 0 || pn > 0) ? qp[(int64_t)(i - 1) * wb + j] : 0;"),
+    "lorenzo1_resets_at_rows": ("const int64_t prev = k > 0 ? q[k - 1] : 0;", "const int64_t prev = k % wb > 0 ? q[k - 1] : 0;"),
+    "lorenzo3_corner_sign": ("+ corner[1][1][1];\n        delta_out", "- corner[1][1][1];\n        delta_out"),
+    "lorenzo3_no_stack": ("const int inside = (a == 0 || pn > 0) && (b == 0 || i > 0) && (c == 0 || j > 0);\n              corner[a][b][c] = inside ?",
+                          "const int inside = (a == 0) && (b == 0 || i > 0) && (c == 0 || j > 0);\n              corner[a][b][c] = inside ?"),
+    "dims_not_in_header": ("put_u32(out + 72, p->lorenzo_dims == 2 ? 0u : (uint32_t)p->lorenzo_dims);", "put_u32(out + 72, 0u);"),
     # a7 codes
     "code_sign_flipped": ("? (uint16_t)(d + radius)", "? (uint16_t)(radius - d)"),
     # a9 Huffman
@@ -60,6 +65,8 @@ MUTANTS = {
     "nan_not_canonical": ("if (isnan(binned[i])) bits = ORC_CANONICAL_NAN;", ""),
     # a13 decompression
     "inverse_diag_sign": ("= delta[base + (size_t)i * wb + j] + up + left - diag;", "= delta[base + (size_t)i * wb + j] + up + left + diag;"),
+    "inverse1_resets_at_rows": ("q[k] = delta[k] + (k > 0 ? q[k - 1] : 0);", "q[k] = delta[k] + (k % wb > 0 ? q[k - 1] : 0);"),
+    "inverse3_corner_sign": ("+ corner[1][1][1];\n            q[(size_t)pn", "- corner[1][1][1];\n            q[(size_t)pn"),
     "restore_skips_roi": ("memcpy(&frame_out[pn * plane + (size_t)(r0 + i) * g->cols + (size_t)(c0 + j)],", "if (0) memcpy(&frame_out[pn * plane + (size_t)(r0 + i) * g->cols + (size_t)(c0 + j)],"),
     "upsample_wrong_axis": ("bhat[((size_t)pn * hb + r / p.bin_h) * wb + c / p.bin_w];", "bhat[((size_t)pn * hb + r / p.bin_w) * wb + c / p.bin_h];"),
 }
