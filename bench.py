@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-decompress", action="store_true", help="skip the decompression timing")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-geometry graph timing")
+    ap.add_argument("--no-dims", action="store_true", help="skip the Lorenzo-dimension variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--min-load-seconds", type=float, default=2.0,
                     help="keep the GPU busy at least this long before timing (clock sampling)")
@@ -292,6 +293,52 @@ def mixed_graph(args, dev, local, stream):
     return res
 
 
+def lorenzo_dims(args, frames, out, nbytes, status, stride, stream, local):
+    """The same resident batch with the Lorenzo predictor in dimension 1, 2
+    and 3 (the paper's "dimension" parameter), each on the plain path in its
+    autotuned shape and decompressed on the multi-pass path: throughput both
+    ways and the compression ratio."""
+    import torch
+    import paper_2206_11297_gb300 as rb
+    n = frames.shape[0]
+    frame_bytes = frames[0].numel() * 4
+    offsets = torch.arange(n, dtype=torch.int64, device=frames.device) * stride
+    recon = torch.empty_like(frames)
+    dstat = torch.empty(n, dtype=torch.int32, device=frames.device)
+    reps = max(3, min(args.steps, 10))
+    res = {"unit": "GB/s", "path": "plain, multi-pass decompression", "frames": n}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for dims in (1, 2, 3):
+        params = rb.default_params(lorenzo_dims=dims)
+        with rb.Context(frames.shape[1:], params, max_frames=n, device=local) as c:
+            c.set_path(rb.PATH_PLAIN)
+            shape, _ = c.autotune(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
+            t_c = timed(lambda: c.compress(frames, out=out, out_stride=stride, frame_bytes=nbytes,
+                                           status=status))
+            assert (status.cpu() == 0).all()
+            out_bytes = int(nbytes.sum())
+            c.set_decompress_path(rb.DEC_MULTIPASS)
+            t_d = timed(lambda: c.decompress(out.view(-1), offsets, n, out=recon, status=dstat))
+            assert (dstat.cpu() == 0).all()
+        res[str(dims)] = {"compress": n * frame_bytes / 1e9 / (t_c / 1e3),
+                          "decompress": n * frame_bytes / 1e9 / (t_d / 1e3),
+                          "ratio_vs_f32": n * frame_bytes / out_bytes,
+                          "plain_shape": {"rows_per_step": shape[0], "bands_per_panel": shape[1]}}
+    return res
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(args, rank, local, world):
     import torch
@@ -483,11 +530,14 @@ def run_ours(args, rank, local, world):
                          "kernels_ms_per_step": {k: v[0] / args.steps for k, v in pr["kernels"].items()}}
     if not args.no_mixed:
         line["mixed_graph"] = mixed_graph(args, dev, local, stream)
+    if not args.no_dims:
+        ctx.close()  # its scratch is not needed again; the variants take their own
+        line["lorenzo_dims"] = lorenzo_dims(args, frames, out, nbytes, status, stride, stream, local)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host.numpy(), params.as_dict())
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
+    ctx.close()  # a no-op when the variants closed it
 
 
 def main():

@@ -30,7 +30,8 @@
  *           u16 roi_h, roi_w, bin_h, bin_w | f32 abs_eb | u32 quant_radius |
  *           u32 n_peaks | u32 n_lorenzo_outliers | u32 n_prequant_outliers |
  *           u32 n_symbols | u32 chunk_symbols (4096) | u32 n_chunks |
- *           u32 bitstream_words | u64 total_bytes | 24 zero bytes
+ *           u32 bitstream_words | u64 total_bytes | u32 lorenzo dimension
+ *           (0 for the default 2, else 1 or 3) | 20 zero bytes
  *   then, each starting on a 16-byte boundary, zero padded:
  *     peaks       u16[n_peaks][3] (panel, row, col)
  *     roi         f32[n_peaks][roi_h][roi_w]
@@ -64,13 +65,15 @@ extern "C" {
                                           frames below 5,702,887 bins)                */
 
 /* ---- execution paths for roibin_compress ----------------------------- */
-#define ROIBIN_PATH_AUTO 0  /* fused when the geometry allows it, else plain          */
+#define ROIBIN_PATH_AUTO 0  /* fused when the geometry and parameters allow it, else
+                               plain                                                 */
 #define ROIBIN_PATH_PLAIN 1 /* one kernel per stage, intermediates in device memory  */
 #define ROIBIN_PATH_FUSED 2 /* one persistent kernel per batch: work items of a few
                                panels each, then each frame's coding stages        */
 
 /* Decompression paths (roibin_ctx_set_decompress_path). */
-#define ROIBIN_DEC_AUTO 0      /* PANEL when the geometry allows it, else MULTIPASS      */
+#define ROIBIN_DEC_AUTO 0      /* PANEL when the geometry and lorenzo_dims (2) allow it,
+                                  else MULTIPASS                                         */
 #define ROIBIN_DEC_PANEL 1     /* prefix-table decode to symbols, then one block per
                                   (frame, panel) rebuilds the panel in shared memory
                                   and writes its pixels once; needs bins per panel row
@@ -99,13 +102,24 @@ typedef struct {
  *   ROI (§4): roi_h x roi_w window centred on each peak (17 x 17), fill 0 past
  *   the panel edge.  Binning (§4.1, §6): bin_h x bin_w mean per panel (2 x 2).
  *   Coding (§5.3.3): |b - b^| <= abs_eb on every binned value; quant_radius R
- *   gives 2R symbols (512 -> 1024); max_peaks (2048, §4) caps the peak list. */
+ *   gives 2R symbols (512 -> 1024); max_peaks (2048, §4) caps the peak list.
+ *   lorenzo_dims (§6, the "dimension" of the quality search: the row of
+ *   pixels, the panel, the stack of panels) is the order of the Lorenzo
+ *   predictor on the binned array [n_panels][rows/bin_h][cols/bin_w]:
+ *     1: the whole frame as one row-major run, delta = q[k] - q[k-1];
+ *     2: each panel on its own, the 2-D predictor (default);
+ *     3: the panels as a volume, the 3-D predictor (seven neighbours in the
+ *        previous panel, row and column);
+ *   neighbours outside the array count as 0.  Only 2 runs on the fused path
+ *   and on the PANEL decompression path; 1 and 3 take the plain path and the
+ *   multi-pass decompression path. */
 typedef struct {
   float amax_thr, atot_thr, son_min, pix_nsigma;
   int32_t rank, ring_r0, ring_dr, npix_min, npix_max;
   int32_t roi_h, roi_w, bin_h, bin_w;
   float abs_eb;
   int32_t quant_radius, max_peaks;
+  int32_t lorenzo_dims;
 } roibin_params;
 
 /* Fills *p with the defaults listed above.  Never fails for non-NULL p. */
@@ -115,6 +129,7 @@ int roibin_default_params(roibin_params* p);
  * 1 <= n_panels, rows, cols <= 65535; cols/bin_w <= 8192; 1 <= bin <= 8;
  * 1 <= roi <= 63; 1 <= rank <= 7; ring_r0, ring_dr >= 1, r0 + dr <= 16;
  * 2 <= quant_radius <= 512; 0 <= max_peaks <= 8192; pix_nsigma >= 0;
+ * lorenzo_dims 1, 2 or 3;
  * abs_eb > 0 with 2 abs_eb and 1/(2 abs_eb) finite; binned size below
  * 5,702,887 (so that no Huffman code exceeds 32 bits). */
 int roibin_validate(const roibin_geometry* g, const roibin_params* p);

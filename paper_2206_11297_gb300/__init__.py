@@ -46,6 +46,7 @@ class Params(ctypes.Structure):
         ("roi_h", ctypes.c_int32), ("roi_w", ctypes.c_int32),
         ("bin_h", ctypes.c_int32), ("bin_w", ctypes.c_int32),
         ("abs_eb", ctypes.c_float), ("quant_radius", ctypes.c_int32), ("max_peaks", ctypes.c_int32),
+        ("lorenzo_dims", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(256) k_dec_parse(DevParams p, Scratch s, DecAr
         bh != (uint32_t)p.bh || bw != (uint32_t)p.bw || roi_h < 1 || roi_h > 63 || roi_w < 1 ||
         roi_w > 63 || hdr[8] < 2 || hdr[8] > 512 || hdr[12] != p.M || hdr[13] != kChunk ||
         hdr[14] != p.n_chunks || pl.n_lo > p.M || pl.n_pq > p.M || pl.n_words > p.M ||
-        pl.n_peaks > 65535u || !(di.eb > 0.0f) || !isfinite(di.two_eb))
+        pl.n_peaks > 65535u || !(di.eb > 0.0f) || !isfinite(di.two_eb) ||
+        hdr[18] != (p.dims == 2 ? 0u : (uint32_t)p.dims))  // the context's Lorenzo dimension
       ok = 0;
     pl.off_peaks = kHeaderBytes;
     pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
@@ -310,20 +311,81 @@ __global__ void k_dec_rows(DevParams p, Scratch s, DecArgs a) {
   }
 }
 
-// cols: prefix sum down each column of a binned panel, then b^ = fl(q * 2eb).
-__global__ void k_dec_cols(DevParams p, Scratch s, DecArgs a) {
+// cols: prefix sum down each column of a binned panel, then b^ = fl(q * 2eb)
+// (dequant), or the sums back in place for the 3-D inverse (k_dec_stack).
+__global__ void k_dec_cols(DevParams p, Scratch s, DecArgs a, int dequant) {
   const uint32_t f = blockIdx.y;
   if (s.status[f] != ROIBIN_OK) return;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.P * p.Wb) return;
   const uint32_t pn = t / p.Wb, j = t - pn * p.Wb;
   const float two_eb = s.dec_info[f].two_eb;
-  const uint32_t* dq = reinterpret_cast<const uint32_t*>(s.dq + (size_t)f * p.M + (size_t)pn * p.Hb * p.Wb);
+  uint32_t* dq = reinterpret_cast<uint32_t*>(s.dq + (size_t)f * p.M + (size_t)pn * p.Hb * p.Wb);
   float* bh = s.bhat + (size_t)f * p.M + (size_t)pn * p.Hb * p.Wb;
   uint32_t q = 0;
   for (uint32_t i = 0; i < p.Hb; ++i) {
     q += dq[(size_t)i * p.Wb + j];
-    bh[(size_t)i * p.Wb + j] = __fmul_rn((float)(int32_t)q, two_eb);
+    if (dequant) bh[(size_t)i * p.Wb + j] = __fmul_rn((float)(int32_t)q, two_eb);
+    else dq[(size_t)i * p.Wb + j] = q;
+  }
+}
+
+// stack (3-D inverse, last axis): prefix sum across the panels at each binned
+// position of the 2-D sums, then b^ = fl(q * 2eb).  The three axes' prefix
+// sums commute, so rows, columns, then panels inverts the 3-D predictor.
+__global__ void k_dec_stack(DevParams p, Scratch s, DecArgs a) {
+  const uint32_t f = blockIdx.y;
+  if (s.status[f] != ROIBIN_OK) return;
+  const uint32_t plane = p.Hb * p.Wb;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= plane) return;
+  const float two_eb = s.dec_info[f].two_eb;
+  const uint32_t* dq = reinterpret_cast<const uint32_t*>(s.dq + (size_t)f * p.M);
+  float* bh = s.bhat + (size_t)f * p.M;
+  uint32_t q = 0;
+  for (uint32_t pn = 0; pn < p.P; ++pn) {
+    q += dq[(size_t)pn * plane + t];
+    bh[(size_t)pn * plane + t] = __fmul_rn((float)(int32_t)q, two_eb);
+  }
+}
+
+// chain (1-D inverse): after the row sums, every binned row adds the sum of
+// all rows before it in the frame's row-major order.  One block per frame
+// walks the rows in tiles of blockDim.x, scanning the tile's row totals.
+constexpr uint32_t kChainThreads = 1024;
+__global__ void __launch_bounds__(kChainThreads) k_dec_chain(DevParams p, Scratch s, DecArgs a) {
+  __shared__ uint32_t carry[kChainThreads];
+  __shared__ uint32_t warp_sum[kChainThreads / 32];
+  const uint32_t f = blockIdx.x;
+  if (s.status[f] != ROIBIN_OK) return;
+  const float two_eb = s.dec_info[f].two_eb;
+  const uint32_t* dq = reinterpret_cast<const uint32_t*>(s.dq + (size_t)f * p.M);
+  float* bh = s.bhat + (size_t)f * p.M;
+  const uint32_t rows = p.P * p.Hb, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  uint32_t base = 0;  // sum of every row before the tile (unsigned: wraps like the stream's int32)
+  for (uint32_t r0 = 0; r0 < rows; r0 += kChainThreads) {
+    const uint32_t r = r0 + tid;
+    const uint32_t total = r < rows ? dq[(size_t)r * p.Wb + p.Wb - 1] : 0u;  // the row's inclusive sum
+    const uint32_t inc = warp_incl_scan(total);
+    if (lane == 31) warp_sum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = warp_incl_scan(warp_sum[lane]);
+      warp_sum[lane] = w;
+    }
+    __syncthreads();
+    carry[tid] = base + (warp ? warp_sum[warp - 1] : 0u) + inc - total;  // exclusive
+    const uint32_t tile_sum = warp_sum[31];
+    __syncthreads();
+    const uint32_t n = min(kChainThreads, rows - r0);
+    for (uint32_t k = warp; k < n; k += kChainThreads / 32) {
+      const size_t row = (size_t)(r0 + k) * p.Wb;
+      const uint32_t c = carry[k];
+      for (uint32_t j = lane; j < p.Wb; j += 32)
+        bh[row + j] = __fmul_rn((float)(int32_t)(dq[row + j] + c), two_eb);
+    }
+    base += tile_sum;
+    __syncthreads();
   }
 }
 
@@ -1000,9 +1062,18 @@ cudaError_t launch_dec_rows(const DevParams& p, const Scratch& s, const DecArgs&
   k_dec_rows<<<grid, 256, 0, st>>>(p, s, a);
   return cudaGetLastError();
 }
-cudaError_t launch_dec_cols(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st) {
+cudaError_t launch_dec_cols(const DevParams& p, const Scratch& s, const DecArgs& a, bool dequant, cudaStream_t st) {
   dim3 grid(ceil_div(p.P * p.Wb, 128), a.n_frames);
-  k_dec_cols<<<grid, 128, 0, st>>>(p, s, a);
+  k_dec_cols<<<grid, 128, 0, st>>>(p, s, a, dequant ? 1 : 0);
+  return cudaGetLastError();
+}
+cudaError_t launch_dec_carry(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st) {
+  if (p.dims == 3) {
+    dim3 grid(ceil_div(p.Hb * p.Wb, 256), a.n_frames);
+    k_dec_stack<<<grid, 256, 0, st>>>(p, s, a);
+  } else {
+    k_dec_chain<<<a.n_frames, kChainThreads, 0, st>>>(p, s, a);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_dec_pq(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st) {

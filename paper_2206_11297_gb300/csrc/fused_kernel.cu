@@ -1354,7 +1354,7 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
 
 bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, uint32_t stages,
                      FusedShape* out) {
-  if (p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > kConsumerWarps * 31) return false;
+  if (p.dims != 2 || p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > kConsumerWarps * 31) return false;
   if (ctas_per_sm < 1 || ctas_per_sm > 8 || stages < 1 || stages > 8) return false;
   if (rows_per_step != 0 && (rows_per_step < 2 || rows_per_step > 3)) return false;
   FusedShape sh;

@@ -15,7 +15,7 @@ const char* kernel_name(int id) {
   static const char* names[K_COUNT] = {
       "reset", "stream", "peaks", "peaks_final", "huffman", "chunks", "plan", "encode", "roi",
       "fused", "dec_parse", "dec_decode", "dec_lorenzo", "dec_rows", "dec_cols", "dec_pq",
-      "dec_upsample", "dec_roi", "dec_panel", "roi_mask", "pack"};
+      "dec_upsample", "dec_roi", "dec_panel", "roi_mask", "pack", "dec_carry"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 
@@ -153,6 +153,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(DevParams p, Scratch 
   const uint32_t RB = a.rows_per_step;
   int32_t* qbuf = reinterpret_cast<int32_t*>(dsm + sizeof(StreamSmem));  // [(RB+1) * Wb]
   uint8_t* pqf = reinterpret_cast<uint8_t*>(qbuf + (size_t)(RB + 1) * p.Wb);  // [RB * Wb]
+  // 3-D predictor: the same rows of the previous panel, [(RB+1) * Wb] after pqf
+  int32_t* qprev = reinterpret_cast<int32_t*>(pqf + align16((uint64_t)RB * p.Wb));
 
   const uint32_t f = blockIdx.y;
   const uint32_t pn = blockIdx.x / a.bands_per_panel, band = blockIdx.x % a.bands_per_panel;
@@ -161,15 +163,28 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(DevParams p, Scratch 
   const uint32_t ie = min(p.Hb, ib + rows_per_band);
   if (ib >= ie) return;
   const float* panel = a.frames + (size_t)f * p.frame_px + (size_t)pn * p.H * p.W;
+  const float* prev_panel = panel - (size_t)p.H * p.W;  // read only when pn > 0
+  const bool stack = p.dims == 3 && pn > 0;            // the 3-D predictor's previous panel
 
   for (uint32_t k = threadIdx.x; k < p.nsym; k += kStreamThreads) sm.hist[k] = 0;
-  // the row above the band
-  if (ib == 0) {
+  // the row above the band; for the 1-D predictor at the top of a panel, the
+  // previous panel's last row (its last bin precedes this panel's first)
+  if (ib == 0 && !(p.dims == 1 && pn > 0)) {
     for (uint32_t j = threadIdx.x; j < p.Wb; j += kStreamThreads) qbuf[j] = 0;
-  } else if (vec4) {
-    phase_a_v4<false>(panel, p, ib - 1, 1, qbuf, pqf, s, f, pn);
   } else {
-    phase_a_generic<false>(panel, p, ib - 1, 1, qbuf, pqf, s, f, pn);
+    const float* src = ib == 0 ? prev_panel : panel;
+    const uint32_t row = ib == 0 ? p.Hb - 1 : ib - 1;
+    if (vec4) phase_a_v4<false>(src, p, row, 1, qbuf, pqf, s, f, pn);
+    else phase_a_generic<false>(src, p, row, 1, qbuf, pqf, s, f, pn);
+  }
+  if (stack) {
+    if (ib == 0) {
+      for (uint32_t j = threadIdx.x; j < p.Wb; j += kStreamThreads) qprev[j] = 0;
+    } else if (vec4) {
+      phase_a_v4<false>(prev_panel, p, ib - 1, 1, qprev, pqf, s, f, pn);
+    } else {
+      phase_a_generic<false>(prev_panel, p, ib - 1, 1, qprev, pqf, s, f, pn);
+    }
   }
   __syncthreads();
 
@@ -178,6 +193,10 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(DevParams p, Scratch 
     const uint32_t rows = min(RB, ie - i0);
     if (vec4) phase_a_v4<true>(panel, p, i0, rows, qbuf + p.Wb, pqf, s, f, pn);
     else phase_a_generic<true>(panel, p, i0, rows, qbuf + p.Wb, pqf, s, f, pn);
+    if (stack) {
+      if (vec4) phase_a_v4<false>(prev_panel, p, i0, rows, qprev + p.Wb, pqf, s, f, pn);
+      else phase_a_generic<false>(prev_panel, p, i0, rows, qprev + p.Wb, pqf, s, f, pn);
+    }
     __syncthreads();
     // phase B: residuals, codes, histogram, outliers
     const uint32_t items = rows * p.Wb;
@@ -191,7 +210,20 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(DevParams p, Scratch 
         const int32_t* up = qbuf + (size_t)il * p.Wb;
         const int32_t qc = cur[j], qu = up[j];
         const int32_t ql = j > 0 ? cur[j - 1] : 0, qd = j > 0 ? up[j - 1] : 0;
-        const int32_t delta = qc - qu - ql + qd;
+        // integer differences wrap like the oracle's int64 result cast to int32
+        int32_t delta;
+        if (p.dims == 1) {
+          delta = (int32_t)((uint32_t)qc - (uint32_t)(j > 0 ? ql : up[p.Wb - 1]));
+        } else {
+          uint32_t d = (uint32_t)qc - (uint32_t)qu - (uint32_t)ql + (uint32_t)qd;
+          if (stack) {  // minus the previous panel's 2-D difference at the same place
+            const int32_t* pc = qprev + (size_t)(il + 1) * p.Wb;
+            const int32_t* pu = qprev + (size_t)il * p.Wb;
+            d -= (uint32_t)pc[j] - (uint32_t)pu[j] - (uint32_t)(j > 0 ? pc[j - 1] : 0) +
+                 (uint32_t)(j > 0 ? pu[j - 1] : 0);
+          }
+          delta = (int32_t)d;
+        }
         code = quant_code(delta, p.R);
         const uint32_t bin = (pn * p.Hb + i0 + il) * p.Wb + j;
         const uint32_t flag = pqf[(size_t)il * p.Wb + j] ? 0x8000u : 0u;
@@ -202,8 +234,10 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream(DevParams p, Scratch 
     }
     __syncthreads();
     // the last row of this step is the row above the next one
-    for (uint32_t j = threadIdx.x; j < p.Wb; j += kStreamThreads)
+    for (uint32_t j = threadIdx.x; j < p.Wb; j += kStreamThreads) {
       qbuf[j] = qbuf[(size_t)rows * p.Wb + j];
+      if (stack) qprev[j] = qprev[(size_t)rows * p.Wb + j];
+    }
     __syncthreads();
   }
   for (uint32_t k = threadIdx.x; k < p.nsym; k += kStreamThreads)
@@ -537,7 +571,8 @@ __global__ void __launch_bounds__(1024) k_plan(DevParams p, Scratch s, PlainArgs
     h[15] = pl.n_words;
     h[16] = (uint32_t)(pl.total & 0xFFFFFFFFu);
     h[17] = (uint32_t)(pl.total >> 32);
-    for (int i = 18; i < 24; ++i) h[i] = 0;
+    h[18] = p.dims == 2 ? 0u : (uint32_t)p.dims;  // Lorenzo dimension, 0 for the default 2
+    for (int i = 19; i < 24; ++i) h[i] = 0;
   }
   // peaks (u16 triples) + padding
   const uint32_t* keys = s.peak_key + (size_t)f * p.max_peaks;
@@ -671,7 +706,8 @@ __global__ void k_last_peaks(DevParams p, Scratch s, uint16_t* peaks, uint32_t* 
 // ---------------------------------------------------------------------------
 // launchers
 static size_t stream_smem_bytes(const DevParams& p, uint32_t rows_per_step) {
-  return sizeof(StreamSmem) + (size_t)(rows_per_step + 1) * p.Wb * 4 + (size_t)rows_per_step * p.Wb;
+  const size_t q_rows = (size_t)(rows_per_step + 1) * p.Wb * 4;
+  return sizeof(StreamSmem) + q_rows + align16((uint64_t)rows_per_step * p.Wb) + (p.dims == 3 ? q_rows : 0);
 }
 
 cudaError_t launch_reset(const DevParams& p, const Scratch& s, uint32_t n, cudaStream_t st) {

@@ -80,6 +80,7 @@ int validate_impl(const roibin_geometry* g, const roibin_params* p) {
   if (p->npix_min < 0 || p->npix_max < p->npix_min) return ROIBIN_ERR_INVALID_ARG;
   if (p->quant_radius < 2 || p->quant_radius > 512) return ROIBIN_ERR_INVALID_ARG;
   if (p->max_peaks < 0 || p->max_peaks > (int32_t)kMaxPeaksLimit) return ROIBIN_ERR_INVALID_ARG;
+  if (p->lorenzo_dims < 1 || p->lorenzo_dims > 3) return ROIBIN_ERR_INVALID_ARG;
   if (!(p->pix_nsigma >= 0.0f) || std::isnan(p->amax_thr) || std::isnan(p->atot_thr) ||
       std::isnan(p->son_min))
     return ROIBIN_ERR_INVALID_ARG;
@@ -134,6 +135,7 @@ DevParams make_dev_params(const roibin_geometry& g, const roibin_params& p) {
   d.nsym = 2u * (uint32_t)p.quant_radius;
   d.max_peaks = (uint32_t)p.max_peaks;
   d.thr_cap = kThrCap;
+  d.dims = p.lorenzo_dims;
   return d;
 }
 
@@ -166,7 +168,8 @@ struct Carver {
 uint32_t max_plain_bands(const DevParams& d) { return std::max<uint32_t>(1, ceil_div(d.Hb, 2)); }
 // Rows per step of the plain path that fit its shared memory.
 bool plain_rows_ok(const DevParams& d, uint32_t rows) {
-  return rows >= 1 && rows <= 16 && (uint64_t)(rows + 1) * d.Wb * 4 + (uint64_t)rows * d.Wb + 4096 <= 200 * 1024;
+  const uint64_t q_rows = (uint64_t)(rows + 1) * d.Wb * 4 * (d.dims == 3 ? 2 : 1);  // 3-D: the previous panel too
+  return rows >= 1 && rows <= 16 && q_rows + (uint64_t)rows * d.Wb + 16 + 4096 <= 200 * 1024;
 }
 
 // Lays out the per-frame scratch for n frames; with base == nullptr only sizes it.
@@ -268,7 +271,7 @@ int compress_plain(roibin_ctx* ctx, const PlainArgs& a, cudaStream_t st) {
 
 int resolved_dec_path(const roibin_ctx* ctx) {
   if (ctx->dec_path_req == ROIBIN_DEC_MULTIPASS) return ROIBIN_DEC_MULTIPASS;
-  return dec_panel_rows(ctx->dp) ? ROIBIN_DEC_PANEL : ROIBIN_DEC_MULTIPASS;
+  return dec_panel_rows(ctx->dp) && ctx->dp.dims == 2 ? ROIBIN_DEC_PANEL : ROIBIN_DEC_MULTIPASS;
 }
 
 int resolved_path(const roibin_ctx* ctx) {
@@ -480,6 +483,7 @@ int roibin_default_params(roibin_params* p) {
   p->abs_eb = 10.0f;
   p->quant_radius = 512;
   p->max_peaks = 2048;
+  p->lorenzo_dims = 2;
   return ROIBIN_OK;
 }
 
@@ -702,7 +706,14 @@ int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes, c
   if ((e = timed(ctx, K_DEC_DECODE, st, [&] { return launch_dec_decode(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_LORENZO, st, [&] { return launch_dec_lorenzo(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_ROWS, st, [&] { return launch_dec_rows(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
-  if ((e = timed(ctx, K_DEC_COLS, st, [&] { return launch_dec_cols(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
+  // the inverse predictor after the row sums: down the columns (2-D), then
+  // across the panels (3-D); or the carry from row to row (1-D)
+  if (p.dims >= 2)
+    if ((e = timed(ctx, K_DEC_COLS, st, [&] { return launch_dec_cols(p, s, a, p.dims == 2, st); })) != cudaSuccess)
+      return cuda_status(e);
+  if (p.dims != 2)
+    if ((e = timed(ctx, K_DEC_CARRY, st, [&] { return launch_dec_carry(p, s, a, st); })) != cudaSuccess)
+      return cuda_status(e);
   if ((e = timed(ctx, K_DEC_PQ, st, [&] { return launch_dec_pq(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_UPSAMPLE, st, [&] { return launch_dec_upsample(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_ROI, st, [&] { return launch_dec_roi(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
@@ -714,7 +725,7 @@ int roibin_ctx_set_decompress_path(roibin_ctx* ctx, int path) {
   if (!ctx) return ROIBIN_ERR_INVALID_ARG;
   if (path != ROIBIN_DEC_AUTO && path != ROIBIN_DEC_PANEL && path != ROIBIN_DEC_MULTIPASS)
     return ROIBIN_ERR_INVALID_ARG;
-  if (path == ROIBIN_DEC_PANEL && dec_panel_rows(ctx->dp) == 0) return ROIBIN_ERR_INVALID_ARG;
+  if (path == ROIBIN_DEC_PANEL && (dec_panel_rows(ctx->dp) == 0 || ctx->dp.dims != 2)) return ROIBIN_ERR_INVALID_ARG;
   ctx->dec_path_req = path;
   return ROIBIN_OK;
 }

@@ -46,6 +46,7 @@ struct DevParams {
   uint32_t nsym;            // 2R
   uint32_t max_peaks;
   uint32_t thr_cap;
+  int32_t dims;             // Lorenzo predictor order: 1 (frame run), 2 (panel), 3 (panel stack)
 };
 
 // Byte layout of one frame's stream, filled by the plan step.
@@ -829,6 +830,7 @@ enum KernelId {
   K_DEC_PANEL,
   K_ROI_MASK,
   K_PACK,
+  K_DEC_CARRY,
   K_COUNT
 };
 const char* kernel_name(int id);
@@ -857,7 +859,8 @@ cudaError_t launch_dec_parse(const DevParams& p, const Scratch& s, const DecArgs
 cudaError_t launch_dec_decode(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_lorenzo(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_rows(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
-cudaError_t launch_dec_cols(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+cudaError_t launch_dec_cols(const DevParams& p, const Scratch& s, const DecArgs& a, bool dequant, cudaStream_t st);
+cudaError_t launch_dec_carry(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_pq(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_upsample(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_roi(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);

@@ -39,6 +39,7 @@ def test_default_params_are_the_papers():
     p = rb.default_params()
     assert (p.amax_thr, p.atot_thr, p.son_min, p.npix_min, p.npix_max) == (300.0, 600.0, 10.0, 2, 30)
     assert (p.rank, p.roi_h, p.roi_w, p.bin_h, p.bin_w, p.max_peaks) == (3, 17, 17, 2, 2, 2048)
+    assert p.lorenzo_dims == 2
 
 
 @pytest.mark.parametrize("change,ok", [
@@ -47,6 +48,8 @@ def test_default_params_are_the_papers():
     ({"abs_eb": 0.0}, False), ({"abs_eb": float("nan")}, False), ({"abs_eb": 3e38}, False),
     ({"pix_nsigma": -1.0}, False), ({"max_peaks": 8193}, False), ({"max_peaks": 0}, True),
     ({"npix_max": 1, "npix_min": 2}, False), ({"ring_r0": 10, "ring_dr": 7}, False),
+    ({"lorenzo_dims": 0}, False), ({"lorenzo_dims": 1}, True), ({"lorenzo_dims": 3}, True),
+    ({"lorenzo_dims": 4}, False),
 ])
 def test_validate(change, ok):
     p = rb.default_params(**change)
