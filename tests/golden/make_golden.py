@@ -29,6 +29,9 @@ CASES = [
     ("hot_pixels_eb1", (2, 40, 48), {"bg_mean": 30.0, "bg_sd": 8.0, "hot_fraction": 0.01,
                                      "peaks": ("fixed", 3), "seed": 103}, {"abs_eb": 1.0, "max_peaks": 512}),
     ("small_radius", (1, 64, 64), {"peaks": ("fixed", 6), "seed": 104}, {"quant_radius": 16, "abs_eb": 2.0}),
+    ("lorenzo_run_1d", (3, 25, 29), {"peaks": ("fixed", 3), "seed": 105}, {"lorenzo_dims": 1, "abs_eb": 4.0}),
+    ("lorenzo_stack_3d", (4, 30, 36), {"peaks": ("uniform", 2, 6), "seed": 106},
+     {"lorenzo_dims": 3, "atot_thr": 300.0}),
 ]
 
 
