@@ -36,9 +36,9 @@ WORKLOAD = "cspad_batch"
 N_FRAMES = 1000
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per frame of the
 # current k_fused launch, from one single-pass ncu capture of one launch of
-# this workload (1,000 frames: 10.303 GB read + 0.878 GB written).  None
+# this workload (1,000 frames: 10.203 GB read + 0.776 GB written).  None
 # whenever the kernel or its schedule has changed since the capture.
-FUSED_DRAM_BYTES_PER_FRAME = 11.181e6
+FUSED_DRAM_BYTES_PER_FRAME = 10.979e6
 
 
 def parse():
