@@ -78,3 +78,17 @@ def test_status_strings():
     for code in range(0, -8, -1):
         assert rb.status_string(code) != "unknown status"
     assert rb.status_string(-99) == "unknown status"
+
+
+def test_graph_create_rejects_bad_arguments_before_touching_the_device():
+    """Argument checks of roibin_graph_create run on the host first: no jobs,
+    and an unknown mode, are refused without a context or a GPU."""
+    import ctypes
+    lib = rb.library()
+    h = ctypes.c_void_p()
+    arr = (rb.Job * 1)()
+    assert lib.roibin_graph_create(ctypes.byref(h), arr, 0, rb.GRAPH_SERIAL) == rb.ERR_INVALID_ARG
+    assert lib.roibin_graph_create(ctypes.byref(h), None, 1, rb.GRAPH_SERIAL) == rb.ERR_INVALID_ARG
+    assert lib.roibin_graph_create(ctypes.byref(h), arr, 1, 7) == rb.ERR_INVALID_ARG
+    assert not h.value
+    assert lib.roibin_graph_create(None, arr, 1, rb.GRAPH_SERIAL) == rb.ERR_INVALID_ARG
