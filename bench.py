@@ -34,6 +34,7 @@ from synthetic import RECIPES, make_batch_threaded, make_frame  # noqa: E402
 
 WORKLOAD = "cspad_batch"
 N_FRAMES = 1000
+EPIX_FRAMES = 1000
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per frame of the
 # current k_fused launch, from one single-pass ncu capture of one launch of
 # this workload (1,000 frames: 10.203 GB read + 0.776 GB written).  None
@@ -52,6 +53,8 @@ def parse():
     ap.add_argument("--no-decompress", action="store_true", help="skip the decompression timing")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-geometry graph timing")
     ap.add_argument("--no-dims", action="store_true", help="skip the Lorenzo-dimension variants")
+    ap.add_argument("--no-epix", action="store_true", help="skip the epix10k hot-pixel workload")
+    ap.add_argument("--no-npix", action="store_true", help="skip the npix_max = 49 variant")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--min-load-seconds", type=float, default=2.0,
                     help="keep the GPU busy at least this long before timing (clock sampling)")
@@ -293,6 +296,93 @@ def mixed_graph(args, dev, local, stream):
     return res
 
 
+def timed_variant(args, frames, params, stream, local, path=None):
+    """One resident batch through one context on the path and shape the
+    project's autotuner keeps (AUTO unless `path` is given): input GB/s,
+    frames/s, per-kernel times, peaks per frame, the compression ratio and the
+    roofline of the dominant kernel (frames in + streams out per launch)."""
+    import torch
+    import paper_2206_11297_gb300 as rb
+    n = frames.shape[0]
+    frame_bytes = frames[0].numel() * 4
+    geom = tuple(frames.shape[1:])
+    with rb.Context(geom, params, max_frames=n, device=local) as c:
+        stride = c.bound
+        out = torch.empty((n, stride), dtype=torch.uint8, device=frames.device)
+        nbytes = torch.empty(n, dtype=torch.int64, device=frames.device)
+        status = torch.empty(n, dtype=torch.int32, device=frames.device)
+        if path is not None:
+            c.set_path(path)
+        shape, _ = c.autotune(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
+        resolved = {rb.PATH_PLAIN: "plain", rb.PATH_FUSED: "fused"}[c.resolved_path]
+        run = lambda: c.compress(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
+        for _ in range(max(3, args.warmup)):
+            run()
+        torch.cuda.synchronize()
+        reps = max(3, min(args.steps, 10))
+        c.enable_timing(True)
+        c.kernel_times()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kt = c.kernel_times()
+        c.enable_timing(False)
+        st = status.cpu().numpy()
+        assert (st == 0).all(), f"frame status {np.unique(st)}"
+        out_bytes = int(nbytes.sum())
+        _, npk = c.last_peaks(n)
+        npk = npk.cpu().numpy()
+        ms = e0.elapsed_time(e1) / reps
+        kname, (kms, kcnt) = max(kt.items(), key=lambda kv: kv[1][0])
+        algo = n * frame_bytes + (out_bytes if kname == "fused" else 0)
+        ach = algo / 1e9 / (kms / 1e3 / kcnt)
+        hbm_peak = _hbm_peak()
+        res = {"value": n * frame_bytes / 1e9 / (ms / 1e3), "unit": "GB/s", "frames": n,
+               "frames_per_s": n / (ms / 1e3), "ms_per_step": ms, "path": resolved,
+               "shape": ({"ctas_per_sm": shape[0], "rows_per_step": shape[1], "stages": shape[2],
+                          "dense_peaks": c.fused_dense_peaks} if resolved == "fused" else
+                         {"rows_per_step": shape[0], "bands_per_panel": shape[1]}),
+               "peaks_per_frame": {"mean": float(npk.mean()), "min": int(npk.min()), "max": int(npk.max())},
+               "compression_ratio": {"vs_f32": n * frame_bytes / out_bytes, "vs_u16": n * frame_bytes / 2 / out_bytes},
+               "stream_bytes_per_frame": out_bytes / n,
+               "kernels_ms_per_step": {k: v[0] / reps for k, v in kt.items()},
+               "roofline": {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": ach / hbm_peak,
+                            "bytes_per_launch": algo,
+                            "basis": "frames in + streams out" if kname == "fused" else "frames in"}}
+    return res
+
+
+def epix_variants(args, stream, local):
+    """The epix10k-like workload: 16 x 352 x 384 float32 frames, background
+    N(30, 8), 1% hot pixels at 5,000, 0-300 peaks per frame (heavy-tailed),
+    1,000 resident frames per step at eb 1, 10 and 50, each on its autotuned
+    path and shape.  max_peaks is raised to 8,192: the hot-pixel pairs give
+    about 3,600 peaks per frame, above the default cap of 2,048."""
+    import torch
+    import paper_2206_11297_gb300 as rb
+    r = RECIPES["epix_hot"]
+    n = min(args.frames, EPIX_FRAMES)
+    host = torch.empty((n, *r.geometry), dtype=torch.float32).pin_memory()
+    make_batch_threaded(r, n, first=0, out=host.numpy())
+    frames = host.to(torch.device("cuda", local))
+    res = {"workload": f"{n} epix10k-like frames 16x352x384 f32, N(30,8) background, 1% hot pixels at 5000, "
+                       "0-300 peaks (floor(301^U) - 1), ROI 17x17, bin 2x2, max_peaks 8192"}
+    for eb in (1.0, 10.0, 50.0):
+        res[f"eb{eb:g}"] = timed_variant(args, frames, rb.default_params(abs_eb=eb, max_peaks=8192), stream, local)
+    del frames
+    torch.cuda.empty_cache()
+    return res
+
+
+def _hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path))["hbm_gbs"] if os.path.exists(path) else 6800.0
+
+
 def lorenzo_dims(args, frames, out, nbytes, status, stride, stream, local):
     """The same resident batch with the Lorenzo predictor in dimension 1, 2
     and 3 (the paper's "dimension" parameter), each on the plain path in its
@@ -444,7 +534,7 @@ def run_ours(args, rank, local, world):
     steps_ms = sorted(r["steps_ms"])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
-    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    hbm_peak = _hbm_peak()
     # dominant kernel: the one with the largest share of the timed region
     kname, (kms, kcnt) = max(r["kernels"].items(), key=lambda kv: kv[1][0])
     per_launch_s = kms / 1e3 / kcnt
@@ -528,6 +618,13 @@ def run_ours(args, rank, local, world):
         pr = res[rb.PATH_PLAIN]
         line["plain"] = {"value": args.steps * n * frame_bytes / 1e9 / (pr["total_ms"] / 1e3), "unit": "GB/s",
                          "kernels_ms_per_step": {k: v[0] / args.steps for k, v in pr["kernels"].items()}}
+    if not args.no_npix:
+        # the same frames with the peak-pixel cap at the whole 7x7 window: at the
+        # paper's cap of 30, most planted spots of these frames have more pixels
+        # above bkg + 3 sigma than that and fall back into the lossy background
+        line["npix_max_49"] = timed_variant(args, frames, rb.default_params(npix_max=49), stream, local)
+    if not args.no_epix:
+        line["epix"] = epix_variants(args, stream, local)
     if not args.no_mixed:
         line["mixed_graph"] = mixed_graph(args, dev, local, stream)
     if not args.no_dims:

@@ -94,8 +94,10 @@ typedef struct {
  *   Peak finder (§4.2): a pixel is a candidate when it is the maximum of its
  *   (2 rank + 1)^2 window clipped to the panel (ties: the first pixel in
  *   row-major order wins) and >= amax_thr (300).  The background is the mean
- *   and population standard deviation (fp64) of the in-panel ring
- *   ring_r0^2 <= di^2 + dj^2 < (ring_r0 + ring_dr)^2 (5, 2).  Peak pixels are
+ *   and population standard deviation of the in-panel ring
+ *   ring_r0^2 <= di^2 + dj^2 < (ring_r0 + ring_dr)^2 (5, 2), both in float32:
+ *   every add, subtract, multiply, divide and sqrt rounds once to nearest, and
+ *   the sums run in row-major order over the ring.  Peak pixels are
  *   window pixels with I - bkg > pix_nsigma * sigma (3; 0 = the paper's plain
  *   above-zero test).  A candidate is kept when npix_min <= npix <= npix_max
  *   (2, 30), atot > atot_thr (600) and atot > son_min * sigma * sqrt(npix) (10).
@@ -215,6 +217,17 @@ int roibin_ctx_plain_shape(const roibin_ctx* ctx, uint32_t* rows_per_step, uint3
  * shared memory bytes per CTA.  Any output pointer may be NULL. */
 int roibin_ctx_fused_shape(const roibin_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* rows_per_step,
                            uint32_t* stages, uint32_t* grid_ctas, uint32_t* smem_bytes);
+
+/* Failure-detection hook of the fused path.  Its later stages hand over
+ * through flags in device memory, and every wait on a flag is bounded: after
+ * `polls` unsuccessful polls (about 130 ns apart) the waiting work item gives
+ * up and marks its frame ROIBIN_ERR_TIMEOUT in the frame status, instead of
+ * waiting forever.  polls < 0 restores the default (4,194,304 polls, about
+ * half a second); polls = 0 makes every flag wait give up at once, which a
+ * test uses to see the timeout reach the caller.  A waiting item only ever
+ * waits for work handed out before it, so with the default limit a wait
+ * always ends first.  Affects later roibin_compress calls on the fused path. */
+int roibin_ctx_set_wait_limit(roibin_ctx* ctx, int64_t polls);
 
 /* Phase trace of the fused path: for frames f < n_frames of later calls the
  * kernel writes 16 u64 words at d_trace[f * 16 + i] (globaltimer ns):
@@ -353,10 +366,14 @@ uint32_t roibin_ctx_last_launch_count(const roibin_ctx* ctx);
  * codebook tables) must fit ROIBIN_STATIC_SCRATCH_BYTES; otherwise the call
  * returns ROIBIN_ERR_OUT_OF_BUDGET before touching the GPU.  A 32 x 185 x 388
  * frame at bin 2x2 needs about 7.3 MB.
- * Setup: the first call on each device looks the area's address up
- * (cudaGetSymbolAddress) with that device current, which may load the
+ * Setup: the first call in each CUDA context (normally one per device, the
+ * device's primary context) looks the area's address up
+ * (cudaGetSymbolAddress) with that context current, which may load the
  * library's device code; make one call per device before any stream capture
- * or latency-critical section.  ROIBIN_ERR_CUDA if the lookup fails.
+ * or latency-critical section.  A context that is reset or replaced
+ * (cudaDeviceReset, a caller's own driver context) gets its own lookup on its
+ * first call, since the area then lives at a new address.  ROIBIN_ERR_CUDA if
+ * the lookup fails.
  * Nothing has to start at zero: the call's first kernel clears the counters
  * the later ones accumulate into.
  * Overlap: every call on a device uses the same area, so two calls in flight

@@ -89,6 +89,7 @@ _SIGNATURES = {
     "roibin_ctx_set_fused_shape": (ctypes.c_int, [_P, _u32, _u32, _u32]),
     "roibin_ctx_fused_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(_u32)] * 5),
     "roibin_ctx_set_trace": (ctypes.c_int, [_P, _P, _u32]),
+    "roibin_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int64]),
     "roibin_compress": (ctypes.c_int, [_P, _P, _u32, _P, _P, _P, _u64, _P, _P, _P]),
     "roibin_decompress": (ctypes.c_int, [_P, _P, _u64, _P, _u32, _P, _P, _P]),
     "roibin_ctx_reserve_host_path": (ctypes.c_int, [_P]),
@@ -174,11 +175,30 @@ def compress_frame_static(geometry, params: Params, frame, out, frame_bytes, sta
                           npeaks=None, stream=None):
     """roibin_compress_frame_static: one CUDA float32 [P, H, W] frame into the caller's
     buffers (out u8 [capacity], frame_bytes int64 [1], status int32 [1]) with the
-    library's static scratch; allocates nothing.  Asynchronous on `stream`."""
+    library's static scratch; allocates nothing.  Asynchronous on `stream`.
+    peaks (int16/uint16 [max_peaks, 3]) and npeaks (int32/uint32 [1]) optionally
+    replace the peak finder, as in Context.compress."""
+    import torch
+    geometry = tuple(int(x) for x in geometry)
+    # the kernels index these buffers by the geometry and dtypes below: a
+    # mismatch would make them read or write out of bounds, so it is refused here
+    assert frame.dtype == torch.float32 and frame.is_cuda and frame.is_contiguous(), "frame: contiguous CUDA float32"
+    assert tuple(frame.shape) == geometry, f"frame shape {tuple(frame.shape)} is not the geometry {geometry}"
+    dev = frame.device
+    assert out.dtype == torch.uint8 and out.is_contiguous() and out.device == dev, "out: contiguous uint8 on the frame's device"
+    assert frame_bytes.dtype == torch.int64 and frame_bytes.numel() >= 1 and frame_bytes.device == dev
+    assert status.dtype == torch.int32 and status.numel() >= 1 and status.device == dev
+    assert (peaks is None) == (npeaks is None), "peaks and npeaks go together"
+    if peaks is not None:
+        mp = max(int(params.max_peaks), 1)
+        assert peaks.dtype in (torch.int16, torch.uint16) and peaks.is_contiguous() and peaks.device == dev
+        assert peaks.numel() >= 3 * mp, "peaks must hold max_peaks (panel, row, col) triples"
+        assert npeaks.dtype in (torch.int32, torch.uint32) and npeaks.numel() >= 1 and npeaks.device == dev
     g = Geometry(*geometry)
-    _check("roibin_compress_frame_static", library().roibin_compress_frame_static(
-        ctypes.byref(g), ctypes.byref(params), _ptr(frame), _ptr(peaks), _ptr(npeaks), _ptr(out),
-        out.numel(), _ptr(frame_bytes), _ptr(status), _stream_handle(stream)))
+    with torch.cuda.device(dev):
+        _check("roibin_compress_frame_static", library().roibin_compress_frame_static(
+            ctypes.byref(g), ctypes.byref(params), _ptr(frame), _ptr(peaks), _ptr(npeaks), _ptr(out),
+            out.numel() // 16 * 16, _ptr(frame_bytes), _ptr(status), _stream_handle(stream)))
 
 
 def _ptr(t):
@@ -302,6 +322,10 @@ class Context:
             self._h, _ptr(frames), n, _ptr(out), stride, _ptr(frame_bytes), _ptr(status),
             _stream_handle(stream), ctypes.byref(ms)))
         return (self.fused_shape if self.resolved_path == PATH_FUSED else self.plain_shape), ms.value
+
+    def set_wait_limit(self, polls: int = -1):
+        """roibin_ctx_set_wait_limit: polls of the fused path's flag waits (-1: the default)."""
+        _check("roibin_ctx_set_wait_limit", self.lib.roibin_ctx_set_wait_limit(self._h, int(polls)))
 
     def set_trace(self, trace=None, n_frames: int = 0):
         """trace: CUDA int64 tensor of n_frames * (16 + 4 P) entries (None switches tracing off)."""

@@ -711,17 +711,41 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
 // done, so every wait ends; waits are bounded anyway (ROIBIN_ERR_TIMEOUT).
 constexpr uint32_t kWaitLimit = 1u << 22;
 
+// Per-frame words, zeroed before each launch:
+//   panel_done, size_done   streaming / size items finished;
+//   ready_cb, ready_plan    the codebook / the plan is published;
+//   timed_out               set by any item whose flag wait gave up (sticky: no
+//                           later write of the frame's status can clear it);
+//   fin_count               the plan and the write items finished; the one that
+//                           finishes last settles the frame's status.
 struct SyncWords {
-  uint32_t *panel_done, *size_done, *ready_cb, *ready_plan, *ticket;
+  uint32_t *panel_done, *size_done, *ready_cb, *ready_plan, *timed_out, *fin_count, *ticket;
 };
+constexpr uint32_t kSyncWordsPerFrame = 6;
 __device__ __forceinline__ SyncWords sync_words(const Scratch& s, uint32_t n) {
   SyncWords w;
   w.panel_done = s.frame_done;
   w.size_done = s.frame_done + n;
   w.ready_cb = s.frame_done + 2 * n;
   w.ready_plan = s.frame_done + 3 * n;
-  w.ticket = s.frame_done + 4 * n;
+  w.timed_out = s.frame_done + 4 * n;
+  w.fin_count = s.frame_done + 5 * n;
+  w.ticket = s.frame_done + kSyncWordsPerFrame * n;
   return w;
+}
+
+// Called by thread 0 of the plan and of every write item of frame g once its
+// work is visible (after a __threadfence): the last of them to finish sees
+// every give-up of the frame's items, and a frame any of them gave up on is
+// reported ROIBIN_ERR_TIMEOUT with no bytes, whatever the plan wrote before.
+__device__ __forceinline__ void finish_frame_item(const PlainArgs& a, const FusedShape& sh, const SyncWords& sw,
+                                                  uint32_t g) {
+  if (atomicAdd(sw.fin_count + g, 1u) != sh.groups) return;
+  __threadfence();
+  if (__ldcg(sw.timed_out + g)) {
+    a.frame_status[g] = ROIBIN_ERR_TIMEOUT;
+    a.frame_bytes[g] = 0;
+  }
 }
 
 __device__ __forceinline__ void flag_release(uint32_t* f) {
@@ -733,11 +757,12 @@ __device__ __forceinline__ uint32_t flag_acquire(const uint32_t* f) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
   return v;
 }
-// Thread 0 waits (bounded) for a flag; every thread gets the outcome.
-__device__ bool wait_flag(const uint32_t* f, uint32_t* slot) {
+// Thread 0 waits (bounded: `limit` polls) for a flag; every thread gets the
+// outcome.  limit = 0 polls nothing, so the wait gives up at once.
+__device__ bool wait_flag(const uint32_t* f, uint32_t* slot, uint32_t limit) {
   if (threadIdx.x == 0) {
     uint32_t ok = 0;
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
       if (flag_acquire(f)) {
         ok = 1;
         break;
@@ -957,9 +982,9 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
                                  ? reinterpret_cast<unsigned long long*>(a.trace + (size_t)g * kTracePoints)
                                  : nullptr;
   const uint64_t t_in = acct ? global_ns() : 0;
-  const bool ready = wait_flag(sw.ready_cb + g, ctl + CTL_WAIT);
+  const bool ready = wait_flag(sw.ready_cb + g, ctl + CTL_WAIT, sh.wait_limit);
   if (acct) atomicAdd(acct + 7, (unsigned long long)(global_ns() - t_in));
-  if (!ready && tid == 0) atomicExch(reinterpret_cast<unsigned int*>(s.status + g), (unsigned int)ROIBIN_ERR_TIMEOUT);
+  if (!ready && tid == 0) atomicOr(sw.timed_out + g, 1u);
   const bool ok = ready && __ldcg(s.status + g) == ROIBIN_OK;
   if (ok) {
     load_byte_tables(p, s, g, btab, ctab);
@@ -1000,7 +1025,10 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
   // the frame's plan: scan the chunks, lay the frame out, write its head
   uint64_t* trace = (a.trace && g < a.trace_frames && tid == 0) ? a.trace + (size_t)g * kTracePoints : nullptr;
   if (trace) trace[3] = global_ns();
-  int32_t st = __ldcg(s.status + g);
+  // a size item of the frame that gave up waiting for the codebook left the
+  // chunk counts unfinished: the frame stops here (its give-up was published
+  // before its size_done increment, which this CTA has seen)
+  int32_t st = __ldcg(sw.timed_out + g) ? ROIBIN_ERR_TIMEOUT : __ldcg(s.status + g);
   uint32_t* cw = reinterpret_cast<uint32_t*>(sm + sh.off_cw);
   uint32_t* clo = cw + p.n_chunks;
   uint32_t* cpq = clo + p.n_chunks;
@@ -1067,27 +1095,43 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
   }
   __syncthreads();
   if (trace) trace[4] = global_ns();
-  if (tid == 0) flag_release(sw.ready_plan + g);
+  if (tid == 0) {
+    flag_release(sw.ready_plan + g);
+    finish_frame_item(a, sh, sw, g);
+  }
 }
 
 // (3) bits, outliers and ROI windows of one group of chunks of frame g.
+__device__ void write_item_work(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                                unsigned char* sm, uint32_t g, uint32_t grp, unsigned long long* acct,
+                                uint64_t t_in);
+
 __device__ void write_item(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
                            unsigned char* sm, uint32_t g, uint32_t grp, const SyncWords& sw) {
-  const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  const uint32_t tid = threadIdx.x;
   uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
-  uint64_t* btab = reinterpret_cast<uint64_t*>(sm + sh.off_huff);
-  uint64_t* ctab = btab + 256;
   unsigned long long* acct = (a.trace && g < a.trace_frames && tid == 0)
                                  ? reinterpret_cast<unsigned long long*>(a.trace + (size_t)g * kTracePoints)
                                  : nullptr;
   const uint64_t t_in = acct ? global_ns() : 0;
-  const bool ready = wait_flag(sw.ready_plan + g, ctl + CTL_WAIT);
+  const bool ready = wait_flag(sw.ready_plan + g, ctl + CTL_WAIT, sh.wait_limit);
   if (acct) atomicAdd(acct + 8, (unsigned long long)(global_ns() - t_in));
-  if (!ready) {
-    if (tid == 0) atomicExch(reinterpret_cast<unsigned int*>(a.frame_status + g), (unsigned int)ROIBIN_ERR_TIMEOUT);
-    return;
-  }
-  if (__ldcg(s.status + g) != ROIBIN_OK) return;
+  if (!ready && tid == 0) atomicOr(sw.timed_out + g, 1u);
+  // a plan that gave up (timed_out, published before ready_plan) wrote no
+  // layout for this launch: nothing of the frame is written then
+  if (ready && __ldcg(sw.timed_out + g) == 0 && __ldcg(s.status + g) == ROIBIN_OK)
+    write_item_work(p, s, a, sh, sm, g, grp, acct, t_in);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) finish_frame_item(a, sh, sw, g);
+}
+
+__device__ void write_item_work(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                                unsigned char* sm, uint32_t g, uint32_t grp, unsigned long long* acct,
+                                uint64_t t_in) {
+  const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  uint64_t* btab = reinterpret_cast<uint64_t*>(sm + sh.off_huff);
+  uint64_t* ctab = btab + 256;
   load_byte_tables(p, s, g, btab, ctab);
   FramePlan pl;
   pl.n_peaks = __ldcg(&s.plan[g].n_peaks);
@@ -1301,6 +1345,7 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   // the streamed rows are read once: first out of L2, so that the code bytes
   // (evict-last) stay there longer (1,000 CSPAD-like frames: +1%)
   sh.input_evict_first = 1;
+  sh.wait_limit = kWaitLimit;
   sh.stage_bytes = sh.k * 2 * rb * p.W * 4;
   sh.ctas_per_sm = ctas_per_sm;
   sh.mask_words = ceil_div(p.Hb * p.Wb, 32) + 1;
@@ -1400,7 +1445,7 @@ bool fused_plan(const DevParams& p, int device, int num_sms, FusedShape* out) {
 cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
                          bool screen, cudaStream_t st) {
   // stage counters, ready flags and the ticket counter start at zero
-  cudaError_t e = cudaMemsetAsync(s.frame_done, 0, sizeof(uint32_t) * (4ull * a.n_frames + 1), st);
+  cudaError_t e = cudaMemsetAsync(s.frame_done, 0, sizeof(uint32_t) * (kSyncWordsPerFrame * (uint64_t)a.n_frames + 1), st);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(screen ? k_fused<true> : k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sh.smem);

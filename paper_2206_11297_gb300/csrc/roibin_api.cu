@@ -46,6 +46,8 @@ struct roibin_ctx {
   bool fused_ok = false;
   bool fused_dense_peaks = false;  // the fused kernel's variant for many peak candidates
   FusedShape fshape{};
+  uint32_t wait_limit = 0;  // 0: the fused kernel's default poll limit; else this many polls
+  bool wait_limit_set = false;
   uint64_t* trace = nullptr;
   uint32_t trace_frames = 0;
   uint32_t last_launches = 0;
@@ -206,7 +208,7 @@ uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s
   t.lane_bit = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
   t.lane_lo = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
   t.lane_pq = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
-  t.frame_done = c.take<uint32_t>(4ull * n + 1);
+  t.frame_done = c.take<uint32_t>(6ull * n + 1);  // the fused kernel's sync words
   if (s) *s = t;
   return c.off + 256;
 }
@@ -310,8 +312,10 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
   a.trace = ctx->trace;
   a.trace_frames = ctx->trace_frames;
   if (resolved_path(ctx) == ROIBIN_PATH_FUSED && (uint64_t)n_frames * ctx->dp.P < (1ull << 31)) {
+    FusedShape sh = ctx->fshape;
+    if (ctx->wait_limit_set) sh.wait_limit = ctx->wait_limit;
     cudaError_t e = timed(ctx, K_FUSED, st,
-                          [&] { return launch_fused(ctx->dp, ctx->s, a, ctx->fshape, ctx->fused_dense_peaks, st); });
+                          [&] { return launch_fused(ctx->dp, ctx->s, a, sh, ctx->fused_dense_peaks, st); });
     return cuda_status(e);
   }
   return compress_plain(ctx, a, st);
@@ -321,20 +325,64 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
 // module global exists once in every device context that loads the library).
 __device__ __align__(256) unsigned char g_static_scratch[ROIBIN_STATIC_SCRATCH_BYTES];
 
-constexpr int kStaticMaxDevices = 64;
+// The area's address belongs to the CUDA context that loaded the library's
+// device code: a reset device (cudaDeviceReset) or a caller's own driver
+// context loads it anew, at another address.  So the address is looked up once
+// per context, keyed by the context's unique id (cuCtxGetId, which is never
+// reused), with that context current.
+constexpr int kStaticMaxContexts = 64;
+struct StaticEntry {
+  unsigned long long ctx_id;
+  void* base;
+};
 std::mutex g_static_mutex;
-void* g_static_base[kStaticMaxDevices] = {};
+StaticEntry g_static_cache[kStaticMaxContexts] = {};
+int g_static_used = 0;
 
-// Address of the current device's area; looked up once per device.
-cudaError_t static_scratch_base(int device, void** out) {
-  std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_base[device]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_static_base[device] = ptr;
+using CtxGetCurrentFn = int (*)(void**);
+using CtxGetIdFn = int (*)(void*, unsigned long long*);
+
+// Unique id of the current context; false when the driver cannot say.
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    cudaGetLastError();
+    looked = true;
   }
-  *out = g_static_base[device];
+  void* ctx = nullptr;
+  return get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, id) == 0;
+}
+
+// Address of the area in the current context: looked up (cudaGetSymbolAddress)
+// the first time a context calls, then taken from the cache.
+cudaError_t static_scratch_base(void** out) {
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  if (have_id)
+    for (int i = 0; i < g_static_used; ++i)
+      if (g_static_cache[i].ctx_id == id) {
+        *out = g_static_cache[i].base;
+        return cudaSuccess;
+      }
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  // once the key is known it is cached; otherwise (or with the cache full)
+  // the lookup simply runs on every call
+  if (have_id && g_static_used < kStaticMaxContexts) g_static_cache[g_static_used++] = {id, ptr};
+  *out = ptr;
   return cudaSuccess;
 }
 
@@ -654,6 +702,13 @@ int roibin_ctx_autotune(roibin_ctx* ctx, const float* d_frames, uint32_t n_frame
   }
   ctx->auto_path = (t_plain >= 0.0f && t_fused >= 0.0f && t_plain < t_fused) ? ROIBIN_PATH_PLAIN : ROIBIN_PATH_FUSED;
   if (best_ms) *best_ms = ctx->auto_path == ROIBIN_PATH_PLAIN ? t_plain : t_fused;
+  return ROIBIN_OK;
+}
+
+int roibin_ctx_set_wait_limit(roibin_ctx* ctx, int64_t polls) {
+  if (!ctx || polls > (int64_t)UINT32_MAX) return ROIBIN_ERR_INVALID_ARG;
+  ctx->wait_limit_set = polls >= 0;
+  ctx->wait_limit = polls >= 0 ? (uint32_t)polls : 0u;
   return ROIBIN_OK;
 }
 
@@ -1024,9 +1079,9 @@ int roibin_compress_frame_static(const roibin_geometry* g, const roibin_params* 
   const DevParams dp = make_dev_params(*g, *p);
   if (carve_scratch(dp, 1, nullptr, nullptr) > ROIBIN_STATIC_SCRATCH_BYTES) return ROIBIN_ERR_OUT_OF_BUDGET;
   int device = 0, sms = 0;
-  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kStaticMaxDevices) return ROIBIN_ERR_CUDA;
+  if (cudaGetDevice(&device) != cudaSuccess) return ROIBIN_ERR_CUDA;
   void* base = nullptr;
-  if (static_scratch_base(device, &base) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  if (static_scratch_base(&base) != cudaSuccess) return ROIBIN_ERR_CUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return ROIBIN_ERR_CUDA;
   Scratch s{};
   carve_scratch(dp, 1, static_cast<uint8_t*>(base), &s);

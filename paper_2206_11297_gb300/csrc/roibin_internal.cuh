@@ -101,7 +101,7 @@ struct Scratch {
   uint32_t* lane_bit;         // [n][n_chunks][32] bit offset of each lane's symbols in its chunk
   uint32_t* lane_lo;          // [n][n_chunks][32] Lorenzo outliers before the lane, in its chunk
   uint32_t* lane_pq;          // [n][n_chunks][32] prequantisation outliers before the lane
-  uint32_t* frame_done;     // [4 n + 1] stage counters and flags, ticket counter
+  uint32_t* frame_done;     // [6 n + 1] stage counters and flags, ticket counter
 };
 
 // count, first, index (34 words each), symbols; padded to 16 bytes
@@ -789,6 +789,7 @@ struct FusedShape {
   uint32_t group_chunks, groups; // chunks per size/write work item; items per frame
   uint32_t lag1, lag2;           // frames between stages in the ticket order (per launch)
   uint32_t input_evict_first;    // L2 policy of the streamed rows (1 = evict first)
+  uint32_t wait_limit;           // polls of a flag wait before it reports ROIBIN_ERR_TIMEOUT
   uint32_t off_ctl, off_bar, off_hist, off_pql, off_thr, off_ring, off_nb, off_acc, off_cand;  // streaming role
   uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw, off_offs;  // codebook / plan roles
   uint32_t off_stage;                                                        // size / write roles

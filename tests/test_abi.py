@@ -92,3 +92,21 @@ def test_graph_create_rejects_bad_arguments_before_touching_the_device():
     assert lib.roibin_graph_create(ctypes.byref(h), arr, 1, 7) == rb.ERR_INVALID_ARG
     assert not h.value
     assert lib.roibin_graph_create(None, arr, 1, rb.GRAPH_SERIAL) == rb.ERR_INVALID_ARG
+
+
+def test_static_call_wrapper_refuses_mismatched_buffers():
+    """compress_frame_static checks dtype, device, layout and shape before the
+    call: a mismatch would make the kernels index out of bounds."""
+    import torch
+    geom = (2, 16, 24)
+    p = rb.default_params()
+    frame = torch.zeros(geom, dtype=torch.float32)  # host memory: refused
+    out = torch.zeros(rb.compress_bound(geom, p), dtype=torch.uint8)
+    nb = torch.zeros(1, dtype=torch.int64)
+    st = torch.zeros(1, dtype=torch.int32)
+    with pytest.raises(AssertionError):
+        rb.compress_frame_static(geom, p, frame, out, nb, st)
+    with pytest.raises(AssertionError):  # wrong shape (checked before the device)
+        rb.compress_frame_static((2, 16, 25), p, frame, out, nb, st)
+    with pytest.raises(AssertionError):  # int32 frame_bytes would be overrun by the u64 store
+        rb.compress_frame_static(geom, p, frame, out, nb.to(torch.int32), st)
