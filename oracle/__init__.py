@@ -27,6 +27,8 @@ ERR_INVALID_ARG = -1
 ERR_CAPACITY = -2
 ERR_CORRUPT_STREAM = -3
 ERR_CODE_LENGTH = -7
+REJECTED = 1  # non-hit rejection: the frame has fewer than nhr_min_peaks peaks
+ROI_CLASSES = 33
 
 CHUNK_SYMBOLS = 4096
 HEADER_BYTES = 96
@@ -45,13 +47,14 @@ class Params(ctypes.Structure):
         ("roi_h", ctypes.c_int32), ("roi_w", ctypes.c_int32),
         ("bin_h", ctypes.c_int32), ("bin_w", ctypes.c_int32),
         ("abs_eb", ctypes.c_float), ("quant_radius", ctypes.c_int32), ("max_peaks", ctypes.c_int32),
-        ("lorenzo_dims", ctypes.c_int32),
+        ("lorenzo_dims", ctypes.c_int32), ("nhr_min_peaks", ctypes.c_int32), ("roi_coder", ctypes.c_int32),
     ]
 
 
 DEFAULTS = dict(amax_thr=300.0, atot_thr=600.0, son_min=10.0, pix_nsigma=3.0, rank=3,
                 ring_r0=5, ring_dr=2, npix_min=2, npix_max=30, roi_h=17, roi_w=17,
-                bin_h=2, bin_w=2, abs_eb=10.0, quant_radius=512, max_peaks=2048, lorenzo_dims=2)
+                bin_h=2, bin_w=2, abs_eb=10.0, quant_radius=512, max_peaks=2048, lorenzo_dims=2,
+                nhr_min_peaks=0, roi_coder=0)
 
 
 def make_params(**kw) -> Params:
@@ -101,6 +104,11 @@ def _bind(path: str):
         "orc_huffman_lengths": (ctypes.c_int, [P, u32, P]),
         "orc_canonical_codes": (None, [P, u32, P]),
         "orc_pack_chunks": (u32, [P, u64, P, P, P, P]),
+        "orc_roi_order_bits": (u32, [ctypes.c_float]),
+        "orc_roi_residuals": (None, [P, i32, i32, P]),
+        "orc_roi_class": (u32, [u32]),
+        "orc_roi_encode": (u64, [P, u32, i32, i32, P, P, P]),
+        "orc_roi_decode": (ctypes.c_int, [P, u64, u32, u32, u32, i32, i32, P]),
         "orc_compress_bound": (u64, [G, Pr]),
         "orc_compress_frame": (ctypes.c_int, [P, G, Pr, P, i64, P, u64, P]),
         "orc_decompress_frame": (ctypes.c_int, [P, u64, G, P]),
@@ -269,6 +277,45 @@ def pack_chunks(codes: np.ndarray, lengths: np.ndarray, codewords: np.ndarray):
     return idx, words[:n].copy()
 
 
+# ---------------------------------------------------------------- ROI coding
+def roi_order_bits(x: float) -> int:
+    return int(lib().orc_roi_order_bits(ctypes.c_float(x)))
+
+
+def roi_residuals(window: np.ndarray) -> np.ndarray:
+    """Folded prediction residuals z of one roi_h x roi_w float32 window."""
+    w = np.ascontiguousarray(window, dtype=np.float32)
+    z = np.zeros(w.shape, np.uint32)
+    lib().orc_roi_residuals(_ptr(w), w.shape[0], w.shape[1], _ptr(z))
+    return z
+
+
+def roi_class(z: int) -> int:
+    return int(lib().orc_roi_class(int(z) & 0xFFFFFFFF))
+
+
+def roi_encode(windows: np.ndarray):
+    """Section of n float32 windows [n, h, w]: (coding 1 or 2, n_words, section bytes)."""
+    w = np.ascontiguousarray(windows, dtype=np.float32)
+    n, h, ww = w.shape
+    out = np.zeros(w.size * 4 + 64, np.uint8)
+    coding, words = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    nb = lib().orc_roi_encode(_ptr(w), n, h, ww, _ptr(out), ctypes.byref(coding), ctypes.byref(words))
+    return coding.value, words.value, out[:nb].copy()
+
+
+def roi_decode(section: np.ndarray, coding: int, n_words: int, n: int, h: int, w: int):
+    """(status, windows float32 [n, h, w]) from a section written by roi_encode."""
+    sec = np.ascontiguousarray(section, dtype=np.uint8)
+    if sec.size == 0:
+        sec = np.zeros(16, np.uint8)[:0]
+    out = np.zeros((n, h, w), np.float32)
+    buf = np.zeros(max(sec.size, 16), np.uint8)
+    buf[:sec.size] = sec
+    st = lib().orc_roi_decode(_ptr(buf), sec.size, coding, n_words, n, h, w, _ptr(out))
+    return st, out
+
+
 # ---------------------------------------------------------------- whole frame
 def compress_bound(shape, params: Params) -> int:
     g = Geometry(*shape)
@@ -306,6 +353,7 @@ def parse_header(stream: np.ndarray) -> dict:
     """Field view of the 96-byte frame header (format version 1)."""
     b = np.ascontiguousarray(stream[:HEADER_BYTES], dtype=np.uint8)
     u32 = b[:64].view(np.uint32)
+    tail = b[76:88].view(np.uint32)
     u16 = b[20:28].view(np.uint16)
     return dict(magic=int(u32[0]), version=int(u32[1]), n_panels=int(u32[2]), rows=int(u32[3]),
                 cols=int(u32[4]), roi_h=int(u16[0]), roi_w=int(u16[1]), bin_h=int(u16[2]),
@@ -314,7 +362,8 @@ def parse_header(stream: np.ndarray) -> dict:
                 n_prequant=int(u32[11]), n_symbols=int(u32[12]), chunk_symbols=int(u32[13]),
                 n_chunks=int(u32[14]), n_words=int(u32[15]),
                 total_bytes=int(b[64:72].view(np.uint64)[0]),
-                lorenzo_dims={0: 2}.get(int(b[72:76].view(np.uint32)[0]), int(b[72:76].view(np.uint32)[0])))
+                lorenzo_dims={0: 2}.get(int(b[72:76].view(np.uint32)[0]), int(b[72:76].view(np.uint32)[0])),
+                roi_coding=int(tail[0]), roi_bytes=int(tail[1]), roi_words=int(tail[2]))
 
 
 def section_offsets(h: dict) -> dict:
@@ -322,10 +371,12 @@ def section_offsets(h: dict) -> dict:
     a16 = lambda x: (x + 15) & ~15
     o = {"peaks": HEADER_BYTES}
     o["roi"] = o["peaks"] + a16(h["n_peaks"] * 6)
-    o["lengths"] = o["roi"] + a16(h["n_peaks"] * h["roi_h"] * h["roi_w"] * 4)
+    in_place = h.get("roi_coding", 0) == 0
+    o["lengths"] = o["roi"] + (a16(h["n_peaks"] * h["roi_h"] * h["roi_w"] * 4) if in_place else 0)
     o["chunk_index"] = o["lengths"] + a16(2 * h["quant_radius"])
     o["lorenzo"] = o["chunk_index"] + a16(h["n_chunks"] * 4)
     o["prequant"] = o["lorenzo"] + a16(h["n_lorenzo"] * 8)
     o["bitstream"] = o["prequant"] + a16(h["n_prequant"] * 8)
-    o["end"] = o["bitstream"] + a16(h["n_words"] * 4)
+    o["roi_section"] = o["bitstream"] + a16(h["n_words"] * 4)
+    o["end"] = o["roi_section"] + h.get("roi_bytes", 0)
     return o

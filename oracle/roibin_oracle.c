@@ -469,6 +469,268 @@ uint32_t orc_pack_chunks(const uint16_t* codes, uint64_t m, const uint8_t* len,
   return word_base;
 }
 
+/* --------------------------------------------------------------------------
+ * ROI coding (§4: the paper stores each region of interest losslessly with
+ * fpzip, a predictive coder for floating-point data).  The coder here is our
+ * own of that kind; it changes how the ROI windows are stored, never their
+ * values (they come back bit for bit).  For each window, in row-major order:
+ *   1. the float's bits u become an integer in the float's own order:
+ *      m = u + 2^31 when the sign bit is 0, m = NOT u when it is 1;
+ *   2. m is predicted modulo 2^32 by the 2-D Lorenzo rule inside the window,
+ *      m[i-1][j] + m[i][j-1] - m[i-1][j-1], positions outside the window
+ *      taken as 0, except the window's first value, predicted by 2^31 (+0.0);
+ *   3. the residual r = m - prediction (mod 2^32, as int32) is folded to
+ *      z = 2r for r >= 0 and -2r - 1 for r < 0;
+ *   4. z is written as its class c (its bit length: 0 for z = 0, else 1..32),
+ *      Huffman-coded over the 33 classes with one codebook per frame (the
+ *      lengths and canonical codes of a9 and a10's bit order), followed by the
+ *      c - 1 bits of z below its leading one, most significant first.
+ * A window's bits start on a 32-bit word boundary.  Section layout:
+ *   [0, 48)          u8 code length of each class (33), zero padded;
+ *   [48, 48 + A)     u32 first word of each window, A = align16(4 n_windows);
+ *   then             u32 words, padded to 16 bytes.
+ * When that section would not be smaller than the raw windows, the raw float32
+ * windows are stored instead (coding 2); the coded form is coding 1.
+ * ------------------------------------------------------------------------ */
+#define ORC_ROI_CLASSES 33u
+#define ORC_ROI_HEAD 48u
+
+uint32_t orc_roi_order_bits(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+static float roi_float_of(uint32_t m) {
+  const uint32_t u = (m & 0x80000000u) ? (m & 0x7FFFFFFFu) : ~m;
+  float x;
+  memcpy(&x, &u, 4);
+  return x;
+}
+
+/* Steps 1-3 for one window: z_out[i * w + j]. */
+void orc_roi_residuals(const float* win, int32_t h, int32_t w, uint32_t* z_out) {
+  for (long i = 0; i < h; ++i) {
+    for (long j = 0; j < w; ++j) {
+      const uint32_t m = orc_roi_order_bits(win[i * w + j]);
+      uint32_t pred;
+      if (i == 0 && j == 0) {
+        pred = 0x80000000u;
+      } else {
+        const uint32_t up = i > 0 ? orc_roi_order_bits(win[(i - 1) * w + j]) : 0u;
+        const uint32_t left = j > 0 ? orc_roi_order_bits(win[i * w + j - 1]) : 0u;
+        const uint32_t diag = (i > 0 && j > 0) ? orc_roi_order_bits(win[(i - 1) * w + j - 1]) : 0u;
+        pred = up + left - diag;
+      }
+      const int32_t r = (int32_t)(m - pred);
+      z_out[i * w + j] = r >= 0 ? 2u * (uint32_t)r : 2u * (uint32_t)(-(int64_t)r) - 1u;
+    }
+  }
+}
+
+uint32_t orc_roi_class(uint32_t z) {
+  uint32_t c = 0;
+  while (z) {
+    ++c;
+    z >>= 1;
+  }
+  return c;
+}
+
+static uint64_t roi_coded_bytes(uint32_t n_windows, uint32_t n_words) {
+  return ORC_ROI_HEAD + align16((uint64_t)n_windows * 4) + align16((uint64_t)n_words * 4);
+}
+
+/* Writes the ROI section of n_windows windows (f32[n][h][w]) into out (at
+ * least n * h * w * 4 + 64 bytes).  *coding is 1 (coded) or 2 (raw), *n_words
+ * the coded section's words (0 for raw); returns the section's bytes. */
+uint64_t orc_roi_encode(const float* windows, uint32_t n_windows, int32_t h, int32_t w, uint8_t* out,
+                        uint32_t* coding, uint32_t* n_words) {
+  const size_t win = (size_t)h * (size_t)w;
+  const uint64_t raw = align16((uint64_t)n_windows * win * 4);
+  uint32_t* z = (uint32_t*)malloc(sizeof(uint32_t) * (win * n_windows + 1));
+  uint64_t hist[ORC_ROI_CLASSES];
+  memset(hist, 0, sizeof(hist));
+  for (uint32_t k = 0; k < n_windows; ++k) orc_roi_residuals(windows + k * win, h, w, z + k * win);
+  for (size_t i = 0; i < win * n_windows; ++i) hist[orc_roi_class(z[i])] += 1;
+  uint8_t len[ORC_ROI_CLASSES];
+  uint32_t cw[ORC_ROI_CLASSES];
+  orc_huffman_lengths(hist, ORC_ROI_CLASSES, len); /* 33 leaves: every length <= 32 */
+  orc_canonical_codes(len, ORC_ROI_CLASSES, cw);
+  /* sizes first: bits of each window, then the word count */
+  uint64_t words = 0;
+  for (uint32_t k = 0; k < n_windows; ++k) {
+    uint64_t bits = 0;
+    for (size_t i = 0; i < win; ++i) {
+      const uint32_t c = orc_roi_class(z[k * win + i]);
+      bits += len[c] + (c > 1 ? c - 1 : 0);
+    }
+    words += (bits + 31) / 32;
+  }
+  if (n_windows == 0 || roi_coded_bytes(n_windows, (uint32_t)words) >= raw) {
+    memcpy(out, windows, (size_t)n_windows * win * 4);
+    memset(out + (size_t)n_windows * win * 4, 0, raw - (size_t)n_windows * win * 4);
+    *coding = 2;
+    *n_words = 0;
+    free(z);
+    return raw;
+  }
+  const uint64_t total = roi_coded_bytes(n_windows, (uint32_t)words);
+  memset(out, 0, total);
+  memcpy(out, len, ORC_ROI_CLASSES);
+  uint8_t* offs = out + ORC_ROI_HEAD;
+  uint8_t* wbytes = offs + align16((uint64_t)n_windows * 4);
+  uint64_t word0 = 0;
+  for (uint32_t k = 0; k < n_windows; ++k) {
+    const uint32_t o = (uint32_t)word0;
+    memcpy(offs + 4 * k, &o, 4);
+    uint64_t bit = 0;
+    /* one bit at a time, most significant first: stream bit b of the window is
+     * bit 31 - b % 32 of its word b / 32 */
+    for (size_t i = 0; i < win; ++i) {
+      const uint32_t zz = z[k * win + i], c = orc_roi_class(zz);
+      for (int b = len[c] - 1; b >= 0; --b, ++bit)
+        if ((cw[c] >> b) & 1u) {
+          uint32_t v;
+          memcpy(&v, wbytes + 4 * (word0 + bit / 32), 4);
+          v |= 1u << (31 - bit % 32);
+          memcpy(wbytes + 4 * (word0 + bit / 32), &v, 4);
+        }
+      for (int b = (int)c - 2; b >= 0; --b, ++bit)
+        if ((zz >> b) & 1u) {
+          uint32_t v;
+          memcpy(&v, wbytes + 4 * (word0 + bit / 32), 4);
+          v |= 1u << (31 - bit % 32);
+          memcpy(wbytes + 4 * (word0 + bit / 32), &v, 4);
+        }
+    }
+    word0 += (bit + 31) / 32;
+  }
+  *coding = 1;
+  *n_words = (uint32_t)words;
+  free(z);
+  return total;
+}
+
+/* Inverse of orc_roi_encode.  A section whose size, code lengths, window
+ * offsets or bits do not fit together gives ORC_ERR_CORRUPT_STREAM. */
+int orc_roi_decode(const uint8_t* sec, uint64_t bytes, uint32_t coding, uint32_t n_words, uint32_t n_windows,
+                   int32_t h, int32_t w, float* windows_out) {
+  const size_t win = (size_t)h * (size_t)w;
+  if (coding == 2) {
+    if (n_words != 0 || bytes != align16((uint64_t)n_windows * win * 4)) return ORC_ERR_CORRUPT_STREAM;
+    memcpy(windows_out, sec, (size_t)n_windows * win * 4);
+    return ORC_OK;
+  }
+  if (coding != 1 || n_windows == 0 || bytes != roi_coded_bytes(n_windows, n_words)) return ORC_ERR_CORRUPT_STREAM;
+  const uint8_t* len = sec;
+  uint32_t count[34] = {0};
+  uint64_t kraft = 0;
+  uint32_t present = 0;
+  for (uint32_t c = 0; c < ORC_ROI_CLASSES; ++c) {
+    if (len[c] > 32) return ORC_ERR_CORRUPT_STREAM;
+    if (len[c]) {
+      count[len[c]]++;
+      kraft += 1ull << (32 - len[c]);
+      ++present;
+    }
+  }
+  /* a complete code, or one class alone with length 1 */
+  if (!(kraft == (1ull << 32) || (present == 1 && count[1] == 1))) return ORC_ERR_CORRUPT_STREAM;
+  uint32_t first_code[34], first_index[34], sorted[ORC_ROI_CLASSES], n_sorted = 0;
+  {
+    uint64_t c = 0;
+    int prev = 0;
+    for (int L = 1; L <= 32; ++L) {
+      first_index[L] = n_sorted;
+      first_code[L] = 0;
+      for (uint32_t s = 0; s < ORC_ROI_CLASSES; ++s)
+        if (len[s] == L) sorted[n_sorted++] = s;
+      if (count[L] == 0) continue;
+      c = (prev == 0) ? 0 : (c + count[prev]) << (L - prev);
+      first_code[L] = (uint32_t)c;
+      prev = L;
+    }
+  }
+  const uint8_t* offs = sec + ORC_ROI_HEAD;
+  const uint8_t* wbytes = offs + align16((uint64_t)n_windows * 4);
+  uint32_t* z = (uint32_t*)malloc(sizeof(uint32_t) * win);
+  int status = ORC_OK;
+  for (uint32_t k = 0; k < n_windows && status == ORC_OK; ++k) {
+    uint32_t w0, w1;
+    memcpy(&w0, offs + 4 * k, 4);
+    if (k + 1 < n_windows) memcpy(&w1, offs + 4 * (k + 1), 4);
+    else w1 = n_words;
+    if ((k == 0 && w0 != 0) || w0 > w1 || w1 > n_words) {
+      status = ORC_ERR_CORRUPT_STREAM;
+      break;
+    }
+    const uint64_t bit_end = (uint64_t)(w1 - w0) * 32;
+    uint64_t bit = 0;
+#define ROI_NEXT_BIT(dst)                                                   \
+  do {                                                                      \
+    if (bit >= bit_end) {                                                   \
+      status = ORC_ERR_CORRUPT_STREAM;                                      \
+      break;                                                                \
+    }                                                                       \
+    uint32_t v_;                                                            \
+    memcpy(&v_, wbytes + 4 * ((uint64_t)w0 + bit / 32), 4);                 \
+    dst = (v_ >> (31 - bit % 32)) & 1u;                                     \
+    ++bit;                                                                  \
+  } while (0)
+    for (size_t i = 0; i < win && status == ORC_OK; ++i) {
+      uint64_t code = 0;
+      int cls = -1;
+      for (int L = 1; L <= 32 && status == ORC_OK; ++L) {
+        uint32_t b;
+        ROI_NEXT_BIT(b);
+        if (status != ORC_OK) break;
+        code = (code << 1) | b;
+        if (count[L] && code >= first_code[L] && code - first_code[L] < count[L]) {
+          cls = (int)sorted[first_index[L] + (code - first_code[L])];
+          break;
+        }
+      }
+      if (status != ORC_OK) break;
+      if (cls < 0) {
+        status = ORC_ERR_CORRUPT_STREAM;
+        break;
+      }
+      uint32_t zz = cls == 0 ? 0u : 1u;
+      for (int t = 0; t < cls - 1 && status == ORC_OK; ++t) {
+        uint32_t b;
+        ROI_NEXT_BIT(b);
+        zz = (zz << 1) | b;
+      }
+      z[i] = zz;
+    }
+#undef ROI_NEXT_BIT
+    if (status == ORC_OK && (bit + 31) / 32 != (uint64_t)(w1 - w0)) status = ORC_ERR_CORRUPT_STREAM;
+    if (status != ORC_OK) break;
+    /* the inverse of steps 3, 2 and 1, in the window's row-major order */
+    uint32_t* m = (uint32_t*)malloc(sizeof(uint32_t) * win);
+    for (long i = 0; i < h; ++i)
+      for (long j = 0; j < w; ++j) {
+        const uint32_t zz = z[i * w + j];
+        const uint32_t r = (zz & 1u) ? ~(zz >> 1) : (zz >> 1);
+        uint32_t pred;
+        if (i == 0 && j == 0) {
+          pred = 2147483648u; /* m(+0.0) */
+        } else {
+          const uint32_t above = i > 0 ? m[(i - 1) * w + j] : 0u;
+          const uint32_t before = j > 0 ? m[i * w + j - 1] : 0u;
+          const uint32_t corner = (i > 0 && j > 0) ? m[(i - 1) * w + j - 1] : 0u;
+          pred = before + above - corner;
+        }
+        m[i * w + j] = r + pred;
+        windows_out[k * win + (size_t)i * w + (size_t)j] = roi_float_of(m[i * w + j]);
+      }
+    free(m);
+  }
+  free(z);
+  return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Container, format version 1 (ours: the paper defines none).               */
 /* ------------------------------------------------------------------------ */
@@ -483,12 +745,16 @@ typedef struct {
   uint64_t peaks, roi, lengths, chunk_index, lorenzo, prequant, bitstream, total;
 } orc_layout;
 
+/* roi_in_place: the raw windows sit in the ROI section (ROI coding 0); with
+ * the ROI coder they move to their own section after the bitstream, and the
+ * ROI section is empty. */
 static orc_layout layout_of(uint32_t n_peaks, const orc_params* p, uint32_t n_symbols,
-                            uint32_t n_chunks, uint32_t n_lo, uint32_t n_pq, uint32_t words) {
+                            uint32_t n_chunks, uint32_t n_lo, uint32_t n_pq, uint32_t words,
+                            int roi_in_place) {
   orc_layout L;
   L.peaks = ORC_HEADER_BYTES;
   L.roi = L.peaks + align16((uint64_t)n_peaks * 6);
-  L.lengths = L.roi + align16((uint64_t)n_peaks * p->roi_h * p->roi_w * 4);
+  L.lengths = L.roi + (roi_in_place ? align16((uint64_t)n_peaks * p->roi_h * p->roi_w * 4) : 0);
   L.chunk_index = L.lengths + align16(n_symbols);
   L.lorenzo = L.chunk_index + align16((uint64_t)n_chunks * 4);
   L.prequant = L.lorenzo + align16((uint64_t)n_lo * 8);
@@ -507,6 +773,8 @@ static int params_valid(const orc_geometry* g, const orc_params* p) {
   if (p->quant_radius < 2 || p->quant_radius > 512) return 0;
   if (p->max_peaks < 0 || p->max_peaks > 65535) return 0;
   if (p->lorenzo_dims < 1 || p->lorenzo_dims > 3) return 0;
+  if (p->nhr_min_peaks < 0 || p->nhr_min_peaks > 8192) return 0;
+  if (p->roi_coder < 0 || p->roi_coder > 1) return 0;
   if (!(p->pix_nsigma >= 0.0f)) return 0;
   if (!(p->abs_eb > 0.0f) || !isfinite(2.0f * p->abs_eb) || !isfinite(1.0f / (2.0f * p->abs_eb)))
     return 0;
@@ -520,15 +788,21 @@ uint64_t orc_compress_bound(const orc_geometry* g, const orc_params* p) {
   const uint64_t hb = (g->rows + p->bin_h - 1) / p->bin_h, wb = (g->cols + p->bin_w - 1) / p->bin_w;
   const uint64_t m = (uint64_t)g->n_panels * hb * wb;
   const uint64_t n_chunks = (m + ORC_CHUNK_SYMBOLS - 1) / ORC_CHUNK_SYMBOLS;
-  /* every symbol at most 32 bits: at most m words, plus nothing else */
+  /* every symbol at most 32 bits: at most m words, plus nothing else.  The
+   * ROI coder never stores more than the raw windows (it falls back to them),
+   * so the same bound holds for both ROI codings. */
   const orc_layout L = layout_of((uint32_t)p->max_peaks, p, 2u * (uint32_t)p->quant_radius,
-                                 (uint32_t)n_chunks, (uint32_t)m, (uint32_t)m, (uint32_t)m);
+                                 (uint32_t)n_chunks, (uint32_t)m, (uint32_t)m, (uint32_t)m, 1);
   return L.total;
 }
 
 /* a12. Frame assembly.  user_peaks != NULL and n_user_peaks >= 0 replaces the
  * peak finder by a caller-supplied coordinate list (§4.2 allows the regions of
- * interest to be given as coordinates), kept in the order given. */
+ * interest to be given as coordinates), kept in the order given.
+ * Non-hit rejection (§1, §4: frames with too few peaks to index are dropped
+ * before compression): with nhr_min_peaks > 0, a frame whose peak list has
+ * fewer entries is not compressed; the call returns ORC_REJECTED and writes
+ * nothing.  It is off (0) by default. */
 int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_params* p,
                        const uint16_t* user_peaks, int64_t n_user_peaks, uint8_t* out,
                        uint64_t capacity, uint64_t* out_bytes) {
@@ -563,6 +837,10 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
       return st;
     }
   }
+  if ((int64_t)n_peaks < (int64_t)p->nhr_min_peaks) {
+    free(peaks);
+    return ORC_REJECTED;
+  }
 
   /* background path: bin -> prequantise -> Lorenzo -> codes -> histogram */
   float* binned = (float*)malloc(sizeof(float) * m);
@@ -594,13 +872,25 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
     n_lo += codes[i] == 0;
     n_pq += pq[i] != 0;
   }
-  const orc_layout L = layout_of(n_peaks, p, n_symbols, n_chunks, n_lo, n_pq, n_words);
+  const orc_layout L = layout_of(n_peaks, p, n_symbols, n_chunks, n_lo, n_pq, n_words, p->roi_coder == 0);
+  /* the ROI windows, and with the coder their section after the bitstream */
+  const size_t win = (size_t)p->roi_h * p->roi_w;
+  float* roi = (float*)malloc(sizeof(float) * (win * n_peaks + 1));
+  orc_roi_extract(frame, g, p, peaks, n_peaks, roi);
+  uint8_t* roi_sec = NULL;
+  uint64_t roi_bytes = 0;
+  uint32_t roi_coding = 0, roi_words = 0;
+  if (p->roi_coder == 1) {
+    roi_sec = (uint8_t*)malloc(win * n_peaks * 4 + 64);
+    roi_bytes = orc_roi_encode(roi, n_peaks, p->roi_h, p->roi_w, roi_sec, &roi_coding, &roi_words);
+  }
+  const uint64_t total = L.total + roi_bytes;
   if (status == ORC_OK) {
-    *out_bytes = L.total;
-    if (L.total > capacity) status = ORC_ERR_CAPACITY;
+    *out_bytes = total;
+    if (total > capacity) status = ORC_ERR_CAPACITY;
   }
   if (status == ORC_OK) {
-    memset(out, 0, L.total);
+    memset(out, 0, total);
     put_u32(out + 0, ORC_MAGIC);
     put_u32(out + 4, ORC_VERSION);
     put_u32(out + 8, g->n_panels);
@@ -619,14 +909,20 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
     put_u32(out + 52, ORC_CHUNK_SYMBOLS);
     put_u32(out + 56, n_chunks);
     put_u32(out + 60, n_words);
-    put_u64(out + 64, L.total);
+    put_u64(out + 64, total);
     /* Lorenzo dimension: 0 stands for the default 2, so that 2-D streams keep
      * the 24 zero bytes that end the header */
     put_u32(out + 72, p->lorenzo_dims == 2 ? 0u : (uint32_t)p->lorenzo_dims);
+    /* ROI coding (0: raw windows in the ROI section; 1: coded, 2: raw, in a
+     * section after the bitstream), that section's bytes and coded words */
+    put_u32(out + 76, roi_coding);
+    put_u32(out + 80, (uint32_t)roi_bytes);
+    put_u32(out + 84, roi_words);
 
     for (uint32_t k = 0; k < n_peaks; ++k)
       for (int t = 0; t < 3; ++t) put_u16(out + L.peaks + 6 * k + 2 * t, peaks[3 * k + t]);
-    orc_roi_extract(frame, g, p, peaks, n_peaks, (float*)(out + L.roi));
+    if (p->roi_coder == 0) memcpy(out + L.roi, roi, win * n_peaks * 4);
+    else memcpy(out + L.total, roi_sec, roi_bytes);
     memcpy(out + L.lengths, len, n_symbols);
     for (uint32_t k = 0; k < n_chunks; ++k) put_u32(out + L.chunk_index + 4 * k, chunk_index[k]);
     uint32_t a = 0, b = 0;
@@ -648,6 +944,8 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
     for (uint32_t w = 0; w < n_words; ++w) put_u32(out + L.bitstream + 4 * w, words[w]);
   }
 
+  free(roi_sec);
+  free(roi);
   free(words);
   free(chunk_index);
   free(cw);
@@ -688,6 +986,8 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
   const uint64_t total = get_u64(in + 64);
   const uint32_t dims_code = get_u32(in + 72);
   if (dims_code != 0 && dims_code != 1 && dims_code != 3) return ORC_ERR_CORRUPT_STREAM;
+  const uint32_t roi_coding = get_u32(in + 76), roi_bytes = get_u32(in + 80), roi_words = get_u32(in + 84);
+  if (roi_coding > 2 || (roi_coding == 0 && (roi_bytes | roi_words) != 0)) return ORC_ERR_CORRUPT_STREAM;
   const int dims = dims_code == 0 ? 2 : (int)dims_code;
   if (p.bin_h < 1 || p.bin_w < 1 || p.roi_h < 1 || p.roi_w < 1 || p.quant_radius < 2 ||
       p.quant_radius > 512 || chunk != ORC_CHUNK_SYMBOLS)
@@ -697,8 +997,18 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
   if (m != m_hdr || n_chunks != (m + chunk - 1) / chunk || n_lo > m || n_pq > m || n_words > m)
     return ORC_ERR_CORRUPT_STREAM;
   const uint32_t n_symbols = 2u * (uint32_t)p.quant_radius;
-  const orc_layout L = layout_of(n_peaks, &p, n_symbols, n_chunks, n_lo, n_pq, n_words);
-  if (L.total != total || total > in_bytes) return ORC_ERR_CORRUPT_STREAM;
+  const orc_layout L = layout_of(n_peaks, &p, n_symbols, n_chunks, n_lo, n_pq, n_words, roi_coding == 0);
+  if (L.total + roi_bytes != total || total > in_bytes) return ORC_ERR_CORRUPT_STREAM;
+  /* the ROI windows: in place, or decoded from their section */
+  const size_t win = (size_t)p.roi_h * p.roi_w;
+  float* roi = (float*)malloc(sizeof(float) * (win * n_peaks + 1));
+  if (roi_coding == 0) {
+    memcpy(roi, in + L.roi, win * n_peaks * 4);
+  } else if (orc_roi_decode(in + L.total, roi_bytes, roi_coding, roi_words, n_peaks, p.roi_h, p.roi_w, roi) !=
+             ORC_OK) {
+    free(roi);
+    return ORC_ERR_CORRUPT_STREAM;
+  }
 
   /* canonical decoding tables from the code lengths */
   const uint8_t* len = in + L.lengths;
@@ -833,7 +1143,6 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
               bhat[((size_t)pn * hb + r / p.bin_h) * wb + c / p.bin_w];
     /* ROI restoration */
     const uint8_t* pk = in + L.peaks;
-    const size_t win = (size_t)p.roi_h * p.roi_w;
     for (uint32_t k = 0; k < n_peaks && status == ORC_OK; ++k) {
       const uint32_t pn = get_u16(pk + 6 * k), pr = get_u16(pk + 6 * k + 2), pc = get_u16(pk + 6 * k + 4);
       if (pn >= g->n_panels || pr >= g->rows || pc >= g->cols) {
@@ -844,10 +1153,11 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
       for (long i = 0; i < p.roi_h; ++i)
         for (long j = 0; j < p.roi_w; ++j)
           if (in_panel(r0 + i, c0 + j, g->rows, g->cols))
-            memcpy(&frame_out[pn * plane + (size_t)(r0 + i) * g->cols + (size_t)(c0 + j)],
-                   in + L.roi + 4 * (k * win + (size_t)i * p.roi_w + (size_t)j), 4);
+            frame_out[pn * plane + (size_t)(r0 + i) * g->cols + (size_t)(c0 + j)] =
+                roi[k * win + (size_t)i * p.roi_w + (size_t)j];
     }
   }
+  free(roi);
   free(bhat);
   free(delta);
   free(sorted);

@@ -23,7 +23,8 @@ enum {
   ORC_ERR_INVALID_ARG = -1,
   ORC_ERR_CAPACITY = -2,
   ORC_ERR_CORRUPT_STREAM = -3,
-  ORC_ERR_CODE_LENGTH = -7 /* a Huffman code longer than 32 bits (cannot occur below 5,702,887 symbols) */
+  ORC_ERR_CODE_LENGTH = -7, /* a Huffman code longer than 32 bits (cannot occur below 5,702,887 symbols) */
+  ORC_REJECTED = 1          /* non-hit rejection: fewer than nhr_min_peaks peaks, nothing written */
 };
 
 /* Format version 1 constants (the paper defines no container; this one is ours). */
@@ -57,6 +58,8 @@ typedef struct {
   int32_t quant_radius; /* R: codes 1..2R-1 hold |delta| < R, code 0 = outlier */
   int32_t max_peaks;    /* 2048 */
   int32_t lorenzo_dims; /* 1: the frame as one row-major run; 2: each panel (default); 3: the panel stack */
+  int32_t nhr_min_peaks; /* non-hit rejection: frames with fewer peaks are dropped (0 = off) */
+  int32_t roi_coder;     /* 0: raw float32 ROI windows; 1: the predictive lossless ROI coder */
 } orc_params;
 
 /* ---- step-level entry points (each is one row of the method) ---- */
@@ -87,6 +90,15 @@ void orc_canonical_codes(const uint8_t* len, uint32_t n_symbols, uint32_t* code_
 uint32_t orc_pack_chunks(const uint16_t* codes, uint64_t m, const uint8_t* len,
                          const uint32_t* codewords, uint32_t* chunk_index_out,
                          uint32_t* words_out);
+
+/* ---- lossless ROI coding (fpzip-style; see the source) ---- */
+uint32_t orc_roi_order_bits(float x);
+void orc_roi_residuals(const float* win, int32_t h, int32_t w, uint32_t* z_out);
+uint32_t orc_roi_class(uint32_t z);
+uint64_t orc_roi_encode(const float* windows, uint32_t n_windows, int32_t h, int32_t w, uint8_t* out,
+                        uint32_t* coding, uint32_t* n_words);
+int orc_roi_decode(const uint8_t* sec, uint64_t bytes, uint32_t coding, uint32_t n_words, uint32_t n_windows,
+                   int32_t h, int32_t w, float* windows_out);
 
 /* ---- whole-frame entry points ---- */
 uint64_t orc_compress_bound(const orc_geometry* g, const orc_params* p);

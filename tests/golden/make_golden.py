@@ -32,6 +32,11 @@ CASES = [
     ("lorenzo_run_1d", (3, 25, 29), {"peaks": ("fixed", 3), "seed": 105}, {"lorenzo_dims": 1, "abs_eb": 4.0}),
     ("lorenzo_stack_3d", (4, 30, 36), {"peaks": ("uniform", 2, 6), "seed": 106},
      {"lorenzo_dims": 3, "atot_thr": 300.0}),
+    # the lossless ROI coder: windows of hot-pixel pairs, and of Bragg spots
+    ("roi_coded_hot", (2, 40, 48), {"bg_mean": 30.0, "bg_sd": 8.0, "hot_fraction": 0.01,
+                                    "peaks": ("fixed", 3), "seed": 107}, {"roi_coder": 1, "max_peaks": 512}),
+    ("roi_coded_spots", (3, 37, 52), {"peaks": ("uniform", 4, 8), "seed": 108},
+     {"roi_coder": 1, "atot_thr": 300.0, "npix_max": 49}),
 ]
 
 

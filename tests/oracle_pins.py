@@ -111,9 +111,15 @@ def decode_stream(stream: np.ndarray):
     lo = stream[o["lorenzo"]:o["lorenzo"] + 8 * h["n_lorenzo"]].view("<u4").reshape(-1, 2)
     pq = stream[o["prequant"]:o["prequant"] + 8 * h["n_prequant"]].view("<u4").reshape(-1, 2)
     peaks = stream[o["peaks"]:o["peaks"] + 6 * h["n_peaks"]].view("<u2").reshape(-1, 3)
-    roi = stream[o["roi"]:o["roi"] + 4 * h["n_peaks"] * h["roi_h"] * h["roi_w"]].view("<f4")
-    return dict(header=h, codes=codes, lengths=lengths, lorenzo=lo, prequant=pq, peaks=peaks,
-                roi=roi.reshape(-1, h["roi_h"], h["roi_w"]))
+    n_roi = h["n_peaks"] * h["roi_h"] * h["roi_w"]
+    if h["roi_coding"] == 0:
+        roi = stream[o["roi"]:o["roi"] + 4 * n_roi].view("<f4").reshape(-1, h["roi_h"], h["roi_w"])
+    elif h["roi_coding"] == 2:
+        roi = stream[o["roi_section"]:o["roi_section"] + 4 * n_roi].view("<f4").reshape(-1, h["roi_h"], h["roi_w"])
+    else:
+        roi = decode_roi_section(stream[o["roi_section"]:o["end"]], h["n_peaks"], h["roi_h"], h["roi_w"],
+                                 h["roi_words"])[1]
+    return dict(header=h, codes=codes, lengths=lengths, lorenzo=lo, prequant=pq, peaks=peaks, roi=roi)
 
 
 def tiny_frame(seed=0, shape=(2, 12, 13)):
@@ -598,10 +604,212 @@ def pin_nonsquare_bins_roundtrip():
         assert np.array_equal(rec[mask == 1], f[mask == 1])
 
 
+# ---------------------------------------------------------------- ROI coding (§4, fpzip-style)
+def _zigzag(r: int) -> int:
+    r = ((r + (1 << 31)) % (1 << 32)) - (1 << 31)  # as int32
+    return (2 * r) if r >= 0 else (-2 * r - 1)
+
+
+def _float_of_order(m: np.ndarray) -> np.ndarray:
+    """Inverse of the order map, written from its definition: m >= 2^31 came
+    from a sign bit of 0 (u = m - 2^31), m < 2^31 from a sign bit of 1 (u = NOT m)."""
+    m = m.astype(np.uint64)
+    u = np.where(m >= (1 << 31), m - (1 << 31), (~m) & 0xFFFFFFFF)
+    return u.astype(np.uint32).view(np.float32)
+
+
+def decode_roi_section(sec: np.ndarray, n: int, h: int, w: int, n_words: int):
+    """Independent decoder of a coded ROI section: a {(length, codeword): class}
+    map from the canonical rule, bits read one at a time, and the prediction
+    undone as a 2-D prefix sum (cumulative sums down and across, modulo 2^32),
+    which is what inverting the Lorenzo rule amounts to."""
+    lengths = sec[:O.ROI_CLASSES].astype(int)
+    order = sorted((l, c) for c, l in enumerate(lengths) if l > 0)
+    table, code, prev = {}, 0, None
+    for l, c in order:
+        if prev is not None:
+            code = (code + 1) << (l - prev)
+        table[(l, code)] = c
+        prev = l
+    a16 = lambda x: (x + 15) & ~15
+    offs = sec[48:48 + 4 * n].view("<u4")
+    words = sec[48 + a16(4 * n):48 + a16(4 * n) + 4 * n_words].view("<u4")
+    out = np.zeros((n, h, w), np.float32)
+    bits_total = 0
+    for k in range(n):
+        pos = int(offs[k]) * 32
+        start = pos
+
+        def bit():
+            nonlocal pos
+            b = (int(words[pos // 32]) >> (31 - pos % 32)) & 1
+            pos += 1
+            return b
+        z = np.zeros(h * w, np.int64)
+        for i in range(h * w):
+            l, cw = 0, 0
+            while (l, cw) not in table:
+                cw = (cw << 1) | bit()
+                l += 1
+                assert l <= 32
+            c = table[(l, cw)]
+            v = 0 if c == 0 else 1
+            for _ in range(c - 1):
+                v = (v << 1) | bit()
+            z[i] = v
+        bits_total += pos - start
+        r = np.where(z & 1, -((z + 1) >> 1), z >> 1)  # unfold
+        r = r.reshape(h, w)
+        r[0, 0] += 1 << 31  # the first value was predicted by m(+0.0) = 2^31
+        m = np.cumsum(np.cumsum(r, axis=0), axis=1) % (1 << 32)
+        out[k] = _float_of_order(m)
+    return lengths, out, bits_total
+
+
+def pin_roi_order_and_classes():
+    xs = np.array([-np.inf, -3e38, -1.0, -1e-40, -0.0, 0.0, 1e-40, 1.0, 2.0, 3e38, np.inf], np.float32)
+    m = [O.roi_order_bits(float(x)) for x in xs]
+    assert all(a < b for a, b in zip(m, m[1:])), "the integer order is the float order"
+    assert O.roi_order_bits(0.0) == 1 << 31 and O.roi_order_bits(-0.0) == (1 << 31) - 1
+    assert O.roi_order_bits(1.0) == 0x3F800000 + (1 << 31)
+    for z, c in ((0, 0), (1, 1), (2, 2), (3, 2), (4, 3), (255, 8), (1 << 31, 32), (0xFFFFFFFF, 32)):
+        assert O.roi_class(z) == c, (z, c)
+
+
+def pin_roi_residual_closed_forms():
+    # a constant window: only the first value carries anything
+    for x in (0.0, 37.5, -2.25):
+        z = O.roi_residuals(np.full((5, 7), x, np.float32))
+        assert z[0, 0] == _zigzag(O.roi_order_bits(x) - (1 << 31))
+        assert np.count_nonzero(z) == (z[0, 0] != 0)
+    # float bits in a plane u = U0 + A i + B j: the 2-D predictor is exact inside,
+    # the first row differs by B, the first column by A (A != B catches a swap)
+    i, j = np.mgrid[0:6, 0:9]
+    for sign in (0, 1):
+        U0, A, B = 0x3F800000, 3, -2
+        u = (U0 + A * i + B * j).astype(np.uint32) | np.uint32(sign << 31)
+        z = O.roi_residuals(u.view(np.float32))
+        s = -1 if sign else 1  # NOT u reverses the order of negative floats
+        assert z[0, 0] == _zigzag(O.roi_order_bits(float(u.view(np.float32)[0, 0])) - (1 << 31))
+        assert np.all(z[0, 1:] == _zigzag(s * B)), "first row: the left neighbour predicts"
+        assert np.all(z[1:, 0] == _zigzag(s * A)), "first column: the value above predicts"
+        assert np.all(z[1:, 1:] == 0), "inside: the Lorenzo rule is exact on a plane"
+
+
+def pin_roi_roundtrip_and_independent_decoder():
+    rng = np.random.default_rng(7)
+    cases = [rng.normal(30, 8, (6, 17, 17)).astype(np.float32),       # background-like windows
+             (rng.normal(30, 8, (3, 5, 3)) + np.arange(3)).astype(np.float32),
+             rng.normal(0, 1e-3, (2, 9, 11)).astype(np.float32)]
+    spec = rng.normal(100, 5, (2, 7, 7)).astype(np.float32)
+    spec[0, 1, 1] = np.nan
+    spec[0, 2, 2] = np.array([0xFFC01234], np.uint32).view(np.float32)[0]  # NaN with a payload
+    spec[0, 3, 3], spec[0, 4, 4], spec[1, 0, 0], spec[1, 6, 6] = np.inf, -np.inf, -0.0, 1e-42
+    cases.append(spec)
+    cases.append(np.full((1, 1, 1), 5.0, np.float32))
+    for win in cases:
+        coding, nw, sec = O.roi_encode(win)
+        n, h, w = win.shape
+        st, dec = O.roi_decode(sec, coding, nw, n, h, w)
+        assert st == O.OK and np.array_equal(dec.view(np.uint32), win.view(np.uint32)), "lossless, bit for bit"
+        if coding == 2:
+            assert np.array_equal(sec[:win.size * 4].view(np.float32).view(np.uint32), win.ravel().view(np.uint32))
+            continue
+        lengths, dec2, bits = decode_roi_section(sec, n, h, w, nw)
+        assert np.array_equal(dec2.view(np.uint32), win.view(np.uint32)), "the independent decoder agrees"
+        # the code is a complete prefix code, optimal for the class counts
+        cls = np.array([O.roi_class(int(z)) for wi in win for z in O.roi_residuals(wi).ravel()])
+        counts = np.bincount(cls, minlength=O.ROI_CLASSES)
+        used = lengths[lengths > 0]
+        if len(used) > 1:
+            assert sum(2.0 ** -l for l in used) == 1.0
+        extra = int(np.maximum(cls - 1, 0).sum())
+        assert bits == heap_huffman_cost(counts) + extra, "Huffman-optimal classes plus the raw low bits"
+        assert len(sec) == 48 + ((4 * n + 15) & ~15) + ((4 * nw + 15) & ~15)
+    # incompressible windows (random bit patterns) fall back to the raw floats
+    raw = rng.integers(0, 1 << 32, (4, 17, 17), dtype=np.uint64).astype(np.uint32).view(np.float32)
+    coding, nw, sec = O.roi_encode(raw)
+    assert coding == 2 and nw == 0 and np.array_equal(sec[:raw.size * 4], raw.view(np.uint8).ravel())
+    assert O.roi_decode(sec, 2, 0, 4, 17, 17)[0] == O.OK
+
+
+def pin_roi_corrupt_sections():
+    rng = np.random.default_rng(8)
+    win = rng.normal(30, 8, (3, 17, 17)).astype(np.float32)
+    coding, nw, sec = O.roi_encode(win)
+    assert coding == 1
+    ok = lambda s, c=coding, w=nw: O.roi_decode(s, c, w, 3, 17, 17)[0]
+    assert ok(sec) == O.OK
+    assert ok(sec[:-16]) == O.ERR_CORRUPT_STREAM, "short section"
+    assert ok(sec, w=nw + 4) == O.ERR_CORRUPT_STREAM, "word count off"
+    bad = sec.copy()
+    bad[0] = 40
+    assert ok(bad) == O.ERR_CORRUPT_STREAM, "code length above 32"
+    bad = sec.copy()
+    bad[int(np.flatnonzero(sec[:33])[0])] += 1
+    assert ok(bad) == O.ERR_CORRUPT_STREAM, "incomplete code"
+    bad = sec.copy()
+    bad[48:52] = np.array([1], "<u4").view(np.uint8)
+    assert ok(bad) == O.ERR_CORRUPT_STREAM, "first window must start at word 0"
+    bad = sec.copy()
+    bad[52:56], bad[56:60] = bad[56:60].copy(), bad[52:56].copy()
+    assert ok(bad) == O.ERR_CORRUPT_STREAM, "window offsets out of order"
+    assert ok(sec, c=3) == O.ERR_CORRUPT_STREAM
+
+
+def pin_roi_frame():
+    """With the ROI coder the stream differs from the raw one only in where the
+    windows live: the same header counts, peaks, lengths, index, outliers and
+    bitstream, then a section that decodes to the raw windows."""
+    f = tiny_frame(3, shape=(3, 30, 36))
+    for i, (pn, r, c) in enumerate(((0, 8, 9), (1, 20, 25), (2, 2, 3))):
+        f[pn, r - 1:r + 2, c - 1:c + 2] += 900.0 + 50 * i
+    base = O.make_params(atot_thr=300.0)
+    st0, s0 = O.compress_frame(f, base)
+    p1 = O.make_params(atot_thr=300.0, roi_coder=1)
+    s1, dec1, rec1 = _roundtrip(f, p1)
+    h0, h1 = O.parse_header(s0), O.parse_header(s1)
+    assert st0 == O.OK and h0["n_peaks"] >= 3 and h0["roi_coding"] == 0
+    assert h1["roi_coding"] in (1, 2) and h1["roi_bytes"] > 0
+    o0, o1 = O.section_offsets(h0), O.section_offsets(h1)
+    assert o1["lengths"] == o1["roi"], "no windows in the ROI section"
+    assert np.array_equal(s0[o0["lengths"]:o0["end"]], s1[o1["lengths"]:o1["roi_section"]])
+    assert np.array_equal(s0[:o0["roi"]][:64], s1[:64]) and np.array_equal(s0[96:o0["roi"]], s1[96:o1["roi"]])
+    assert len(s1) == o1["end"] == h1["total_bytes"]
+    win = O.roi_extract(f, base, dec1["peaks"])
+    coding, nw, sec = O.roi_encode(win)
+    assert (coding, nw) == (h1["roi_coding"], h1["roi_words"]) and np.array_equal(s1[o1["roi_section"]:], sec)
+    st, rec0 = O.decompress_frame(s0, f.shape)
+    assert st == O.OK and np.array_equal(rec0.view(np.uint32), rec1.view(np.uint32)), "same frame back"
+    bad = s1.copy()
+    bad[80:84] = np.array([h1["roi_bytes"] - 16], "<u4").view(np.uint8)
+    assert O.decompress_frame(bad, f.shape)[0] == O.ERR_CORRUPT_STREAM
+
+
+def pin_non_hit_rejection():
+    f = tiny_frame(3, shape=(3, 30, 36))
+    for i, (pn, r, c) in enumerate(((0, 8, 9), (1, 20, 25), (2, 2, 3))):
+        f[pn, r - 1:r + 2, c - 1:c + 2] += 900.0 + 50 * i
+    p = O.make_params(atot_thr=300.0)
+    st, peaks, n = O.find_peaks(f, p)
+    assert st == O.OK and n >= 3
+    st, ref = O.compress_frame(f, p)
+    st_eq, s_eq = O.compress_frame(f, O.make_params(atot_thr=300.0, nhr_min_peaks=n))
+    assert st_eq == O.OK and np.array_equal(s_eq, ref), "a hit with exactly nhr_min_peaks peaks is kept, unchanged"
+    assert O.compress_frame(f, O.make_params(atot_thr=300.0, nhr_min_peaks=n + 1))[0] == O.REJECTED
+    up = np.array([[0, 1, 1]], np.uint16)
+    assert O.compress_frame(f, O.make_params(nhr_min_peaks=2), user_peaks=up)[0] == O.REJECTED
+    assert O.compress_frame(f, O.make_params(nhr_min_peaks=1), user_peaks=up)[0] == O.OK
+    # too many peaks is still CAPACITY, whatever the rejection threshold
+    assert O.compress_frame(f, O.make_params(atot_thr=300.0, max_peaks=1, nhr_min_peaks=5))[0] == O.ERR_CAPACITY
+
+
 ALL_PINS = [
     pin_candidates_brute_force, pin_candidate_special_cases, pin_evaluation_special_cases,
     pin_evaluation_brute_force, pin_find_peaks_frame, pin_roi, pin_binning, pin_prequantize,
     pin_lorenzo, pin_codes_histogram, pin_huffman_small, pin_huffman_optimal, pin_pack_decode,
     pin_frame_roundtrip, pin_identity_binning_bound, pin_user_peaks_and_corruption,
     pin_nonsquare_bins_roundtrip, pin_lorenzo_dims, pin_lorenzo_dims_roundtrip,
+    pin_roi_order_and_classes, pin_roi_residual_closed_forms, pin_roi_roundtrip_and_independent_decoder,
+    pin_roi_corrupt_sections, pin_roi_frame, pin_non_hit_rejection,
 ]

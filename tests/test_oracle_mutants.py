@@ -67,7 +67,20 @@ MUTANTS = {
     "inverse_diag_sign": ("= delta[base + (size_t)i * wb + j] + up + left - diag;", "= delta[base + (size_t)i * wb + j] + up + left + diag;"),
     "inverse1_resets_at_rows": ("q[k] = delta[k] + (k > 0 ? q[k - 1] : 0);", "q[k] = delta[k] + (k % wb > 0 ? q[k - 1] : 0);"),
     "inverse3_corner_sign": ("+ corner[1][1][1];\n            q[(size_t)pn", "- corner[1][1][1];\n            q[(size_t)pn"),
-    "restore_skips_roi": ("memcpy(&frame_out[pn * plane + (size_t)(r0 + i) * g->cols + (size_t)(c0 + j)],", "if (0) memcpy(&frame_out[pn * plane + (size_t)(r0 + i) * g->cols + (size_t)(c0 + j)],"),
+    "restore_skips_roi": ("            frame_out[pn * plane + (size_t)(r0 + i) * g->cols + (size_t)(c0 + j)] =",
+                          "            if (0) frame_out[pn * plane + (size_t)(r0 + i) * g->cols + (size_t)(c0 + j)] ="),
+    # ROI coding (§4, fpzip-style) and non-hit rejection (§1, §4)
+    "roi_order_ignores_sign": ("return (u & 0x80000000u) ? ~u : (u | 0x80000000u);", "return u | 0x80000000u;"),
+    "roi_pred_no_diag": ("pred = up + left - diag;", "pred = up + left;"),
+    "roi_first_pred_zero": ("        pred = 0x80000000u;\n", "        pred = 0u;\n"),
+    "roi_zigzag_swapped": ("r >= 0 ? 2u * (uint32_t)r : 2u * (uint32_t)(-(int64_t)r) - 1u;",
+                           "r >= 0 ? 2u * (uint32_t)r + 1u : 2u * (uint32_t)(-(int64_t)r) - 2u;"),
+    "roi_class_short": ("  while (z) {\n    ++c;", "  while (z > 1) {\n    ++c;"),
+    "roi_extra_lsb_first": ("for (int b = (int)c - 2; b >= 0; --b, ++bit)", "for (int b = 0; b <= (int)c - 2; ++b, ++bit)"),
+    "roi_no_fallback": ("if (n_windows == 0 || roi_coded_bytes(n_windows, (uint32_t)words) >= raw) {",
+                        "if (n_windows == 0) {"),
+    "roi_section_size_not_in_header": ("put_u32(out + 80, (uint32_t)roi_bytes);", "put_u32(out + 80, 0u);"),
+    "nhr_inclusive": ("if ((int64_t)n_peaks < (int64_t)p->nhr_min_peaks) {", "if ((int64_t)n_peaks <= (int64_t)p->nhr_min_peaks) {"),
     "upsample_wrong_axis": ("bhat[((size_t)pn * hb + r / p.bin_h) * wb + c / p.bin_w];", "bhat[((size_t)pn * hb + r / p.bin_w) * wb + c / p.bin_h];"),
 }
 
