@@ -48,13 +48,14 @@ class Params(ctypes.Structure):
         ("bin_h", ctypes.c_int32), ("bin_w", ctypes.c_int32),
         ("abs_eb", ctypes.c_float), ("quant_radius", ctypes.c_int32), ("max_peaks", ctypes.c_int32),
         ("lorenzo_dims", ctypes.c_int32), ("nhr_min_peaks", ctypes.c_int32), ("roi_coder", ctypes.c_int32),
+        ("chunk_frames", ctypes.c_int32),
     ]
 
 
 DEFAULTS = dict(amax_thr=300.0, atot_thr=600.0, son_min=10.0, pix_nsigma=3.0, rank=3,
                 ring_r0=5, ring_dr=2, npix_min=2, npix_max=30, roi_h=17, roi_w=17,
                 bin_h=2, bin_w=2, abs_eb=10.0, quant_radius=512, max_peaks=2048, lorenzo_dims=2,
-                nhr_min_peaks=0, roi_coder=0)
+                nhr_min_peaks=0, roi_coder=0, chunk_frames=1)
 
 
 def make_params(**kw) -> Params:
@@ -112,6 +113,8 @@ def _bind(path: str):
         "orc_compress_bound": (u64, [G, Pr]),
         "orc_compress_frame": (ctypes.c_int, [P, G, Pr, P, i64, P, u64, P]),
         "orc_decompress_frame": (ctypes.c_int, [P, u64, G, P]),
+        "orc_compress_frames": (ctypes.c_int, [P, u32, G, Pr, P, P, P, u64, P, P]),
+        "orc_decompress_frames": (ctypes.c_int, [P, u64, P, u32, G, P, P]),
     }
     _SIGNATURES = sorted(sig)
     for name, (res, args) in sig.items():
@@ -341,6 +344,52 @@ def compress_frame(frame: np.ndarray, params: Params, user_peaks=None, capacity=
     return st, out[: nbytes.value].copy()
 
 
+def compress_frames(frames: np.ndarray, params: Params, user_peaks=None, n_user=None, stride=None):
+    """A call of frames (chunks of params.chunk_frames share a codebook).
+    user_peaks: u16 [n, max_peaks, 3] with n_user[f] entries each (or None).
+    Returns (status int32 [n], streams: list of uint8 arrays or None, sizes int64 [n])."""
+    frames = np.ascontiguousarray(frames, dtype=np.float32)
+    n = frames.shape[0]
+    g = Geometry(*frames.shape[1:])
+    st_ = stride or compress_bound(frames.shape[1:], params)
+    outs = np.zeros((n, max(int(st_), 16)), np.uint8)
+    sizes = np.zeros(n, np.uint64)
+    status = np.zeros(n, np.int32)
+    up = nu = None
+    if user_peaks is not None:
+        upa = np.ascontiguousarray(user_peaks, dtype=np.uint16)
+        nua = np.ascontiguousarray(n_user, dtype=np.int64)
+        up, nu = _ptr(upa), _ptr(nua)
+    lib().orc_compress_frames(_ptr(frames), n, ctypes.byref(g), ctypes.byref(params), up, nu, _ptr(outs),
+                              outs.shape[1], _ptr(sizes), _ptr(status))
+    streams = [outs[k, :sizes[k]].copy() if status[k] == OK else None for k in range(n)]
+    return status, streams, sizes.astype(np.int64)
+
+
+def pack_streams(streams):
+    """Streams back to back, each padded to 16 bytes: (buffer, offsets)."""
+    offs, pos = [], 0
+    for s in streams:
+        offs.append(pos)
+        pos += (len(s) + 15) // 16 * 16
+    buf = np.zeros(max(pos, 16), np.uint8)
+    for o, s in zip(offs, streams):
+        buf[o:o + len(s)] = s
+    return buf, np.array(offs, np.uint64)
+
+
+def decompress_frames(streams, shape):
+    """A call of streams (a stream may take its code lengths from its chunk's
+    head earlier in the call).  Returns (status int32 [n], frames float32)."""
+    buf, offs = pack_streams(streams)
+    n = len(streams)
+    out = np.zeros((n, *shape), np.float32)
+    status = np.zeros(n, np.int32)
+    g = Geometry(*shape)
+    lib().orc_decompress_frames(_ptr(buf), buf.size, _ptr(offs), n, ctypes.byref(g), _ptr(out), _ptr(status))
+    return status, out
+
+
 def decompress_frame(stream: np.ndarray, shape):
     s = np.ascontiguousarray(stream, dtype=np.uint8)
     out = np.zeros(shape, np.float32)
@@ -353,7 +402,7 @@ def parse_header(stream: np.ndarray) -> dict:
     """Field view of the 96-byte frame header (format version 1)."""
     b = np.ascontiguousarray(stream[:HEADER_BYTES], dtype=np.uint8)
     u32 = b[:64].view(np.uint32)
-    tail = b[76:88].view(np.uint32)
+    tail = b[76:92].view(np.uint32)
     u16 = b[20:28].view(np.uint16)
     return dict(magic=int(u32[0]), version=int(u32[1]), n_panels=int(u32[2]), rows=int(u32[3]),
                 cols=int(u32[4]), roi_h=int(u16[0]), roi_w=int(u16[1]), bin_h=int(u16[2]),
@@ -363,7 +412,7 @@ def parse_header(stream: np.ndarray) -> dict:
                 n_chunks=int(u32[14]), n_words=int(u32[15]),
                 total_bytes=int(b[64:72].view(np.uint64)[0]),
                 lorenzo_dims={0: 2}.get(int(b[72:76].view(np.uint32)[0]), int(b[72:76].view(np.uint32)[0])),
-                roi_coding=int(tail[0]), roi_bytes=int(tail[1]), roi_words=int(tail[2]))
+                roi_coding=int(tail[0]), roi_bytes=int(tail[1]), roi_words=int(tail[2]), back_ref=int(tail[3]))
 
 
 def section_offsets(h: dict) -> dict:
@@ -373,7 +422,7 @@ def section_offsets(h: dict) -> dict:
     o["roi"] = o["peaks"] + a16(h["n_peaks"] * 6)
     in_place = h.get("roi_coding", 0) == 0
     o["lengths"] = o["roi"] + (a16(h["n_peaks"] * h["roi_h"] * h["roi_w"] * 4) if in_place else 0)
-    o["chunk_index"] = o["lengths"] + a16(2 * h["quant_radius"])
+    o["chunk_index"] = o["lengths"] + (a16(2 * h["quant_radius"]) if h.get("back_ref", 0) == 0 else 0)
     o["lorenzo"] = o["chunk_index"] + a16(h["n_chunks"] * 4)
     o["prequant"] = o["lorenzo"] + a16(h["n_lorenzo"] * 8)
     o["bitstream"] = o["prequant"] + a16(h["n_prequant"] * 8)

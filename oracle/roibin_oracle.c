@@ -750,12 +750,12 @@ typedef struct {
  * ROI section is empty. */
 static orc_layout layout_of(uint32_t n_peaks, const orc_params* p, uint32_t n_symbols,
                             uint32_t n_chunks, uint32_t n_lo, uint32_t n_pq, uint32_t words,
-                            int roi_in_place) {
+                            int roi_in_place, int lengths_here) {
   orc_layout L;
   L.peaks = ORC_HEADER_BYTES;
   L.roi = L.peaks + align16((uint64_t)n_peaks * 6);
   L.lengths = L.roi + (roi_in_place ? align16((uint64_t)n_peaks * p->roi_h * p->roi_w * 4) : 0);
-  L.chunk_index = L.lengths + align16(n_symbols);
+  L.chunk_index = L.lengths + (lengths_here ? align16(n_symbols) : 0);
   L.lorenzo = L.chunk_index + align16((uint64_t)n_chunks * 4);
   L.prequant = L.lorenzo + align16((uint64_t)n_lo * 8);
   L.bitstream = L.prequant + align16((uint64_t)n_pq * 8);
@@ -775,6 +775,7 @@ static int params_valid(const orc_geometry* g, const orc_params* p) {
   if (p->lorenzo_dims < 1 || p->lorenzo_dims > 3) return 0;
   if (p->nhr_min_peaks < 0 || p->nhr_min_peaks > 8192) return 0;
   if (p->roi_coder < 0 || p->roi_coder > 1) return 0;
+  if (p->chunk_frames < 1 || p->chunk_frames > 64) return 0;
   if (!(p->pix_nsigma >= 0.0f)) return 0;
   if (!(p->abs_eb > 0.0f) || !isfinite(2.0f * p->abs_eb) || !isfinite(1.0f / (2.0f * p->abs_eb)))
     return 0;
@@ -792,40 +793,60 @@ uint64_t orc_compress_bound(const orc_geometry* g, const orc_params* p) {
    * ROI coder never stores more than the raw windows (it falls back to them),
    * so the same bound holds for both ROI codings. */
   const orc_layout L = layout_of((uint32_t)p->max_peaks, p, 2u * (uint32_t)p->quant_radius,
-                                 (uint32_t)n_chunks, (uint32_t)m, (uint32_t)m, (uint32_t)m, 1);
+                                 (uint32_t)n_chunks, (uint32_t)m, (uint32_t)m, (uint32_t)m, 1, 1);
   return L.total;
 }
 
-/* a12. Frame assembly.  user_peaks != NULL and n_user_peaks >= 0 replaces the
+/* One frame's work up to its histogram (a1-a8).  A frame is "coded" when its
+ * status is still ORC_OK here; only coded frames feed a chunk's codebook. */
+typedef struct {
+  int status;
+  uint16_t* peaks;
+  uint32_t n_peaks;
+  float* binned;
+  uint8_t* pq;
+  int32_t* delta;
+  uint16_t* codes;
+  uint64_t* hist;
+} orc_frame_work;
+
+static void work_free(orc_frame_work* w) {
+  free(w->peaks);
+  free(w->binned);
+  free(w->pq);
+  free(w->delta);
+  free(w->codes);
+  free(w->hist);
+  memset(w, 0, sizeof(*w));
+}
+
+/* a1-a8 for one frame.  user_peaks != NULL and n_user_peaks >= 0 replaces the
  * peak finder by a caller-supplied coordinate list (§4.2 allows the regions of
  * interest to be given as coordinates), kept in the order given.
  * Non-hit rejection (§1, §4: frames with too few peaks to index are dropped
  * before compression): with nhr_min_peaks > 0, a frame whose peak list has
- * fewer entries is not compressed; the call returns ORC_REJECTED and writes
- * nothing.  It is off (0) by default. */
-int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_params* p,
-                       const uint16_t* user_peaks, int64_t n_user_peaks, uint8_t* out,
-                       uint64_t capacity, uint64_t* out_bytes) {
-  *out_bytes = 0;
-  if (!params_valid(g, p)) return ORC_ERR_INVALID_ARG;
+ * fewer entries is not compressed and gets ORC_REJECTED.  Off (0) by default. */
+static void frame_analyse(const float* frame, const orc_geometry* g, const orc_params* p, const uint16_t* user_peaks,
+                          int64_t n_user_peaks, orc_frame_work* w) {
+  memset(w, 0, sizeof(*w));
   const uint32_t hb = (g->rows + p->bin_h - 1) / p->bin_h, wb = (g->cols + p->bin_w - 1) / p->bin_w;
   const uint64_t m = (uint64_t)g->n_panels * hb * wb;
   const uint32_t n_symbols = 2u * (uint32_t)p->quant_radius;
-  const uint32_t n_chunks = (uint32_t)((m + ORC_CHUNK_SYMBOLS - 1) / ORC_CHUNK_SYMBOLS);
 
   /* peaks */
   uint16_t* peaks = (uint16_t*)malloc(sizeof(uint16_t) * 3 * ((size_t)p->max_peaks + 1));
+  w->peaks = peaks;
   uint32_t n_peaks = 0;
   if (user_peaks != NULL && n_user_peaks >= 0) {
     if (n_user_peaks > p->max_peaks) {
-      free(peaks);
-      return ORC_ERR_CAPACITY;
+      w->status = ORC_ERR_CAPACITY;
+      return;
     }
     for (int64_t k = 0; k < n_user_peaks; ++k) {
       if (user_peaks[3 * k] >= g->n_panels || user_peaks[3 * k + 1] >= g->rows ||
           user_peaks[3 * k + 2] >= g->cols) {
-        free(peaks);
-        return ORC_ERR_INVALID_ARG;
+        w->status = ORC_ERR_INVALID_ARG;
+        return;
       }
       memcpy(peaks + 3 * k, user_peaks + 3 * k, 6);
     }
@@ -833,14 +854,15 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
   } else {
     const int st = orc_find_peaks(frame, g, p, peaks, (uint32_t)p->max_peaks, &n_peaks);
     if (st != ORC_OK) {
-      free(peaks);
-      return st;
+      w->status = st;
+      return;
     }
   }
   if ((int64_t)n_peaks < (int64_t)p->nhr_min_peaks) {
-    free(peaks);
-    return ORC_REJECTED;
+    w->status = ORC_REJECTED;
+    return;
   }
+  w->n_peaks = n_peaks;
 
   /* background path: bin -> prequantise -> Lorenzo -> codes -> histogram */
   float* binned = (float*)malloc(sizeof(float) * m);
@@ -849,17 +871,42 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
   int32_t* delta = (int32_t*)malloc(sizeof(int32_t) * m);
   uint16_t* codes = (uint16_t*)malloc(sizeof(uint16_t) * m);
   uint64_t* hist = (uint64_t*)malloc(sizeof(uint64_t) * n_symbols);
-  uint8_t* len = (uint8_t*)malloc(n_symbols);
-  uint32_t* cw = (uint32_t*)malloc(sizeof(uint32_t) * n_symbols);
-  uint32_t* chunk_index = (uint32_t*)malloc(sizeof(uint32_t) * n_chunks);
-  uint32_t* words = (uint32_t*)malloc(sizeof(uint32_t) * (m + 1));
-
   orc_bin(frame, g, p->bin_h, p->bin_w, binned);
   orc_prequantize(binned, m, p->abs_eb, q, pq);
   orc_lorenzo_nd(q, g->n_panels, hb, wb, p->lorenzo_dims, delta);
   orc_quant_codes(delta, m, p->quant_radius, codes);
   orc_histogram(codes, m, n_symbols, hist);
-  int status = orc_huffman_lengths(hist, n_symbols, len);
+  free(q);
+  w->binned = binned;
+  w->pq = pq;
+  w->delta = delta;
+  w->codes = codes;
+  w->hist = hist;
+  w->status = ORC_OK;
+}
+
+/* a10-a12 for one coded frame with the codebook `len` (status cb_status from
+ * a9).  back_ref = 0: the stream carries the code lengths; back_ref = b > 0:
+ * the lengths live in the stream b frames earlier in the same call (the head
+ * of its chunk), and this stream has none. */
+static int frame_assemble(const float* frame, const orc_geometry* g, const orc_params* p, const orc_frame_work* w,
+                          const uint8_t* len, int cb_status, uint32_t back_ref, uint8_t* out, uint64_t capacity,
+                          uint64_t* out_bytes) {
+  *out_bytes = 0;
+  const uint32_t hb = (g->rows + p->bin_h - 1) / p->bin_h, wb = (g->cols + p->bin_w - 1) / p->bin_w;
+  const uint64_t m = (uint64_t)g->n_panels * hb * wb;
+  const uint32_t n_symbols = 2u * (uint32_t)p->quant_radius;
+  const uint32_t n_chunks = (uint32_t)((m + ORC_CHUNK_SYMBOLS - 1) / ORC_CHUNK_SYMBOLS);
+  const uint16_t* peaks = w->peaks;
+  const uint32_t n_peaks = w->n_peaks;
+  const float* binned = w->binned;
+  const uint8_t* pq = w->pq;
+  const int32_t* delta = w->delta;
+  const uint16_t* codes = w->codes;
+  uint32_t* cw = (uint32_t*)malloc(sizeof(uint32_t) * n_symbols);
+  uint32_t* chunk_index = (uint32_t*)malloc(sizeof(uint32_t) * n_chunks);
+  uint32_t* words = (uint32_t*)malloc(sizeof(uint32_t) * (m + 1));
+  int status = cb_status;
   uint32_t n_words = 0;
   if (status == ORC_OK) {
     orc_canonical_codes(len, n_symbols, cw);
@@ -872,7 +919,8 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
     n_lo += codes[i] == 0;
     n_pq += pq[i] != 0;
   }
-  const orc_layout L = layout_of(n_peaks, p, n_symbols, n_chunks, n_lo, n_pq, n_words, p->roi_coder == 0);
+  const orc_layout L =
+      layout_of(n_peaks, p, n_symbols, n_chunks, n_lo, n_pq, n_words, p->roi_coder == 0, back_ref == 0);
   /* the ROI windows, and with the coder their section after the bitstream */
   const size_t win = (size_t)p->roi_h * p->roi_w;
   float* roi = (float*)malloc(sizeof(float) * (win * n_peaks + 1));
@@ -918,12 +966,14 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
     put_u32(out + 76, roi_coding);
     put_u32(out + 80, (uint32_t)roi_bytes);
     put_u32(out + 84, roi_words);
+    /* where the code lengths are: 0 here, b in the stream b frames earlier */
+    put_u32(out + 88, back_ref);
 
     for (uint32_t k = 0; k < n_peaks; ++k)
       for (int t = 0; t < 3; ++t) put_u16(out + L.peaks + 6 * k + 2 * t, peaks[3 * k + t]);
     if (p->roi_coder == 0) memcpy(out + L.roi, roi, win * n_peaks * 4);
     else memcpy(out + L.total, roi_sec, roi_bytes);
-    memcpy(out + L.lengths, len, n_symbols);
+    if (back_ref == 0) memcpy(out + L.lengths, len, n_symbols);
     for (uint32_t k = 0; k < n_chunks; ++k) put_u32(out + L.chunk_index + 4 * k, chunk_index[k]);
     uint32_t a = 0, b = 0;
     for (uint64_t i = 0; i < m; ++i) {
@@ -941,7 +991,7 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
         ++b;
       }
     }
-    for (uint32_t w = 0; w < n_words; ++w) put_u32(out + L.bitstream + 4 * w, words[w]);
+    for (uint32_t w2 = 0; w2 < n_words; ++w2) put_u32(out + L.bitstream + 4 * w2, words[w2]);
   }
 
   free(roi_sec);
@@ -949,14 +999,82 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
   free(words);
   free(chunk_index);
   free(cw);
+  return status;
+}
+
+/* a9 + a12 over a call of n_frames frames (frames[f] at f * frame_px).  Chunks
+ * (§5.3.4: a compressor call takes 1-64 events) are the frames f with the same
+ * f / chunk_frames.  A chunk's coded frames share one Huffman codebook, built
+ * from the sum of their histograms; the first coded frame of the chunk (its
+ * head) stores the code lengths, and each later one records how many frames
+ * back its head is.  chunk_frames = 1 gives each frame its own codebook.
+ *   user_peaks   NULL, or u16[n_frames][max_peaks][3] with n_user_peaks[f]
+ *                entries for frame f (n_user_peaks[f] < 0: the finder runs);
+ *   outs         n_frames slots of `stride` bytes; out_bytes[f] the stream's
+ *                size (on ORC_ERR_CAPACITY the size it needs), status[f] its
+ *                outcome (ORC_OK, ORC_REJECTED or an error). */
+int orc_compress_frames(const float* frames, uint32_t n_frames, const orc_geometry* g, const orc_params* p,
+                        const uint16_t* user_peaks, const int64_t* n_user_peaks, uint8_t* outs, uint64_t stride,
+                        uint64_t* out_bytes, int32_t* status) {
+  for (uint32_t f = 0; f < n_frames; ++f) {
+    out_bytes[f] = 0;
+    status[f] = ORC_ERR_INVALID_ARG;
+  }
+  if (!params_valid(g, p)) return ORC_ERR_INVALID_ARG;
+  const size_t frame_px = (size_t)g->n_panels * g->rows * g->cols;
+  const uint32_t n_symbols = 2u * (uint32_t)p->quant_radius;
+  const uint32_t C = (uint32_t)p->chunk_frames;
+  orc_frame_work* w = (orc_frame_work*)calloc(n_frames + 1, sizeof(orc_frame_work));
+  for (uint32_t f = 0; f < n_frames; ++f) {
+    const uint16_t* up = user_peaks ? user_peaks + (size_t)f * (size_t)p->max_peaks * 3 : NULL;
+    const int64_t nu = user_peaks ? n_user_peaks[f] : -1;
+    frame_analyse(frames + f * frame_px, g, p, up, nu, &w[f]);
+    status[f] = w[f].status;
+  }
+  uint64_t* hsum = (uint64_t*)malloc(sizeof(uint64_t) * n_symbols);
+  uint8_t* len = (uint8_t*)malloc(n_symbols);
+  for (uint32_t c0 = 0; c0 < n_frames; c0 += C) {
+    const uint32_t c1 = c0 + C < n_frames ? c0 + C : n_frames;
+    /* a9 once per chunk: the Huffman code of the chunk's summed histogram */
+    memset(hsum, 0, sizeof(uint64_t) * n_symbols);
+    int64_t head = -1;
+    for (uint32_t f = c0; f < c1; ++f) {
+      if (w[f].status != ORC_OK) continue;
+      if (head < 0) head = f;
+      for (uint32_t s2 = 0; s2 < n_symbols; ++s2) hsum[s2] += w[f].hist[s2];
+    }
+    if (head < 0) continue;
+    const int cb = orc_huffman_lengths(hsum, n_symbols, len);
+    for (uint32_t f = c0; f < c1; ++f) {
+      if (w[f].status != ORC_OK) continue;
+      status[f] = frame_assemble(frames + f * frame_px, g, p, &w[f], len, cb, f - (uint32_t)head,
+                                 outs + f * stride, stride, &out_bytes[f]);
+    }
+  }
+  for (uint32_t f = 0; f < n_frames; ++f) work_free(&w[f]);
+  free(w);
+  free(hsum);
   free(len);
-  free(hist);
-  free(codes);
-  free(delta);
-  free(pq);
-  free(q);
-  free(binned);
-  free(peaks);
+  return ORC_OK;
+}
+
+/* a12. One frame on its own: a call of one frame (its own codebook). */
+int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_params* p,
+                       const uint16_t* user_peaks, int64_t n_user_peaks, uint8_t* out,
+                       uint64_t capacity, uint64_t* out_bytes) {
+  *out_bytes = 0;
+  if (!params_valid(g, p)) return ORC_ERR_INVALID_ARG;
+  orc_frame_work w;
+  frame_analyse(frame, g, p, user_peaks, user_peaks ? n_user_peaks : -1, &w);
+  int status = w.status;
+  if (status == ORC_OK) {
+    const uint32_t n_symbols = 2u * (uint32_t)p->quant_radius;
+    uint8_t* len = (uint8_t*)malloc(n_symbols);
+    const int cb = orc_huffman_lengths(w.hist, n_symbols, len);
+    status = frame_assemble(frame, g, p, &w, len, cb, 0, out, capacity, out_bytes);
+    free(len);
+  }
+  work_free(&w);
   return status;
 }
 
@@ -966,8 +1084,18 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
  * prequantisation outliers overwrite b^ -> every pixel of a bin takes b^ ->
  * every in-panel ROI position takes its stored value.
  * ------------------------------------------------------------------------ */
-int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometry* g,
-                         float* frame_out) {
+/* The fields of a stream's header, checked against the geometry and each
+ * other, and the stream's layout. */
+typedef struct {
+  orc_params p;
+  uint32_t n_peaks, n_lo, n_pq, n_chunks, n_words, roi_coding, roi_bytes, roi_words, back_ref;
+  int dims;
+  uint64_t m, total;
+  orc_layout L;
+} orc_header;
+
+static int read_header(const uint8_t* in, uint64_t in_bytes, const orc_geometry* g, orc_header* h) {
+  memset(h, 0, sizeof(*h));
   if (in_bytes < ORC_HEADER_BYTES) return ORC_ERR_CORRUPT_STREAM;
   if (get_u32(in) != ORC_MAGIC || get_u32(in + 4) != ORC_VERSION) return ORC_ERR_CORRUPT_STREAM;
   if (get_u32(in + 8) != g->n_panels || get_u32(in + 12) != g->rows || get_u32(in + 16) != g->cols)
@@ -988,6 +1116,8 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
   if (dims_code != 0 && dims_code != 1 && dims_code != 3) return ORC_ERR_CORRUPT_STREAM;
   const uint32_t roi_coding = get_u32(in + 76), roi_bytes = get_u32(in + 80), roi_words = get_u32(in + 84);
   if (roi_coding > 2 || (roi_coding == 0 && (roi_bytes | roi_words) != 0)) return ORC_ERR_CORRUPT_STREAM;
+  const uint32_t back_ref = get_u32(in + 88);
+  if (back_ref > 63) return ORC_ERR_CORRUPT_STREAM;  /* chunks hold at most 64 frames */
   const int dims = dims_code == 0 ? 2 : (int)dims_code;
   if (p.bin_h < 1 || p.bin_w < 1 || p.roi_h < 1 || p.roi_w < 1 || p.quant_radius < 2 ||
       p.quant_radius > 512 || chunk != ORC_CHUNK_SYMBOLS)
@@ -997,8 +1127,39 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
   if (m != m_hdr || n_chunks != (m + chunk - 1) / chunk || n_lo > m || n_pq > m || n_words > m)
     return ORC_ERR_CORRUPT_STREAM;
   const uint32_t n_symbols = 2u * (uint32_t)p.quant_radius;
-  const orc_layout L = layout_of(n_peaks, &p, n_symbols, n_chunks, n_lo, n_pq, n_words, roi_coding == 0);
+  const orc_layout L =
+      layout_of(n_peaks, &p, n_symbols, n_chunks, n_lo, n_pq, n_words, roi_coding == 0, back_ref == 0);
   if (L.total + roi_bytes != total || total > in_bytes) return ORC_ERR_CORRUPT_STREAM;
+  h->p = p;
+  h->n_peaks = n_peaks;
+  h->n_lo = n_lo;
+  h->n_pq = n_pq;
+  h->n_chunks = n_chunks;
+  h->n_words = n_words;
+  h->roi_coding = roi_coding;
+  h->roi_bytes = roi_bytes;
+  h->roi_words = roi_words;
+  h->back_ref = back_ref;
+  h->dims = dims;
+  h->m = m;
+  h->total = total;
+  h->L = L;
+  return ORC_OK;
+}
+
+/* Decodes one stream whose header is h, with the code lengths `len` (its own,
+ * or its chunk head's). */
+static int decode_stream(const uint8_t* in, const orc_header* h, const uint8_t* len, const orc_geometry* g,
+                         float* frame_out) {
+  const orc_params p = h->p;
+  const uint32_t n_peaks = h->n_peaks, n_lo = h->n_lo, n_pq = h->n_pq, n_chunks = h->n_chunks;
+  const uint32_t n_words = h->n_words, roi_coding = h->roi_coding, roi_bytes = h->roi_bytes;
+  const uint32_t roi_words = h->roi_words, chunk = ORC_CHUNK_SYMBOLS;
+  const int dims = h->dims;
+  const uint64_t m = h->m;
+  const orc_layout L = h->L;
+  const uint32_t hb = (g->rows + p.bin_h - 1) / p.bin_h, wb = (g->cols + p.bin_w - 1) / p.bin_w;
+  const uint32_t n_symbols = 2u * (uint32_t)p.quant_radius;
   /* the ROI windows: in place, or decoded from their section */
   const size_t win = (size_t)p.roi_h * p.roi_w;
   float* roi = (float*)malloc(sizeof(float) * (win * n_peaks + 1));
@@ -1011,7 +1172,6 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
   }
 
   /* canonical decoding tables from the code lengths */
-  const uint8_t* len = in + L.lengths;
   uint32_t count[34] = {0};
   for (uint32_t s = 0; s < n_symbols; ++s) {
     if (len[s] > 32) return ORC_ERR_CORRUPT_STREAM;
@@ -1162,4 +1322,48 @@ int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometr
   free(delta);
   free(sorted);
   return status;
+}
+
+int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometry* g,
+                         float* frame_out) {
+  orc_header h;
+  const int st = read_header(in, in_bytes, g, &h);
+  if (st != ORC_OK) return st;
+  if (h.back_ref != 0) return ORC_ERR_CORRUPT_STREAM;  /* its code lengths are in another stream */
+  return decode_stream(in, &h, in + h.L.lengths, g, frame_out);
+}
+
+/* A call of streams: frame f's stream at in + offsets[f].  A stream that keeps
+ * no code lengths (back reference b > 0) takes them from the stream of frame
+ * f - b of the same call, which must be in the call, keep its own lengths and
+ * have the same alphabet; otherwise the frame is ORC_ERR_CORRUPT_STREAM. */
+int orc_decompress_frames(const uint8_t* in, uint64_t in_bytes, const uint64_t* offsets, uint32_t n_frames,
+                          const orc_geometry* g, float* frames_out, int32_t* status) {
+  const size_t frame_px = (size_t)g->n_panels * g->rows * g->cols;
+  for (uint32_t f = 0; f < n_frames; ++f) {
+    orc_header h, hh;
+    float* out = frames_out + f * frame_px;
+    if (offsets[f] > in_bytes) {
+      status[f] = ORC_ERR_CORRUPT_STREAM;
+      continue;
+    }
+    int st = read_header(in + offsets[f], in_bytes - offsets[f], g, &h);
+    const uint8_t* len = NULL;
+    if (st == ORC_OK) {
+      if (h.back_ref == 0) {
+        len = in + offsets[f] + h.L.lengths;
+      } else if (h.back_ref > f || offsets[f - h.back_ref] > in_bytes) {
+        st = ORC_ERR_CORRUPT_STREAM;
+      } else {
+        const uint64_t o = offsets[f - h.back_ref];
+        st = read_header(in + o, in_bytes - o, g, &hh);
+        if (st == ORC_OK && (hh.back_ref != 0 || hh.p.quant_radius != h.p.quant_radius)) st = ORC_ERR_CORRUPT_STREAM;
+        if (st == ORC_OK) len = in + o + hh.L.lengths;
+        else st = ORC_ERR_CORRUPT_STREAM;
+      }
+    }
+    if (st == ORC_OK) st = decode_stream(in + offsets[f], &h, len, g, out);
+    status[f] = st;
+  }
+  return ORC_OK;
 }

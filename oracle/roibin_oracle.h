@@ -60,6 +60,7 @@ typedef struct {
   int32_t lorenzo_dims; /* 1: the frame as one row-major run; 2: each panel (default); 3: the panel stack */
   int32_t nhr_min_peaks; /* non-hit rejection: frames with fewer peaks are dropped (0 = off) */
   int32_t roi_coder;     /* 0: raw float32 ROI windows; 1: the predictive lossless ROI coder */
+  int32_t chunk_frames;  /* frames per chunk sharing one codebook (1..64; 1 = a codebook per frame) */
 } orc_params;
 
 /* ---- step-level entry points (each is one row of the method) ---- */
@@ -107,6 +108,12 @@ int orc_compress_frame(const float* frame, const orc_geometry* g, const orc_para
                        uint64_t capacity, uint64_t* out_bytes);
 int orc_decompress_frame(const uint8_t* in, uint64_t in_bytes, const orc_geometry* g,
                          float* frame_out);
+/* A call of frames sharing chunk codebooks (see the source). */
+int orc_compress_frames(const float* frames, uint32_t n_frames, const orc_geometry* g, const orc_params* p,
+                        const uint16_t* user_peaks, const int64_t* n_user_peaks, uint8_t* outs, uint64_t stride,
+                        uint64_t* out_bytes, int32_t* status);
+int orc_decompress_frames(const uint8_t* in, uint64_t in_bytes, const uint64_t* offsets, uint32_t n_frames,
+                          const orc_geometry* g, float* frames_out, int32_t* status);
 
 #ifdef __cplusplus
 }

@@ -76,14 +76,16 @@ def heap_huffman_cost(freqs) -> int:
     return cost
 
 
-def decode_stream(stream: np.ndarray):
+def decode_stream(stream: np.ndarray, lengths=None):
     """Independent decoder: walks the container with the header counts, builds a
     {(length, codeword): symbol} map from the canonical rule and reads each chunk
-    bit by bit.  Returns dict with codes, lorenzo, prequant, peaks, roi."""
+    bit by bit.  Returns dict with codes, lorenzo, prequant, peaks, roi.
+    `lengths`: the code lengths of a stream that keeps none (its chunk head's)."""
     h = O.parse_header(stream)
     o = O.section_offsets(h)
     nsym = 2 * h["quant_radius"]
-    lengths = stream[o["lengths"]:o["lengths"] + nsym].astype(int)
+    if lengths is None:
+        lengths = stream[o["lengths"]:o["lengths"] + nsym].astype(int)
     order = sorted((l, s) for s, l in enumerate(lengths) if l > 0)
     table, code, prev = {}, 0, None
     for l, s in order:
@@ -804,6 +806,87 @@ def pin_non_hit_rejection():
     assert O.compress_frame(f, O.make_params(atot_thr=300.0, max_peaks=1, nhr_min_peaks=5))[0] == O.ERR_CAPACITY
 
 
+# ---------------------------------------------------------------- chunks sharing a codebook (§5.3.4)
+def _chunk_frames(n=6, seed=9, shape=(2, 20, 24)):
+    fs = []
+    for k in range(n):
+        f = tiny_frame(seed + k, shape=shape)
+        f[k % 2, 8, 9] += 900.0 + 40 * k  # a peak in every frame
+        fs.append(f)
+    return np.stack(fs)
+
+
+def _codes_of(frame, p):
+    b = O.bin_frame(frame, p.bin_h, p.bin_w)
+    q, pq = O.prequantize(b, p.abs_eb)
+    return O.quant_codes(O.lorenzo(q), p.quant_radius).ravel()
+
+
+def pin_chunks_share_one_codebook():
+    fs = _chunk_frames()
+    p1 = O.make_params(atot_thr=300.0)
+    # chunk_frames = 1: a call equals its frames compressed one by one
+    st, streams, _ = O.compress_frames(fs, p1)
+    assert (st == O.OK).all()
+    for k in range(len(fs)):
+        assert np.array_equal(streams[k], O.compress_frame(fs[k], p1)[1])
+    p4 = O.make_params(atot_thr=300.0, chunk_frames=4)
+    st, streams4, _ = O.compress_frames(fs, p4)
+    assert (st == O.OK).all()
+    nsym = 2 * p4.quant_radius
+    for c0, c1 in ((0, 4), (4, 6)):  # chunks by frame index: [0, 4) and [4, 6)
+        hs = [O.parse_header(streams4[k]) for k in range(c0, c1)]
+        assert [h["back_ref"] for h in hs] == list(range(c1 - c0)), "the first frame of a chunk is its head"
+        o = O.section_offsets(hs[0])
+        lengths = streams4[c0][o["lengths"]:o["lengths"] + nsym].astype(int)
+        # one codebook from the summed histogram: optimal for it (heap Huffman),
+        # and equal to the oracle's lengths for that histogram
+        hist = sum(np.bincount(_codes_of(fs[k], p4), minlength=nsym) for k in range(c0, c1))
+        st_l, ref_len = O.huffman_lengths(hist.astype(np.uint64))
+        assert np.array_equal(lengths, ref_len.astype(int))
+        assert int((hist * lengths).sum()) == heap_huffman_cost(hist)
+        for k in range(c0 + 1, c1):  # later frames keep no lengths: decoded with the head's
+            ok = O.section_offsets(O.parse_header(streams4[k]))
+            assert ok["chunk_index"] == ok["lengths"] and len(streams4[k]) == ok["end"]
+            dec = decode_stream(streams4[k], lengths=lengths)
+            assert np.array_equal(dec["codes"], _codes_of(fs[k], p4))
+    # decoded frames equal the frames decoded from per-frame codebooks (only the code changes)
+    st_d, rec4 = O.decompress_frames(streams4, fs.shape[1:])
+    st_1, rec1 = O.decompress_frames(streams, fs.shape[1:])
+    assert (st_d == O.OK).all() and (st_1 == O.OK).all()
+    assert np.array_equal(rec4.view(np.uint32), rec1.view(np.uint32))
+    # a later frame alone has no code lengths: its own decoder refuses it
+    assert O.decompress_frame(streams4[1], fs.shape[1:])[0] == O.ERR_CORRUPT_STREAM
+    assert O.decompress_frames([streams4[1]], fs.shape[1:])[0][0] == O.ERR_CORRUPT_STREAM
+    # chunk membership follows the frame index: a change to frame 5 leaves chunk 0's streams alone
+    fs2 = fs.copy()
+    fs2[5] += 1.0
+    st2, streams_b, _ = O.compress_frames(fs2, p4)
+    assert all(np.array_equal(streams4[k], streams_b[k]) for k in range(4))
+
+
+def pin_chunk_head_skips_frames_not_coded():
+    """Frames rejected or in error do not feed the codebook; the head is the
+    chunk's first coded frame."""
+    fs = _chunk_frames(n=4)
+    p = O.make_params(atot_thr=300.0, chunk_frames=4)
+    up = np.zeros((4, p.max_peaks, 3), np.uint16)
+    up[1, 0] = [0, 8, 9]
+    up[2, 0] = [1, 8, 9]
+    up[3, 0] = [0, 3, 3]
+    n_user = np.array([0, 1, 1, 1], np.int64)
+    pr = O.make_params(atot_thr=300.0, chunk_frames=4, nhr_min_peaks=1)
+    st, streams, _ = O.compress_frames(fs, pr, user_peaks=up, n_user=n_user)
+    assert st.tolist() == [O.REJECTED, O.OK, O.OK, O.OK]
+    assert [O.parse_header(streams[k])["back_ref"] for k in (1, 2, 3)] == [0, 1, 2]
+    nsym = 2 * pr.quant_radius
+    hist = sum(np.bincount(_codes_of(fs[k], pr), minlength=nsym) for k in (1, 2, 3))
+    o = O.section_offsets(O.parse_header(streams[1]))
+    assert np.array_equal(streams[1][o["lengths"]:o["lengths"] + nsym], O.huffman_lengths(hist.astype(np.uint64))[1])
+    st_d, rec = O.decompress_frames([streams[k] for k in (1, 2, 3)], fs.shape[1:])
+    assert (st_d == O.OK).all()
+
+
 ALL_PINS = [
     pin_candidates_brute_force, pin_candidate_special_cases, pin_evaluation_special_cases,
     pin_evaluation_brute_force, pin_find_peaks_frame, pin_roi, pin_binning, pin_prequantize,
@@ -811,5 +894,6 @@ ALL_PINS = [
     pin_frame_roundtrip, pin_identity_binning_bound, pin_user_peaks_and_corruption,
     pin_nonsquare_bins_roundtrip, pin_lorenzo_dims, pin_lorenzo_dims_roundtrip,
     pin_roi_order_and_classes, pin_roi_residual_closed_forms, pin_roi_roundtrip_and_independent_decoder,
-    pin_roi_corrupt_sections, pin_roi_frame, pin_non_hit_rejection,
+    pin_roi_corrupt_sections, pin_roi_frame, pin_non_hit_rejection, pin_chunks_share_one_codebook,
+    pin_chunk_head_skips_frames_not_coded,
 ]

@@ -81,6 +81,11 @@ MUTANTS = {
                         "if (n_windows == 0) {"),
     "roi_section_size_not_in_header": ("put_u32(out + 80, (uint32_t)roi_bytes);", "put_u32(out + 80, 0u);"),
     "nhr_inclusive": ("if ((int64_t)n_peaks < (int64_t)p->nhr_min_peaks) {", "if ((int64_t)n_peaks <= (int64_t)p->nhr_min_peaks) {"),
+    # chunks sharing one codebook (§5.3.4)
+    "chunk_head_last": ("      if (head < 0) head = f;", "      head = f;"),
+    "chunk_hist_not_summed": ("hsum[s2] += w[f].hist[s2];", "hsum[s2] = w[f].hist[s2];"),
+    "chunk_lengths_always_kept": ("L.chunk_index = L.lengths + (lengths_here ? align16(n_symbols) : 0);",
+                                  "L.chunk_index = L.lengths + align16(n_symbols);"),
     "upsample_wrong_axis": ("bhat[((size_t)pn * hb + r / p.bin_h) * wb + c / p.bin_w];", "bhat[((size_t)pn * hb + r / p.bin_w) * wb + c / p.bin_h];"),
 }
 
