@@ -373,6 +373,9 @@ def epix_variants(args, stream, local):
                        "0-300 peaks (floor(301^U) - 1), ROI 17x17, bin 2x2, max_peaks 8192"}
     for eb in (1.0, 10.0, 50.0):
         res[f"eb{eb:g}"] = timed_variant(args, frames, rb.default_params(abs_eb=eb, max_peaks=8192), stream, local)
+    # the same frames with the ROI windows coded losslessly (they are most of these streams)
+    res["eb10_roi_coded"] = timed_variant(args, frames, rb.default_params(max_peaks=8192, roi_coder=1), stream,
+                                          local)
     del frames
     torch.cuda.empty_cache()
     return res

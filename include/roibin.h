@@ -31,17 +31,38 @@
  *           u32 n_peaks | u32 n_lorenzo_outliers | u32 n_prequant_outliers |
  *           u32 n_symbols | u32 chunk_symbols (4096) | u32 n_chunks |
  *           u32 bitstream_words | u64 total_bytes | u32 lorenzo dimension
- *           (0 for the default 2, else 1 or 3) | 20 zero bytes
+ *           (0 for the default 2, else 1 or 3) | u32 roi coding | u32 roi
+ *           section bytes | u32 roi section words | u32 code-length back
+ *           reference (0: this stream keeps its code lengths; b > 0: they are
+ *           in the stream of the frame b frames earlier in the same call, the
+ *           head of its chunk) | 4 zero bytes
  *   then, each starting on a 16-byte boundary, zero padded:
  *     peaks       u16[n_peaks][3] (panel, row, col)
- *     roi         f32[n_peaks][roi_h][roi_w]
+ *     roi         f32[n_peaks][roi_h][roi_w] (roi coding 0; empty otherwise)
  *     lengths     u8[2 * quant_radius]        Huffman code length per symbol
+ *                                             (back reference 0 only; absent otherwise)
  *     chunk index u32[n_chunks]               word offset of each 4096-symbol chunk
  *     lorenzo     (u32 bin index, i32 delta)[n_lorenzo_outliers], ascending
  *     prequant    (u32 bin index, u32 float bits)[n_prequant_outliers], ascending
  *     bitstream   u32[bitstream_words]; inside a chunk, codeword bits are
  *                 appended MSB first, stream bit b is bit 31-(b%32) of word b/32;
  *                 every chunk starts on a word boundary.
+ *     roi section (roi coding 1 or 2 only; roi section bytes long):
+ *                 coding 2: f32[n_peaks][roi_h][roi_w], the raw windows;
+ *                 coding 1: the windows coded losslessly (paper §4 keeps them
+ *                 with fpzip; this coder is our own of that kind):
+ *                   u8[33] Huffman code length per class, zero padded to 48;
+ *                   u32[n_peaks] first word of each window, padded to 16;
+ *                   u32[roi section words], padded to 16.
+ *                 In a window, row-major, each float's bits u become
+ *                 m = u + 2^31 (sign 0) or NOT u (sign 1); m is predicted mod
+ *                 2^32 by m[i-1][j] + m[i][j-1] - m[i-1][j-1] (0 outside the
+ *                 window; the first value by 2^31); the residual r (int32) is
+ *                 folded to z = 2r or -2r-1; z is written as the Huffman code
+ *                 of its bit length c (0..32), then its c-1 bits below the
+ *                 leading one, MSB first.  Each window starts on a word.
+ *                 The coder stores coding 2 whenever coding 1 would not be
+ *                 smaller, so a stream never exceeds roibin_compress_bound.
  */
 #ifndef ROIBIN_H
 #define ROIBIN_H
@@ -63,6 +84,11 @@ extern "C" {
 #define ROIBIN_ERR_TIMEOUT (-6)        /* a bounded device-side wait gave up          */
 #define ROIBIN_ERR_CODE_LENGTH (-7)    /* Huffman code > 32 bits (cannot occur for
                                           frames below 5,702,887 bins)                */
+/* Per-frame outcome that is not an error: non-hit rejection (paper §1, §4:
+ * frames with too few peaks to index are dropped before compression).  The
+ * frame has fewer peaks than nhr_min_peaks; nothing is written for it and its
+ * size is 0. */
+#define ROIBIN_REJECTED 1
 
 /* ---- execution paths for roibin_compress ----------------------------- */
 #define ROIBIN_PATH_AUTO 0  /* fused when the geometry and parameters allow it, else
@@ -114,7 +140,26 @@ typedef struct {
  *        previous panel, row and column);
  *   neighbours outside the array count as 0.  Only 2 runs on the fused path
  *   and on the PANEL decompression path; 1 and 3 take the plain path and the
- *   multi-pass decompression path. */
+ *   multi-pass decompression path.
+ *   nhr_min_peaks (§1, §4, non-hit rejection): frames whose peak list (found
+ *   or given) has fewer entries are not compressed; their status is
+ *   ROIBIN_REJECTED and their size 0.  0 (default) keeps every frame.  A frame
+ *   with more than max_peaks peaks still reports ROIBIN_ERR_CAPACITY.
+ *   roi_coder (§4, the ROI kept losslessly): 0 (default) stores the ROI
+ *   windows as raw float32 in the roi section; 1 codes them with the
+ *   predictive lossless coder described above (roi section after the
+ *   bitstream).  Either way the windows come back bit for bit.
+ *   chunk_frames (§5.3.4, events per compressor call): frames f of one
+ *   roibin_compress call with the same f / chunk_frames form a chunk, and the
+ *   chunk's coded frames (those still OK after the peak stage: not rejected,
+ *   no error) share one Huffman code, built from the sum of their histograms.
+ *   The chunk's first coded frame (its head) keeps the code lengths; each
+ *   later one keeps a back reference instead and saves those 2R bytes.  A
+ *   stream with a back reference decodes only in a roibin_decompress call that
+ *   also holds its head at that many frames before it.  1 (default): every
+ *   frame has its own code, and every stream decodes alone.  Chunks follow the
+ *   frame index within the call, so a frame's bytes depend on the other
+ *   frames of its chunk (and on nothing else). */
 typedef struct {
   float amax_thr, atot_thr, son_min, pix_nsigma;
   int32_t rank, ring_r0, ring_dr, npix_min, npix_max;
@@ -122,6 +167,9 @@ typedef struct {
   float abs_eb;
   int32_t quant_radius, max_peaks;
   int32_t lorenzo_dims;
+  int32_t nhr_min_peaks;
+  int32_t roi_coder;
+  int32_t chunk_frames;
 } roibin_params;
 
 /* Fills *p with the defaults listed above.  Never fails for non-NULL p. */
@@ -131,7 +179,8 @@ int roibin_default_params(roibin_params* p);
  * 1 <= n_panels, rows, cols <= 65535; cols/bin_w <= 8192; 1 <= bin <= 8;
  * 1 <= roi <= 63; 1 <= rank <= 7; ring_r0, ring_dr >= 1, r0 + dr <= 16;
  * 2 <= quant_radius <= 512; 0 <= max_peaks <= 8192; pix_nsigma >= 0;
- * lorenzo_dims 1, 2 or 3;
+ * lorenzo_dims 1, 2 or 3; 0 <= nhr_min_peaks <= 8192; roi_coder 0 or 1;
+ * 1 <= chunk_frames <= 64;
  * abs_eb > 0 with 2 abs_eb and 1/(2 abs_eb) finite; binned size below
  * 5,702,887 (so that no Huffman code exceeds 32 bits). */
 int roibin_validate(const roibin_geometry* g, const roibin_params* p);
@@ -256,8 +305,12 @@ int roibin_ctx_set_trace(roibin_ctx* ctx, uint64_t* d_trace, uint32_t n_frames);
  *   out_stride      bytes per frame slot, a multiple of 16.
  *   d_frame_bytes   u64[n_frames] out: stream size of each frame (on CAPACITY
  *                   because of out_stride: the size it needs; else 0 on error).
- *   d_frame_status  i32[n_frames] out: ROIBIN_OK or the frame's error.
+ *   d_frame_status  i32[n_frames] out: ROIBIN_OK, ROIBIN_REJECTED (non-hit
+ *                   rejection, size 0) or the frame's error.
  *   stream          cudaStream_t as void*.
+ * With roi_coder = 1 the windows are coded by three more kernels after the
+ * main ones (classes and counts per window, one codebook and layout per
+ * frame, the bits), on both paths.
  * Returns ROIBIN_OK when the work was enqueued. */
 int roibin_compress(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames,
                     const uint16_t* d_peaks, const uint32_t* d_npeaks, uint8_t* d_out,

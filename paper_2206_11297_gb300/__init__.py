@@ -25,6 +25,7 @@ ERR_OUT_OF_BUDGET = -4
 ERR_CUDA = -5
 ERR_TIMEOUT = -6
 ERR_CODE_LENGTH = -7
+REJECTED = 1  # per-frame status: non-hit rejection, nothing written
 
 PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
 DEC_AUTO, DEC_PANEL, DEC_MULTIPASS = 0, 1, 2
@@ -46,7 +47,8 @@ class Params(ctypes.Structure):
         ("roi_h", ctypes.c_int32), ("roi_w", ctypes.c_int32),
         ("bin_h", ctypes.c_int32), ("bin_w", ctypes.c_int32),
         ("abs_eb", ctypes.c_float), ("quant_radius", ctypes.c_int32), ("max_peaks", ctypes.c_int32),
-        ("lorenzo_dims", ctypes.c_int32),
+        ("lorenzo_dims", ctypes.c_int32), ("nhr_min_peaks", ctypes.c_int32), ("roi_coder", ctypes.c_int32),
+        ("chunk_frames", ctypes.c_int32),
     ]
 
     def as_dict(self):

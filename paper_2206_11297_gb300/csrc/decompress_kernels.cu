@@ -23,19 +23,67 @@ __device__ __forceinline__ void mark_corrupt(Scratch& s, uint32_t f) {
   s.status[f] = ROIBIN_ERR_CORRUPT_STREAM;
 }
 
-// parse: one block per frame.  Reads the header and the code lengths, builds
+// The fields of a stream's header (24 words), checked against the context's
+// geometry and each other as the oracle checks them; the stream's layout.
+__device__ bool read_header(const uint32_t* hdr, const DevParams& p, uint64_t base, uint64_t in_bytes, DecInfo& di) {
+  di = DecInfo{};
+  di.base = base;
+  const uint32_t roi_h = hdr[5] & 0xFFFFu, roi_w = hdr[5] >> 16;
+  const uint32_t bh = hdr[6] & 0xFFFFu, bw = hdr[6] >> 16;
+  di.eb = __uint_as_float(hdr[7]);
+  di.two_eb = __fmul_rn(2.0f, di.eb);
+  di.R = (int32_t)hdr[8];
+  di.roi_h = (int32_t)roi_h;
+  di.roi_w = (int32_t)roi_w;
+  di.nsym = 2u * hdr[8];
+  FramePlan& pl = di.pl;
+  di.roi_coding = hdr[19];
+  di.roi_bytes = hdr[20];
+  di.roi_words = hdr[21];
+  di.back_ref = hdr[22];
+  pl.n_peaks = hdr[9];
+  pl.n_lo = hdr[10];
+  pl.n_pq = hdr[11];
+  pl.n_words = hdr[15];
+  const uint64_t total = (uint64_t)hdr[16] | ((uint64_t)hdr[17] << 32);
+  bool ok = !(hdr[0] != kMagic || hdr[1] != kVersion || hdr[2] != p.P || hdr[3] != p.H || hdr[4] != p.W ||
+              bh != (uint32_t)p.bh || bw != (uint32_t)p.bw || roi_h < 1 || roi_h > 63 || roi_w < 1 ||
+              roi_w > 63 || hdr[8] < 2 || hdr[8] > 512 || hdr[12] != p.M || hdr[13] != kChunk ||
+              hdr[14] != p.n_chunks || pl.n_lo > p.M || pl.n_pq > p.M || pl.n_words > p.M ||
+              pl.n_peaks > 65535u || !(di.eb > 0.0f) || !isfinite(di.two_eb) ||
+              hdr[18] != (p.dims == 2 ? 0u : (uint32_t)p.dims) ||  // the context's Lorenzo dimension
+              di.roi_coding > 2 || (di.roi_coding == 0 && (di.roi_bytes | di.roi_words) != 0) ||
+              di.back_ref > 63);  // a chunk holds at most 64 frames
+  pl.off_peaks = kHeaderBytes;
+  pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
+  pl.off_len = pl.off_roi + (di.roi_coding == 0 ? align16((uint64_t)pl.n_peaks * roi_h * roi_w * 4) : 0);
+  pl.off_cidx = pl.off_len + (di.back_ref == 0 ? align16(di.nsym) : 0);  // lengths: a chunk's head only
+  pl.off_lo = pl.off_cidx + align16((uint64_t)p.n_chunks * 4);
+  pl.off_pq = pl.off_lo + align16((uint64_t)pl.n_lo * 8);
+  pl.off_bits = pl.off_pq + align16((uint64_t)pl.n_pq * 8);
+  pl.total = pl.off_bits + align16((uint64_t)pl.n_words * 4);
+  di.off_roi_sec = pl.total;  // the ROI section after the bitstream (roi coding 1, 2)
+  pl.total += di.roi_bytes;
+  if (pl.total != total || base + pl.total > in_bytes) ok = false;
+  return ok;
+}
+
+// parse: one block per frame.  Reads the header and the code lengths (its own,
+// or those of its chunk's head, back_ref frames earlier in the call), builds
 // the canonical decoding tables and the prefix table, checks that both outlier
 // lists are strictly ascending and inside the frame, and records where each
 // panel's outliers start in them.
 __global__ void __launch_bounds__(256) k_dec_parse(DevParams p, Scratch s, DecArgs a) {
-  __shared__ uint32_t hdr[24];
+  __shared__ uint32_t hdr[24], hhdr[24];
   __shared__ int ok;
+  __shared__ uint64_t len_at;  // byte offset of the code lengths in the input
   __shared__ uint32_t cnt[34], first[34], idx0[34];
   __shared__ uint8_t lens[kMaxSymbols];
   __shared__ uint16_t order[kMaxSymbols];
   __shared__ uint32_t nsym_s;
   __shared__ int sparse;
   const uint32_t f = blockIdx.x;
+  DecInfo di = {};
   if (threadIdx.x == 0) {
     s.dec_zero[f] = 0;
     ok = 1;
@@ -44,51 +92,32 @@ __global__ void __launch_bounds__(256) k_dec_parse(DevParams p, Scratch s, DecAr
     if (ok) {
       const uint32_t* h = reinterpret_cast<const uint32_t*>(a.in + base);
       for (int i = 0; i < 24; ++i) hdr[i] = h[i];
+      ok = read_header(hdr, p, base, a.in_bytes, di) ? 1 : 0;
+      len_at = base + di.pl.off_len;
     }
-  }
-  __syncthreads();
-  DecInfo di = {};
-  if (ok) {
-    di.base = a.offsets[f];
-    const uint32_t roi_h = hdr[5] & 0xFFFFu, roi_w = hdr[5] >> 16;
-    const uint32_t bh = hdr[6] & 0xFFFFu, bw = hdr[6] >> 16;
-    di.eb = __uint_as_float(hdr[7]);
-    di.two_eb = __fmul_rn(2.0f, di.eb);
-    di.R = (int32_t)hdr[8];
-    di.roi_h = (int32_t)roi_h;
-    di.roi_w = (int32_t)roi_w;
-    di.nsym = 2u * hdr[8];
-    FramePlan& pl = di.pl;
-    pl.n_peaks = hdr[9];
-    pl.n_lo = hdr[10];
-    pl.n_pq = hdr[11];
-    pl.n_words = hdr[15];
-    const uint64_t total = (uint64_t)hdr[16] | ((uint64_t)hdr[17] << 32);
-    if (hdr[0] != kMagic || hdr[1] != kVersion || hdr[2] != p.P || hdr[3] != p.H || hdr[4] != p.W ||
-        bh != (uint32_t)p.bh || bw != (uint32_t)p.bw || roi_h < 1 || roi_h > 63 || roi_w < 1 ||
-        roi_w > 63 || hdr[8] < 2 || hdr[8] > 512 || hdr[12] != p.M || hdr[13] != kChunk ||
-        hdr[14] != p.n_chunks || pl.n_lo > p.M || pl.n_pq > p.M || pl.n_words > p.M ||
-        pl.n_peaks > 65535u || !(di.eb > 0.0f) || !isfinite(di.two_eb) ||
-        hdr[18] != (p.dims == 2 ? 0u : (uint32_t)p.dims))  // the context's Lorenzo dimension
-      ok = 0;
-    pl.off_peaks = kHeaderBytes;
-    pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
-    pl.off_len = pl.off_roi + align16((uint64_t)pl.n_peaks * roi_h * roi_w * 4);
-    pl.off_cidx = pl.off_len + align16(di.nsym);
-    pl.off_lo = pl.off_cidx + align16((uint64_t)p.n_chunks * 4);
-    pl.off_pq = pl.off_lo + align16((uint64_t)pl.n_lo * 8);
-    pl.off_bits = pl.off_pq + align16((uint64_t)pl.n_pq * 8);
-    pl.total = pl.off_bits + align16((uint64_t)pl.n_words * 4);
-    if (pl.total != total || di.base + pl.total > a.in_bytes) ok = 0;
-  }
-  __syncthreads();
-  if (!ok) {
-    if (threadIdx.x == 0) {
+    // a stream without code lengths takes its chunk head's: the frame back_ref
+    // earlier in this call, which must be a valid stream keeping its own
+    // lengths, with the same alphabet
+    if (ok && di.back_ref != 0) {
+      DecInfo hd;
+      const uint64_t hb = di.back_ref <= f ? a.offsets[f - di.back_ref] : 0;
+      ok = di.back_ref <= f && (hb & 15u) == 0 && hb + kHeaderBytes <= a.in_bytes;
+      if (ok) {
+        const uint32_t* h = reinterpret_cast<const uint32_t*>(a.in + hb);
+        for (int i = 0; i < 24; ++i) hhdr[i] = h[i];
+        ok = read_header(hhdr, p, hb, a.in_bytes, hd) && hd.back_ref == 0 && hd.R == di.R;
+        len_at = hb + hd.pl.off_len;
+      }
+    }
+    if (!ok) {
       s.status[f] = ROIBIN_ERR_CORRUPT_STREAM;
       s.dec_info[f] = di;
     }
-    return;
   }
+  __syncthreads();
+  if (!ok) return;
+  if (threadIdx.x != 0) read_header(hdr, p, a.offsets[f], a.in_bytes, di);  // every thread's copy
+  __syncthreads();
   // canonical decoding tables: count per length, first code per length, index
   // of the first symbol of each length in the (length, symbol) order.
   const uint8_t* base = a.in + di.base;
@@ -97,7 +126,7 @@ __global__ void __launch_bounds__(256) k_dec_parse(DevParams p, Scratch s, DecAr
   if (threadIdx.x == 0) nsym_s = di.nsym;
   __syncthreads();
   for (uint32_t k = threadIdx.x; k < di.nsym; k += blockDim.x) {
-    const uint32_t L = base[di.pl.off_len + k];
+    const uint32_t L = a.in[len_at + k];
     lens[k] = (uint8_t)L;
     if (L > 32) ok = 0;
     else if (L > 0) atomicAdd(&cnt[L], 1u);
@@ -442,7 +471,8 @@ __global__ void k_dec_roi(DevParams p, Scratch s, DecArgs a) {
   const float* roi = reinterpret_cast<const float*>(base + di.pl.off_roi);
   const uint32_t win = (uint32_t)(di.roi_h * di.roi_w);
   const uint32_t wpb = blockDim.x >> 5;
-  for (uint32_t k = blockIdx.x * wpb + (threadIdx.x >> 5); k < di.pl.n_peaks; k += gridDim.x * wpb) {
+  const uint32_t n_in_place = di.roi_coding == 0 ? di.pl.n_peaks : 0u;  // else k_dec_roi_coded
+  for (uint32_t k = blockIdx.x * wpb + (threadIdx.x >> 5); k < n_in_place; k += gridDim.x * wpb) {
     const uint32_t pn = pk[3 * k], r = pk[3 * k + 1], c = pk[3 * k + 2];
     if (pn >= p.P || r >= p.H || c >= p.W) {
       if (lane_id() == 0) mark_corrupt(s, f);
@@ -988,11 +1018,13 @@ __global__ void __launch_bounds__(kPanelThreads, 8) k_dec_panel(DevParams p, Scr
     if (threadIdx.x == 0) s.status[f] = ROIBIN_ERR_TIMEOUT;
     return;
   }
-  // ROI windows of this panel's peaks (every block checks every peak's place)
+  // ROI windows of this panel's peaks (every block checks every peak's place);
+  // a ROI section after the bitstream is restored by k_dec_roi_coded instead
   const uint16_t* pk = reinterpret_cast<const uint16_t*>(base + di.pl.off_peaks);
   const float* roi = reinterpret_cast<const float*>(base + di.pl.off_roi);
   const uint32_t win = (uint32_t)(di.roi_h * di.roi_w);
-  for (uint32_t k = threadIdx.x >> 5; k < di.pl.n_peaks; k += blockDim.x >> 5) {
+  const uint32_t n_in_place = di.roi_coding == 0 ? di.pl.n_peaks : 0u;
+  for (uint32_t k = threadIdx.x >> 5; k < n_in_place; k += blockDim.x >> 5) {
     const uint32_t kp = pk[3 * k], r = pk[3 * k + 1], c = pk[3 * k + 2];
     if (kp >= p.P || r >= H || c >= W) {
       bad = true;
@@ -1091,7 +1123,9 @@ cudaError_t launch_dec_upsample(const DevParams& p, const Scratch& s, const DecA
 cudaError_t launch_dec_roi(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st) {
   dim3 grid(64, a.n_frames);
   k_dec_roi<<<grid, 256, 0, st>>>(p, s, a);
-  if (cudaGetLastError() != cudaSuccess) return cudaGetLastError();
+  return cudaGetLastError();
+}
+cudaError_t launch_dec_finish(const Scratch& s, const DecArgs& a, cudaStream_t st) {
   k_dec_finish<<<ceil_div(a.n_frames, 256), 256, 0, st>>>(s, a.frame_status, a.n_frames);
   return cudaGetLastError();
 }
@@ -1124,8 +1158,6 @@ cudaError_t launch_dec_panel(const DevParams& p, const Scratch& s, const DecArgs
   while (lg_seg > 0 && (sb << lg_seg) > (uint32_t)kPanelThreads) --lg_seg;
   dim3 grid(p.P, a.n_frames);
   k_dec_panel<<<grid, kPanelThreads, smem, st>>>(p, s, a, sb, lg_seg, vec4 ? 1 : 0);
-  if (cudaGetLastError() != cudaSuccess) return cudaGetLastError();
-  k_dec_finish<<<ceil_div(a.n_frames, 256), 256, 0, st>>>(s, a.frame_status, a.n_frames);
   return cudaGetLastError();
 }
 cudaError_t launch_roi_mask(const DevParams& p, const uint16_t* peaks, const uint32_t* npeaks, uint32_t n,

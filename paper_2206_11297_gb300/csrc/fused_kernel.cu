@@ -92,7 +92,7 @@ __device__ __forceinline__ uint32_t byte_code(uint32_t b, const uint16_t* esc_bi
 // padding byte of a frame (block-cooperative).  keys (pixel index per peak)
 // and cb_len are global arrays written by other CTAs: read through L2.
 __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePlan& pl, const uint32_t* keys,
-                                 const uint8_t* cb_len, const uint32_t* chunk_word_off) {
+                                 const uint8_t* cb_len, const uint32_t* chunk_word_off, uint32_t ref) {
   if (threadIdx.x == 0) {
     uint32_t h[24];
     h[0] = kMagic;
@@ -114,6 +114,7 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
     h[16] = (uint32_t)(pl.total & 0xFFFFFFFFu);
     h[17] = (uint32_t)(pl.total >> 32);
     for (int i = 18; i < 24; ++i) h[i] = 0;
+    h[22] = ref;  // frames back to the stream with the code lengths (0: this one)
     uint4* o4 = reinterpret_cast<uint4*>(out);
     for (int i = 0; i < 6; ++i) o4[i] = make_uint4(h[4 * i], h[4 * i + 1], h[4 * i + 2], h[4 * i + 3]);
   }
@@ -130,9 +131,11 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
     for (uint64_t b = from + threadIdx.x; b < to; b += blockDim.x) out[b] = 0;
   };
   zero(pl.off_peaks + (uint64_t)pl.n_peaks * 6, pl.off_roi);
-  zero(pl.off_roi + (uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4, pl.off_len);
-  for (uint32_t k = threadIdx.x; k < p.nsym; k += blockDim.x) out[pl.off_len + k] = __ldcg(cb_len + k);
-  zero(pl.off_len + p.nsym, pl.off_cidx);
+  zero(pl.off_roi + (p.roi_coder ? 0 : (uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4), pl.off_len);
+  if (ref == 0) {  // the code lengths: a chunk's head only
+    for (uint32_t k = threadIdx.x; k < p.nsym; k += blockDim.x) out[pl.off_len + k] = __ldcg(cb_len + k);
+    zero(pl.off_len + p.nsym, pl.off_cidx);
+  }
   uint32_t* ci = reinterpret_cast<uint32_t*>(out + pl.off_cidx);
   for (uint32_t k = threadIdx.x; k < p.n_chunks; k += blockDim.x) ci[k] = chunk_word_off[k];
   zero(pl.off_cidx + (uint64_t)p.n_chunks * 4, pl.off_lo);
@@ -215,6 +218,76 @@ __device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape&
   v.offs = reinterpret_cast<uint32_t*>(sm + sh.off_offs);
   v.ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
   return v;
+}
+
+// ---------------------------------------------------------------------------
+// a1 + a2 for an item with more candidates than its list holds (hot pixels),
+// one lane per candidate, every pixel read from shared memory.  The item's
+// panels are taken in bands of rows: a band of B rows plus `reach` rows above
+// and below (the whole neighbourhood of every candidate in it) is staged in
+// the ring's memory with coalesced 16-byte loads.  The band's pixels >=
+// amax_thr are ranked in a block-wide scan (each thread counts its own run of
+// the band, then the runs' counts are scanned), and rank q goes to thread
+// q mod 256 in rounds, so every thread holds a candidate whatever their number.
+// Each thread runs the local-maximum rule and the evaluation in the sequential
+// order of is_local_max_at / evaluate_peak_at.  Accepted pixels (item-local
+// index) are collected in the item's slot of s.peak_part; the caller sorts them.
+__device__ __noinline__ void dense_band_peaks(const DevParams& p, const Scratch& s, const FusedShape& sh,
+                                              const StreamView& v, const float* item_px, uint32_t kp, size_t fu) {
+  const uint32_t tid = threadIdx.x, W = p.W, H = p.H, plane = H * W;
+  const uint32_t reach = (uint32_t)peak_reach(p), B = sh.band_rows - 2 * reach;
+  float* band = reinterpret_cast<float*>(v.ring);
+  uint32_t* run_start = v.thr;  // [kPT] first rank of each thread's run
+  uint32_t* acc = s.peak_part + fu * sh.peak_cap;
+  for (uint32_t j = 0; j < kp; ++j) {
+    const float* pan = item_px + (size_t)j * plane;
+    for (uint32_t r0 = 0; r0 < H; r0 += B) {
+      const uint32_t r1 = min(H, r0 + B);
+      const uint32_t rb0 = r0 >= reach ? r0 - reach : 0u, rb1 = min(H, r1 + reach);
+      __syncthreads();  // the previous band is no longer read
+      const float4* src = reinterpret_cast<const float4*>(pan + (size_t)rb0 * W);
+      float4* dst = reinterpret_cast<float4*>(band);
+      for (uint32_t e = tid; e < (rb1 - rb0) * (W / 4); e += kPT) dst[e] = __ldg(src + e);
+      __syncthreads();
+      // pass 1: each thread counts the candidates of its run of the band's own rows
+      const float* core = band + (size_t)(r0 - rb0) * W;
+      const uint32_t n_core = (r1 - r0) * W, run = ceil_div(n_core, kPT);
+      const uint32_t x0 = min(n_core, tid * run), x1 = min(n_core, x0 + run);
+      uint32_t cnt = 0;
+      for (uint32_t x = x0; x < x1; ++x) cnt += core[x] >= p.amax;
+      uint32_t total;
+      const uint32_t first = block_excl_scan(cnt, v.ctl + CTL_TMP, &total);
+      run_start[tid] = first;
+      __syncthreads();
+      // pass 2: rank q -> the run holding it (the last run starting at or before
+      // q), then the (q - start)-th candidate of that run
+      for (uint32_t q0 = 0; q0 < total; q0 += kPT) {
+        const uint32_t q = q0 + tid;
+        if (q >= total) continue;
+        uint32_t lo = 0, hi = kPT - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (run_start[mid] <= q) lo = mid;
+          else hi = mid - 1;
+        }
+        uint32_t skip = q - run_start[lo], x = min(n_core, lo * run);
+        for (;; ++x)
+          if (core[x] >= p.amax && skip-- == 0) break;
+        const int r = (int)(r0 + x / W), c = (int)(x % W);
+        const float* at = band + (size_t)(r - (int)rb0) * W + c;
+        auto px = [&](int dr, int dc) { return at[dr * (int)W + dc]; };
+        if (peak_test_one(px, (int)H, (int)W, r, c, p)) {
+          const uint32_t slot = atomicAdd(v.ctl + CTL_ACC, 1u);
+          if (slot < sh.peak_cap) acc[slot] = j * plane + (uint32_t)r * W + (uint32_t)c;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // the item's accepted pixels into the shared list the caller sorts
+  const uint32_t n_acc = v.ctl[CTL_ACC];
+  if (n_acc <= p.max_peaks)
+    for (uint32_t k = tid; k < n_acc; k += kPT) v.acc[k] = __ldcg(acc + k);
 }
 
 // ---------------------------------------------------------------------------
@@ -604,6 +677,9 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
         }
       }
     } else if constexpr (kDense) {
+      if (sh.band_rows >= 2u * (uint32_t)peak_reach(p) + 2u) {
+        dense_band_peaks(p, s, sh, v, item_px, kp, fu);
+      } else {
       // many candidates (hot pixels): one lane per candidate.  The warp gathers
       // the pixels >= amax_thr of its slices, 32 at a time, and each lane runs
       // the local-maximum rule and the evaluation on its own candidate in the
@@ -617,8 +693,7 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
           const int r = (int)(rem / p.W), c = (int)(rem - (uint32_t)r * p.W);
           const float* pan = item_px + (size_t)pj * plane;
           auto px = [&](int dr, int dc) { return __ldg(pan + (size_t)(r + dr) * p.W + (c + dc)); };
-          if (is_local_max_at(px, (int)p.H, (int)p.W, r, c, p) &&
-              evaluate_peak_at(px, (int)p.H, (int)p.W, r, c, p)) {
+          if (is_local_max_at(px, (int)p.H, (int)p.W, r, c, p) && evaluate_peak_at(px, (int)p.H, (int)p.W, r, c, p)) {
             const uint32_t slot = atomicAdd(v.ctl + CTL_ACC, 1u);
             if (slot < sh.sort_n2) v.acc[slot] = mine;
           }
@@ -632,6 +707,7 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
         uint32_t m = __ballot_sync(0xffffffffu, hot);
         while (m) {
           // the first `take` hot lanes hand their pixels to lanes nq .. nq + take - 1
+          // (this fallback serves panels too wide for a band of rows in shared memory)
           // through the warp's 32 slots of the candidate list (unused on this path)
           static_assert(kThrLocalCap >= kPW * 32, "32 candidate slots per warp");
           uint32_t* q = v.cand + warp * 32;
@@ -648,6 +724,7 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
         }
       }
       if (nq) flush();
+      }
     } else {
       const uint32_t n_px = kp * plane;
       for (uint32_t base = warp * 32; base < n_px; base += kPW * 32) {
@@ -717,11 +794,12 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 //   timed_out               set by any item whose flag wait gave up (sticky: no
 //                           later write of the frame's status can clear it);
 //   fin_count               the plan and the write items finished; the one that
-//                           finishes last settles the frame's status.
+//                           finishes last settles the frame's status;
+//   chunk_done              (per chunk of frames) frames whose peaks are known.
 struct SyncWords {
-  uint32_t *panel_done, *size_done, *ready_cb, *ready_plan, *timed_out, *fin_count, *ticket;
+  uint32_t *panel_done, *size_done, *ready_cb, *ready_plan, *timed_out, *fin_count, *chunk_done, *ticket;
 };
-constexpr uint32_t kSyncWordsPerFrame = 6;
+constexpr uint32_t kSyncWordsPerFrame = 7;
 __device__ __forceinline__ SyncWords sync_words(const Scratch& s, uint32_t n) {
   SyncWords w;
   w.panel_done = s.frame_done;
@@ -730,6 +808,7 @@ __device__ __forceinline__ SyncWords sync_words(const Scratch& s, uint32_t n) {
   w.ready_plan = s.frame_done + 3 * n;
   w.timed_out = s.frame_done + 4 * n;
   w.fin_count = s.frame_done + 5 * n;
+  w.chunk_done = s.frame_done + 6 * n;
   w.ticket = s.frame_done + kSyncWordsPerFrame * n;
   return w;
 }
@@ -775,6 +854,63 @@ __device__ bool wait_flag(const uint32_t* f, uint32_t* slot, uint32_t limit) {
   const bool ok = *slot != 0;
   __syncthreads();
   return ok;
+}
+
+// (1b) chunks of frames sharing one codebook (§5.3.4; chunk_frames > 1).  Each
+// frame's CTA publishes the frame's histogram (in FinView::total) and its
+// status after the peaks; the CTA that completes the chunk's last frame sums
+// the histograms of the chunk's coded frames (status OK), builds the code,
+// gives it to each of them with its distance to the chunk's head (the first
+// coded frame, whose stream alone keeps the code lengths), and releases every
+// frame of the chunk to its size items.
+__device__ void chunk_codebook(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
+                               unsigned char* sm, uint32_t f, const SyncWords& sw) {
+  const FinView v = fin_view(sm, sh);
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t k = tid; k < p.nsym; k += kPT) s.hist[(size_t)f * kMaxSymbols + k] = v.total[k];
+  if (tid == 0) s.status[f] = (int32_t)v.ctl[CTL_STATUS];
+  __threadfence();
+  __syncthreads();
+  const uint32_t j = f / p.chunk, c0 = j * p.chunk, c1 = min(a.n_frames, c0 + p.chunk);
+  if (tid == 0) v.ctl[CTL_LAST] = atomicAdd(sw.chunk_done + j, 1u) == c1 - c0 - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!v.ctl[CTL_LAST]) return;  // another frame's CTA completes the chunk
+  __threadfence();
+  if (tid == 0) {
+    int head = -1;
+    for (uint32_t g = c0; g < c1 && head < 0; ++g)
+      if (__ldcg(s.status + g) == ROIBIN_OK) head = (int)g;
+    v.ctl[CTL_CARRY1] = head < 0 ? 0xFFFFFFFFu : (uint32_t)head;
+  }
+  __syncthreads();
+  const uint32_t head = v.ctl[CTL_CARRY1];
+  if (head != 0xFFFFFFFFu) {
+    for (uint32_t k = tid; k < p.nsym; k += kPT) {
+      uint32_t t = 0;
+      for (uint32_t g = head; g < c1; ++g)
+        if (__ldcg(s.status + g) == ROIBIN_OK) t += __ldcg(s.hist + (size_t)g * kMaxSymbols + k);
+      v.total[k] = t;
+    }
+    __syncthreads();
+    const int cb = build_codebook(v.total, p.nsym, *v.hs, v.cb_len, v.cb_code);
+    for (uint32_t g = head; g < c1; ++g) {
+      if (__ldcg(s.status + g) != ROIBIN_OK) continue;
+      for (uint32_t k = tid; k < p.nsym; k += kPT) {
+        s.cb_len[(size_t)g * kMaxSymbols + k] = v.cb_len[k];
+        s.cb_code[(size_t)g * kMaxSymbols + k] = v.cb_code[k];
+      }
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (uint32_t g = head; g < c1; ++g) {
+        if (__ldcg(s.status + g) != ROIBIN_OK) continue;
+        s.chunk_ref[g] = g - head;
+        if (cb != ROIBIN_OK) s.status[g] = cb;
+      }
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (uint32_t g = c0; g < c1; ++g) flag_release(sw.ready_cb + g);
 }
 
 // (1) peak list + codebook of frame f, by the CTA that completed its last streaming item.
@@ -848,9 +984,16 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
   if (tid == 0) {
     if (v.ctl[CTL_BAD] == 2) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_TIMEOUT;
     else if (v.ctl[CTL_BAD] && v.ctl[CTL_STATUS] == ROIBIN_OK) v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_ERR_INVALID_ARG;
+    // non-hit rejection (§1, §4): too few peaks, the frame is not compressed
+    if (v.ctl[CTL_STATUS] == ROIBIN_OK && v.ctl[CTL_CARRY0] < (uint32_t)p.nhr_min)
+      v.ctl[CTL_STATUS] = (uint32_t)ROIBIN_REJECTED;
     a.peaks_count_out[f] = v.ctl[CTL_CARRY0];
   }
   if (trace) trace[1] = global_ns();
+  if (p.chunk > 1) {
+    chunk_codebook(p, s, a, sh, sm, f, sw);
+    return;
+  }
   // a9: the codebook, published in the frame's global tables
   const int cb = build_codebook(v.total, p.nsym, *v.hs, v.cb_len, v.cb_code);
   for (uint32_t k = tid; k < p.nsym; k += kPT) {
@@ -1029,6 +1172,7 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
   // chunk counts unfinished: the frame stops here (its give-up was published
   // before its size_done increment, which this CTA has seen)
   int32_t st = __ldcg(sw.timed_out + g) ? ROIBIN_ERR_TIMEOUT : __ldcg(s.status + g);
+  const uint32_t ref = p.chunk > 1 ? __ldcg(s.chunk_ref + g) : 0u;  // frames back to the chunk's head
   uint32_t* cw = reinterpret_cast<uint32_t*>(sm + sh.off_cw);
   uint32_t* clo = cw + p.n_chunks;
   uint32_t* cpq = clo + p.n_chunks;
@@ -1069,8 +1213,8 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
     pl.n_pq = ctl[CTL_CARRY2];
     pl.off_peaks = kHeaderBytes;
     pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
-    pl.off_len = pl.off_roi + align16((uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4);
-    pl.off_cidx = pl.off_len + align16(p.nsym);
+    pl.off_len = pl.off_roi + roi_in_place_bytes(p, pl.n_peaks);
+    pl.off_cidx = pl.off_len + (ref == 0 ? align16(p.nsym) : 0);  // a chunk's head keeps the lengths
     pl.off_lo = pl.off_cidx + align16((uint64_t)p.n_chunks * 4);
     pl.off_pq = pl.off_lo + align16((uint64_t)pl.n_lo * 8);
     pl.off_bits = pl.off_pq + align16((uint64_t)pl.n_pq * 8);
@@ -1091,7 +1235,7 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
     }
     if (tid == 0) s.plan[g] = pl;
     write_frame_head(a.out + (size_t)g * a.out_stride, p, pl, a.peaks_key_out + (size_t)g * p.max_peaks,
-                     s.cb_len + (size_t)g * kMaxSymbols, cw);
+                     s.cb_len + (size_t)g * kMaxSymbols, cw, ref);
   }
   __syncthreads();
   if (trace) trace[4] = global_ns();
@@ -1262,7 +1406,8 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
   const uint32_t win = (uint32_t)(p.roi_h * p.roi_w), plane = p.H * p.W;
   const float* frame = a.frames + (size_t)g * p.frame_px;
   const uint32_t* keys = a.peaks_key_out + (size_t)g * p.max_peaks;
-  for (uint32_t k = grp + sh.groups * warp; k < pl.n_peaks; k += sh.groups * kPW) {
+  const uint32_t n_in_place = p.roi_coder ? 0u : pl.n_peaks;  // else the ROI coder writes them
+  for (uint32_t k = grp + sh.groups * warp; k < n_in_place; k += sh.groups * kPW) {
     const uint32_t px = __ldcg(keys + k);
     const uint32_t pn = px / plane, rem = px - pn * plane;
     const int r = (int)(rem / p.W), c = (int)(rem % p.W);
@@ -1396,6 +1541,13 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   sh.off_offs = take((uint64_t)sh.U * 4);
   const uint64_t fin_end = off > stage_end ? off : stage_end;
   sh.smem = (uint32_t)(stream_end > fin_end ? stream_end : fin_end);
+  // The dense-peaks variant takes all the shared memory its CTAs per SM leave
+  // it: from the ring on, that memory holds a band of rows of one panel once
+  // the item's rows are coded.  A band's candidates are tested in parallel, one
+  // per thread, so a taller band keeps more threads busy.
+  const uint32_t share = 233472u / ctas_per_sm - 1024u;
+  sh.smem_dense = sh.smem > share ? sh.smem : (share < 227u * 1024u ? share : 227u * 1024u);
+  sh.band_rows = (sh.smem_dense - sh.off_ring) / (p.W * 4);
   *out = sh;
   return sh.smem <= 227 * 1024;
 }
@@ -1447,8 +1599,9 @@ cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& 
   // stage counters, ready flags and the ticket counter start at zero
   cudaError_t e = cudaMemsetAsync(s.frame_done, 0, sizeof(uint32_t) * (kSyncWordsPerFrame * (uint64_t)a.n_frames + 1), st);
   if (e != cudaSuccess) return e;
+  const uint32_t smem = screen ? sh.smem_dense : sh.smem;
   e = cudaFuncSetAttribute(screen ? k_fused<true> : k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sh.smem);
+                           (int)smem);
   if (e != cudaSuccess) return e;
   FusedShape s2 = sh;
   // frames between the stages in the ticket order.  Streaming -> chunk sizes:
@@ -1461,7 +1614,7 @@ cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& 
   s2.lag2 = a.n_frames < kLagWrite ? a.n_frames : kLagWrite;
   const uint64_t tickets = (uint64_t)(a.n_frames + s2.lag1 + s2.lag2) * (s2.U + 2 * s2.groups);
   const uint32_t grid = (uint32_t)(tickets < sh.n_ctas ? tickets : sh.n_ctas);
-  if (screen) k_fused<true><<<grid, kPT, sh.smem, st>>>(p, s, a, s2);
+  if (screen) k_fused<true><<<grid, kPT, smem, st>>>(p, s, a, s2);
   else k_fused<false><<<grid, kPT, sh.smem, st>>>(p, s, a, s2);
   return cudaGetLastError();
 }

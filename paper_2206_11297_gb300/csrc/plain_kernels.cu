@@ -15,7 +15,7 @@ const char* kernel_name(int id) {
   static const char* names[K_COUNT] = {
       "reset", "stream", "peaks", "peaks_final", "huffman", "chunks", "plan", "encode", "roi",
       "fused", "dec_parse", "dec_decode", "dec_lorenzo", "dec_rows", "dec_cols", "dec_pq",
-      "dec_upsample", "dec_roi", "dec_panel", "roi_mask", "pack", "dec_carry"};
+      "dec_upsample", "dec_roi", "dec_panel", "roi_mask", "pack", "dec_carry", "roi_code", "dec_roi_coded"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 
@@ -381,6 +381,7 @@ __global__ void __launch_bounds__(1024) k_peaks_final(DevParams p, Scratch s, Pl
     if (threadIdx.x == 0) {
       s.peak_count[f] = n;
       if (bad) s.status[f] = ROIBIN_ERR_INVALID_ARG;
+      else if (n < (uint32_t)p.nhr_min) s.status[f] = ROIBIN_REJECTED;  // non-hit rejection
     }
     return;
   }
@@ -411,17 +412,64 @@ __global__ void __launch_bounds__(1024) k_peaks_final(DevParams p, Scratch s, Pl
     }
   }
   for (uint32_t k = threadIdx.x; k < count; k += blockDim.x) out[k] = keys[k];
+  // non-hit rejection (§1, §4): too few peaks, the frame is not compressed
+  if (threadIdx.x == 0 && count < (uint32_t)p.nhr_min) s.status[f] = ROIBIN_REJECTED;
 }
 
 // ---------------------------------------------------------------------------
-// huffman: one block per frame builds its canonical codebook.
-__global__ void __launch_bounds__(1024) k_huffman(DevParams p, Scratch s) {
+// huffman: one block per chunk of frames builds its canonical codebook (§5.3.4:
+// chunk_frames frames of the call share one).  A chunk of one frame (the
+// default) builds the frame's own codebook.  A larger chunk builds the code of
+// the summed histogram of its coded frames (status OK) and gives it to each of
+// them; chunk_ref[f] = f - the chunk's first coded frame, which alone keeps
+// the code lengths in its stream.
+__global__ void __launch_bounds__(1024) k_huffman(DevParams p, Scratch s, uint32_t n_frames) {
   extern __shared__ __align__(16) unsigned char dsm[];
   HuffSmem& h = *reinterpret_cast<HuffSmem*>(dsm);
-  const uint32_t f = blockIdx.x;
-  const int st = build_codebook(s.hist + (size_t)f * kMaxSymbols, p.nsym, h,
-                                s.cb_len + (size_t)f * kMaxSymbols, s.cb_code + (size_t)f * kMaxSymbols);
-  if (threadIdx.x == 0 && st != ROIBIN_OK && s.status[f] == ROIBIN_OK) s.status[f] = st;
+  uint32_t* hsum = reinterpret_cast<uint32_t*>(dsm + align16(sizeof(HuffSmem)));  // [kMaxSymbols]
+  __shared__ int head;
+  const uint32_t c0 = blockIdx.x * p.chunk, c1 = min(n_frames, c0 + p.chunk);
+  if (p.chunk == 1) {
+    const uint32_t f = c0;
+    const int st = build_codebook(s.hist + (size_t)f * kMaxSymbols, p.nsym, h,
+                                  s.cb_len + (size_t)f * kMaxSymbols, s.cb_code + (size_t)f * kMaxSymbols);
+    if (threadIdx.x == 0) {
+      if (st != ROIBIN_OK && s.status[f] == ROIBIN_OK) s.status[f] = st;
+      s.chunk_ref[f] = 0;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    head = -1;
+    for (uint32_t f = c0; f < c1 && head < 0; ++f)
+      if (s.status[f] == ROIBIN_OK) head = (int)f;
+  }
+  __syncthreads();
+  if (head < 0) return;  // no coded frame in the chunk
+  for (uint32_t k = threadIdx.x; k < p.nsym; k += blockDim.x) {
+    uint32_t t = 0;
+    for (uint32_t f = c0; f < c1; ++f)
+      if (s.status[f] == ROIBIN_OK) t += s.hist[(size_t)f * kMaxSymbols + k];
+    hsum[k] = t;
+  }
+  __syncthreads();
+  const int st = build_codebook(hsum, p.nsym, h, s.cb_len + (size_t)head * kMaxSymbols,
+                                s.cb_code + (size_t)head * kMaxSymbols);
+  __syncthreads();
+  for (uint32_t f = (uint32_t)head + 1; f < c1; ++f) {
+    if (s.status[f] != ROIBIN_OK) continue;
+    for (uint32_t k = threadIdx.x; k < p.nsym; k += blockDim.x) {
+      s.cb_len[(size_t)f * kMaxSymbols + k] = s.cb_len[(size_t)head * kMaxSymbols + k];
+      s.cb_code[(size_t)f * kMaxSymbols + k] = s.cb_code[(size_t)head * kMaxSymbols + k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (uint32_t f = (uint32_t)head; f < c1; ++f) {
+      if (s.status[f] != ROIBIN_OK) continue;
+      s.chunk_ref[f] = f - (uint32_t)head;
+      if (st != ROIBIN_OK) s.status[f] = st;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -535,8 +583,9 @@ __global__ void __launch_bounds__(1024) k_plan(DevParams p, Scratch s, PlainArgs
   pl.n_pq = carry[2];
   pl.off_peaks = kHeaderBytes;
   pl.off_roi = pl.off_peaks + align16((uint64_t)pl.n_peaks * 6);
-  pl.off_len = pl.off_roi + align16((uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4);
-  pl.off_cidx = pl.off_len + align16(p.nsym);
+  const uint32_t ref = p.chunk > 1 ? s.chunk_ref[f] : 0u;  // the code lengths live in the chunk's head
+  pl.off_len = pl.off_roi + roi_in_place_bytes(p, pl.n_peaks);
+  pl.off_cidx = pl.off_len + (ref == 0 ? align16(p.nsym) : 0);
   pl.off_lo = pl.off_cidx + align16((uint64_t)p.n_chunks * 4);
   pl.off_pq = pl.off_lo + align16((uint64_t)pl.n_lo * 8);
   pl.off_bits = pl.off_pq + align16((uint64_t)pl.n_pq * 8);
@@ -573,6 +622,7 @@ __global__ void __launch_bounds__(1024) k_plan(DevParams p, Scratch s, PlainArgs
     h[17] = (uint32_t)(pl.total >> 32);
     h[18] = p.dims == 2 ? 0u : (uint32_t)p.dims;  // Lorenzo dimension, 0 for the default 2
     for (int i = 19; i < 24; ++i) h[i] = 0;
+    h[22] = ref;  // frames back to the stream with the code lengths (0: this one)
   }
   // peaks (u16 triples) + padding
   const uint32_t* keys = s.peak_key + (size_t)f * p.max_peaks;
@@ -585,11 +635,13 @@ __global__ void __launch_bounds__(1024) k_plan(DevParams p, Scratch s, PlainArgs
     pk[3 * k + 2] = (uint16_t)(rem % p.W);
   }
   zero_bytes(out, pl.off_peaks + (uint64_t)pl.n_peaks * 6, pl.off_roi);
-  zero_bytes(out, pl.off_roi + (uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4, pl.off_len);
-  // code lengths + padding
-  for (uint32_t k = threadIdx.x; k < p.nsym; k += blockDim.x)
-    out[pl.off_len + k] = s.cb_len[(size_t)f * kMaxSymbols + k];
-  zero_bytes(out, pl.off_len + p.nsym, pl.off_cidx);
+  zero_bytes(out, pl.off_roi + (p.roi_coder ? 0 : (uint64_t)pl.n_peaks * p.roi_h * p.roi_w * 4), pl.off_len);
+  // code lengths + padding (a chunk's head only)
+  if (ref == 0) {
+    for (uint32_t k = threadIdx.x; k < p.nsym; k += blockDim.x)
+      out[pl.off_len + k] = s.cb_len[(size_t)f * kMaxSymbols + k];
+    zero_bytes(out, pl.off_len + p.nsym, pl.off_cidx);
+  }
   // chunk index + padding
   uint32_t* ci = reinterpret_cast<uint32_t*>(out + pl.off_cidx);
   for (uint32_t k = threadIdx.x; k < p.n_chunks; k += blockDim.x) ci[k] = cw[k];
@@ -749,10 +801,11 @@ cudaError_t launch_peaks_final(const DevParams& p, const Scratch& s, const Plain
 cudaError_t launch_huffman(const DevParams& p, const Scratch& s, uint32_t n, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_huffman, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HuffSmem));
+    cudaFuncSetAttribute(k_huffman, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(align16(sizeof(HuffSmem)) + kMaxSymbols * 4));
     attr_set = true;
   }
-  k_huffman<<<n, 1024, sizeof(HuffSmem), st>>>(p, s);
+  k_huffman<<<ceil_div(n, p.chunk), 1024, align16(sizeof(HuffSmem)) + kMaxSymbols * 4, st>>>(p, s, n);
   return cudaGetLastError();
 }
 

@@ -83,6 +83,9 @@ int validate_impl(const roibin_geometry* g, const roibin_params* p) {
   if (p->quant_radius < 2 || p->quant_radius > 512) return ROIBIN_ERR_INVALID_ARG;
   if (p->max_peaks < 0 || p->max_peaks > (int32_t)kMaxPeaksLimit) return ROIBIN_ERR_INVALID_ARG;
   if (p->lorenzo_dims < 1 || p->lorenzo_dims > 3) return ROIBIN_ERR_INVALID_ARG;
+  if (p->nhr_min_peaks < 0 || p->nhr_min_peaks > (int32_t)kMaxPeaksLimit) return ROIBIN_ERR_INVALID_ARG;
+  if (p->roi_coder < 0 || p->roi_coder > 1) return ROIBIN_ERR_INVALID_ARG;
+  if (p->chunk_frames < 1 || p->chunk_frames > 64) return ROIBIN_ERR_INVALID_ARG;
   if (!(p->pix_nsigma >= 0.0f) || std::isnan(p->amax_thr) || std::isnan(p->atot_thr) ||
       std::isnan(p->son_min))
     return ROIBIN_ERR_INVALID_ARG;
@@ -138,6 +141,9 @@ DevParams make_dev_params(const roibin_geometry& g, const roibin_params& p) {
   d.max_peaks = (uint32_t)p.max_peaks;
   d.thr_cap = kThrCap;
   d.dims = p.lorenzo_dims;
+  d.nhr_min = p.nhr_min_peaks;
+  d.roi_coder = p.roi_coder;
+  d.chunk = (uint32_t)p.chunk_frames;
   return d;
 }
 
@@ -208,7 +214,16 @@ uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s
   t.lane_bit = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
   t.lane_lo = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
   t.lane_pq = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
-  t.frame_done = c.take<uint32_t>(6ull * n + 1);  // the fused kernel's sync words
+  t.frame_done = c.take<uint32_t>(7ull * n + 1);  // the fused kernel's sync words
+  t.chunk_ref = c.take<uint32_t>(n);
+  if (d.roi_coder) {
+    const uint64_t mp = std::max<uint32_t>(d.max_peaks, 1);
+    t.roi_hist = c.take<uint32_t>((uint64_t)n * kRoiClasses);
+    t.roi_cnt = c.take<uint16_t>((uint64_t)n * mp * kRoiClasses);
+    t.roi_off = c.take<uint32_t>((uint64_t)n * mp);
+    t.roi_book = c.take<uint32_t>((uint64_t)n * 2 * kRoiClasses);
+    t.roi_plan = c.take<uint4>(n);
+  }
   if (s) *s = t;
   return c.off + 256;
 }
@@ -253,6 +268,14 @@ void choose_shape(const roibin_ctx* ctx, uint32_t n_frames, PlainArgs* a) {
   if (ctx->plain_bands) a->bands_per_panel = ctx->plain_bands;
 }
 
+// The ROI coder after either path (three kernels; none without the coder).
+int roi_code(roibin_ctx* ctx, const PlainArgs& a, cudaStream_t st) {
+  if (!ctx->dp.roi_coder) return ROIBIN_OK;
+  const cudaError_t e = timed(ctx, K_ROI_CODE, st, [&] { return launch_roi_code(ctx->dp, ctx->s, a, st); });
+  ctx->last_launches += 2;  // the coder is three kernels
+  return cuda_status(e);
+}
+
 int compress_plain(roibin_ctx* ctx, const PlainArgs& a, cudaStream_t st) {
   const DevParams& p = ctx->dp;
   const Scratch& s = ctx->s;
@@ -266,9 +289,9 @@ int compress_plain(roibin_ctx* ctx, const PlainArgs& a, cudaStream_t st) {
   if ((e = timed(ctx, K_CHUNKS, st, [&] { return launch_chunks(p, s, a.n_frames, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_PLAN, st, [&] { return launch_plan(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_ENCODE, st, [&] { return launch_encode(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
-  if (p.max_peaks > 0)
+  if (p.max_peaks > 0 && !p.roi_coder)
     if ((e = timed(ctx, K_ROI, st, [&] { return launch_roi(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
-  return ROIBIN_OK;
+  return roi_code(ctx, a, st);
 }
 
 int resolved_dec_path(const roibin_ctx* ctx) {
@@ -316,7 +339,8 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
     if (ctx->wait_limit_set) sh.wait_limit = ctx->wait_limit;
     cudaError_t e = timed(ctx, K_FUSED, st,
                           [&] { return launch_fused(ctx->dp, ctx->s, a, sh, ctx->fused_dense_peaks, st); });
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    return roi_code(ctx, a, st);
   }
   return compress_plain(ctx, a, st);
 }
@@ -532,6 +556,9 @@ int roibin_default_params(roibin_params* p) {
   p->quant_radius = 512;
   p->max_peaks = 2048;
   p->lorenzo_dims = 2;
+  p->nhr_min_peaks = 0;
+  p->roi_coder = 0;
+  p->chunk_frames = 1;
   return ROIBIN_OK;
 }
 
@@ -736,6 +763,21 @@ int roibin_compress(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
                          d_frame_status, static_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+namespace {
+// The end of every decompression: the ROI windows of frames whose ROI section
+// comes after the bitstream (any stream may carry one), then the statuses.
+int dec_finish(roibin_ctx* ctx, const DecArgs& a, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = timed(ctx, K_DEC_ROI_CODED, st, [&] { return launch_dec_roi_coded(ctx->dp, ctx->s, a, st); })) !=
+      cudaSuccess)
+    return cuda_status(e);
+  ctx->last_launches++;  // the status copy
+  return cuda_status(launch_dec_finish(ctx->s, a, st));
+}
+}  // namespace
+extern "C" {
+
 int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes, const uint64_t* d_frame_offsets,
                       uint32_t n_frames, float* d_frames_out, int32_t* d_frame_status, void* stream) {
   if (!ctx || !d_in || !d_frame_offsets || !d_frames_out || !d_frame_status) return ROIBIN_ERR_INVALID_ARG;
@@ -755,8 +797,7 @@ int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes, c
     ctx->last_launches++;  // the decode step is two kernels: sparse frames, then dense ones
     if ((e = timed(ctx, K_DEC_PANEL, st, [&] { return launch_dec_panel(p, s, a, st); })) != cudaSuccess)
       return cuda_status(e);
-    ctx->last_launches++;  // the status copy that ends the panel launch
-    return ROIBIN_OK;
+    return dec_finish(ctx, a, st);
   }
   if ((e = timed(ctx, K_DEC_DECODE, st, [&] { return launch_dec_decode(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_LORENZO, st, [&] { return launch_dec_lorenzo(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
@@ -772,8 +813,7 @@ int roibin_decompress(roibin_ctx* ctx, const uint8_t* d_in, uint64_t in_bytes, c
   if ((e = timed(ctx, K_DEC_PQ, st, [&] { return launch_dec_pq(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_UPSAMPLE, st, [&] { return launch_dec_upsample(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
   if ((e = timed(ctx, K_DEC_ROI, st, [&] { return launch_dec_roi(p, s, a, st); })) != cudaSuccess) return cuda_status(e);
-  ctx->last_launches++;  // the status copy that ends the ROI launch
-  return ROIBIN_OK;
+  return dec_finish(ctx, a, st);
 }
 
 int roibin_ctx_set_decompress_path(roibin_ctx* ctx, int path) {
@@ -1111,7 +1151,8 @@ int roibin_compress_frame_static(const roibin_geometry* g, const roibin_params* 
   if ((e = launch_chunks(dp, s, 1, st)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_plan(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
   if ((e = launch_encode(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
-  if (dp.max_peaks > 0 && (e = launch_roi(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
+  if (dp.max_peaks > 0 && !dp.roi_coder && (e = launch_roi(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
+  if (dp.roi_coder && (e = launch_roi_code(dp, s, a, st)) != cudaSuccess) return cuda_status(e);
   return ROIBIN_OK;
 }
 

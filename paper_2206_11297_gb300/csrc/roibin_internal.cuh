@@ -47,7 +47,18 @@ struct DevParams {
   uint32_t max_peaks;
   uint32_t thr_cap;
   int32_t dims;             // Lorenzo predictor order: 1 (frame run), 2 (panel), 3 (panel stack)
+  int32_t nhr_min;          // non-hit rejection: frames with fewer peaks are not compressed (0: off)
+  int32_t roi_coder;        // 0: raw ROI windows in place; 1: the lossless ROI coder (section at the end)
+  uint32_t chunk;           // frames of a call per chunk sharing one codebook (1: a codebook per frame)
 };
+
+// ROI coding (the section after the bitstream): 33 classes of a folded residual
+constexpr uint32_t kRoiClasses = 33u;
+constexpr uint32_t kRoiHead = 48u;  // code lengths, zero padded
+// bytes of the in-place ROI section of a frame with n peaks
+__host__ __device__ inline uint64_t roi_in_place_bytes(const DevParams& p, uint32_t n) {
+  return p.roi_coder ? 0u : (((uint64_t)n * p.roi_h * p.roi_w * 4 + 15u) & ~uint64_t(15u));
+}
 
 // Byte layout of one frame's stream, filled by the plan step.
 struct FramePlan {
@@ -63,6 +74,9 @@ struct DecInfo {
   int32_t R, roi_h, roi_w;
   uint32_t nsym;
   uint32_t sparse;    // 1: a length-1 code, and few other symbols in every chunk
+  uint32_t roi_coding, roi_words;  // header: ROI coding (0 in place, 1 coded, 2 raw at the end), its words
+  uint32_t back_ref;               // frames back to the stream with the code lengths (0: this one)
+  uint64_t off_roi_sec, roi_bytes; // the ROI section after the bitstream
 };
 
 // Per-frame scratch owned by the context (indexed by frame slot).
@@ -102,6 +116,13 @@ struct Scratch {
   uint32_t* lane_lo;          // [n][n_chunks][32] Lorenzo outliers before the lane, in its chunk
   uint32_t* lane_pq;          // [n][n_chunks][32] prequantisation outliers before the lane
   uint32_t* frame_done;     // [6 n + 1] stage counters and flags, ticket counter
+  // ROI coder (after either compression path)
+  uint32_t* roi_hist;       // [n][kRoiClasses] classes of the frame's windows
+  uint16_t* roi_cnt;        // [n][max_peaks][kRoiClasses] classes of each window
+  uint32_t* roi_off;        // [n][max_peaks] first word of each window
+  uint32_t* roi_book;       // [n][2 kRoiClasses] code length, then codeword, per class
+  uint4* roi_plan;          // [n] coding, section words, section offset (lo, hi)
+  uint32_t* chunk_ref;      // [n] frames back to the chunk's head (which keeps the code lengths); 0: a head
 };
 
 // count, first, index (34 words each), symbols; padded to 16 bytes
@@ -331,6 +352,194 @@ __device__ inline bool is_local_max_at(Px px, int H, int W, int r, int c, const 
   return true;
 }
 
+// is_local_max_at + evaluate_peak_at for one compile-time window and ring
+// (RANK, ring R0 .. R0 + DR): the same operations in the same order (so the
+// same float32 results), with every loop unrolled, so that the compiler sees
+// each neighbour's offset and issues the loads ahead of the ordered sums.
+// In-panel tests stay per pixel (a candidate may sit at the panel's edge).
+template <int RANK, int R0, int DR, class Px>
+__device__ __forceinline__ bool peak_test_fixed(Px px, int H, int W, int r, int c, const DevParams& p) {
+  constexpr int OUT = R0 + DR, RING = OUT - 1;
+  const float v = px(0, 0);
+  if (!(v >= p.amax)) return false;
+  bool ok = true;
+#pragma unroll
+  for (int dr = -RANK; dr <= RANK; ++dr) {
+#pragma unroll
+    for (int dc = -RANK; dc <= RANK; ++dc) {
+      if (dr == 0 && dc == 0) continue;
+      const int rr = r + dr, cc = c + dc;
+      if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+      const float u = px(dr, dc);
+      ok &= (dr < 0 || (dr == 0 && dc < 0)) ? (v > u) : (v >= u);
+    }
+  }
+  if (!ok) return false;
+  float sum = 0.0f;
+  int n = 0;
+#pragma unroll
+  for (int dr = -RING; dr <= RING; ++dr) {
+#pragma unroll
+    for (int dc = -RING; dc <= RING; ++dc) {
+      if (dr * dr + dc * dc < R0 * R0 || dr * dr + dc * dc >= OUT * OUT) continue;
+      const int rr = r + dr, cc = c + dc;
+      if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+      sum = __fadd_rn(sum, px(dr, dc));
+      ++n;
+    }
+  }
+  float bkg = 0.0f, var = 0.0f;
+  if (n > 0) {
+    bkg = __fdiv_rn(sum, (float)n);
+    float ss = 0.0f;
+#pragma unroll
+    for (int dr = -RING; dr <= RING; ++dr) {
+#pragma unroll
+      for (int dc = -RING; dc <= RING; ++dc) {
+        if (dr * dr + dc * dc < R0 * R0 || dr * dr + dc * dc >= OUT * OUT) continue;
+        const int rr = r + dr, cc = c + dc;
+        if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+        const float d = __fsub_rn(px(dr, dc), bkg);
+        ss = __fadd_rn(ss, __fmul_rn(d, d));
+      }
+    }
+    var = __fdiv_rn(ss, (float)n);
+  }
+  const float sigma = __fsqrt_rn(var);
+  const float thr = __fmul_rn(p.pix_nsigma, sigma);
+  int npix = 0;
+  float atot = 0.0f;
+#pragma unroll
+  for (int dr = -RANK; dr <= RANK; ++dr) {
+#pragma unroll
+    for (int dc = -RANK; dc <= RANK; ++dc) {
+      const int rr = r + dr, cc = c + dc;
+      if (rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+      const float d = __fsub_rn(px(dr, dc), bkg);
+      if (d > thr) {
+        ++npix;
+        atot = __fadd_rn(atot, d);
+      }
+    }
+  }
+  if (npix < p.npix_min || npix > p.npix_max) return false;
+  if (!(atot > p.atot_thr)) return false;
+  const float noise = __fmul_rn(__fmul_rn(p.son_min, sigma), __fsqrt_rn((float)npix));
+  return atot > noise;
+}
+
+// The same test for a candidate whose neighbourhood rows [rb0, rb1) of its
+// panel sit in `band` (row pitch W).  It goes row by row: the row's pixels are
+// read unconditionally from clamped in-band addresses (so the reads of a row
+// are issued together), and out-of-panel or off-ring pixels are then masked
+// out by selects, so no pixel is a branch.  The sums take exactly the
+// in-panel pixels in row-major order, as evaluate_peak_at does, so the results
+// are the same bit for bit.
+template <int RANK, int R0, int DR>
+__device__ __forceinline__ bool peak_test_band(const float* band, int rb0, int rb1, int H, int W, int r, int c,
+                                               const DevParams& p) {
+  constexpr int OUT = R0 + DR, RING = OUT - 1, REACH = RANK > RING ? RANK : RING, SIDE = 2 * REACH + 1;
+  static_assert(SIDE <= 32, "one bit per column of the neighbourhood");
+  int col[SIDE];        // clamped columns c - REACH .. c + REACH
+  uint32_t col_in = 0;  // bit k: column c + k - REACH is in the panel
+#pragma unroll
+  for (int k = 0; k < SIDE; ++k) {
+    const int cc = c + k - REACH;
+    col_in |= (uint32_t)(cc >= 0 && cc < W) << k;
+    col[k] = min(max(cc, 0), W - 1);
+  }
+  auto row_at = [&](int dr) { return band + (min(max(r + dr, rb0), rb1 - 1) - rb0) * W; };
+  auto row_mask = [&](int dr) { return (r + dr >= 0 && r + dr < H) ? col_in : 0u; };
+  const float v = band[(r - rb0) * W + c];
+  if (!(v >= p.amax)) return false;
+  bool ok = true;
+#pragma unroll 1
+  for (int dr = -RANK; dr <= RANK; ++dr) {
+    const float* rp = row_at(dr);
+    const uint32_t m = row_mask(dr);
+    float x[2 * RANK + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * RANK + 1; ++k) x[k] = rp[col[REACH - RANK + k]];
+#pragma unroll
+    for (int k = 0; k < 2 * RANK + 1; ++k) {
+      const int dc = k - RANK;
+      const bool in = ((m >> (REACH + dc)) & 1u) && (dr != 0 || dc != 0);
+      const bool pass = (dr < 0 || (dr == 0 && dc < 0)) ? (v > x[k]) : (v >= x[k]);
+      ok &= pass || !in;
+    }
+  }
+  if (!ok) return false;
+  float sum = 0.0f;
+  int n = 0;
+#pragma unroll 1
+  for (int dr = -RING; dr <= RING; ++dr) {
+    const float* rp = row_at(dr);
+    const uint32_t m = row_mask(dr);
+    float x[2 * RING + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * RING + 1; ++k) x[k] = rp[col[REACH - RING + k]];
+#pragma unroll
+    for (int k = 0; k < 2 * RING + 1; ++k) {
+      const int dc = k - RING, d2 = dr * dr + dc * dc;
+      const bool in = ((m >> (REACH + dc)) & 1u) && d2 >= R0 * R0 && d2 < OUT * OUT;
+      sum = in ? __fadd_rn(sum, x[k]) : sum;
+      n += in;
+    }
+  }
+  float bkg = 0.0f, var = 0.0f;
+  if (n > 0) {
+    bkg = __fdiv_rn(sum, (float)n);
+    float ss = 0.0f;
+#pragma unroll 1
+    for (int dr = -RING; dr <= RING; ++dr) {
+      const float* rp = row_at(dr);
+      const uint32_t m = row_mask(dr);
+      float x[2 * RING + 1];
+#pragma unroll
+      for (int k = 0; k < 2 * RING + 1; ++k) x[k] = rp[col[REACH - RING + k]];
+#pragma unroll
+      for (int k = 0; k < 2 * RING + 1; ++k) {
+        const int dc = k - RING, d2 = dr * dr + dc * dc;
+        const bool in = ((m >> (REACH + dc)) & 1u) && d2 >= R0 * R0 && d2 < OUT * OUT;
+        const float d = __fsub_rn(x[k], bkg);
+        ss = in ? __fadd_rn(ss, __fmul_rn(d, d)) : ss;
+      }
+    }
+    var = __fdiv_rn(ss, (float)n);
+  }
+  const float sigma = __fsqrt_rn(var);
+  const float thr = __fmul_rn(p.pix_nsigma, sigma);
+  int npix = 0;
+  float atot = 0.0f;
+#pragma unroll 1
+  for (int dr = -RANK; dr <= RANK; ++dr) {
+    const float* rp = row_at(dr);
+    const uint32_t m = row_mask(dr);
+    float x[2 * RANK + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * RANK + 1; ++k) x[k] = rp[col[REACH - RANK + k]];
+#pragma unroll
+    for (int k = 0; k < 2 * RANK + 1; ++k) {
+      const float d = __fsub_rn(x[k], bkg);
+      const bool take = ((m >> (REACH + k - RANK)) & 1u) && d > thr;
+      npix += take;
+      atot = take ? __fadd_rn(atot, d) : atot;
+    }
+  }
+  if (npix < p.npix_min || npix > p.npix_max) return false;
+  if (!(atot > p.atot_thr)) return false;
+  const float noise = __fmul_rn(__fmul_rn(p.son_min, sigma), __fsqrt_rn((float)npix));
+  return atot > noise;
+}
+
+// a1 + a2 for one thread: the unrolled form for the paper's window and ring
+// (rank 3, ring 5 .. 7), else the general loops.  Same results either way.
+template <class Px>
+__device__ __forceinline__ bool peak_test_one(Px px, int H, int W, int r, int c, const DevParams& p) {
+  if (p.rank == 3 && p.ring_r0 == 5 && p.ring_dr == 2) return peak_test_fixed<3, 5, 2>(px, H, W, r, c, p);
+  return is_local_max_at(px, H, W, r, c, p) && evaluate_peak_at(px, H, W, r, c, p);
+}
+
 __device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int W, int r, int c,
                                      const DevParams& p) {
   return evaluate_peak_at([&](int dr, int dc) { return __ldg(panel + (size_t)(r + dr) * W + (c + dc)); },
@@ -338,21 +547,22 @@ __device__ inline bool evaluate_peak(const float* __restrict__ panel, int H, int
 }
 
 // One warp copies the roi_h x roi_w window centred on (r, c) of `panel` to
-// dst (fill 0 past the panel edge).  Loads are batched ahead of the stores.
+// dst (fill 0 past the panel edge).  Loads are batched ahead of the stores,
+// 12 per lane, so a window of up to 384 pixels (19 x 19) costs one round trip.
 __device__ inline void warp_copy_roi(const float* __restrict__ panel, int H, int W, int r, int c, int roi_h,
                                      int roi_w, float* dst) {
   const int r0 = r - roi_h / 2, c0 = c - roi_w / 2, win = roi_h * roi_w;
   const int lane = (int)lane_id();
-  for (int base = 0; base < win; base += 8 * 32) {
-    float vals[8];
+  for (int base = 0; base < win; base += 12 * 32) {
+    float vals[12];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 12; ++u) {
       const int e = base + u * 32 + lane;
       const int rr = r0 + e / roi_w, cc = c0 + e % roi_w;
       vals[u] = (e < win && rr >= 0 && rr < H && cc >= 0 && cc < W) ? __ldg(panel + (size_t)rr * W + cc) : 0.0f;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 12; ++u) {
       const int e = base + u * 32 + lane;
       if (e < win) dst[e] = vals[u];
     }
@@ -790,6 +1000,8 @@ struct FusedShape {
   uint32_t lag1, lag2;           // frames between stages in the ticket order (per launch)
   uint32_t input_evict_first;    // L2 policy of the streamed rows (1 = evict first)
   uint32_t wait_limit;           // polls of a flag wait before it reports ROIBIN_ERR_TIMEOUT
+  uint32_t band_rows;            // dense peaks: panel rows staged at once (band + halo)
+  uint32_t smem_dense;           // shared memory of the dense-peaks variant (>= smem)
   uint32_t off_ctl, off_bar, off_hist, off_pql, off_thr, off_ring, off_nb, off_acc, off_cand;  // streaming role
   uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw, off_offs;  // codebook / plan roles
   uint32_t off_stage;                                                        // size / write roles
@@ -832,6 +1044,8 @@ enum KernelId {
   K_ROI_MASK,
   K_PACK,
   K_DEC_CARRY,
+  K_ROI_CODE,
+  K_DEC_ROI_CODED,
   K_COUNT
 };
 const char* kernel_name(int id);
@@ -845,6 +1059,9 @@ cudaError_t launch_chunks(const DevParams& p, const Scratch& s, uint32_t n, cuda
 cudaError_t launch_plan(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
 cudaError_t launch_encode(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
 cudaError_t launch_roi(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
+// ROI coder: classes and counts per window, codebook and layout per frame,
+// then the bits (three kernels); frames whose status is not OK are skipped
+cudaError_t launch_roi_code(const DevParams& p, const Scratch& s, const PlainArgs& a, cudaStream_t st);
 cudaError_t launch_last_peaks(const DevParams& p, const Scratch& s, uint16_t* peaks, uint32_t* npeaks,
                               uint32_t n, cudaStream_t st);
 
@@ -865,6 +1082,10 @@ cudaError_t launch_dec_carry(const DevParams& p, const Scratch& s, const DecArgs
 cudaError_t launch_dec_pq(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_upsample(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
 cudaError_t launch_dec_roi(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+// restores the ROI windows of frames with a coded (or moved raw) ROI section
+cudaError_t launch_dec_roi_coded(const DevParams& p, const Scratch& s, const DecArgs& a, cudaStream_t st);
+// copies the per-frame statuses to the caller (ends every decompression)
+cudaError_t launch_dec_finish(const Scratch& s, const DecArgs& a, cudaStream_t st);
 // the panel path: decode through the prefix table into symbols, then one block
 // per (frame, panel) rebuilds the panel strip by strip
 uint32_t dec_panel_rows(const DevParams& p);  // binned rows per strip; 0: panel path unavailable

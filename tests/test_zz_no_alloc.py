@@ -121,3 +121,13 @@ def test_static_scratch_capacity_error():
     assert int(nb.item()) == need
     ost, osize = oracle.compress_frame(frame, oracle.make_params(**p.as_dict()), capacity=small)
     assert ost == oracle.ERR_CAPACITY and osize == need
+
+
+@pytest.mark.gpu
+def test_static_scratch_with_roi_coder():
+    """The ROI coder's kernels run from the same fixed area."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    r = RECIPES["cspad_single"]
+    _static_vs_context(r.geometry, make_frame(r, 0), rb.default_params(roi_coder=1, npix_max=49))
