@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-dims", action="store_true", help="skip the Lorenzo-dimension variants")
     ap.add_argument("--no-epix", action="store_true", help="skip the epix10k hot-pixel workload")
     ap.add_argument("--no-npix", action="store_true", help="skip the npix_max = 49 variant")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--min-load-seconds", type=float, default=2.0,
                     help="keep the GPU busy at least this long before timing (clock sampling)")
@@ -381,6 +382,47 @@ def epix_variants(args, stream, local):
     return res
 
 
+def serving_runs(args, local):
+    """The serving loop under Poisson arrivals of 1-64-frame requests over three
+    detector geometries (CSPAD-like, epix10k-like with 1% hot pixels, 8 x 512 x
+    1024), 40 GB admission budget, eb 10: once with the frames arriving in
+    pinned host memory and the streams returned to the host, once with the
+    frames already in device memory (a detector writing into HBM) and the
+    streams left there.  Latency runs from a request's arrival to its streams
+    being in place."""
+    import torch
+    import paper_2206_11297_gb300 as rb
+    from paper_2206_11297_gb300 import serving
+    host_pools = {}
+    for name in ("cspad_batch", "epix_hot", "jungfrau_mixed"):
+        r = RECIPES[name]
+        host_pools[r.geometry] = torch.from_numpy(make_batch_threaded(r, 96))
+    params = rb.default_params(max_peaks=8192)
+    res = {}
+    for mode, rate in (("host", 300.0), ("device", 3000.0)):
+        dev = mode == "device"
+        pools = {g: (t.to(torch.device("cuda", local)) if dev else t.pin_memory()) for g, t in host_pools.items()}
+        server = serving.Server(params, hbm_budget=40 << 30, lane_frames=64, keep_streams=False,
+                                max_queued_frames=4096, output=mode, device=torch.device("cuda", local))
+        serving.run(pools, serving.poisson_requests(pools, rate, 0.5, 64, seed=1), server)  # warm-up
+        sched = serving.poisson_requests(pools, rate, 2.0, 64, seed=2)
+        server.rejected = 0
+        t0 = time.perf_counter()
+        reqs = serving.run(pools, sched, server)
+        wall = time.perf_counter() - t0
+        lat = np.array([r.latency for r in reqs]) * 1e3
+        in_bytes = sum(r.frames.numel() * 4 for r in reqs)
+        res[mode] = {"input": mode, "output": mode, "offered_requests_per_s": rate, "requests": len(reqs),
+                     "rejected": server.rejected, "sustained_gbs": in_bytes / 1e9 / wall,
+                     "frames_per_s": sum(r.frames.shape[0] for r in reqs) / wall,
+                     "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                     "all_ok": all(x == 0 for r in reqs for x in r.status)}
+        server.close()
+        del pools
+        torch.cuda.empty_cache()
+    return res
+
+
 def _hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     return json.load(open(path))["hbm_gbs"] if os.path.exists(path) else 6800.0
@@ -630,6 +672,8 @@ def run_ours(args, rank, local, world):
         line["epix"] = epix_variants(args, stream, local)
     if not args.no_mixed:
         line["mixed_graph"] = mixed_graph(args, dev, local, stream)
+    if not args.no_serving:
+        line["serving"] = serving_runs(args, local)
     if not args.no_dims:
         ctx.close()  # its scratch is not needed again; the variants take their own
         line["lorenzo_dims"] = lorenzo_dims(args, frames, out, nbytes, status, stride, stream, local)

@@ -3,7 +3,8 @@
 //
 // Work items are handed out in order by an atomic ticket counter to a grid of
 // resident CTAs (several per SM).  A streaming item is a group of k panels of
-// one frame side by side (k NP <= 256 float4 columns, NP = cols / 4).  For it
+// one frame side by side (k NP <= 217 kG float4 columns, NP = cols / 4, kG
+// column groups of 217: 1, or 2 for panels wider than 868 columns).  For it
 // a CTA:
 //   - streams the raw rows through a ring of 1-D TMA bulk copies (L2
 //     evict-first) while the previous rows are coded;
@@ -34,6 +35,8 @@ constexpr int kPT = 256;       // threads per CTA
 constexpr int kPW = kPT / 32;  // warps per CTA
 constexpr uint32_t kMaxK = 8;   // panels per streaming item
 constexpr uint32_t kConsumerWarps = 7;  // warps that code rows (31 columns each)
+constexpr uint32_t kGroupCols = kConsumerWarps * 31;  // float4 columns of one column group
+constexpr uint32_t kMaxG = 2;           // column groups per consumer lane
 constexpr uint32_t kProducerWarp = 7;   // the warp whose lane 0 issues the row copies
 constexpr uint32_t kThrLocalCap = 256;
 constexpr uint32_t kBlockKey = 1u << 31;  // a listed 2x4 block (else a listed candidate pixel)
@@ -293,14 +296,14 @@ __device__ __noinline__ void dense_band_peaks(const DevParams& p, const Scratch&
 // ---------------------------------------------------------------------------
 // One streaming item: panels pn0 .. pn0 + kp - 1 of frame f, side by side.
 //
-// Thread t < kp NP owns float4 column pc = t mod NP of panel slot pi = t / NP
-// (two bins per binned row) and walks down the rows.  The q values of the row
+// A consumer lane owns float4 columns of the item (two bins per binned row),
+// one per column group, and walks down the rows.  The q values of the row
 // above stay in its registers; the bin to the left comes from the previous
 // lane by shuffle, and lane 0 reads the previous warp's last column from
 // shared memory.  A step covers RB binned rows: phase A bins and
 // prequantises them into registers, one barrier (it also frees the ring
 // slot), then phase B forms the Lorenzo residuals, code bytes and histogram.
-template <int RB, bool kDense>
+template <int RB, bool kDense, int kG>
 __device__ void process_item(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
                              unsigned char* sm, uint32_t f, uint32_t u, uint32_t& ring_iter) {
   const StreamView v = stream_view(sm, sh);
@@ -310,21 +313,11 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   const uint32_t NP = p.W >> 2, Mp = p.Hb * p.Wb, plane = p.H * p.W;
   const uint32_t pn0 = u * sh.k, kp = min(sh.k, p.P - pn0);
-  // lane l >= 1 of warp w owns float4 column 31 w + l - 1 of the item; lane 0
-  // recomputes the column before (the previous warp's last) for its left
-  // neighbour, so warps never wait for one another
+  // lane l >= 1 of warp w owns float4 column 217 g + 31 w + l - 1 of the item
+  // in each column group g; lane 0 recomputes the column before (the previous
+  // warp's last) for its left neighbour, so warps never wait for one another
   const uint32_t C = kp * NP;
-  const int gc = 31 * (int)warp + (int)lane - 1;
-  const bool col_ok = gc >= 0 && (uint32_t)gc < C;
-  const bool owned = col_ok && lane >= 1 && warp < kConsumerWarps;
-  const uint32_t gcol = col_ok ? (uint32_t)gc : 0u;
-  const uint32_t pi = gcol / NP, pc = gcol - pi * NP;
   const float* item_px = a.frames + (size_t)f * p.frame_px + (size_t)pn0 * plane;
-  const size_t fbin = (size_t)f * p.M + (size_t)(pn0 + pi) * Mp;  // first bin of the lane's panel
-  uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride + (size_t)(pn0 + pi) * Mp + 2 * pc;
-  uint16_t* esc = s.codes + fbin;
-  int32_t* lo_delta = s.lo_delta + fbin;
-  uint32_t* pq_bits = s.pq_bits + fbin;
   const uint32_t slot_floats = 2 * RB * p.W;  // one panel's rows in a ring slot
   const size_t fu = (size_t)f * p.P + u;
   uint64_t* full_bar = v.bars;                 // [stages] rows landed (TMA transaction count)
@@ -346,6 +339,10 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
 
   const uint32_t n_steps = ceil_div(p.Hb, (uint32_t)RB);
   const bool find = a.user_peaks == nullptr;
+  // candidates past the shared list go to the CTA's list in global memory
+  // (the dense-peaks variant tests such items band by band instead)
+  const bool spills = !kDense && blockIdx.x < s.thr_spill_ctas;
+  auto spill_at = [&](uint32_t e) -> uint32_t& { return s.thr_spill[(size_t)blockIdx.x * kThrSpill + e]; };
   bool timed_out = false;
   uint32_t slot = ring_iter % sh.stages, phase = (ring_iter / sh.stages) & 1u;
   auto advance = [&]() {
@@ -379,103 +376,139 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
       advance();
     }
   } else {
-    int2 qu = make_int2(0, 0);  // q of the lane's two bins in the row above
-    int32_t qd = 0;             // q of the bin left of them in the row above
-    const bool first_col = pc == 0;  // the bin to the left lies outside the panel
+    // kG column groups: a panel of up to 868 kG pixels per row fits one item
+    struct Col {
+      bool owned, first;
+      uint32_t pi, pc;
+      uint8_t* codes;      // the column's code bytes in binned row 0
+      uint16_t* esc;       // the lane's panel: escape codes, Lorenzo-outlier deltas and
+      int32_t* lo_delta;   // prequantisation-outlier bits, at their bin
+      uint32_t* pq_bits;
+    };
+    Col cols[kG];
+    int2 qu[kG];   // q of the lane's two bins in the row above, per group
+    int32_t qd[kG];  // q of the bin left of them in the row above
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      Col& c = cols[g];
+      const int gc = (int)kGroupCols * g + 31 * (int)warp + (int)lane - 1;
+      const bool ok = gc >= 0 && (uint32_t)gc < C;
+      c.owned = ok && lane >= 1 && warp < kConsumerWarps;
+      const uint32_t gcol = ok ? (uint32_t)gc : 0u;
+      c.pi = gcol / NP;
+      c.pc = gcol - c.pi * NP;
+      c.first = c.pc == 0;  // the bin to the left lies outside the panel
+      const size_t fbin = (size_t)f * p.M + (size_t)(pn0 + c.pi) * Mp;  // first bin of the lane's panel
+      c.codes = s.codes8 + (size_t)f * sh.codes_stride + (size_t)(pn0 + c.pi) * Mp + 2 * c.pc;
+      c.esc = s.codes + fbin;
+      c.lo_delta = s.lo_delta + fbin;
+      c.pq_bits = s.pq_bits + fbin;
+      qu[g] = make_int2(0, 0);
+      qd[g] = 0;
+    }
 
     // One step: RB binned rows.  FULL steps have RB rows of two raw rows each
     // (every step but possibly the panel's last), so they need no row checks.
     // Rare cases (prequantisation screen undecided, a block >= amax_thr, a
     // non-zero residual) are flagged per row and handled after the rows by
-    // the whole warp, so the common path has no divergent branch.
+    // the whole warp, so the common path has no divergent branch.  Every
+    // group reads its rows (phase A) before the warp leaves the ring slot.
     auto step = [&](uint32_t st, auto full_tag) {
       constexpr bool FULL = decltype(full_tag)::value;
       const uint32_t i0 = st * RB;
-      const float4* rows =
-          reinterpret_cast<const float4*>(v.ring + (size_t)slot * sh.stage_bytes) + pi * (slot_floats / 4) + pc;
-      int2 qa[RB];
-      // phase A: q of the lane's bins in the step's rows
-      uint32_t redo = 0, hot = 0;  // bit ii: row ii needs the full test / holds a block >= amax_thr
+      int2 qa[kG][RB];
 #pragma unroll
-      for (int ii = 0; ii < RB; ++ii) {
-        const uint32_t i = i0 + ii;
-        qa[ii] = make_int2(0, 0);
-        if (!FULL && i >= p.Hb) continue;
-        const bool two = FULL || 2 * i + 1 < p.H;
-        const float4 va = rows[(2 * ii) * NP];
-        const float4 vb = two ? rows[(2 * ii + 1) * NP] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float v0, v1;
-        bin_pair(va, vb, two, v0, v1);
-        int32_t q0, q1;
-        const bool ok = prequant_fast(v0, p, q0) & prequant_fast(v1, p, q1);
-        redo |= (uint32_t)!ok << ii;
-        qa[ii] = make_int2(q0, q1);
-        if (find) {
-          const float m =
-              fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)), fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
-          hot |= (uint32_t)(m >= p.amax) << ii;
-        }
-      }
-      if (__any_sync(0xffffffffu, redo != 0)) {  // the screen could not decide: the full test
+      for (int g = 0; g < kG; ++g) {
+        const uint32_t pi = cols[g].pi, pc = cols[g].pc;
+        const bool owned = cols[g].owned;
+        uint32_t* pq_bits = cols[g].pq_bits;
+        const float4* rows =
+            reinterpret_cast<const float4*>(v.ring + (size_t)slot * sh.stage_bytes) + pi * (slot_floats / 4) + pc;
+        // phase A: q of the lane's bins in the step's rows
+        uint32_t redo = 0, hot = 0;  // bit ii: row ii needs the full test / holds a block >= amax_thr
 #pragma unroll
         for (int ii = 0; ii < RB; ++ii) {
-          if (!((redo >> ii) & 1u)) continue;
           const uint32_t i = i0 + ii;
-          const bool two = 2 * i + 1 < p.H;
+          qa[g][ii] = make_int2(0, 0);
+          if (!FULL && i >= p.Hb) continue;
+          const bool two = FULL || 2 * i + 1 < p.H;
           const float4 va = rows[(2 * ii) * NP];
           const float4 vb = two ? rows[(2 * ii + 1) * NP] : make_float4(0.f, 0.f, 0.f, 0.f);
           float v0, v1;
           bin_pair(va, vb, two, v0, v1);
-          const Quant Q0 = prequantize(v0, p), Q1 = prequantize(v1, p);
-          qa[ii] = make_int2(Q0.q, Q1.q);
-          if (owned && (Q0.outlier | Q1.outlier)) {
-            const uint32_t lb = i * p.Wb + 2 * pc;
-            atomicAdd(v.ctl + CTL_PQ + pi, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
-            const uint32_t at = atomicAdd(v.ctl + CTL_PQN, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
-            uint32_t e = at;
-            if (Q0.outlier) {
-              pq_bits[lb] = Q0.outlier_bits;
-              if (e < kPqList) v.pql[e] = pi * Mp + lb;
-              ++e;
-            }
-            if (Q1.outlier) {
-              pq_bits[lb + 1] = Q1.outlier_bits;
-              if (e < kPqList) v.pql[e] = pi * Mp + lb + 1;
+          int32_t q0, q1;
+          const bool ok = prequant_fast(v0, p, q0) & prequant_fast(v1, p, q1);
+          redo |= (uint32_t)!ok << ii;
+          qa[g][ii] = make_int2(q0, q1);
+          if (find) {
+            const float m =
+                fmaxf(fmaxf(fmaxf(va.x, va.y), fmaxf(va.z, va.w)), fmaxf(fmaxf(vb.x, vb.y), fmaxf(vb.z, vb.w)));
+            hot |= (uint32_t)(m >= p.amax) << ii;
+          }
+        }
+        if (__any_sync(0xffffffffu, redo != 0)) {  // the screen could not decide: the full test
+#pragma unroll
+          for (int ii = 0; ii < RB; ++ii) {
+            if (!((redo >> ii) & 1u)) continue;
+            const uint32_t i = i0 + ii;
+            const bool two = 2 * i + 1 < p.H;
+            const float4 va = rows[(2 * ii) * NP];
+            const float4 vb = two ? rows[(2 * ii + 1) * NP] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float v0, v1;
+            bin_pair(va, vb, two, v0, v1);
+            const Quant Q0 = prequantize(v0, p), Q1 = prequantize(v1, p);
+            qa[g][ii] = make_int2(Q0.q, Q1.q);
+            if (owned && (Q0.outlier | Q1.outlier)) {
+              const uint32_t lb = i * p.Wb + 2 * pc;
+              atomicAdd(v.ctl + CTL_PQ + pi, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
+              const uint32_t at = atomicAdd(v.ctl + CTL_PQN, (uint32_t)Q0.outlier + (uint32_t)Q1.outlier);
+              uint32_t e = at;
+              if (Q0.outlier) {
+                pq_bits[lb] = Q0.outlier_bits;
+                if (e < kPqList) v.pql[e] = pi * Mp + lb;
+                ++e;
+              }
+              if (Q1.outlier) {
+                pq_bits[lb + 1] = Q1.outlier_bits;
+                if (e < kPqList) v.pql[e] = pi * Mp + lb + 1;
+              }
             }
           }
         }
-      }
-      if (!owned) hot = 0;
-      if (__any_sync(0xffffffffu, hot != 0)) {
-        // a 2x4 block holding a pixel >= amax_thr.  With rank >= 3 the block
-        // lies inside the window of each of its pixels, so only its first
-        // maximum can be a candidate: that pixel and its value are listed.
-        // With a smaller rank the block itself is listed.
+        if (!owned) hot = 0;
+        if (__any_sync(0xffffffffu, hot != 0)) {
+          // a 2x4 block holding a pixel >= amax_thr.  With rank >= 3 the block
+          // lies inside the window of each of its pixels, so only its first
+          // maximum can be a candidate: that pixel and its value are listed.
+          // With a smaller rank the block itself is listed.
 #pragma unroll
-        for (int ii = 0; ii < RB; ++ii) {
-          if (!((hot >> ii) & 1u)) continue;
-          const uint32_t i = i0 + ii;
-          uint32_t key = kBlockKey | (pi * plane + 2 * i * p.W + 4 * pc);
-          float best = 0.0f;
-          if (p.rank >= 3) {
-            const bool two = 2 * i + 1 < p.H;
-            const float4 va = rows[(2 * ii) * NP];
-            const float4 vb = rows[(2 * ii + 1) * NP];  // inside the slot; used only when two
-            const float px[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-            uint32_t at = 0;
-            best = px[0];
+          for (int ii = 0; ii < RB; ++ii) {
+            if (!((hot >> ii) & 1u)) continue;
+            const uint32_t i = i0 + ii;
+            uint32_t key = kBlockKey | (pi * plane + 2 * i * p.W + 4 * pc);
+            float best = 0.0f;
+            if (p.rank >= 3) {
+              const bool two = 2 * i + 1 < p.H;
+              const float4 va = rows[(2 * ii) * NP];
+              const float4 vb = rows[(2 * ii + 1) * NP];  // inside the slot; used only when two
+              const float px[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+              uint32_t at = 0;
+              best = px[0];
 #pragma unroll
-            for (int e = 1; e < 8; ++e)
-              if ((e < 4 || two) && (px[e] > best || best != best)) {
-                best = px[e];
-                at = e;
-              }
-            key = pi * plane + (2 * i + (at >> 2)) * p.W + 4 * pc + (at & 3u);
-          }
-          const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
-          if (slot_t < kThrLocalCap) {
-            v.thr[slot_t] = key;
-            v.thrv[slot_t] = best;
+              for (int e = 1; e < 8; ++e)
+                if ((e < 4 || two) && (px[e] > best || best != best)) {
+                  best = px[e];
+                  at = e;
+                }
+              key = pi * plane + (2 * i + (at >> 2)) * p.W + 4 * pc + (at & 3u);
+            }
+            const uint32_t slot_t = atomicAdd(v.ctl + CTL_THR, 1u);
+            if (slot_t < kThrLocalCap) {
+              v.thr[slot_t] = key;
+              v.thrv[slot_t] = best;
+            } else if (spills && slot_t - kThrLocalCap < kThrSpill) {
+              spill_at(slot_t - kThrLocalCap) = key;
+            }
           }
         }
       }
@@ -488,63 +521,71 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
       // Residuals in [-128, 127] store residual + 128 here; the rare pass
       // below fixes the bytes of outliers and escapes and counts every
       // non-zero residual.
-      uint32_t nz = 0;
-      const int2 qu_step = qu;  // the chain's start, replayed by the rare pass
-      const int32_t qd_step = qd;
-      auto left_of = [&](int ii) {  // q of the bin left of the lane's bins in row i0 + ii
-        const int32_t from_lane = __shfl_up_sync(0xffffffffu, qa[ii].y, 1);
-        return first_col ? 0 : from_lane;
-      };
 #pragma unroll
-      for (int ii = 0; ii < RB; ++ii) {
-        const uint32_t i = i0 + ii;
-        if (!FULL && i >= p.Hb) break;
-        const int32_t left = left_of(ii);
-        const int32_t d0 = qa[ii].x - qu.x - left + qd;
-        const int32_t d1 = qa[ii].y - qu.y - qa[ii].x + qu.x;
-        qu = qa[ii];
-        qd = left;
-        nz |= (uint32_t)((d0 | d1) != 0) << ii;
-        const uint32_t pair = (uint32_t)((d0 + 128) & 0xFF) | ((uint32_t)((d1 + 128) & 0xFF) << 8);
-        st_keep_u16_if(codes + (size_t)i * p.Wb, (uint16_t)pair, keep_pol, owned);  // 2 pc is even
-      }
-      if (!owned) nz = 0;
-      if (__any_sync(0xffffffffu, nz != 0)) {
-        int2 qu_r = qu_step;
-        int32_t qd_r = qd_step;
+      for (int g = 0; g < kG; ++g) {
+        const uint32_t pc = cols[g].pc;
+        const bool owned = cols[g].owned, first_col = cols[g].first;
+        uint8_t* codes = cols[g].codes;
+        uint16_t* esc = cols[g].esc;
+        int32_t* lo_delta = cols[g].lo_delta;
+        uint32_t nz = 0;
+        const int2 qu_step = qu[g];  // the chain's start, replayed by the rare pass
+        const int32_t qd_step = qd[g];
+        auto left_of = [&](int ii) {  // q of the bin left of the lane's bins in row i0 + ii
+          const int32_t from_lane = __shfl_up_sync(0xffffffffu, qa[g][ii].y, 1);
+          return first_col ? 0 : from_lane;
+        };
 #pragma unroll
         for (int ii = 0; ii < RB; ++ii) {
           const uint32_t i = i0 + ii;
           if (!FULL && i >= p.Hb) break;
           const int32_t left = left_of(ii);
-          const int32_t d0 = qa[ii].x - qu_r.x - left + qd_r;
-          const int32_t d1 = qa[ii].y - qu_r.y - qa[ii].x + qu_r.x;
-          qu_r = qa[ii];
-          qd_r = left;
-          const bool row_nz = (nz >> ii) & 1u;
-          if (!__any_sync(0xffffffffu, row_nz)) continue;
-          uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
-          if (row_nz) {
-            const uint32_t lb = i * p.Wb + 2 * pc;
-            c0 = quant_code(d0, p.R);
-            c1 = quant_code(d1, p.R);
-            // byte = residual + 128 for residuals in [-127, 126]; 0 = Lorenzo
-            // outlier (delta on the side); 255 = escape (code on the side)
-            auto to_byte = [&](int32_t d, uint32_t c, uint32_t bin) -> uint32_t {
-              if (c == 0) {
-                lo_delta[bin] = d;
-                return 0u;
-              }
-              if (d >= -127 && d <= 126) return (uint32_t)(d + 128);
-              esc[bin] = (uint16_t)c;
-              return 255u;
-            };
-            const uint32_t b0 = to_byte(d0, c0, lb), b1 = to_byte(d1, c1, lb + 1);
-            if (b0 != (uint32_t)((d0 + 128) & 0xFF) || b1 != (uint32_t)((d1 + 128) & 0xFF))
-              st_keep_u16_if(codes + (size_t)i * p.Wb, (uint16_t)(b0 | (b1 << 8)), keep_pol, true);
+          const int32_t d0 = qa[g][ii].x - qu[g].x - left + qd[g];
+          const int32_t d1 = qa[g][ii].y - qu[g].y - qa[g][ii].x + qu[g].x;
+          qu[g] = qa[g][ii];
+          qd[g] = left;
+          nz |= (uint32_t)((d0 | d1) != 0) << ii;
+          const uint32_t pair = (uint32_t)((d0 + 128) & 0xFF) | ((uint32_t)((d1 + 128) & 0xFF) << 8);
+          st_keep_u16_if(codes + (size_t)i * p.Wb, (uint16_t)pair, keep_pol, owned);  // 2 pc is even
+        }
+        if (!owned) nz = 0;
+        if (__any_sync(0xffffffffu, nz != 0)) {
+          int2 qu_r = qu_step;
+          int32_t qd_r = qd_step;
+#pragma unroll
+          for (int ii = 0; ii < RB; ++ii) {
+            const uint32_t i = i0 + ii;
+            if (!FULL && i >= p.Hb) break;
+            const int32_t left = left_of(ii);
+            const int32_t d0 = qa[g][ii].x - qu_r.x - left + qd_r;
+            const int32_t d1 = qa[g][ii].y - qu_r.y - qa[g][ii].x + qu_r.x;
+            qu_r = qa[g][ii];
+            qd_r = left;
+            const bool row_nz = (nz >> ii) & 1u;
+            if (!__any_sync(0xffffffffu, row_nz)) continue;
+            uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
+            if (row_nz) {
+              const uint32_t lb = i * p.Wb + 2 * pc;
+              c0 = quant_code(d0, p.R);
+              c1 = quant_code(d1, p.R);
+              // byte = residual + 128 for residuals in [-127, 126]; 0 = Lorenzo
+              // outlier (delta on the side); 255 = escape (code on the side)
+              auto to_byte = [&](int32_t d, uint32_t c, uint32_t bin) -> uint32_t {
+                if (c == 0) {
+                  lo_delta[bin] = d;
+                  return 0u;
+                }
+                if (d >= -127 && d <= 126) return (uint32_t)(d + 128);
+                esc[bin] = (uint16_t)c;
+                return 255u;
+              };
+              const uint32_t b0 = to_byte(d0, c0, lb), b1 = to_byte(d1, c1, lb + 1);
+              if (b0 != (uint32_t)((d0 + 128) & 0xFF) || b1 != (uint32_t)((d1 + 128) & 0xFF))
+                st_keep_u16_if(codes + (size_t)i * p.Wb, (uint16_t)(b0 | (b1 << 8)), keep_pol, true);
+            }
+            hist_add_warp(v.hist, c0 != (uint32_t)p.R ? c0 : 0xFFFFu, 0xFFFFFFFFu);
+            hist_add_warp(v.hist, c1 != (uint32_t)p.R ? c1 : 0xFFFFu, 0xFFFFFFFFu);
           }
-          hist_add_warp(v.hist, c0 != (uint32_t)p.R ? c0 : 0xFFFFu, 0xFFFFFFFFu);
-          hist_add_warp(v.hist, c1 != (uint32_t)p.R ? c1 : 0xFFFFu, 0xFFFFFFFFu);
         }
       }
     };
@@ -620,13 +661,42 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
         if (slot < sh.sort_n2) v.acc[slot] = lp;
       }
     };
-    if (cnt <= kThrLocalCap) {
-      // a listed candidate beaten by another listed candidate inside its
-      // window (larger, or equal and earlier in row-major order) fails the
-      // local-maximum rule; the others are tested in full
+    // a listed pixel is tested; a listed 2x4 block is screened first (a pixel
+    // beaten inside its own block, which lies inside its window, by the
+    // local-maximum rule can never be a candidate)
+    auto test_listed = [&](uint32_t listed) {
+      if (!(listed & kBlockKey)) {
+        test(listed);
+        return;
+      }
+      const uint32_t key = listed & ~kBlockKey, pj = key / plane, rem = key - pj * plane;
+      const uint32_t r0 = rem / p.W;
+      const uint32_t npx = r0 + 1 < p.H ? 8u : 4u;
+      const uint32_t me = lane & 7u;
+      const float x = me < npx ? __ldg(item_px + key + (me >> 2) * p.W + (me & 3u)) : 0.0f;
+      bool keep = lane < npx && x >= p.amax;
+#pragma unroll
+      for (uint32_t q = 0; q < 8; ++q) {
+        const float y = __shfl_sync(0xffffffffu, x, q);
+        const int dc = (int)(q & 3u) - (int)(me & 3u);
+        if (q == me || q >= npx || dc > p.rank || -dc > p.rank) continue;
+        if (q < me ? !(x > y) : !(x >= y)) keep = false;
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, keep);
+      while (m) {
+        const uint32_t l = __ffs(m) - 1;
+        m &= m - 1;
+        test(key + (l >> 2) * p.W + (l & 3u));
+      }
+    };
+    if (cnt <= kThrLocalCap + (spills ? kThrSpill : 0u)) {
+      // a listed candidate beaten by another candidate of the shared list
+      // inside its window (larger, or equal and earlier in row-major order)
+      // fails the local-maximum rule; the others are tested in full
+      const uint32_t cnt_local = min(cnt, kThrLocalCap);
       if (tid == 0) v.ctl[CTL_NCAND] = 0;
       __syncthreads();
-      for (uint32_t e = tid; e < cnt; e += kPT) {
+      for (uint32_t e = tid; e < cnt_local; e += kPT) {
         const uint32_t key = v.thr[e];
         bool keep = true;
         if (!(key & kBlockKey)) {
@@ -634,7 +704,7 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
           const uint32_t pj = key / plane, rem = key - pj * plane;
           const int r = (int)(rem / p.W), c = (int)(rem % p.W);
           keep = x >= p.amax;
-          for (uint32_t o = 0; o < cnt && keep; ++o) {
+          for (uint32_t o = 0; o < cnt_local && keep; ++o) {
             const uint32_t k2 = v.thr[o];
             if (o == e || (k2 & kBlockKey) || k2 / plane != pj) continue;
             const uint32_t rem2 = k2 - pj * plane;
@@ -647,35 +717,10 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
         if (keep) v.cand[atomicAdd(v.ctl + CTL_NCAND, 1u)] = key;
       }
       __syncthreads();
-      // survivors: a listed pixel is tested; a listed 2x4 block is screened
-      // first (a pixel beaten inside its own block, which lies inside its
-      // window, by the local-maximum rule can never be a candidate)
       const uint32_t n_cand = v.ctl[CTL_NCAND];
-      for (uint32_t e = warp; e < n_cand; e += kPW) {
-        if (!(v.cand[e] & kBlockKey)) {
-          test(v.cand[e]);
-          continue;
-        }
-        const uint32_t key = v.cand[e] & ~kBlockKey, pj = key / plane, rem = key - pj * plane;
-        const uint32_t r0 = rem / p.W;
-        const uint32_t npx = r0 + 1 < p.H ? 8u : 4u;
-        const uint32_t me = lane & 7u;
-        const float x = me < npx ? __ldg(item_px + key + (me >> 2) * p.W + (me & 3u)) : 0.0f;
-        bool keep = lane < npx && x >= p.amax;
-#pragma unroll
-        for (uint32_t q = 0; q < 8; ++q) {
-          const float y = __shfl_sync(0xffffffffu, x, q);
-          const int dc = (int)(q & 3u) - (int)(me & 3u);
-          if (q == me || q >= npx || dc > p.rank || -dc > p.rank) continue;
-          if (q < me ? !(x > y) : !(x >= y)) keep = false;
-        }
-        uint32_t m = __ballot_sync(0xffffffffu, keep);
-        while (m) {
-          const uint32_t l = __ffs(m) - 1;
-          m &= m - 1;
-          test(key + (l >> 2) * p.W + (l & 3u));
-        }
-      }
+      for (uint32_t e = warp; e < n_cand; e += kPW) test_listed(v.cand[e]);
+      // the spilled candidates (written before the barriers above)
+      for (uint32_t e = warp; e < cnt - cnt_local; e += kPW) test_listed(spill_at(e));
     } else if constexpr (kDense) {
       if (sh.band_rows >= 2u * (uint32_t)peak_reach(p) + 2u) {
         dense_band_peaks(p, s, sh, v, item_px, kp, fu);
@@ -1426,7 +1471,8 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
 // warp tests of listed candidates first try the exact rejection screen
 // (screen_rejects), and an item whose candidates overflow the list evaluates
 // them one per lane.  Both variants write the same bytes.
-template <bool kDense>
+// kG: column groups per consumer lane (FusedShape::kG; 2 only with RB = 2).
+template <bool kDense, int kG>
 __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainArgs a, FusedShape sh) {
   extern __shared__ __align__(128) unsigned char sm[];
   uint32_t* ctl = reinterpret_cast<uint32_t*>(sm + sh.off_ctl);
@@ -1453,8 +1499,8 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
     const uint32_t r = t / round, j = t - r * round;
     if (j < sh.U) {
       if (r >= n) continue;
-      if (sh.RB == 2) process_item<2, kDense>(p, s, a, sh, sm, r, j, ring_iter);
-      else process_item<3, kDense>(p, s, a, sh, sm, r, j, ring_iter);
+      if (kG > 1 || sh.RB == 2) process_item<2, kDense, kG>(p, s, a, sh, sm, r, j, ring_iter);
+      else process_item<3, kDense, 1>(p, s, a, sh, sm, r, j, ring_iter);
       // publish the item; the CTA that completes the frame builds its codebook
       __threadfence();
       __syncthreads();
@@ -1481,8 +1527,10 @@ __global__ void __launch_bounds__(kPT, 4) k_fused(DevParams p, Scratch s, PlainA
 static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, uint32_t stages, FusedShape* out) {
   FusedShape sh{};
   const uint32_t NP = p.W / 4;
-  if (NP < 1 || NP > kConsumerWarps * 31 || rb < 2 || rb > 3) return false;
-  sh.k = min(kMaxK, kConsumerWarps * 31 / NP);
+  if (NP < 1 || NP > kMaxG * kGroupCols || rb < 2 || rb > 3) return false;
+  sh.kG = ceil_div(NP, kGroupCols);
+  if (sh.kG > 1 && rb != 2) return false;  // wide panels: two binned rows per step
+  sh.k = min(kMaxK, sh.kG * kGroupCols / NP);
   if ((uint64_t)sh.k * p.H * p.W >= kBlockKey) return false;  // item-local keys stay below the flag
   sh.U = ceil_div(p.P, sh.k);
   sh.RB = rb;
@@ -1552,9 +1600,15 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
   return sh.smem <= 227 * 1024;
 }
 
+// The kernel instantiation for a shape: dense-peaks variant or not, column groups.
+static const void* fused_kernel(bool dense, uint32_t kG) {
+  if (kG > 1) return dense ? (const void*)k_fused<true, kMaxG> : (const void*)k_fused<false, kMaxG>;
+  return dense ? (const void*)k_fused<true, 1> : (const void*)k_fused<false, 1>;
+}
+
 bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, uint32_t stages,
                      FusedShape* out) {
-  if (p.dims != 2 || p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > kConsumerWarps * 31) return false;
+  if (p.dims != 2 || p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > kMaxG * kGroupCols) return false;
   if (ctas_per_sm < 1 || ctas_per_sm > 8 || stages < 1 || stages > 8) return false;
   if (rows_per_step != 0 && (rows_per_step < 2 || rows_per_step > 3)) return false;
   FusedShape sh;
@@ -1567,12 +1621,13 @@ bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per
     for (uint32_t rb = 3; rb >= 2 && !ok; --rb) ok = make_shape(p, ctas_per_sm, rb, stages, &sh) && sh.smem <= budget;
   }
   if (!ok) return false;
-  if (cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
+  const void* kern = fused_kernel(false, sh.kG);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, kPT, sh.smem) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, sh.smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return false;
   }
@@ -1600,8 +1655,7 @@ cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& 
   cudaError_t e = cudaMemsetAsync(s.frame_done, 0, sizeof(uint32_t) * (kSyncWordsPerFrame * (uint64_t)a.n_frames + 1), st);
   if (e != cudaSuccess) return e;
   const uint32_t smem = screen ? sh.smem_dense : sh.smem;
-  e = cudaFuncSetAttribute(screen ? k_fused<true> : k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  e = cudaFuncSetAttribute(fused_kernel(screen, sh.kG), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   FusedShape s2 = sh;
   // frames between the stages in the ticket order.  Streaming -> chunk sizes:
@@ -1614,8 +1668,13 @@ cudaError_t launch_fused(const DevParams& p, const Scratch& s, const PlainArgs& 
   s2.lag2 = a.n_frames < kLagWrite ? a.n_frames : kLagWrite;
   const uint64_t tickets = (uint64_t)(a.n_frames + s2.lag1 + s2.lag2) * (s2.U + 2 * s2.groups);
   const uint32_t grid = (uint32_t)(tickets < sh.n_ctas ? tickets : sh.n_ctas);
-  if (screen) k_fused<true><<<grid, kPT, smem, st>>>(p, s, a, s2);
-  else k_fused<false><<<grid, kPT, sh.smem, st>>>(p, s, a, s2);
+  if (sh.kG > 1) {
+    if (screen) k_fused<true, kMaxG><<<grid, kPT, smem, st>>>(p, s, a, s2);
+    else k_fused<false, kMaxG><<<grid, kPT, smem, st>>>(p, s, a, s2);
+  } else {
+    if (screen) k_fused<true, 1><<<grid, kPT, smem, st>>>(p, s, a, s2);
+    else k_fused<false, 1><<<grid, kPT, smem, st>>>(p, s, a, s2);
+  }
   return cudaGetLastError();
 }
 

@@ -180,8 +180,9 @@ bool plain_rows_ok(const DevParams& d, uint32_t rows) {
   return rows >= 1 && rows <= 16 && q_rows + (uint64_t)rows * d.Wb + 16 + 4096 <= 200 * 1024;
 }
 
-// Lays out the per-frame scratch for n frames; with base == nullptr only sizes it.
-uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s) {
+// Lays out the per-frame scratch for n frames, and candidate spill lists for
+// spill_ctas CTAs of the persistent kernel; with base == nullptr only sizes it.
+uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s, uint32_t spill_ctas) {
   Carver c{base};
   Scratch t{};
   t.thr_count = c.take<uint32_t>(n);
@@ -216,6 +217,8 @@ uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s
   t.lane_pq = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
   t.frame_done = c.take<uint32_t>(7ull * n + 1);  // the fused kernel's sync words
   t.chunk_ref = c.take<uint32_t>(n);
+  t.thr_spill_ctas = spill_ctas;
+  if (spill_ctas) t.thr_spill = c.take<uint32_t>((uint64_t)spill_ctas * kThrSpill);
   if (d.roi_coder) {
     const uint64_t mp = std::max<uint32_t>(d.max_peaks, 1);
     t.roi_hist = c.take<uint32_t>((uint64_t)n * kRoiClasses);
@@ -589,7 +592,9 @@ int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_p
   ctx->budget = hbm_budget_bytes;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   ctx->fused_ok = fused_plan(ctx->dp, device, ctx->num_sms, &ctx->fshape);
-  const uint64_t need = carve_scratch(ctx->dp, max_frames_per_call, nullptr, nullptr);
+  // a spill list for every CTA the persistent kernel may run (at most 8 per SM)
+  const uint32_t spill_ctas = ctx->fused_ok ? 8u * (uint32_t)ctx->num_sms : 0u;
+  const uint64_t need = carve_scratch(ctx->dp, max_frames_per_call, nullptr, nullptr, spill_ctas);
   if (hbm_budget_bytes && need > hbm_budget_bytes) {
     delete ctx;
     return ROIBIN_ERR_OUT_OF_BUDGET;
@@ -600,7 +605,7 @@ int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_p
     return ROIBIN_ERR_OUT_OF_BUDGET;
   }
   ctx->scratch_bytes = need;
-  carve_scratch(ctx->dp, max_frames_per_call, static_cast<uint8_t*>(ctx->scratch), &ctx->s);
+  carve_scratch(ctx->dp, max_frames_per_call, static_cast<uint8_t*>(ctx->scratch), &ctx->s, spill_ctas);
   *out = ctx;
   return ROIBIN_OK;
 }
@@ -1117,14 +1122,14 @@ int roibin_compress_frame_static(const roibin_geometry* g, const roibin_params* 
   if (reinterpret_cast<uintptr_t>(d_frame) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0)
     return ROIBIN_ERR_INVALID_ARG;
   const DevParams dp = make_dev_params(*g, *p);
-  if (carve_scratch(dp, 1, nullptr, nullptr) > ROIBIN_STATIC_SCRATCH_BYTES) return ROIBIN_ERR_OUT_OF_BUDGET;
+  if (carve_scratch(dp, 1, nullptr, nullptr, 0) > ROIBIN_STATIC_SCRATCH_BYTES) return ROIBIN_ERR_OUT_OF_BUDGET;
   int device = 0, sms = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return ROIBIN_ERR_CUDA;
   void* base = nullptr;
   if (static_scratch_base(&base) != cudaSuccess) return ROIBIN_ERR_CUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return ROIBIN_ERR_CUDA;
   Scratch s{};
-  carve_scratch(dp, 1, static_cast<uint8_t*>(base), &s);
+  carve_scratch(dp, 1, static_cast<uint8_t*>(base), &s, 0);
   PlainArgs a{};
   a.frames = d_frame;
   a.n_frames = 1;

@@ -123,7 +123,11 @@ struct Scratch {
   uint32_t* roi_book;       // [n][2 kRoiClasses] code length, then codeword, per class
   uint4* roi_plan;          // [n] coding, section words, section offset (lo, hi)
   uint32_t* chunk_ref;      // [n] frames back to the chunk's head (which keeps the code lengths); 0: a head
+  // persistent batched path: candidate keys past a CTA's shared-memory list
+  uint32_t* thr_spill;      // [thr_spill_ctas][kThrSpill], by CTA index
+  uint32_t thr_spill_ctas;  // CTAs with a spill list (0: none)
 };
+constexpr uint32_t kThrSpill = 3840;  // spilled candidate keys per CTA (4,096 with the shared list)
 
 // count, first, index (34 words each), symbols; padded to 16 bytes
 constexpr uint32_t kDecCanonWords = (34 + 34 + 34 + kMaxSymbols + 3) & ~3u;
@@ -222,16 +226,13 @@ __device__ __forceinline__ bool prequant_fast(float b, const DevParams& p, int32
 // sum in row-major order from the first pixel, one IEEE division.
 __device__ __forceinline__ void bin_pair(const float4& a, const float4& b, bool two, float& b0, float& b1) {
   float s0 = __fadd_rn(a.x, a.y), s1 = __fadd_rn(a.z, a.w);
-  float c = 2.0f;
   if (two) {
     s0 = __fadd_rn(__fadd_rn(s0, b.x), b.y);
     s1 = __fadd_rn(__fadd_rn(s1, b.z), b.w);
-    c = 4.0f;
   }
   // division by 2 or 4: the exact product with 0.5 or 0.25 is the correctly
   // rounded quotient, bit for bit, so this is the same IEEE division
   const float rc = two ? 0.25f : 0.5f;
-  (void)c;
   b0 = __fmul_rn(s0, rc);
   b1 = __fmul_rn(s1, rc);
 }
@@ -988,6 +989,7 @@ constexpr uint32_t kTracePoints = 16;
 struct FusedShape {
   uint32_t ctas_per_sm, n_ctas;  // resident CTAs per SM, grid size
   uint32_t k, U;                 // panels per streaming item; streaming items per frame
+  uint32_t kG;                   // column groups per consumer lane (1, or 2 for panels above 868 columns)
   uint32_t RB;                   // binned rows per streaming step (2 or 3)
   uint32_t stages, stage_bytes;  // TMA ring: slots, bytes per slot (2 RB raw rows of k panels)
   uint32_t mask_words;           // prequantisation-outlier bitmask words per panel

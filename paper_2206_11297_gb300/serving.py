@@ -46,124 +46,181 @@ class Request:
         return None if self.done is None else self.done - self.arrival
 
 
-class _Lane:
-    """One context, its batch buffers and its stream."""
+class _Slot:
+    """One batch's buffers in a lane: frames in, streams out, and the batch's
+    progress (idle -> sizes -> bytes -> host -> idle)."""
 
-    PACKED_START = 64 << 20  # pinned bytes for a batch's streams at first; grown on demand
-
-    def __init__(self, geometry, params: Params, max_frames: int, device, budget: int, pool,
-                 keep_streams: bool = True):
-        """Raises RoibinError(ERR_OUT_OF_BUDGET) when the lane does not fit `budget` bytes."""
+    def __init__(self, geometry, max_frames, stride, device):
         import torch
-        self.geometry = geometry
-        self.max_frames = max_frames
-        self.stride = compress_bound(geometry, params)
-        buffers = max_frames * (int(np.prod(geometry)) * 4 + self.stride + 12)
-        if buffers >= budget:
-            raise RoibinError("lane buffers", ERR_OUT_OF_BUDGET)
-        # the library refuses (without allocating) a scratch above the budget left
-        self.ctx = Context(geometry, params, max_frames=max_frames, hbm_budget=budget - buffers,
-                           device=device.index or 0)
-        self.stream = torch.cuda.Stream(device=device)
         self.d_frames = torch.empty((max_frames, *geometry), dtype=torch.float32, device=device)
-        self.d_out = torch.empty((max_frames, self.stride), dtype=torch.uint8, device=device)
+        self.d_out = torch.empty((max_frames, stride), dtype=torch.uint8, device=device)
         self.d_nb = torch.empty(max_frames, dtype=torch.int64, device=device)
         self.d_st = torch.empty(max_frames, dtype=torch.int32, device=device)
         self.h_nb = torch.empty(max_frames, dtype=torch.int64).pin_memory()
         self.h_st = torch.empty(max_frames, dtype=torch.int32).pin_memory()
         # the batch's streams come back packed, back to back, into one pinned
         # buffer; host copies out of it run on the server's thread pool
-        self.h_packed = torch.empty(self.PACKED_START, dtype=torch.uint8).pin_memory()
-        self.pool = pool
-        self.keep_streams = keep_streams
+        self.h_packed = None
         self.offsets: list = []
         self.futures: list = []
-        self.batch: list[Request] = []
+        self.batch: list = []
         self.n = 0
-        # idle -> sizes (kernel + sizes copy in flight) -> bytes (streams copy in flight)
-        #      -> host (copies out of the pinned buffer running) -> idle
         self.phase = "idle"
         self.event = None
+
+    @property
+    def bytes(self):
+        return sum(t.numel() * t.element_size() for t in (self.d_frames, self.d_out, self.d_nb, self.d_st))
+
+
+class _Lane:
+    """One context and its streams, with two batch slots, so that a batch can
+    start (its frames copied in and its kernels queued behind the running
+    batch) while the previous batch's streams are still being copied out.
+    Frames come in on `in_stream`, are compressed on `stream` and go out on
+    `out_stream`; events order the three.  Requests whose frames are already in
+    device memory (a detector writing into HBM) are gathered into the slot by
+    device-to-device copies, or compressed where they are when the batch is a
+    single request."""
+
+    PACKED_START = 64 << 20  # pinned bytes for a batch's streams at first; grown on demand
+    SLOTS = 2
+
+    def __init__(self, geometry, params: Params, max_frames: int, device, budget: int, pool,
+                 keep_streams: bool = True, output: str = "host"):
+        """Raises RoibinError(ERR_OUT_OF_BUDGET) when the lane does not fit `budget` bytes."""
+        import torch
+        self.geometry = geometry
+        self.max_frames = max_frames
+        self.stride = compress_bound(geometry, params)
+        buffers = self.SLOTS * max_frames * (int(np.prod(geometry)) * 4 + self.stride + 12)
+        if buffers >= budget:
+            raise RoibinError("lane buffers", ERR_OUT_OF_BUDGET)
+        # the library refuses (without allocating) a scratch above the budget left
+        self.ctx = Context(geometry, params, max_frames=max_frames, hbm_budget=budget - buffers,
+                           device=device.index or 0)
+        self.stream = torch.cuda.Stream(device=device)
+        self.in_stream = torch.cuda.Stream(device=device)
+        self.out_stream = torch.cuda.Stream(device=device)
+        self.slots = [_Slot(geometry, max_frames, self.stride, device) for _ in range(self.SLOTS)]
+        self.pool = pool
+        self.keep_streams = keep_streams
+        self.output = output
         self.last_used = 0.0
         self.bytes = self.ctx.scratch_bytes + buffers
 
-    def start(self, batch):
+    @property
+    def phase(self):
+        """"idle" when no slot holds a batch."""
+        return "idle" if all(s.phase == "idle" for s in self.slots) else "busy"
+
+    def free_slot(self):
+        for s in self.slots:
+            if s.phase == "idle":
+                return s
+        return None
+
+    def start(self, batch, slot=None):
         import torch
-        self.batch = batch
-        self.n = sum(r.frames.shape[0] for r in batch)
+        slot = slot or self.free_slot()
+        slot.batch = batch
+        slot.n = sum(r.frames.shape[0] for r in batch)
+        frames = slot.d_frames[:slot.n]
+        f0 = batch[0].frames
+        if len(batch) == 1 and f0.is_cuda and f0.is_contiguous() and f0.data_ptr() % 16 == 0:
+            frames = f0  # already in device memory: compressed where it is
+        else:
+            with torch.cuda.stream(self.in_stream):
+                k = 0
+                for r in batch:
+                    m = r.frames.shape[0]
+                    slot.d_frames[k:k + m].copy_(r.frames, non_blocking=True)
+                    k += m
+            self.stream.wait_stream(self.in_stream)
         with torch.cuda.stream(self.stream):
-            k = 0
-            for r in batch:
-                m = r.frames.shape[0]
-                self.d_frames[k:k + m].copy_(r.frames, non_blocking=True)
-                k += m
-            self.ctx.compress(self.d_frames[:self.n], out=self.d_out, out_stride=self.stride,
-                              frame_bytes=self.d_nb, status=self.d_st, stream=self.stream)
-            self.h_nb[:self.n].copy_(self.d_nb[:self.n], non_blocking=True)
-            self.h_st[:self.n].copy_(self.d_st[:self.n], non_blocking=True)
-            self.event = torch.cuda.Event()
-            self.event.record(self.stream)
-        self.phase = "sizes"
+            self.ctx.compress(frames, out=slot.d_out, out_stride=self.stride, frame_bytes=slot.d_nb,
+                              status=slot.d_st, stream=self.stream)
+        # the sizes (and later the streams) leave on the output stream, so the
+        # next batch's kernels can follow this one at once
+        self.out_stream.wait_stream(self.stream)
+        with torch.cuda.stream(self.out_stream):
+            slot.h_nb[:slot.n].copy_(slot.d_nb[:slot.n], non_blocking=True)
+            slot.h_st[:slot.n].copy_(slot.d_st[:slot.n], non_blocking=True)
+            slot.event = torch.cuda.Event()
+            slot.event.record(self.out_stream)
+        slot.phase = "sizes"
+
+    def _finish(self, slot, with_streams):
+        now = time.perf_counter()
+        st = slot.h_st[:slot.n].numpy()
+        k = 0
+        for r in slot.batch:
+            m = r.frames.shape[0]
+            r.status = [int(x) for x in st[k:k + m]]
+            r.done = now
+            k += m
+        finished, slot.batch, slot.phase = slot.batch, [], "idle"
+        self.last_used = now
+        return finished
 
     def advance(self):
-        """Moves a running batch on when its copies are done; returns finished requests."""
+        """Moves the running batches on when their copies are done; returns finished requests."""
+        out = []
+        for slot in self.slots:
+            out.extend(self._advance(slot))
+        return out
+
+    def _advance(self, slot):
         import torch
-        if self.phase == "idle":
+        if slot.phase == "idle":
             return []
-        if self.phase in ("sizes", "bytes") and not self.event.query():
+        if slot.phase in ("sizes", "bytes") and not slot.event.query():
             return []
-        if self.phase == "sizes":
-            nb, st = self.h_nb[:self.n].numpy(), self.h_st[:self.n].numpy()
-            self.offsets, total = [], 0
-            for k in range(self.n):
+        if slot.phase == "sizes":
+            if self.output == "device":  # the streams stay in the slot's device buffer
+                return self._finish(slot, False)
+            nb, st = slot.h_nb[:slot.n].numpy(), slot.h_st[:slot.n].numpy()
+            slot.offsets, total = [], 0
+            for k in range(slot.n):
                 m = int(nb[k]) if st[k] == 0 else 0
-                self.offsets.append((total, m))
+                slot.offsets.append((total, m))
                 total += m
-            if total > self.h_packed.numel():
-                self.h_packed = torch.empty(max(total, 2 * self.h_packed.numel()), dtype=torch.uint8).pin_memory()
-            with torch.cuda.stream(self.stream):
-                for k, (o, m) in enumerate(self.offsets):
+            if slot.h_packed is None or total > slot.h_packed.numel():
+                size = max(total, self.PACKED_START if slot.h_packed is None else 2 * slot.h_packed.numel())
+                slot.h_packed = torch.empty(size, dtype=torch.uint8).pin_memory()
+            with torch.cuda.stream(self.out_stream):
+                for k, (o, m) in enumerate(slot.offsets):
                     if m:
-                        self.h_packed[o:o + m].copy_(self.d_out[k, :m], non_blocking=True)
-                self.event = torch.cuda.Event()
-                self.event.record(self.stream)
-            self.phase = "bytes"
+                        slot.h_packed[o:o + m].copy_(slot.d_out[k, :m], non_blocking=True)
+                slot.event = torch.cuda.Event()
+                slot.event.record(self.out_stream)
+            slot.phase = "bytes"
             return []
-        if self.phase == "bytes":
+        if slot.phase == "bytes":
             if not self.keep_streams:  # the bytes are on the host: done
-                now = time.perf_counter()
-                st = self.h_st[:self.n].numpy()
-                k = 0
-                for r in self.batch:
-                    m = r.frames.shape[0]
-                    r.status = [int(x) for x in st[k:k + m]]
-                    r.done = now
-                    k += m
-                finished, self.batch, self.phase = self.batch, [], "idle"
-                self.last_used = now
-                return finished
+                return self._finish(slot, False)
             # each request's streams are copied out of the pinned buffer in parallel
-            packed = self.h_packed.numpy()
-            st = self.h_st[:self.n].numpy().copy()
+            packed = slot.h_packed.numpy()
+            st = slot.h_st[:slot.n].numpy().copy()
             k = 0
-            self.futures = []
-            for r in self.batch:
+            slot.futures = []
+            for r in slot.batch:
                 m = r.frames.shape[0]
-                spans = self.offsets[k:k + m]
+                spans = slot.offsets[k:k + m]
                 stats = [int(x) for x in st[k:k + m]]
-                self.futures.append(self.pool.submit(
+                slot.futures.append(self.pool.submit(
                     lambda spans=spans, stats=stats: (stats, [packed[o:o + n].copy() if s == 0 else None
                                                               for (o, n), s in zip(spans, stats)])))
                 k += m
-            self.phase = "host"
+            slot.phase = "host"
             return []
-        if not all(f.done() for f in self.futures):
+        if not all(f.done() for f in slot.futures):
             return []
         now = time.perf_counter()
-        for r, f in zip(self.batch, self.futures):
+        for r, f in zip(slot.batch, slot.futures):
             r.status, r.streams = f.result()
             r.done = now
-        finished, self.batch, self.futures, self.phase = self.batch, [], [], "idle"
+        finished, slot.batch, slot.futures, slot.phase = slot.batch, [], [], "idle"
         self.last_used = now
         return finished
 
@@ -182,11 +239,14 @@ class Server:
     that, so an offered load above capacity is shed instead of queued without
     bound); keep_streams: hand each request a copy of its streams (False: a
     request is done once its bytes are in the lane's pinned host buffer, where
-    a consumer would write them out)."""
+    a consumer would write them out); output: "host" (streams copied to host
+    memory) or "device" (a request is done once its streams are in device
+    memory, as for a consumer on the GPU).  A request's frames may be in host
+    memory (pinned) or already in device memory."""
 
     def __init__(self, params: Params | None = None, hbm_budget: int = 40 << 30, lane_frames: int = 128,
                  lanes_per_geometry: int = 2, device=None, host_threads: int = 8,
-                 max_queued_frames: int = 1 << 20, keep_streams: bool = True):
+                 max_queued_frames: int = 1 << 20, keep_streams: bool = True, output: str = "host"):
         import torch
         self.params = params or default_params()
         self.budget = int(hbm_budget)
@@ -199,6 +259,9 @@ class Server:
         self.pool = concurrent.futures.ThreadPoolExecutor(host_threads)
         self.max_queued_frames = int(max_queued_frames)
         self.keep_streams = bool(keep_streams)
+        if output not in ("host", "device"):
+            raise ValueError("output is 'host' or 'device'")
+        self.output = output
         self.queued_frames = 0
         self.rejected = 0
 
@@ -220,15 +283,16 @@ class Server:
         return True
 
     def _lane_for(self, geometry):
-        idle = [l for l in self.lanes if l.geometry == geometry and l.phase == "idle"]
-        if idle:
-            return idle[0]
+        # a lane with a free slot takes the batch, even while its other slot runs
+        free = [l for l in self.lanes if l.geometry == geometry and l.free_slot() is not None]
+        if free:
+            return free[0]
         if sum(1 for l in self.lanes if l.geometry == geometry) >= self.lanes_per_geometry:
             return None
         while True:
             try:
                 lane = _Lane(geometry, self.params, self.lane_frames, self.device,
-                             self.budget - self.held_bytes, self.pool, self.keep_streams)
+                             self.budget - self.held_bytes, self.pool, self.keep_streams, self.output)
                 self.lanes.append(lane)
                 return lane
             except RoibinError as e:
@@ -283,6 +347,7 @@ class Server:
 
 
 def poisson_requests(pools: dict, rate_hz: float, seconds: float, max_frames: int = 64, seed: int = 0):
+    # pools: geometry -> frames (pinned host or device tensor [n, P, H, W])
     """(arrival offset, geometry, n_frames, first frame) of Poisson request arrivals: geometry
     uniform over the pools, 1..max_frames frames each (uniform)."""
     rng = np.random.default_rng(seed)
@@ -331,16 +396,21 @@ def main():
     ap.add_argument("--pool-frames", type=int, default=96)
     ap.add_argument("--max-peaks", type=int, default=8192)
     ap.add_argument("--max-queued-frames", type=int, default=8192)
+    ap.add_argument("--input", choices=["host", "device"], default="host",
+                    help="requests' frames in pinned host memory, or already in device memory")
+    ap.add_argument("--output", choices=["host", "device"], default="host",
+                    help="a request is done when its streams are in host memory, or in device memory")
     args = ap.parse_args()
     pools = {}
     for name in ("cspad_batch", "epix_hot", "jungfrau_mixed"):
         r = RECIPES[name]
-        pools[r.geometry] = torch.from_numpy(make_batch_threaded(r, args.pool_frames)).pin_memory()
+        host = torch.from_numpy(make_batch_threaded(r, args.pool_frames))
+        pools[r.geometry] = host.cuda() if args.input == "device" else host.pin_memory()
     # epix-like frames with 1% hot pixels hold about 3,600 accepted peaks (pairs of hot pixels pass
     # the tests), above the default list size: allow the largest
     params = default_params(max_peaks=args.max_peaks)
     server = Server(params, hbm_budget=int(args.budget_gb * 1e9), lane_frames=args.lane_frames,
-                    max_queued_frames=args.max_queued_frames, keep_streams=False)
+                    max_queued_frames=args.max_queued_frames, keep_streams=False, output=args.output)
     warm = poisson_requests(pools, args.rate, 0.5, args.max_request_frames, seed=1)
     run(pools, warm, server)
     sched = poisson_requests(pools, args.rate, args.seconds, args.max_request_frames, seed=2)
@@ -353,7 +423,8 @@ def main():
     in_bytes = sum(r.frames.numel() * 4 for r in reqs)
     ok = all(s == 0 for r in reqs for s in r.status)
     bad = collections.Counter((str(r.geometry), s) for r in reqs for s in r.status if s != 0)
-    print(json.dumps({"requests": len(reqs), "frames": frames, "seconds": wall,
+    print(json.dumps({"input": args.input, "output": args.output, "requests": len(reqs), "frames": frames,
+                      "seconds": wall,
                       "offered_rate_hz": args.rate, "sustained_gbs": in_bytes / 1e9 / wall,
                       "frames_per_s": frames / wall,
                       "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

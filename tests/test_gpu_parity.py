@@ -43,7 +43,8 @@ def fused_or_skip(geom, params, path):
 
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("geom", [(2, 12, 13), (1, 7, 8), (3, 21, 27), (4, 37, 52), (2, 64, 100), (1, 3, 1),
-                                  (5, 33, 400), (2, 21, 1024), (9, 10, 4), (3, 5, 96)])
+                                  (5, 33, 400), (2, 21, 1024), (9, 10, 4), (3, 5, 96),
+                                  (1, 19, 872), (1, 10, 1736)])
 def test_small_geometries(geom, path):
     f = small_batch(geom, 3, seed=sum(geom))
     assert_parity(f, rb.default_params(atot_thr=300.0), path)
@@ -102,6 +103,16 @@ def test_epix_hot_pixels_round_trip(eb, path):
     f = np.stack([make_frame(r, k) for k in range(2)])
     st, _, _ = assert_parity(f, rb.default_params(abs_eb=eb, max_peaks=8192), path)
     assert (st == 0).all()
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("hot", [0.001, 0.03, 0.2])
+def test_many_candidates_per_item(hot, path):
+    """A 1,024-column panel (one fused item, two column groups) with hot pixels:
+    its candidates fit the shared list, spill past it to the CTA's list in
+    global memory, or overflow both (a rescan of the item)."""
+    f = small_batch((1, 64, 1024), 2, seed=int(hot * 1000), bg_mean=30.0, bg_sd=8.0, hot_fraction=hot)
+    assert_parity(f, rb.default_params(max_peaks=8192, abs_eb=1.0), path)
 
 
 @pytest.mark.parametrize("path", PATHS)
@@ -364,7 +375,7 @@ def test_plain_autotuner_and_shapes_write_the_same_bytes():
     """The plain path's autotuner keeps one of its shapes; a few fixed shapes,
     and the kept one, all write the oracle's bytes."""
     import torch
-    geom = (2, 21, 1024)   # wider than the fused path takes
+    geom = (2, 21, 1744)   # wider than the fused path takes (436 float4 columns)
     f = small_batch(geom, 2, seed=91)
     p = rb.default_params(atot_thr=300.0)
     refs = [oracle.compress_frame(f[k], oparams(p)) for k in range(2)]
@@ -414,7 +425,7 @@ def test_new_entry_points_reject_bad_arguments():
     """The dense-peaks switch needs a fused path; decompression paths and plain
     shapes out of range are refused; the context keeps its settings."""
     import torch
-    wide = (2, 21, 1024)   # no fused path
+    wide = (2, 21, 1744)   # no fused path
     p = rb.default_params(atot_thr=300.0)
     with rb.Context(wide, p, max_frames=1) as ctx:
         with pytest.raises(rb.RoibinError):

@@ -68,7 +68,9 @@ def test_graph_matches_separate_calls_and_refills(concurrent):
     params = rb.default_params(max_peaks=8192)
     jobs = _jobs(torch, params, first=0, tune=True)
     paths = {j["name"]: j["ctx"].resolved_path for j in jobs}
-    assert paths["jungfrau_mixed"] == rb.PATH_PLAIN and paths["cspad_mixed"] == rb.PATH_FUSED
+    assert paths["cspad_mixed"] == rb.PATH_FUSED
+    with rb.Context(RECIPES["jungfrau_mixed"].geometry, params, max_frames=1) as c:
+        assert c.resolved_path == rb.PATH_FUSED   # 1,024-column panels: two column groups
     with rb.Graph(jobs, concurrent=concurrent) as g:
         assert g.launch_count >= len(jobs)
         g.launch()

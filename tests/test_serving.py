@@ -32,7 +32,7 @@ def _alone(pools, req, params):
     import torch
     g = req.geometry
     with rb.Context(g, params, max_frames=req.frames.shape[0]) as ctx:
-        out, nb, st = ctx.compress(req.frames.cuda())
+        out, nb, st = ctx.compress(req.frames.cuda().clone())  # a fresh, 16-byte aligned copy
         torch.cuda.synchronize()
         out, nb, st = out.cpu().numpy(), nb.cpu().numpy(), st.cpu().numpy()
     return [out[k, :nb[k]] if st[k] == 0 else None for k in range(len(nb))]
@@ -53,7 +53,7 @@ def _check_mixed(server, pools, schedule, params):
         if r.geometry in seen:
             continue
         seen.add(r.geometry)
-        st, ref = oracle.compress_frame(r.frames[0].numpy(), oracle.make_params(**params.as_dict()))
+        st, ref = oracle.compress_frame(r.frames[0].cpu().numpy(), oracle.make_params(**params.as_dict()))
         assert st == 0 and np.array_equal(r.streams[0], ref)
     return reqs
 
@@ -129,7 +129,8 @@ def test_packed_buffer_grows_and_streams_stay_exact(monkeypatch):
     server = serving.Server(params, hbm_budget=4 << 30, lane_frames=16)
     try:
         _check_mixed(server, pools, schedule, params)
-        assert all(l.h_packed.numel() > 4096 for l in server.lanes)
+        grown = [sl.h_packed.numel() for l in server.lanes for sl in l.slots if sl.h_packed is not None]
+        assert grown and all(n > 4096 for n in grown)
     finally:
         server.close()
 
@@ -148,5 +149,67 @@ def test_requests_done_without_keeping_streams():
         reqs = serving.run(pools, schedule, server)
         assert len(reqs) == len(schedule) and server.rejected == 0
         assert all(r.done is not None and r.streams is None and all(s == 0 for s in r.status) for r in reqs)
+    finally:
+        server.close()
+
+
+def _device_pools(geoms, n=24):
+    return {g: t.cuda() for g, t in _pools(geoms, n).items()}
+
+
+@pytest.mark.gpu
+def test_device_resident_requests_same_bytes():
+    """Frames already in device memory (a detector writing into HBM): a batch of
+    one request is compressed where it lies, larger batches are gathered by
+    device copies; every request's bytes still equal compressing it alone."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    geoms = [(3, 40, 44), (2, 21, 27)]   # the second has frames that are not 16-byte multiples
+    pools = _device_pools(geoms)
+    params = rb.default_params(atot_thr=300.0)
+    schedule = serving.poisson_requests(pools, rate_hz=2000, seconds=0.05, max_frames=8, seed=13)
+    server = serving.Server(params, hbm_budget=4 << 30, lane_frames=16)
+    try:
+        _check_mixed(server, pools, schedule, params)
+    finally:
+        server.close()
+
+
+@pytest.mark.gpu
+def test_device_output_and_a_second_batch_while_the_first_runs():
+    """With output in device memory a request is done once its streams are on
+    the GPU; a lane starts a second batch in its other slot while the first
+    batch still runs, instead of waiting for it."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = (4, 37, 52)
+    pools = _device_pools([g], n=40)
+    params = rb.default_params(atot_thr=300.0)
+    server = serving.Server(params, hbm_budget=4 << 30, lane_frames=16, lanes_per_geometry=1,
+                            output="device")
+    try:
+        r1 = serving.Request(0, pools[g][0:16], 0.0)
+        r2 = serving.Request(1, pools[g][16:32], 0.0)
+        lane = server._lane_for(g)
+        # a bounded spin (about 0.1 s) ahead of r1's kernels on the lane's
+        # stream, so that r1 is certain to be running when r2 is scheduled
+        with torch.cuda.stream(lane.stream):
+            torch.cuda._sleep(200_000_000)
+        assert server.submit(r1)
+        server.step()
+        assert server.submit(r2)
+        server.step()   # r1's batch is still on the GPU: r2 goes to the other slot
+        assert sum(sl.phase != "idle" for sl in lane.slots) == 2 and len(server.lanes) == 1
+        server.drain()
+        for r in (r1, r2):
+            assert r.done is not None and r.streams is None and all(x == 0 for x in r.status)
+        # the second slot's streams are the second request's, byte for byte
+        sl = lane.slots[1]  # free_slot gave r1 the first slot and r2 the second
+        alone = _alone(pools, r2, params)
+        nb = sl.h_nb.numpy()
+        for k in range(16):
+            assert np.array_equal(sl.d_out[k, :nb[k]].cpu().numpy(), alone[k])
     finally:
         server.close()
