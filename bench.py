@@ -237,9 +237,9 @@ MIXED = (("cspad_mixed", 300), ("epix_mixed", 300), ("jungfrau_mixed", 150))
 
 def mixed_graph(args, dev, local, stream):
     """The mixed batch under one CUDA graph (roibin_graph_*), each context on the
-    path and shape its autotuner picked, with the three jobs chained and on
-    concurrent branches, timed against the same three compress calls issued
-    one after another on one stream."""
+    path and shape its autotuner picked, with the three jobs chained, on
+    concurrent branches, and in one persistent launch (fused), timed against
+    the same three compress calls issued one after another on one stream."""
     import torch
     import paper_2206_11297_gb300 as rb
     params = rb.default_params(max_peaks=8192)
@@ -263,7 +263,8 @@ def mixed_graph(args, dev, local, stream):
         jobs.append(dict(ctx=ctx, frames=frames, out=out, frame_bytes=nb, status=st))
         frames_of[name] = n
         total += frames.numel() * 4
-    graphs = {"serial": rb.Graph(jobs), "concurrent": rb.Graph(jobs, concurrent=True)}
+    graphs = {"serial": rb.Graph(jobs), "concurrent": rb.Graph(jobs, concurrent=True),
+              "fused": rb.Graph(jobs, fused=True)}
 
     def sequential():
         for j in jobs:

@@ -457,6 +457,7 @@ typedef struct roibin_graph roibin_graph;
 
 #define ROIBIN_GRAPH_SERIAL 0     /* the jobs run one after another (a chain)        */
 #define ROIBIN_GRAPH_CONCURRENT 1 /* each job on its own branch, free to overlap     */
+#define ROIBIN_GRAPH_FUSED 2      /* the fused-path jobs in ONE persistent launch    */
 
 /* Captures the jobs' compression launches into one CUDA graph and
  * instantiates it.  A launch of the graph runs every job once, in the order
@@ -466,6 +467,19 @@ typedef struct roibin_graph roibin_graph;
  * concurrent branches cannot block one another).  Which is faster depends on
  * the mix: a persistent kernel that fills the GPU leaves little for a
  * concurrent branch to overlap with.
+ * ROIBIN_GRAPH_FUSED runs the jobs whose contexts take the fused path (at most
+ * 16) in one persistent kernel launch (§4.1, §5.3.5: the work of many events,
+ * here of several detectors, spread over the device at once).  Their work
+ * items take consecutive runs of one ticket counter, in the order given, so
+ * a job's work fills the tail of the one before it; each keeps its own
+ * geometry, parameters, scratch and outputs, and every frame's bytes equal
+ * those of compressing its job alone.  The jobs share the CTAs per SM and ring slots
+ * of the first (CTAs per SM, slots) pair all of them fit, at two binned rows
+ * per step; each keeps its dense-peaks choice and wait limit.  The ROI coder
+ * (if a context has it) follows the launch, then the jobs on the plain path,
+ * one after another.  The graph owns a small device buffer (the launch's
+ * ticket counter and sync words) that every launch zeroes first;
+ * ROIBIN_ERR_INVALID_ARG if the jobs have no common shape.
  * Each context compiles into the graph with its path and fused shape at
  * capture time (tune them first, e.g. with roibin_ctx_autotune).
  * The graph keeps the job pointers: the caller refills d_frames (and the

@@ -29,7 +29,7 @@ REJECTED = 1  # per-frame status: non-hit rejection, nothing written
 
 PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
 DEC_AUTO, DEC_PANEL, DEC_MULTIPASS = 0, 1, 2
-GRAPH_SERIAL, GRAPH_CONCURRENT = 0, 1
+GRAPH_SERIAL, GRAPH_CONCURRENT, GRAPH_FUSED = 0, 1, 2
 
 GEOMETRIES = {"cspad": (32, 185, 388), "epix10k": (16, 352, 384), "jungfrau": (8, 512, 1024)}
 
@@ -421,13 +421,16 @@ class Context:
 
 class Graph:
     """Several contexts' compress calls captured into one CUDA graph
-    (roibin_graph_create): one after another, or with `concurrent` on branches
-    the GPU may overlap.  `jobs` is a list of dicts with the keys ctx, frames,
-    out, frame_bytes, status and optionally out_stride, peaks, npeaks (CUDA
+    (roibin_graph_create): one after another, with `concurrent` on branches
+    the GPU may overlap, or with `fused` the fused-path jobs in one persistent
+    launch.  `jobs` is a list of dicts with the keys ctx, frames, out,
+    frame_bytes, status and optionally out_stride, peaks, npeaks (CUDA
     tensors, as Context.compress takes them).  The graph keeps the tensors'
     addresses: refill `frames` in place between launches."""
 
-    def __init__(self, jobs, concurrent: bool = False):
+    def __init__(self, jobs, concurrent: bool = False, fused: bool = False):
+        if concurrent and fused:
+            raise ValueError("a graph is concurrent or fused, not both")
         self.lib = library()
         self._keep = []
         arr = (Job * len(jobs))()
@@ -440,7 +443,8 @@ class Graph:
             self._keep.append(j)
         h = ctypes.c_void_p()
         _check("roibin_graph_create", self.lib.roibin_graph_create(
-            ctypes.byref(h), arr, len(jobs), GRAPH_CONCURRENT if concurrent else GRAPH_SERIAL))
+            ctypes.byref(h), arr, len(jobs),
+            GRAPH_FUSED if fused else GRAPH_CONCURRENT if concurrent else GRAPH_SERIAL))
         self._h = h
 
     def launch(self, stream=None):

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -26,6 +27,7 @@ struct roibin_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint32_t launches = 0;
+  uint32_t* sync = nullptr;  // ROIBIN_GRAPH_FUSED: the joint launch's ticket counter and sync words
 };
 
 struct roibin_ctx {
@@ -215,7 +217,7 @@ uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s
   t.lane_bit = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
   t.lane_lo = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
   t.lane_pq = c.take<uint32_t>((uint64_t)n * d.n_chunks * 32);
-  t.frame_done = c.take<uint32_t>(7ull * n + 1);  // the fused kernel's sync words
+  t.frame_done = c.take<uint32_t>(kSyncWordsPerFrame * (uint64_t)n + 1);  // the fused kernel's sync words
   t.chunk_ref = c.take<uint32_t>(n);
   t.thr_spill_ctas = spill_ctas;
   if (spill_ctas) t.thr_spill = c.take<uint32_t>((uint64_t)spill_ctas * kThrSpill);
@@ -320,9 +322,10 @@ bool compress_args_ok(const roibin_ctx* ctx, const float* d_frames, uint32_t n_f
   if (reinterpret_cast<uintptr_t>(d_frames) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0) return false;
   return true;
 }
-int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, const uint16_t* d_peaks,
-                    const uint32_t* d_npeaks, uint8_t* d_out, uint64_t out_stride, uint64_t* d_frame_bytes,
-                    int32_t* d_frame_status, cudaStream_t st) {
+// The arguments every kernel of a compress call gets.
+PlainArgs plain_args(const roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, const uint16_t* d_peaks,
+                     const uint32_t* d_npeaks, uint8_t* d_out, uint64_t out_stride, uint64_t* d_frame_bytes,
+                     int32_t* d_frame_status) {
   PlainArgs a{};
   a.frames = d_frames;
   a.n_frames = n_frames;
@@ -337,7 +340,20 @@ int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, c
   a.peaks_count_out = ctx->s.peak_count;
   a.trace = ctx->trace;
   a.trace_frames = ctx->trace_frames;
-  if (resolved_path(ctx) == ROIBIN_PATH_FUSED && (uint64_t)n_frames * ctx->dp.P < (1ull << 31)) {
+  return a;
+}
+
+// The call takes the persistent kernel.
+bool takes_fused(const roibin_ctx* ctx, uint32_t n_frames) {
+  return resolved_path(ctx) == ROIBIN_PATH_FUSED && (uint64_t)n_frames * ctx->dp.P < (1ull << 31);
+}
+
+int compress_device(roibin_ctx* ctx, const float* d_frames, uint32_t n_frames, const uint16_t* d_peaks,
+                    const uint32_t* d_npeaks, uint8_t* d_out, uint64_t out_stride, uint64_t* d_frame_bytes,
+                    int32_t* d_frame_status, cudaStream_t st) {
+  const PlainArgs a =
+      plain_args(ctx, d_frames, n_frames, d_peaks, d_npeaks, d_out, out_stride, d_frame_bytes, d_frame_status);
+  if (takes_fused(ctx, n_frames)) {
     FusedShape sh = ctx->fshape;
     if (ctx->wait_limit_set) sh.wait_limit = ctx->wait_limit;
     cudaError_t e = timed(ctx, K_FUSED, st,
@@ -839,8 +855,9 @@ int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_j
   if (!out) return ROIBIN_ERR_INVALID_ARG;
   *out = nullptr;
   if (!jobs || n_jobs == 0) return ROIBIN_ERR_INVALID_ARG;
-  if (flags != ROIBIN_GRAPH_SERIAL && flags != ROIBIN_GRAPH_CONCURRENT) return ROIBIN_ERR_INVALID_ARG;
-  const bool concurrent = flags == ROIBIN_GRAPH_CONCURRENT;
+  if (flags != ROIBIN_GRAPH_SERIAL && flags != ROIBIN_GRAPH_CONCURRENT && flags != ROIBIN_GRAPH_FUSED)
+    return ROIBIN_ERR_INVALID_ARG;
+  const bool concurrent = flags == ROIBIN_GRAPH_CONCURRENT, fused = flags == ROIBIN_GRAPH_FUSED;
   for (uint32_t j = 0; j < n_jobs; ++j) {
     const roibin_job& b = jobs[j];
     if (!compress_args_ok(b.ctx, b.d_frames, b.n_frames, b.d_peaks, b.d_npeaks, b.d_out, b.out_stride,
@@ -852,6 +869,47 @@ int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_j
   }
   const int device = jobs[0].ctx->device;
   if (cudaSetDevice(device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  // ROIBIN_GRAPH_FUSED: the jobs that take the persistent kernel share one
+  // launch (their sync words and the ticket counter in one buffer the graph
+  // owns and zeroes); the others follow it, one after another
+  std::vector<uint32_t> joint, alone;
+  std::unique_ptr<FusedJobs> fj;
+  uint32_t* sync = nullptr;
+  uint64_t sync_words = 1;
+  uint32_t fj_smem = 0, fj_grid = 0;
+  for (uint32_t j = 0; j < n_jobs; ++j)
+    ((fused && takes_fused(jobs[j].ctx, jobs[j].n_frames) && joint.size() < kMaxFusedJobs) ? joint : alone)
+        .push_back(j);
+  if (!joint.empty()) {
+    fj.reset(new (std::nothrow) FusedJobs{});
+    if (!fj) return ROIBIN_ERR_OUT_OF_BUDGET;
+    for (uint32_t j : joint) sync_words += kSyncWordsPerFrame * (uint64_t)jobs[j].n_frames + 1;
+    if (cudaMalloc(&sync, sync_words * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return ROIBIN_ERR_OUT_OF_BUDGET;
+    }
+    std::vector<FusedShape> tuned(joint.size());
+    uint64_t off = 1;  // word 0: the ticket counter
+    for (uint32_t i = 0; i < joint.size(); ++i) {
+      const roibin_job& b = jobs[joint[i]];
+      FusedJob& J = fj->job[i];
+      J.p = b.ctx->dp;
+      J.s = b.ctx->s;
+      J.s.frame_done = sync + off;
+      off += kSyncWordsPerFrame * (uint64_t)b.n_frames + 1;
+      J.a = plain_args(b.ctx, b.d_frames, b.n_frames, b.d_peaks, b.d_npeaks, b.d_out, b.out_stride,
+                       b.d_frame_bytes, b.d_frame_status);
+      J.dense = b.ctx->fused_dense_peaks ? 1u : 0u;
+      tuned[i] = b.ctx->fshape;
+      if (b.ctx->wait_limit_set) tuned[i].wait_limit = b.ctx->wait_limit;
+    }
+    fj->ticket = sync;
+    fj->n_jobs = (uint32_t)joint.size();
+    if (!fused_jobs_plan(fj.get(), tuned.data(), jobs[0].ctx->num_sms, &fj_smem, &fj_grid)) {
+      cudaFree(sync);
+      return ROIBIN_ERR_INVALID_ARG;
+    }
+  }
   cudaStream_t cs = nullptr;
   std::vector<cudaStream_t> side(n_jobs, nullptr);
   std::vector<cudaEvent_t> ev(n_jobs + 1, nullptr);
@@ -864,7 +922,36 @@ int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_j
   // relaxed mode: the fused launcher sets a kernel attribute while capturing
   if (status == ROIBIN_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     status = ROIBIN_ERR_CUDA;
-  if (status == ROIBIN_OK) {
+  if (status == ROIBIN_OK && fused) {
+    if (!joint.empty()) {
+      if (cudaMemsetAsync(sync, 0, sync_words * 4, cs) != cudaSuccess ||
+          launch_fused_jobs(*fj, fj_smem, fj_grid, cs) != cudaSuccess)
+        status = ROIBIN_ERR_CUDA;
+      launches += 1;
+      for (uint32_t i = 0; status == ROIBIN_OK && i < joint.size(); ++i) {  // the ROI coder after the joint launch
+        roibin_ctx* ctx = jobs[joint[i]].ctx;
+        const bool timing = ctx->timing;
+        ctx->timing = false;
+        ctx->last_launches = 0;
+        status = roi_code(ctx, fj->job[i].a, cs);
+        ctx->timing = timing;
+        launches += ctx->last_launches;
+      }
+    }
+    for (uint32_t j : alone) {
+      if (status != ROIBIN_OK) break;
+      const roibin_job& b = jobs[j];
+      const bool timing = b.ctx->timing;
+      b.ctx->timing = false;
+      b.ctx->last_launches = 0;
+      status = compress_device(b.ctx, b.d_frames, b.n_frames, b.d_peaks, b.d_npeaks, b.d_out, b.out_stride,
+                               b.d_frame_bytes, b.d_frame_status, cs);
+      b.ctx->timing = timing;
+      launches += b.ctx->last_launches;
+    }
+    // capture always ends, so that the stream leaves capture mode
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess && status == ROIBIN_OK) status = ROIBIN_ERR_CUDA;
+  } else if (status == ROIBIN_OK) {
     if (cudaEventRecord(ev[n_jobs], cs) != cudaSuccess) status = ROIBIN_ERR_CUDA;  // the fork
     for (uint32_t j = 0; status == ROIBIN_OK && j < n_jobs; ++j) {
       const roibin_job& b = jobs[j];
@@ -895,22 +982,20 @@ int roibin_graph_create(roibin_graph** out, const roibin_job* jobs, uint32_t n_j
   for (auto st : side)
     if (st) cudaStreamDestroy(st);
   if (cs) cudaStreamDestroy(cs);
+  roibin_graph* g = status == ROIBIN_OK ? new (std::nothrow) roibin_graph : nullptr;
+  if (status == ROIBIN_OK && !g) status = ROIBIN_ERR_OUT_OF_BUDGET;
   if (status != ROIBIN_OK) {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    if (sync) cudaFree(sync);
     cudaGetLastError();
     return status;
-  }
-  roibin_graph* g = new (std::nothrow) roibin_graph;
-  if (!g) {
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-    return ROIBIN_ERR_OUT_OF_BUDGET;
   }
   g->device = device;
   g->graph = graph;
   g->exec = exec;
   g->launches = launches;
+  g->sync = sync;
   *out = g;
   return ROIBIN_OK;
 }
@@ -929,6 +1014,7 @@ int roibin_graph_destroy(roibin_graph* g) {
   cudaDeviceSynchronize();
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->sync) cudaFree(g->sync);
   delete g;
   return ROIBIN_OK;
 }

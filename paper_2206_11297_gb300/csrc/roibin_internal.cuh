@@ -127,6 +127,7 @@ struct Scratch {
   uint32_t* thr_spill;      // [thr_spill_ctas][kThrSpill], by CTA index
   uint32_t thr_spill_ctas;  // CTAs with a spill list (0: none)
 };
+constexpr uint32_t kSyncWordsPerFrame = 7;  // the persistent kernel's sync words per frame (+1: its ticket)
 constexpr uint32_t kThrSpill = 3840;  // spilled candidate keys per CTA (4,096 with the shared list)
 
 // count, first, index (34 words each), symbols; padded to 16 bytes
@@ -1004,6 +1005,7 @@ struct FusedShape {
   uint32_t wait_limit;           // polls of a flag wait before it reports ROIBIN_ERR_TIMEOUT
   uint32_t band_rows;            // dense peaks: panel rows staged at once (band + halo)
   uint32_t smem_dense;           // shared memory of the dense-peaks variant (>= smem)
+  uint32_t dense;                // multi-job launch: this job takes the dense-peaks code
   uint32_t off_ctl, off_bar, off_hist, off_pql, off_thr, off_ring, off_nb, off_acc, off_cand;  // streaming role
   uint32_t off_huff, off_total, off_cblen, off_cbcode, off_keys, off_cw, off_offs;  // codebook / plan roles
   uint32_t off_stage;                                                        // size / write roles
@@ -1014,6 +1016,42 @@ bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per
                      FusedShape* out);
 cudaError_t launch_fused(const DevParams& p, const Scratch& fs, const PlainArgs& a, const FusedShape& sh,
                          bool screen, cudaStream_t st);
+
+// One persistent launch over several batches (fused_jobs.cu): each job is a
+// batch of frames of one geometry with its own parameters, scratch, outputs
+// and shape.  The launch's counter is cut into slices; each slice holds the
+// next `chunk` tickets of every job, in job order, and each job's own tickets
+// come in their order.  One slice (each job's tickets in one run, the next
+// job filling the previous one's tail) was the fastest on a CSPAD + epix10k +
+// 8 x 512 x 1024 batch: 7.35 ms, against 8.26 ms with 8 slices and 10.07 ms
+// with 256 (running a job's HBM streaming beside another's latency-bound
+// peak tests slowed the peak tests more than it gained).
+constexpr uint32_t kMaxFusedJobs = 16;
+constexpr uint32_t kJobSlices = 1;  // slices of a launch (fewer if every job has fewer tickets)
+struct FusedJob {
+  DevParams p;
+  Scratch s;              // frame_done: this job's sync words in the launch's buffer
+  PlainArgs a;
+  FusedShape sh;
+  uint32_t tickets;       // the job's own tickets (those of a k_fused launch of it)
+  uint32_t chunk;         // of them per slice
+  uint32_t cbegin, cend;  // the job's place [cbegin, cend) in a slice
+  uint32_t dense;         // the dense-peaks code
+};
+struct FusedJobs {
+  uint32_t* ticket;       // the launch's ticket counter (zero before the launch)
+  uint32_t total;         // tickets of the launch: slices x slice
+  uint32_t slice;         // tickets per slice (the jobs' chunks)
+  uint32_t n_jobs;
+  FusedJob job[kMaxFusedJobs];
+};
+// Gives every job of *m (p, s, a and dense set) a shape for one joint launch:
+// the CTAs per SM and ring slots are common, the first pair every job fits
+// (two binned rows per step; tuned[i] gives job i's wait limit); sets the
+// jobs' lags and ticket slices, m->total, the launch's shared memory and
+// grid.  False if no common shape exists or the tickets overflow.
+bool fused_jobs_plan(FusedJobs* m, const FusedShape* tuned, int num_sms, uint32_t* smem, uint32_t* grid);
+cudaError_t launch_fused_jobs(const FusedJobs& m, uint32_t smem, uint32_t grid, cudaStream_t st);
 
 // Each launcher enqueues one kernel and returns cudaGetLastError().
 // `timer` may be null; when set, it brackets the launch with events.
