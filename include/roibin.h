@@ -84,6 +84,8 @@ extern "C" {
 #define ROIBIN_ERR_TIMEOUT (-6)        /* a bounded device-side wait gave up          */
 #define ROIBIN_ERR_CODE_LENGTH (-7)    /* Huffman code > 32 bits (cannot occur for
                                           frames below 5,702,887 bins)                */
+#define ROIBIN_ERR_CHECK (-8)          /* checks build: a device bounds check failed
+                                          or a scratch guard band was overwritten     */
 /* Per-frame outcome that is not an error: non-hit rejection (paper §1, §4:
  * frames with too few peaks to index are dropped before compression).  The
  * frame has fewer peaks than nhr_min_peaks; nothing is written for it and its
@@ -198,8 +200,40 @@ uint64_t roibin_compress_bound(const roibin_geometry* g, const roibin_params* p)
 int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_params* p,
                       uint32_t max_frames_per_call, uint64_t hbm_budget_bytes, int device);
 
-/* Frees the context and its scratch.  Synchronises the device first.  NULL ok. */
+/* Frees the context and its scratch.  Synchronises the device first.  NULL ok.
+ * In a checks build (below) it first runs roibin_ctx_debug_status and returns
+ * ROIBIN_ERR_CHECK if that finds a failure (the context is freed all the
+ * same). */
 int roibin_ctx_destroy(roibin_ctx* ctx);
+
+/* Checks build.  The library built with -DROIBIN_CHECKS stands in for a
+ * memory checker, which cannot run on every GPU (the paper has no
+ * counterpart):
+ *  - device code checks the bounds of its stores into the caller's output
+ *    buffers and into offset-computed scratch; a failing check records its id
+ *    (ROIBIN_CHECK_*) and a count in the context's scratch and skips the store,
+ *    instead of trapping;
+ *  - the context's scratch sections are separated by 256-byte guard bands
+ *    filled with 0xA5 bytes at creation.
+ * roibin_ctx_debug_status synchronises the device and reports: *checks_build
+ * (1 in a checks build, else 0 and nothing else is examined), *first_check
+ * (id of the first failed check, 0 if none), *failed (failed checks so far)
+ * and *bad_guard (byte offset in the scratch of the first overwritten guard
+ * band, UINT64_MAX if none).  Returns ROIBIN_ERR_CHECK if a check failed or a
+ * guard was overwritten, else ROIBIN_OK (also in other builds).  Any output
+ * pointer may be NULL.  roibin_ctx_debug_poke_guard (checks builds only; else
+ * ROIBIN_ERR_INVALID_ARG) overwrites one word of guard band `index` from the
+ * host, so that a test can see the guard check report it. */
+#define ROIBIN_CHECK_PLAN_TOTAL 1   /* a frame's planned stream exceeds its output slot  */
+#define ROIBIN_CHECK_BITSTREAM 2    /* a bitstream word past the frame's word count      */
+#define ROIBIN_CHECK_OUTLIERS 3     /* an outlier record past the frame's outlier count  */
+#define ROIBIN_CHECK_ROI 4          /* an ROI window past the frame's stream             */
+#define ROIBIN_CHECK_CODES 5        /* a code byte past the frame's code area            */
+#define ROIBIN_CHECK_ROI_WORDS 6    /* coded ROI words past a window's or frame's share  */
+#define ROIBIN_CHECK_STREAM_READ 7  /* a decoder read past a frame's compressed stream    */
+int roibin_ctx_debug_status(roibin_ctx* ctx, uint32_t* checks_build, uint32_t* first_check, uint32_t* failed,
+                            uint64_t* bad_guard);
+int roibin_ctx_debug_poke_guard(roibin_ctx* ctx, uint32_t index);
 
 /* Bytes of device scratch the context holds. */
 uint64_t roibin_ctx_scratch_bytes(const roibin_ctx* ctx);

@@ -25,6 +25,7 @@ ERR_OUT_OF_BUDGET = -4
 ERR_CUDA = -5
 ERR_TIMEOUT = -6
 ERR_CODE_LENGTH = -7
+ERR_CHECK = -8
 REJECTED = 1  # per-frame status: non-hit rejection, nothing written
 
 PATH_AUTO, PATH_PLAIN, PATH_FUSED = 0, 1, 2
@@ -92,6 +93,9 @@ _SIGNATURES = {
     "roibin_ctx_fused_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(_u32)] * 5),
     "roibin_ctx_set_trace": (ctypes.c_int, [_P, _P, _u32]),
     "roibin_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "roibin_ctx_debug_status": (ctypes.c_int, [_P, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                                               ctypes.POINTER(_u32), ctypes.POINTER(_u64)]),
+    "roibin_ctx_debug_poke_guard": (ctypes.c_int, [_P, _u32]),
     "roibin_compress": (ctypes.c_int, [_P, _P, _u32, _P, _P, _P, _u64, _P, _P, _P]),
     "roibin_decompress": (ctypes.c_int, [_P, _P, _u64, _P, _u32, _P, _P, _P]),
     "roibin_ctx_reserve_host_path": (ctypes.c_int, [_P]),
@@ -113,13 +117,20 @@ EXPORTED_SYMBOLS = sorted(_SIGNATURES)
 _lib = None
 
 
+def checks_requested() -> bool:
+    """ROIBIN_CHECKS=1 in the environment selects the checks build of the library."""
+    return os.environ.get("ROIBIN_CHECKS", "") not in ("", "0")
+
+
 def library(build_if_needed: bool = True):
-    """Loads libroibin.so (building it first if asked); raises if unavailable."""
+    """Loads libroibin.so (libroibin_checks.so when ROIBIN_CHECKS=1), building
+    it first if asked; raises if unavailable."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if build_if_needed and not _build.up_to_date():
-            _build.build()
+        checks = checks_requested()
+        path = _build.LIB_CHECKS if checks else _build.LIB
+        if build_if_needed and not _build.up_to_date(checks):
+            _build.build(checks=checks)
         if not os.path.exists(path):
             raise RuntimeError(f"libroibin.so is not built ({path}); run __graft_entry__.build()")
         try:
@@ -240,9 +251,21 @@ class Context:
 
     # -- lifetime
     def close(self):
+        """Frees the context.  In the checks build a failed device check or an
+        overwritten guard band raises RoibinError(ERR_CHECK) here."""
         if getattr(self, "_h", None):
-            self.lib.roibin_ctx_destroy(self._h)
-            self._h = None
+            h, self._h = self._h, None
+            _check("roibin_ctx_destroy", self.lib.roibin_ctx_destroy(h))
+
+    def debug_status(self):
+        """roibin_ctx_debug_status: (status, checks_build, first_check, failed, bad_guard)."""
+        cb, first, failed, bad = _u32(), _u32(), _u32(), _u64()
+        st = self.lib.roibin_ctx_debug_status(self._h, ctypes.byref(cb), ctypes.byref(first), ctypes.byref(failed),
+                                              ctypes.byref(bad))
+        return st, bool(cb.value), int(first.value), int(failed.value), int(bad.value)
+
+    def debug_poke_guard(self, index: int):
+        _check("roibin_ctx_debug_poke_guard", self.lib.roibin_ctx_debug_poke_guard(self._h, int(index)))
 
     def __del__(self):
         try:

@@ -19,6 +19,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libroibin.so")
+# the checks build (-DROIBIN_CHECKS): device bounds checks that record instead
+# of trapping and guard bands around the scratch sections; for tests only
+BUILD_CHECKS = os.path.join(HERE, "_build_checks")
+LIB_CHECKS = os.path.join(HERE, "libroibin_checks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fno-strict-aliasing", "-I", INCLUDE, "-I", CSRC]
@@ -40,24 +44,27 @@ def _deps():
         [os.path.join(INCLUDE, "roibin.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checks: bool = False) -> bool:
+    lib = LIB_CHECKS if checks else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    """Builds libroibin.so, or with checks=True the checks build libroibin_checks.so."""
+    lib, build_dir = (LIB_CHECKS, BUILD_CHECKS) if checks else (LIB, BUILD)
+    if not force and up_to_date(checks):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     procs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc, *FLAGS, *ARCH, "-c", src, "-o", obj]
+        cmd = [cc, *FLAGS, *(["-DROIBIN_CHECKS"] if checks else []), *ARCH, "-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -70,11 +77,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(os.path.basename(src))
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checks="--checks" in sys.argv))

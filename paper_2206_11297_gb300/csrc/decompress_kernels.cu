@@ -480,6 +480,7 @@ __global__ void k_dec_roi(DevParams p, Scratch s, DecArgs a) {
     }
     float* panel = a.out + (size_t)f * p.frame_px + (size_t)pn * p.H * p.W;
     const int r0 = (int)r - di.roi_h / 2, c0 = (int)c - di.roi_w / 2;
+    if (!RB_CHECK(s, di.pl.off_roi + (uint64_t)(k + 1) * win * 4 <= di.pl.total, ROIBIN_CHECK_STREAM_READ)) continue;
     for (uint32_t e = lane_id(); e < win; e += 32) {
       const int rr = r0 + (int)(e / di.roi_w), cc = c0 + (int)(e % di.roi_w);
       if (rr >= 0 && rr < (int)p.H && cc >= 0 && cc < (int)p.W)

@@ -172,6 +172,7 @@ enum {
   CTL_NZ,                       // codes other than the zero residual's in the item
   CTL_PQN,                      // prequantisation outliers in the item
   CTL_NCAND,                    // listed candidates left after pruning
+  CTL_BAND,                     // band copies so far (the band barrier's phase)
   CTL_PQ,                       // [kMaxK] prequantisation outliers per panel of the item
   CTL_TMP = CTL_PQ + kMaxK,
   CTL_WORDS = CTL_TMP + 33
@@ -211,7 +212,7 @@ __device__ __forceinline__ FinView fin_view(unsigned char* sm, const FusedShape&
 // one lane per candidate, every pixel read from shared memory.  The item's
 // panels are taken in bands of rows: a band of B rows plus `reach` rows above
 // and below (the whole neighbourhood of every candidate in it) is staged in
-// the ring's memory with coalesced 16-byte loads.  The band's pixels >=
+// the ring's memory by one bulk copy.  The band's pixels >=
 // amax_thr are ranked in a block-wide scan (each thread counts its own run of
 // the band, then the runs' counts are scanned), and rank q goes to thread
 // q mod 256 in rounds, so every thread holds a candidate whatever their number.
@@ -225,16 +226,32 @@ __device__ __noinline__ void dense_band_peaks(const DevParams& p, const Scratch&
   float* band = reinterpret_cast<float*>(v.ring);
   uint32_t* run_start = v.thr;  // [kPT] first rank of each thread's run
   uint32_t* acc = s.peak_part + fu * sh.peak_cap;
+  uint64_t* band_bar = v.bars + 2 * sh.stages;
+  const uint64_t pol = evict_normal_policy();  // a band's halo rows are read again by the next band
+  uint32_t bands_done = v.ctl[CTL_BAND];
   for (uint32_t j = 0; j < kp; ++j) {
     const float* pan = item_px + (size_t)j * plane;
     for (uint32_t r0 = 0; r0 < H; r0 += B) {
       const uint32_t r1 = min(H, r0 + B);
       const uint32_t rb0 = r0 >= reach ? r0 - reach : 0u, rb1 = min(H, r1 + reach);
       __syncthreads();  // the previous band is no longer read
-      const float4* src = reinterpret_cast<const float4*>(pan + (size_t)rb0 * W);
-      float4* dst = reinterpret_cast<float4*>(band);
-      for (uint32_t e = tid; e < (rb1 - rb0) * (W / 4); e += kPT) dst[e] = __ldg(src + e);
-      __syncthreads();
+      // one bulk copy of the band's rows (contiguous in the panel, 16-byte
+      // aligned: W % 4 == 0), its arrival counted on the band barrier
+      if (tid == 0) {
+        fence_proxy_async();  // the band's memory was last read through the generic proxy
+        const uint32_t bytes = (rb1 - rb0) * W * 4;
+        mbar_expect_tx(band_bar, bytes);
+        tma_load_1d(band, pan + (size_t)rb0 * W, bytes, band_bar, pol);
+      }
+      const bool landed = mbar_wait(band_bar, (bands_done++) & 1u);
+      if (!__syncthreads_and(landed)) {  // the copy never arrived: the item is marked, see process_item
+        if (tid == 0) {
+          v.ctl[CTL_TIMEOUT] = 1;
+          v.ctl[CTL_BAND] = bands_done;
+        }
+        __syncthreads();
+        return;
+      }
       // pass 1: each thread counts the candidates of its run of the band's own rows
       const float* core = band + (size_t)(r0 - rb0) * W;
       const uint32_t n_core = (r1 - r0) * W, run = ceil_div(n_core, kPT);
@@ -270,6 +287,7 @@ __device__ __noinline__ void dense_band_peaks(const DevParams& p, const Scratch&
     }
   }
   __syncthreads();
+  if (tid == 0) v.ctl[CTL_BAND] = bands_done;
   // the item's accepted pixels into the shared list the caller sorts
   const uint32_t n_acc = v.ctl[CTL_ACC];
   if (n_acc <= p.max_peaks)
@@ -532,7 +550,8 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
           qd[g] = left;
           nz |= (uint32_t)((d0 | d1) != 0) << ii;
           const uint32_t pair = (uint32_t)((d0 + 128) & 0xFF) | ((uint32_t)((d1 + 128) & 0xFF) << 8);
-          st_keep_u16_if(codes + (size_t)i * p.Wb, (uint16_t)pair, keep_pol, owned);  // 2 pc is even
+          st_keep_u16_if(codes + (size_t)i * p.Wb, (uint16_t)pair, keep_pol,
+                         owned && RB_CHECK(s, i < p.Hb && 2 * pc + 1 < p.Wb, ROIBIN_CHECK_CODES));  // 2 pc is even
         }
         if (!owned) nz = 0;
         if (__any_sync(0xffffffffu, nz != 0)) {
@@ -1278,8 +1297,9 @@ __device__ void size_item(const DevParams& p, const Scratch& s, const PlainArgs&
       s.chunk_pq[o] = cpq[k];
     }
     if (tid == 0) s.plan[g] = pl;
-    write_frame_head(a.out + (size_t)g * a.out_stride, p, pl, a.peaks_key_out + (size_t)g * p.max_peaks,
-                     s.cb_len + (size_t)g * kMaxSymbols, cw, ref);
+    if (RB_CHECK(s, pl.total <= a.out_stride, ROIBIN_CHECK_PLAN_TOTAL))
+      write_frame_head(a.out + (size_t)g * a.out_stride, p, pl, a.peaks_key_out + (size_t)g * p.max_peaks,
+                       s.cb_len + (size_t)g * kMaxSymbols, cw, ref);
   }
   __syncthreads();
   if (trace) trace[4] = global_ns();
@@ -1329,6 +1349,10 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
   pl.off_lo = __ldcg(reinterpret_cast<const unsigned long long*>(&s.plan[g].off_lo));
   pl.off_pq = __ldcg(reinterpret_cast<const unsigned long long*>(&s.plan[g].off_pq));
   pl.off_bits = __ldcg(reinterpret_cast<const unsigned long long*>(&s.plan[g].off_bits));
+#ifdef ROIBIN_CHECKS
+  pl.n_lo = __ldcg(&s.plan[g].n_lo);  // the bounds of the checks below
+  pl.total = __ldcg(reinterpret_cast<const unsigned long long*>(&s.plan[g].total));
+#endif
   __syncthreads();
   uint8_t* out = a.out + (size_t)g * a.out_stride;
   uint32_t* words = reinterpret_cast<uint32_t*>(out + pl.off_bits);
@@ -1360,7 +1384,8 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
     const bool full = (k + 1) * kChunk <= p.M;
     if (!full) {
       const uint32_t w1 = pl.n_words;
-      for (uint32_t w = w0 + lane; w < w1; w += 32) words[w] = 0;
+      for (uint32_t w = w0 + lane; w < w1; w += 32)
+        if (RB_CHECK(s, (uint64_t)pl.off_bits + 4ull * (w + 1) <= pl.total, ROIBIN_CHECK_BITSTREAM)) words[w] = 0;
       __threadfence_block();
       __syncwarp();
     }
@@ -1383,8 +1408,8 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
         const uint32_t word = (uint32_t)(accb >> 32);
         if (first) {
           if (full) head = word;
-          else atomicOr(words + wi, word);
-        } else {
+          else if (RB_CHECK(s, wi < pl.n_words, ROIBIN_CHECK_BITSTREAM)) atomicOr(words + wi, word);
+        } else if (RB_CHECK(s, wi < pl.n_words, ROIBIN_CHECK_BITSTREAM)) {
           words[wi] = word;
         }
         first = false;
@@ -1426,21 +1451,25 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
         const uint32_t b = (word >> (8 * t)) & 0xFFu;
         const uint64_t e = symbol_entry(p, s, g, btab, b, bin);
         append((uint32_t)(e >> 32), (uint32_t)e);
-        if (b == 0) lo_out[lo_pos++] = make_uint2(bin, (uint32_t)__ldcg(lo_delta + bin));
+        if (b == 0 && RB_CHECK(s, lo_pos < pl.n_lo, ROIBIN_CHECK_OUTLIERS))
+          lo_out[lo_pos++] = make_uint2(bin, (uint32_t)__ldcg(lo_delta + bin));
       }
     }
     if (full) {
       const uint32_t tail = nacc > 0 ? (uint32_t)(accb >> 32) : 0u;  // shared with the next lane
       const uint32_t prev_tail = __shfl_up_sync(0xffffffffu, tail, 1);
-      if ((start & 31u) != 0) words[first_idx] = head | prev_tail;
-      if (lane == 31 && nacc > 0) words[wi] = tail;  // the chunk's last word, zero padded
-    } else if (nacc > 0) {
+      if ((start & 31u) != 0 && RB_CHECK(s, first_idx < pl.n_words, ROIBIN_CHECK_BITSTREAM))
+        words[first_idx] = head | prev_tail;
+      if (lane == 31 && nacc > 0 && RB_CHECK(s, wi < pl.n_words, ROIBIN_CHECK_BITSTREAM))
+        words[wi] = tail;  // the chunk's last word, zero padded
+    } else if (nacc > 0 && RB_CHECK(s, wi < pl.n_words, ROIBIN_CHECK_BITSTREAM)) {
       atomicOr(words + wi, (uint32_t)(accb >> 32));  // shared with the next lane
     }
     __syncwarp();
     if (any_pq)
       for (uint32_t i = s0; i < s1; ++i)
-        if (pq_bit_of(p, s, sh, g, i)) pq_out[pq_pos++] = make_uint2(i, __ldcg(pq_bits + i));
+        if (pq_bit_of(p, s, sh, g, i) && RB_CHECK(s, pq_pos < pl.n_pq, ROIBIN_CHECK_OUTLIERS))
+          pq_out[pq_pos++] = make_uint2(i, __ldcg(pq_bits + i));
   }
   __syncthreads();
   const uint64_t t_roi = acct ? global_ns() : 0;
@@ -1455,7 +1484,8 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
     const uint32_t px = __ldcg(keys + k);
     const uint32_t pn = px / plane, rem = px - pn * plane;
     const int r = (int)(rem / p.W), c = (int)(rem % p.W);
-    warp_copy_roi(frame + (size_t)pn * plane, p.H, p.W, r, c, p.roi_h, p.roi_w, roi + (size_t)k * win);
+    if (RB_CHECK(s, pl.off_roi + (uint64_t)(k + 1) * win * 4 <= a.out_stride, ROIBIN_CHECK_ROI))
+      warp_copy_roi(frame + (size_t)pn * plane, p.H, p.W, r, c, p.roi_h, p.roi_w, roi + (size_t)k * win);
   }
   // this group's code bytes are dead: drop them from L2 without a write-back
   __syncthreads();
@@ -1520,8 +1550,10 @@ __device__ __forceinline__ void fused_cta_init(unsigned char* sm, const FusedSha
       mbar_init(bars + b, 1);
       mbar_init(bars + sh.stages + b, kConsumerWarps);
     }
+    mbar_init(bars + 2 * sh.stages, 1);  // the dense-peaks band copies
     fence_mbar_init();
     reinterpret_cast<uint32_t*>(sm + sh.off_ctl)[CTL_TIMEOUT] = 0;
+    reinterpret_cast<uint32_t*>(sm + sh.off_ctl)[CTL_BAND] = 0;
   }
   __syncthreads();
 }

@@ -112,7 +112,7 @@ static bool make_shape(const DevParams& p, uint32_t ctas_per_sm, uint32_t rb, ui
     return (uint32_t)o;
   };
   sh.off_ctl = take((uint64_t)CTL_WORDS * 4);  // every role uses the control words
-  sh.off_bar = take(16ull * stages);
+  sh.off_bar = take(16ull * stages + 8);  // ring full / empty barriers, then the band barrier
   const uint64_t base = off;
   // streaming role; the peak tests reuse the ring once the rows are consumed
   sh.off_hist = take(kMaxSymbols * 4);

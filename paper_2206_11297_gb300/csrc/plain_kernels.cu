@@ -598,6 +598,7 @@ __global__ void __launch_bounds__(1024) k_plan(DevParams p, Scratch s, PlainArgs
     a.frame_status[f] = st;
   }
   if (st != ROIBIN_OK) return;
+  if (!RB_CHECK(s, pl.total <= a.out_stride, ROIBIN_CHECK_PLAN_TOTAL)) return;
 
   uint8_t* out = a.out + (size_t)f * a.out_stride;
   if (threadIdx.x == 0) {
@@ -707,8 +708,10 @@ __global__ void __launch_bounds__(kChunkThreads) k_encode(DevParams p, Scratch s
   uint8_t* out = a.out + (size_t)f * a.out_stride;
   const size_t o = (size_t)f * p.n_chunks + k;
   uint32_t* dst = reinterpret_cast<uint32_t*>(out + pl.off_bits) + s.chunk_words[o];
-  for (uint32_t w = threadIdx.x; w < n_words; w += kChunkThreads) dst[w] = buf[w];
-  if (tot_lo | tot_pq) {
+  if (RB_CHECK(s, s.chunk_words[o] + n_words <= pl.n_words, ROIBIN_CHECK_BITSTREAM))
+    for (uint32_t w = threadIdx.x; w < n_words; w += kChunkThreads) dst[w] = buf[w];
+  if ((tot_lo | tot_pq) && RB_CHECK(s, s.chunk_lo[o] + lo_rank + nlo <= pl.n_lo &&
+                                            s.chunk_pq[o] + pq_rank + npq <= pl.n_pq, ROIBIN_CHECK_OUTLIERS)) {
     uint2* lo_out = reinterpret_cast<uint2*>(out + pl.off_lo) + s.chunk_lo[o] + lo_rank;
     uint2* pq_out = reinterpret_cast<uint2*>(out + pl.off_pq) + s.chunk_pq[o] + pq_rank;
     for (int i = 0; i < 32; ++i) {
@@ -736,7 +739,8 @@ __global__ void __launch_bounds__(256) k_roi(DevParams p, Scratch s, PlainArgs a
   const float* panel = a.frames + (size_t)f * p.frame_px + (size_t)pn * p.H * p.W;
   float* dst = reinterpret_cast<float*>(a.out + (size_t)f * a.out_stride + pl.off_roi) +
                (size_t)k * p.roi_h * p.roi_w;
-  warp_copy_roi(panel, p.H, p.W, r, c, p.roi_h, p.roi_w, dst);
+  if (RB_CHECK(s, pl.off_roi + (uint64_t)(k + 1) * p.roi_h * p.roi_w * 4 <= pl.total, ROIBIN_CHECK_ROI))
+    warp_copy_roi(panel, p.H, p.W, r, c, p.roi_h, p.roi_w, dst);
 }
 
 // last_peaks: peak lists of the last call as (panel, row, col) triples.

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kRoiPlanThreads) k_roi_plan(DevParams p, Scrat
                          : make_uint4(0u, 0u, 0u, 0u);
   }
   if (!fits) return;
+  if (!RB_CHECK(s, base + bytes <= a.out_stride, ROIBIN_CHECK_ROI)) return;
   uint8_t* out = a.out + (size_t)f * a.out_stride;
   if (tid == 0) {
     uint32_t* h = reinterpret_cast<uint32_t*>(out);
@@ -228,8 +229,10 @@ __global__ void __launch_bounds__(kRoiWarps * 32) k_roi_write(DevParams p, Scrat
   if (plan.x == 2) {  // raw windows
     for (uint32_t k = blockIdx.x * (blockDim.x >> 5) + warp; k < n; k += gridDim.x * (blockDim.x >> 5)) {
       const uint32_t px = s.peak_key[(size_t)f * p.max_peaks + k], pn = px / plane, rem = px - pn * plane;
-      warp_copy_roi(a.frames + (size_t)f * p.frame_px + (size_t)pn * plane, p.H, p.W, (int)(rem / p.W),
-                    (int)(rem % p.W), p.roi_h, p.roi_w, reinterpret_cast<float*>(sec) + (size_t)k * win);
+      const uint64_t at = (uint64_t)plan.z | ((uint64_t)plan.w << 32);
+      if (RB_CHECK(s, at + (uint64_t)(k + 1) * win * 4 <= a.out_stride, ROIBIN_CHECK_ROI))
+        warp_copy_roi(a.frames + (size_t)f * p.frame_px + (size_t)pn * plane, p.H, p.W, (int)(rem / p.W),
+                      (int)(rem % p.W), p.roi_h, p.roi_w, reinterpret_cast<float*>(sec) + (size_t)k * win);
     }
     return;
   }
@@ -244,8 +247,10 @@ __global__ void __launch_bounds__(kRoiWarps * 32) k_roi_write(DevParams p, Scrat
   uint32_t* mm = roi_sm + warp * win;
   uint32_t* wb = roi_sm + nwarps * win + warp * roi_max_words(win);  // the window's words, then copied out
   for (uint32_t k = blockIdx.x * nwarps + warp; k < n; k += gridDim.x * nwarps) {
-    roi_stage(p, a, s, f, k, mm);
     const uint32_t w0 = off[k], w1 = k + 1 < n ? off[k + 1] : plan.y;
+    // a window's words fit its staging area and the frame's word count (warp-uniform)
+    if (!RB_CHECK(s, w0 <= w1 && w1 <= plan.y && w1 - w0 <= roi_max_words(win), ROIBIN_CHECK_ROI_WORDS)) continue;
+    roi_stage(p, a, s, f, k, mm);
     for (uint32_t w = lane; w < w1 - w0; w += 32) wb[w] = 0;  // every bit lands below w1 - w0
     __syncwarp();
     uint32_t pos = 0;  // bits of the window before this round

@@ -39,6 +39,7 @@ struct roibin_ctx {
   Scratch s{};
   void* scratch = nullptr;
   uint64_t scratch_bytes = 0;
+  std::vector<uint64_t> guards;  // checks build: byte offsets of the scratch guard bands
   uint64_t budget = 0;
   uint32_t max_frames = 0;
   int path_req = ROIBIN_PATH_AUTO;
@@ -162,12 +163,21 @@ uint64_t bound_impl(const DevParams& d) {
   return o;
 }
 
+// Checks build: a guard band of this many bytes (0xA5) before every section.
+constexpr uint64_t kGuardBytes = 256;
+constexpr uint8_t kGuardByte = 0xA5;
+
 struct Carver {
   uint8_t* base;
+  std::vector<uint64_t>* guards = nullptr;  // checks build: where the guard bands go
   uint64_t off = 0;
   template <class T>
   T* take(uint64_t count) {
     off = (off + 255) & ~uint64_t(255);
+#ifdef ROIBIN_CHECKS
+    if (guards) guards->push_back(off);
+    off += kGuardBytes;
+#endif
     T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
     off += count * sizeof(T);
     return p;
@@ -184,9 +194,11 @@ bool plain_rows_ok(const DevParams& d, uint32_t rows) {
 
 // Lays out the per-frame scratch for n frames, and candidate spill lists for
 // spill_ctas CTAs of the persistent kernel; with base == nullptr only sizes it.
-uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s, uint32_t spill_ctas) {
-  Carver c{base};
+uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s, uint32_t spill_ctas,
+                       std::vector<uint64_t>* guards = nullptr) {
+  Carver c{base, guards};
   Scratch t{};
+  t.check = c.take<uint32_t>(2);
   t.thr_count = c.take<uint32_t>(n);
   t.thr_idx = c.take<uint32_t>((uint64_t)n * d.thr_cap);
   t.peak_count = c.take<uint32_t>(n);
@@ -229,6 +241,10 @@ uint64_t carve_scratch(const DevParams& d, uint32_t n, uint8_t* base, Scratch* s
     t.roi_book = c.take<uint32_t>((uint64_t)n * 2 * kRoiClasses);
     t.roi_plan = c.take<uint4>(n);
   }
+#ifdef ROIBIN_CHECKS
+  if (guards) guards->push_back((c.off + 255) & ~uint64_t(255));  // after the last section
+  c.off = ((c.off + 255) & ~uint64_t(255)) + kGuardBytes;
+#endif
   if (s) *s = t;
   return c.off + 256;
 }
@@ -621,13 +637,71 @@ int roibin_ctx_create(roibin_ctx** out, const roibin_geometry* g, const roibin_p
     return ROIBIN_ERR_OUT_OF_BUDGET;
   }
   ctx->scratch_bytes = need;
-  carve_scratch(ctx->dp, max_frames_per_call, static_cast<uint8_t*>(ctx->scratch), &ctx->s, spill_ctas);
+  carve_scratch(ctx->dp, max_frames_per_call, static_cast<uint8_t*>(ctx->scratch), &ctx->s, spill_ctas,
+                &ctx->guards);
+  // the check words start at zero; the guard bands (checks build) hold their pattern
+  bool set = cudaMemset(ctx->s.check, 0, 8) == cudaSuccess;
+  for (uint64_t g : ctx->guards)
+    set = set && cudaMemset(static_cast<uint8_t*>(ctx->scratch) + g, kGuardByte, kGuardBytes) == cudaSuccess;
+  if (!set || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->scratch);
+    delete ctx;
+    return ROIBIN_ERR_CUDA;
+  }
   *out = ctx;
   return ROIBIN_OK;
 }
 
+int roibin_ctx_debug_status(roibin_ctx* ctx, uint32_t* checks_build, uint32_t* first_check, uint32_t* failed,
+                            uint64_t* bad_guard) {
+  if (!ctx) return ROIBIN_ERR_INVALID_ARG;
+  if (checks_build) *checks_build = 0;
+  if (first_check) *first_check = 0;
+  if (failed) *failed = 0;
+  if (bad_guard) *bad_guard = UINT64_MAX;
+#ifndef ROIBIN_CHECKS
+  return ROIBIN_OK;
+#else
+  if (checks_build) *checks_build = 1;
+  if (cudaSetDevice(ctx->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return ROIBIN_ERR_CUDA;
+  uint32_t w[2] = {0, 0};
+  if (cudaMemcpy(w, ctx->s.check, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  uint64_t bad = UINT64_MAX;
+  uint8_t band[kGuardBytes];
+  for (uint64_t g : ctx->guards) {
+    if (cudaMemcpy(band, static_cast<uint8_t*>(ctx->scratch) + g, kGuardBytes, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return ROIBIN_ERR_CUDA;
+    for (uint64_t b = 0; b < kGuardBytes && bad == UINT64_MAX; ++b)
+      if (band[b] != kGuardByte) bad = g;
+    if (bad != UINT64_MAX) break;
+  }
+  if (first_check) *first_check = w[0];
+  if (failed) *failed = w[1];
+  if (bad_guard) *bad_guard = bad;
+  return (w[0] || w[1] || bad != UINT64_MAX) ? ROIBIN_ERR_CHECK : ROIBIN_OK;
+#endif
+}
+
+int roibin_ctx_debug_poke_guard(roibin_ctx* ctx, uint32_t index) {
+#ifndef ROIBIN_CHECKS
+  (void)ctx;
+  (void)index;
+  return ROIBIN_ERR_INVALID_ARG;
+#else
+  if (!ctx || index >= ctx->guards.size()) return ROIBIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ROIBIN_ERR_CUDA;
+  const uint32_t word = 0x12345678u;
+  return cuda_status(cudaMemcpy(static_cast<uint8_t*>(ctx->scratch) + ctx->guards[index] + 64, &word, 4,
+                                cudaMemcpyHostToDevice));
+#endif
+}
+
 int roibin_ctx_destroy(roibin_ctx* ctx) {
   if (!ctx) return ROIBIN_OK;
+  // checks build: the guard bands and device checks, before the scratch goes
+  const int checked = roibin_ctx_debug_status(ctx, nullptr, nullptr, nullptr, nullptr);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   for (auto& t : ctx->pending) {
@@ -640,7 +714,7 @@ int roibin_ctx_destroy(roibin_ctx* ctx) {
   if (ctx->host_stage) cudaFree(ctx->host_stage);
   if (ctx->scratch) cudaFree(ctx->scratch);
   delete ctx;
-  return ROIBIN_OK;
+  return checked == ROIBIN_ERR_CHECK ? ROIBIN_ERR_CHECK : ROIBIN_OK;
 }
 
 uint64_t roibin_ctx_scratch_bytes(const roibin_ctx* ctx) {
@@ -1257,6 +1331,7 @@ const char* roibin_status_string(int status) {
     case ROIBIN_ERR_CUDA: return "CUDA runtime error";
     case ROIBIN_ERR_TIMEOUT: return "bounded device wait timed out";
     case ROIBIN_ERR_CODE_LENGTH: return "Huffman code longer than 32 bits";
+    case ROIBIN_ERR_CHECK: return "checks build: a device bounds check failed or a guard band was overwritten";
     default: return "unknown status";
   }
 }

@@ -126,7 +126,25 @@ struct Scratch {
   // persistent batched path: candidate keys past a CTA's shared-memory list
   uint32_t* thr_spill;      // [thr_spill_ctas][kThrSpill], by CTA index
   uint32_t thr_spill_ctas;  // CTAs with a spill list (0: none)
+  uint32_t* check;          // [2] checks build: first failed check id, failed checks
 };
+
+// Checks build (-DROIBIN_CHECKS): RB_CHECK(s, cond, id) is cond, and when cond
+// is false it records check `id` (ROIBIN_CHECK_*) in s.check instead of
+// trapping, so the caller skips the store it guards.  Other builds compile the
+// condition out (true).
+#ifdef ROIBIN_CHECKS
+__device__ __forceinline__ bool rb_check(uint32_t* w, bool ok, uint32_t id) {
+  if (!ok && w) {
+    atomicCAS(w, 0u, id);
+    atomicAdd(w + 1, 1u);
+  }
+  return ok;
+}
+#define RB_CHECK(s, cond, id) ::roibin::rb_check((s).check, (cond), (id))
+#else
+#define RB_CHECK(s, cond, id) true
+#endif
 constexpr uint32_t kSyncWordsPerFrame = 7;  // the persistent kernel's sync words per frame (+1: its ticket)
 constexpr uint32_t kThrSpill = 3840;  // spilled candidate keys per CTA (4,096 with the shared list)
 

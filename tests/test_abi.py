@@ -75,7 +75,7 @@ def test_compress_bound_matches_oracle(geom):
 
 
 def test_status_strings():
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         assert rb.status_string(code) != "unknown status"
     assert rb.status_string(-99) == "unknown status"
 

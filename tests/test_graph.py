@@ -67,10 +67,12 @@ def test_graph_matches_separate_calls_and_refills(concurrent):
     import torch
     params = rb.default_params(max_peaks=8192)
     jobs = _jobs(torch, params, first=0, tune=True)
-    paths = {j["name"]: j["ctx"].resolved_path for j in jobs}
-    assert paths["cspad_mixed"] == rb.PATH_FUSED
-    with rb.Context(RECIPES["jungfrau_mixed"].geometry, params, max_frames=1) as c:
-        assert c.resolved_path == rb.PATH_FUSED   # 1,024-column panels: two column groups
+    # untuned, every geometry of the mix takes the fused path (the 1,024-column
+    # panels with two column groups); the autotuner may pick either path for
+    # these few frames, and the graph takes each context as tuned
+    for name, _ in MIX:
+        with rb.Context(RECIPES[name].geometry, params, max_frames=1) as c:
+            assert c.resolved_path == rb.PATH_FUSED, name
     with rb.Graph(jobs, concurrent=concurrent) as g:
         assert g.launch_count >= len(jobs)
         g.launch()
