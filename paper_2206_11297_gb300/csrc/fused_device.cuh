@@ -100,6 +100,7 @@ __device__ void write_frame_head(uint8_t* out, const DevParams& p, const FramePl
     h[16] = (uint32_t)(pl.total & 0xFFFFFFFFu);
     h[17] = (uint32_t)(pl.total >> 32);
     for (int i = 18; i < 24; ++i) h[i] = 0;
+    h[18] = p.dims == 2 ? 0u : (uint32_t)p.dims;  // Lorenzo dimension, 0 for the default 2
     h[22] = ref;  // frames back to the stream with the code lengths (0: this one)
     uint4* o4 = reinterpret_cast<uint4*>(out);
     for (int i = 0; i < 6; ++i) o4[i] = make_uint4(h[4 * i], h[4 * i + 1], h[4 * i + 2], h[4 * i + 3]);
@@ -976,6 +977,89 @@ __device__ void chunk_codebook(const DevParams& p, const Scratch& s, const Plain
     for (uint32_t g = c0; g < c1; ++g) flag_release(sw.ready_cb + g);
 }
 
+// The 3-D predictor (a6 over the panel stack, §6) from the streamed 2-D
+// residuals: the 3-D residual of a bin is, exactly in integers, its 2-D
+// residual minus the 2-D residual of the same bin in the panel before (the
+// panel's own residual for the first panel).  One CTA walks every bin position
+// up the stack, keeping the previous panel's 2-D residual in a register, and
+// rewrites the frame's code bytes, escape codes and Lorenzo-outlier deltas in
+// place (each bin is read before it is written); the frame's histogram of the
+// new codes goes to `total`.
+__device__ __noinline__ void stack_residuals(const DevParams& p, const Scratch& s, const FusedShape& sh, uint32_t* total,
+                                uint32_t f) {
+  constexpr uint32_t kAhead = 8;  // panels whose code bytes are loaded at once
+  const uint32_t tid = threadIdx.x, lane = lane_id();
+  for (uint32_t k = tid; k < p.nsym; k += kPT) total[k] = 0;
+  __syncthreads();
+  uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride;
+  uint16_t* esc = s.codes + (size_t)f * p.M;
+  int32_t* lo = s.lo_delta + (size_t)f * p.M;
+  const uint32_t Mp = p.Hb * p.Wb;  // even: the fused path has an even binned width
+  const int32_t R = p.R;
+  auto residual = [&](uint32_t b, uint32_t bin) -> int32_t {  // the stored 2-D residual from its byte
+    if (b == 0) return lo[bin];
+    if (b == 255) return (int32_t)esc[bin] - R;
+    return (int32_t)b - 128;
+  };
+  // the common code (the zero residual) is counted by ballot, the others
+  // (rare) by a shared atomic each
+  auto count = [&](uint32_t c) {
+    const uint32_t mc = __ballot_sync(0xffffffffu, c == (uint32_t)R);
+    if (lane == 0 && mc) atomicAdd(total + R, (uint32_t)__popc(mc));
+    if (c != (uint32_t)R && c != 0xFFFFu) atomicAdd(total + c, 1u);
+  };
+  auto store = [&](int32_t d3, uint32_t bin) -> uint32_t {  // the 3-D residual's byte (side arrays set)
+    const uint32_t c = quant_code(d3, R);
+    if (c == 0) {
+      lo[bin] = d3;
+      return 0u;
+    }
+    if (d3 >= -127 && d3 <= 126) return (uint32_t)(d3 + 128);
+    esc[bin] = (uint16_t)c;
+    return 255u;
+  };
+  // each lane takes two neighbouring bins (one 2-byte load per panel); whole
+  // warps walk the positions, so every lane takes part in the histogram
+  for (uint32_t b0 = 2 * (tid & ~31u); b0 < Mp; b0 += 2 * kPT) {
+    const uint32_t b = b0 + 2 * lane;
+    const bool live = b < Mp;
+    int32_t below0 = 0, below1 = 0;
+    if (live) {
+      const uint32_t raw = *reinterpret_cast<const uint16_t*>(codes + b);
+      below0 = residual(raw & 0xFFu, b);
+      below1 = residual(raw >> 8, b + 1);
+    }
+    count(live ? quant_code(below0, R) : 0xFFFFu);
+    count(live ? quant_code(below1, R) : 0xFFFFu);
+    for (uint32_t pn0 = 1; pn0 < p.P; pn0 += kAhead) {
+      uint32_t raw[kAhead];
+#pragma unroll
+      for (uint32_t j = 0; j < kAhead; ++j)
+        raw[j] = (live && pn0 + j < p.P) ? *reinterpret_cast<const uint16_t*>(codes + (size_t)(pn0 + j) * Mp + b) : 0u;
+#pragma unroll
+      for (uint32_t j = 0; j < kAhead; ++j) {
+        if (pn0 + j >= p.P) break;
+        const uint32_t bin = (pn0 + j) * Mp + b;
+        uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
+        if (live) {
+          const int32_t d0 = residual(raw[j] & 0xFFu, bin), d1 = residual(raw[j] >> 8, bin + 1);
+          // as the oracle's int64 difference cast to int32
+          const int32_t e0 = (int32_t)((uint32_t)d0 - (uint32_t)below0), e1 = (int32_t)((uint32_t)d1 - (uint32_t)below1);
+          below0 = d0;
+          below1 = d1;
+          c0 = quant_code(e0, R);
+          c1 = quant_code(e1, R);
+          const uint32_t y0 = store(e0, bin), y1 = store(e1, bin + 1);
+          *reinterpret_cast<uint16_t*>(codes + bin) = (uint16_t)(y0 | (y1 << 8));
+        }
+        count(c0);
+        count(c1);
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // (1) peak list + codebook of frame f, by the CTA that completed its last streaming item.
 __device__ void frame_codebook(const DevParams& p, const Scratch& s, const PlainArgs& a, const FusedShape& sh,
                                unsigned char* sm, uint32_t f, const SyncWords& sw) {
@@ -984,10 +1068,14 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
   uint64_t* trace = (a.trace && f < a.trace_frames && tid == 0) ? a.trace + (size_t)f * kTracePoints : nullptr;
   if (trace) trace[0] = global_ns();
   // a8: the frame's histogram; prequantisation outliers in the frame
-  for (uint32_t k = tid; k < p.nsym; k += kPT) {
-    uint32_t t = 0;
-    for (uint32_t u = 0; u < sh.U; ++u) t += __ldcg(s.hist_part + ((size_t)f * p.P + u) * kMaxSymbols + k);
-    v.total[k] = t;
+  if (p.dims == 3) {
+    stack_residuals(p, s, sh, v.total, f);
+  } else {
+    for (uint32_t k = tid; k < p.nsym; k += kPT) {
+      uint32_t t = 0;
+      for (uint32_t u = 0; u < sh.U; ++u) t += __ldcg(s.hist_part + ((size_t)f * p.P + u) * kMaxSymbols + k);
+      v.total[k] = t;
+    }
   }
   if (tid == 0) {
     uint32_t t = 0;

@@ -161,7 +161,8 @@ static const void* fused_kernel(bool dense, uint32_t kG) {
 
 bool fused_shape_for(const DevParams& p, uint32_t ctas_per_sm, uint32_t rows_per_step, uint32_t stages,
                      FusedShape* out) {
-  if (p.dims != 2 || p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > kMaxG * kGroupCols) return false;
+  // the 2-D predictor, or the 3-D one (the 2-D residuals stacked by the codebook stage)
+  if (p.dims < 2 || p.bh != 2 || p.bw != 2 || (p.W % 4) != 0 || p.W / 4 > kMaxG * kGroupCols) return false;
   if (ctas_per_sm < 1 || ctas_per_sm > 8 || stages < 1 || stages > 8) return false;
   if (rows_per_step != 0 && (rows_per_step < 2 || rows_per_step > 3)) return false;
   FusedShape sh;

@@ -161,9 +161,9 @@ def test_fused_graph_is_one_launch_and_matches_the_oracle():
 def test_fused_graph_mixes_parameters_features_and_paths():
     """One joint launch over jobs that differ in everything a context fixes:
     error bound, quant radius, the ROI coder, chunk codebooks, non-hit
-    rejection, dense peaks, user peak lists and panel width, next to jobs the
-    persistent kernel does not take (cols % 4 != 0, the 3-D predictor), which
-    follow it."""
+    rejection, dense peaks, user peak lists, panel width and the 3-D predictor,
+    next to jobs the persistent kernel does not take (cols % 4 != 0, the 1-D
+    predictor), which follow it."""
     import torch
     from synthetic import FrameRecipe
     specs = [
@@ -172,8 +172,9 @@ def test_fused_graph_mixes_parameters_features_and_paths():
         ("c", (2, 30, 1024), dict(atot_thr=300.0, chunk_frames=3, nhr_min_peaks=3), False),
         ("d", (4, 48, 64), dict(abs_eb=1.0, max_peaks=2048), True),
         ("e", (2, 21, 27), dict(atot_thr=300.0), False),                  # plain path: cols % 4 != 0
-        ("f", (3, 40, 44), dict(atot_thr=300.0, lorenzo_dims=3), False),  # plain path: 3-D
+        ("f", (3, 40, 44), dict(atot_thr=300.0, lorenzo_dims=1), False),  # plain path: 1-D
         ("g", (2, 24, 32), dict(atot_thr=300.0, roi_coder=1, max_peaks=16), False),  # user peaks
+        ("h", (5, 30, 64), dict(atot_thr=300.0, lorenzo_dims=3), False),  # the panel stack's predictor
     ]
     jobs, prm = [], {}
     for i, (name, geom, kw, hot) in enumerate(specs):
@@ -199,7 +200,7 @@ def test_fused_graph_mixes_parameters_features_and_paths():
             job["_pk"] = pk
         jobs.append(job)
     paths = [j["ctx"].resolved_path for j in jobs]
-    assert paths[4] == rb.PATH_PLAIN and paths[5] == rb.PATH_PLAIN and paths[0] == rb.PATH_FUSED
+    assert paths[4] == rb.PATH_PLAIN and paths[5] == rb.PATH_PLAIN and paths[0] == paths[7] == rb.PATH_FUSED
     # the plain-path jobs' own launch counts, one call each
     chain = 0
     for j in jobs:
