@@ -37,9 +37,9 @@ N_FRAMES = 1000
 EPIX_FRAMES = 1000
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per frame of the
 # current k_fused launch, from one single-pass ncu capture of one launch of
-# this workload (1,000 frames: 10.203 GB read + 0.776 GB written).  None
+# this workload (1,000 frames: 10.18 GB read + 0.775 GB written).  None
 # whenever the kernel or its schedule has changed since the capture.
-FUSED_DRAM_BYTES_PER_FRAME = 10.979e6
+FUSED_DRAM_BYTES_PER_FRAME = 10.955e6
 
 
 def parse():
@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-npix", action="store_true", help="skip the npix_max = 49 variant")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time each path of the headline workload on its default shape (for profiling)")
     ap.add_argument("--min-load-seconds", type=float, default=2.0,
                     help="keep the GPU busy at least this long before timing (clock sampling)")
     return ap.parse_args()
@@ -387,9 +389,11 @@ def serving_runs(args, local):
     """The serving loop under Poisson arrivals of 1-64-frame requests over three
     detector geometries (CSPAD-like, epix10k-like with 1% hot pixels, 8 x 512 x
     1024), 40 GB admission budget, eb 10: once with the frames arriving in
-    pinned host memory and the streams returned to the host, once with the
+    pinned host memory and the streams returned to the host, and with the
     frames already in device memory (a detector writing into HBM) and the
-    streams left there.  Latency runs from a request's arrival to its streams
+    streams left there, at a rate the server keeps up with (latency) and at
+    one above its capacity (the sustained rate; requests beyond the queue's
+    bound are refused).  Latency runs from a request's arrival to its streams
     being in place."""
     import torch
     import paper_2206_11297_gb300 as rb
@@ -400,7 +404,7 @@ def serving_runs(args, local):
         host_pools[r.geometry] = torch.from_numpy(make_batch_threaded(r, 96))
     params = rb.default_params(max_peaks=8192)
     res = {}
-    for mode, rate in (("host", 300.0), ("device", 3000.0)):
+    for key, mode, rate in (("host", "host", 300.0), ("device", "device", 700.0), ("device_saturated", "device", 3000.0)):
         dev = mode == "device"
         pools = {g: (t.to(torch.device("cuda", local)) if dev else t.pin_memory()) for g, t in host_pools.items()}
         server = serving.Server(params, hbm_budget=40 << 30, lane_frames=64, keep_streams=False,
@@ -413,7 +417,7 @@ def serving_runs(args, local):
         wall = time.perf_counter() - t0
         lat = np.array([r.latency for r in reqs]) * 1e3
         in_bytes = sum(r.frames.numel() * 4 for r in reqs)
-        res[mode] = {"input": mode, "output": mode, "offered_requests_per_s": rate, "requests": len(reqs),
+        res[key] = {"input": mode, "output": mode, "offered_requests_per_s": rate, "requests": len(reqs),
                      "rejected": server.rejected, "sustained_gbs": in_bytes / 1e9 / wall,
                      "frames_per_s": sum(r.frames.shape[0] for r in reqs) / wall,
                      "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -433,7 +437,8 @@ def lorenzo_dims(args, frames, out, nbytes, status, stride, stream, local):
     """The same resident batch with the Lorenzo predictor in dimension 1, 2
     and 3 (the paper's "dimension" parameter), each on the plain path in its
     autotuned shape and decompressed on the multi-pass path: throughput both
-    ways and the compression ratio."""
+    ways and the compression ratio; dimension 3 also on the fused path (its
+    2-D residuals stacked by the codebook stage)."""
     import torch
     import paper_2206_11297_gb300 as rb
     n = frames.shape[0]
@@ -468,10 +473,16 @@ def lorenzo_dims(args, frames, out, nbytes, status, stride, stream, local):
             c.set_decompress_path(rb.DEC_MULTIPASS)
             t_d = timed(lambda: c.decompress(out.view(-1), offsets, n, out=recon, status=dstat))
             assert (dstat.cpu() == 0).all()
-        res[str(dims)] = {"compress": n * frame_bytes / 1e9 / (t_c / 1e3),
-                          "decompress": n * frame_bytes / 1e9 / (t_d / 1e3),
-                          "ratio_vs_f32": n * frame_bytes / out_bytes,
-                          "plain_shape": {"rows_per_step": shape[0], "bands_per_panel": shape[1]}}
+            res[str(dims)] = {"compress": n * frame_bytes / 1e9 / (t_c / 1e3),
+                              "decompress": n * frame_bytes / 1e9 / (t_d / 1e3),
+                              "ratio_vs_f32": n * frame_bytes / out_bytes,
+                              "plain_shape": {"rows_per_step": shape[0], "bands_per_panel": shape[1]}}
+            if dims == 3 and c.fused_shape is not None:
+                c.set_path(rb.PATH_FUSED)
+                t_f = timed(lambda: c.compress(frames, out=out, out_stride=stride, frame_bytes=nbytes,
+                                               status=status))
+                assert (status.cpu() == 0).all()
+                res[str(dims)]["compress_fused"] = n * frame_bytes / 1e9 / (t_f / 1e3)
     return res
 
 
@@ -541,7 +552,10 @@ def run_ours(args, rank, local, world):
     tuned = {}
     for path in paths:
         ctx.set_path(path)
-        shape, _ = ctx.autotune(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
+        if args.no_autotune:
+            shape = ctx.plain_shape if path == rb.PATH_PLAIN else ctx.fused_shape
+        else:
+            shape, _ = ctx.autotune(frames, out=out, out_stride=stride, frame_bytes=nbytes, status=status)
         tuned[{rb.PATH_PLAIN: "plain", rb.PATH_FUSED: "fused"}[path]] = (
             {"rows_per_step": shape[0], "bands_per_panel": shape[1]} if path == rb.PATH_PLAIN else
             {"ctas_per_sm": shape[0], "rows_per_step": shape[1], "stages": shape[2], "grid_ctas": shape[3],
