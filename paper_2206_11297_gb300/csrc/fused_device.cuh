@@ -1460,6 +1460,9 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
   uint32_t cw8 = 0;
   if (run8)
     for (int t = 0; t < 8; ++t) cw8 = (cw8 << len1) | cw1;
+  // and 32 of them at once when their codeword is one bit (a 32-bit word of it)
+  const bool run32 = len1 == 1;
+  const uint32_t cw32 = cw1 ? 0xFFFFFFFFu : 0u;
   const uint64_t t_loop = acct ? global_ns() : 0;
   for (uint32_t k = k_begin + warp; k < k_end; k += kPW) {
     const size_t o = (size_t)g * p.n_chunks + k;
@@ -1511,7 +1514,21 @@ __device__ void write_item_work(const DevParams& p, const Scratch& s, const Plai
     for (uint32_t w = 0; w < (n + 3) / 4; ++w) {
       const uint32_t word = lw[w];
       const uint32_t cnt = min(4u, n - 4 * w);
-      // fastest path: eight zero residuals (bytes 0x80) in a row, one append
+      // fastest path: 32 zero residuals (bytes 0x80) in a row, one append of a full word
+      if (run32 && 4 * w + 32 <= n) {
+        uint32_t all = word, any = word;
+#pragma unroll
+        for (uint32_t t = 1; t < 8; ++t) {
+          all &= lw[w + t];
+          any |= lw[w + t];
+        }
+        if (all == 0x80808080u && any == 0x80808080u) {
+          append(cw32, 32);
+          w += 7;
+          continue;
+        }
+      }
+      // next: eight zero residuals in a row, one append
       if (run8 && 4 * w + 8 <= n && (word & lw[w + 1]) == 0x80808080u && (word | lw[w + 1]) == 0x80808080u) {
         append(cw8, len8);
         ++w;
