@@ -704,23 +704,47 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
       // fails the local-maximum rule; the others are tested in full
       const uint32_t cnt_local = min(cnt, kThrLocalCap);
       if (tid == 0) v.ctl[CTL_NCAND] = 0;
+      // each listed pixel's (panel, row, col), decoded once, in the per-warp
+      // neighbourhood buffers (unused until the tests): the pairwise pass below
+      // then compares without dividing
+      uint32_t* pos = reinterpret_cast<uint32_t*>(v.nb);
+      const bool decoded = (uint64_t)kPW * sh.side * sh.side >= 2ull * cnt_local;
+      if (decoded)
+        for (uint32_t e = tid; e < cnt_local; e += kPT) {
+          const uint32_t key = v.thr[e], pj = key / plane, rem = key - pj * plane, r = rem / p.W;
+          pos[2 * e] = (key & kBlockKey) ? 0xFFFFFFFFu : pj;
+          pos[2 * e + 1] = (r << 16) | (rem - r * p.W);
+        }
       __syncthreads();
       for (uint32_t e = tid; e < cnt_local; e += kPT) {
         const uint32_t key = v.thr[e];
         bool keep = true;
         if (!(key & kBlockKey)) {
           const float x = v.thrv[e];
-          const uint32_t pj = key / plane, rem = key - pj * plane;
-          const int r = (int)(rem / p.W), c = (int)(rem % p.W);
           keep = x >= p.amax;
-          for (uint32_t o = 0; o < cnt_local && keep; ++o) {
-            const uint32_t k2 = v.thr[o];
-            if (o == e || (k2 & kBlockKey) || k2 / plane != pj) continue;
-            const uint32_t rem2 = k2 - pj * plane;
-            const int dr = (int)(rem2 / p.W) - r, dc = (int)(rem2 % p.W) - c;
-            if (dr > p.rank || -dr > p.rank || dc > p.rank || -dc > p.rank) continue;
-            const float y = v.thrv[o];
-            if (y > x || (y == x && k2 < key)) keep = false;
+          if (decoded) {
+            const uint32_t pj = pos[2 * e], rc = pos[2 * e + 1];
+            const int r = (int)(rc >> 16), c = (int)(rc & 0xFFFFu);
+            for (uint32_t o = 0; o < cnt_local && keep; ++o) {
+              if (o == e || pos[2 * o] != pj) continue;  // another panel, or a listed block
+              const uint32_t rc2 = pos[2 * o + 1];
+              const int dr = (int)(rc2 >> 16) - r, dc = (int)(rc2 & 0xFFFFu) - c;
+              if (dr > p.rank || -dr > p.rank || dc > p.rank || -dc > p.rank) continue;
+              const float y = v.thrv[o];
+              if (y > x || (y == x && v.thr[o] < key)) keep = false;
+            }
+          } else {
+            const uint32_t pj = key / plane, rem = key - pj * plane;
+            const int r = (int)(rem / p.W), c = (int)(rem % p.W);
+            for (uint32_t o = 0; o < cnt_local && keep; ++o) {
+              const uint32_t k2 = v.thr[o];
+              if (o == e || (k2 & kBlockKey) || k2 / plane != pj) continue;
+              const uint32_t rem2 = k2 - pj * plane;
+              const int dr = (int)(rem2 / p.W) - r, dc = (int)(rem2 % p.W) - c;
+              if (dr > p.rank || -dr > p.rank || dc > p.rank || -dc > p.rank) continue;
+              const float y = v.thrv[o];
+              if (y > x || (y == x && k2 < key)) keep = false;
+            }
           }
         }
         if (keep) v.cand[atomicAdd(v.ctl + CTL_NCAND, 1u)] = key;
