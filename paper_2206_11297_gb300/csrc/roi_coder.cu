@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(kRoiWarps * 32) k_roi_write(DevParams p, Scrat
   if (plan.x == 2) {  // raw windows
     for (uint32_t k = blockIdx.x * (blockDim.x >> 5) + warp; k < n; k += gridDim.x * (blockDim.x >> 5)) {
       const uint32_t px = s.peak_key[(size_t)f * p.max_peaks + k], pn = px / plane, rem = px - pn * plane;
-      const uint64_t at = (uint64_t)plan.z | ((uint64_t)plan.w << 32);
-      if (RB_CHECK(s, at + (uint64_t)(k + 1) * win * 4 <= a.out_stride, ROIBIN_CHECK_ROI))
+      if (RB_CHECK(s, ((uint64_t)plan.z | ((uint64_t)plan.w << 32)) + (uint64_t)(k + 1) * win * 4 <= a.out_stride,
+                   ROIBIN_CHECK_ROI))
         warp_copy_roi(a.frames + (size_t)f * p.frame_px + (size_t)pn * plane, p.H, p.W, (int)(rem / p.W),
                       (int)(rem % p.W), p.roi_h, p.roi_w, reinterpret_cast<float*>(sec) + (size_t)k * win);
     }
