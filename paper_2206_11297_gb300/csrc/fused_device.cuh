@@ -1004,83 +1004,75 @@ __device__ void chunk_codebook(const DevParams& p, const Scratch& s, const Plain
 // The 3-D predictor (a6 over the panel stack, §6) from the streamed 2-D
 // residuals: the 3-D residual of a bin is, exactly in integers, its 2-D
 // residual minus the 2-D residual of the same bin in the panel before (the
-// panel's own residual for the first panel).  One CTA walks every bin position
-// up the stack, keeping the previous panel's 2-D residual in a register, and
-// rewrites the frame's code bytes, escape codes and Lorenzo-outlier deltas in
-// place (each bin is read before it is written); the frame's histogram of the
-// new codes goes to `total`.
+// panel's own residual for the first panel).  One CTA rewrites the frame's
+// code bytes, escape codes and Lorenzo-outlier deltas in place, panel by panel
+// from the last down (so the panel below still holds its 2-D residuals), each
+// thread taking 16 consecutive code bytes of the panel at once; the frame's
+// histogram of the new codes goes to `total`.
 __device__ __noinline__ void stack_residuals(const DevParams& p, const Scratch& s, const FusedShape& sh, uint32_t* total,
-                                uint32_t f) {
-  constexpr uint32_t kAhead = 8;  // panels whose code bytes are loaded at once
+                                             uint32_t f) {
   const uint32_t tid = threadIdx.x, lane = lane_id();
   for (uint32_t k = tid; k < p.nsym; k += kPT) total[k] = 0;
   __syncthreads();
-  uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride;
+  uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride;  // 16-byte aligned (whole chunks per frame)
   uint16_t* esc = s.codes + (size_t)f * p.M;
   int32_t* lo = s.lo_delta + (size_t)f * p.M;
   const uint32_t Mp = p.Hb * p.Wb;  // even: the fused path has an even binned width
   const int32_t R = p.R;
+  uint32_t zeros = 0;  // codes of the zero residual this thread saw (the common code)
   auto residual = [&](uint32_t b, uint32_t bin) -> int32_t {  // the stored 2-D residual from its byte
     if (b == 0) return lo[bin];
     if (b == 255) return (int32_t)esc[bin] - R;
     return (int32_t)b - 128;
   };
-  // the common code (the zero residual) is counted by ballot, the others
-  // (rare) by a shared atomic each
   auto count = [&](uint32_t c) {
-    const uint32_t mc = __ballot_sync(0xffffffffu, c == (uint32_t)R);
-    if (lane == 0 && mc) atomicAdd(total + R, (uint32_t)__popc(mc));
-    if (c != (uint32_t)R && c != 0xFFFFu) atomicAdd(total + c, 1u);
+    if (c == (uint32_t)R) ++zeros;
+    else atomicAdd(total + c, 1u);
   };
-  auto store = [&](int32_t d3, uint32_t bin) -> uint32_t {  // the 3-D residual's byte (side arrays set)
-    const uint32_t c = quant_code(d3, R);
-    if (c == 0) {
-      lo[bin] = d3;
-      return 0u;
-    }
-    if (d3 >= -127 && d3 <= 126) return (uint32_t)(d3 + 128);
-    esc[bin] = (uint16_t)c;
-    return 255u;
-  };
-  // each lane takes two neighbouring bins (one 2-byte load per panel); whole
-  // warps walk the positions, so every lane takes part in the histogram
-  for (uint32_t b0 = 2 * (tid & ~31u); b0 < Mp; b0 += 2 * kPT) {
-    const uint32_t b = b0 + 2 * lane;
-    const bool live = b < Mp;
-    int32_t below0 = 0, below1 = 0;
-    if (live) {
-      const uint32_t raw = *reinterpret_cast<const uint16_t*>(codes + b);
-      below0 = residual(raw & 0xFFu, b);
-      below1 = residual(raw >> 8, b + 1);
-    }
-    count(live ? quant_code(below0, R) : 0xFFFFu);
-    count(live ? quant_code(below1, R) : 0xFFFFu);
-    for (uint32_t pn0 = 1; pn0 < p.P; pn0 += kAhead) {
-      uint32_t raw[kAhead];
+  // panels P - 1 .. 1: 16-byte groups of the frame's code bytes that overlap the panel
+  for (uint32_t pn = p.P - 1; pn >= 1; --pn) {
+    const uint32_t b_lo = pn * Mp, b_hi = b_lo + Mp;
+    for (uint32_t g = (b_lo & ~15u) + 16 * tid; g < b_hi; g += 16 * kPT) {
+      uint4 cur = *reinterpret_cast<const uint4*>(codes + g);
+      uint32_t cw[4] = {cur.x, cur.y, cur.z, cur.w};
+      // the panel below at the same places: 2-byte loads (Mp and g are even)
+      uint32_t below[8];
 #pragma unroll
-      for (uint32_t j = 0; j < kAhead; ++j)
-        raw[j] = (live && pn0 + j < p.P) ? *reinterpret_cast<const uint16_t*>(codes + (size_t)(pn0 + j) * Mp + b) : 0u;
-#pragma unroll
-      for (uint32_t j = 0; j < kAhead; ++j) {
-        if (pn0 + j >= p.P) break;
-        const uint32_t bin = (pn0 + j) * Mp + b;
-        uint32_t c0 = 0xFFFFu, c1 = 0xFFFFu;
-        if (live) {
-          const int32_t d0 = residual(raw[j] & 0xFFu, bin), d1 = residual(raw[j] >> 8, bin + 1);
-          // as the oracle's int64 difference cast to int32
-          const int32_t e0 = (int32_t)((uint32_t)d0 - (uint32_t)below0), e1 = (int32_t)((uint32_t)d1 - (uint32_t)below1);
-          below0 = d0;
-          below1 = d1;
-          c0 = quant_code(e0, R);
-          c1 = quant_code(e1, R);
-          const uint32_t y0 = store(e0, bin), y1 = store(e1, bin + 1);
-          *reinterpret_cast<uint16_t*>(codes + bin) = (uint16_t)(y0 | (y1 << 8));
-        }
-        count(c0);
-        count(c1);
+      for (int t = 0; t < 8; ++t) {
+        const uint32_t bb = g + 2 * t;
+        below[t] = (bb >= b_lo && bb < b_hi) ? *reinterpret_cast<const uint16_t*>(codes + bb - Mp) : 0u;
       }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t bin = g + j;
+        if (bin < b_lo || bin >= b_hi) continue;  // another panel's byte: kept as it is
+        const uint32_t cb = (cw[j >> 2] >> (8 * (j & 3))) & 0xFFu, bb = (below[j >> 1] >> (8 * (j & 1))) & 0xFFu;
+        int32_t d3;
+        if (cb != 0 && cb != 255 && bb != 0 && bb != 255) d3 = (int32_t)cb - (int32_t)bb;  // both ordinary
+        else d3 = (int32_t)((uint32_t)residual(cb, bin) - (uint32_t)residual(bb, bin - Mp));  // as the oracle's int64 -> int32
+        const uint32_t c = quant_code(d3, R);
+        uint32_t y;
+        if (c == 0) {
+          lo[bin] = d3;
+          y = 0;
+        } else if (d3 >= -127 && d3 <= 126) {
+          y = (uint32_t)(d3 + 128);
+        } else {
+          esc[bin] = (uint16_t)c;
+          y = 255;
+        }
+        cw[j >> 2] = (cw[j >> 2] & ~(0xFFu << (8 * (j & 3)))) | (y << (8 * (j & 3)));
+        count(c);
+      }
+      *reinterpret_cast<uint4*>(codes + g) = make_uint4(cw[0], cw[1], cw[2], cw[3]);
     }
+    __syncthreads();  // panel pn is done before panel pn - 1, which it read, is rewritten
   }
+  // the first panel keeps its 2-D residuals: only counted
+  for (uint32_t bin = tid; bin < Mp; bin += kPT) count(quant_code(residual(codes[bin], bin), R));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+  if (lane == 0 && zeros) atomicAdd(total + R, zeros);
   __syncthreads();
 }
 
