@@ -584,9 +584,19 @@ def run_ours(args, rank, local, world):
         for _ in range(e_steps):
             ctx.compress_host(host, h_out, h_nb, h_st)
         dt = max_over_ranks(time.perf_counter() - t0, world)
+        # this machine's host-to-device link: a plain copy of the same pinned frames
+        # into the device batch (the ceiling of any host-fed rate)
+        link = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            tl = time.perf_counter()
+            frames.copy_(host, non_blocking=True)
+            torch.cuda.synchronize()
+            link.append(time.perf_counter() - tl)
         e2e = {"value": sum_over_ranks(e_steps * n * frame_bytes / 1e9, world) / dt, "unit": "GB/s",
                "h2d_bytes_per_step": n * frame_bytes, "d2h_bytes_per_step": int(h_nb.sum()),
-               "steps": e_steps, "ms_per_step": dt / e_steps * 1e3}
+               "steps": e_steps, "ms_per_step": dt / e_steps * 1e3,
+               "host_link_gbs": n * frame_bytes / 1e9 / min(link)}
 
     total_s = max_over_ranks(r["total_ms"] / 1e3, world)
     job_bytes = sum_over_ranks(args.steps * n * frame_bytes, world)

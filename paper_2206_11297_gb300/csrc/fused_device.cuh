@@ -62,6 +62,10 @@ __device__ __forceinline__ void st_keep_u16_if(void* ptr, uint16_t v, uint64_t p
       "h"(v), "l"(policy), "r"((uint32_t)pred)
       : "memory");
 }
+// Requests the 128-byte line holding ptr into L2 (no register written, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
 // Drops a 128-byte line from L2 without writing it back (its contents are dead).
 __device__ __forceinline__ void discard_line(const void* ptr) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(ptr) : "memory");
@@ -605,6 +609,27 @@ __device__ void process_item(const DevParams& p, const Scratch& s, const PlainAr
   if (timed_out) v.ctl[CTL_TIMEOUT] = 1;
   ring_iter += n_steps;
   __syncthreads();
+  // The peak tests below read the neighbourhood of every listed candidate
+  // again, rows the ring streamed (evict-first) as long as an item ago: those
+  // lines are requested into L2 now, so their latency passes during the
+  // flushes and the pruning pass instead of in the tests.
+  if (find && v.ctl[CTL_THR] <= kThrLocalCap) {
+    const uint32_t cnt = v.ctl[CTL_THR];
+    const int reach = peak_reach(p);
+    const uint32_t span = 2u * (uint32_t)reach + 2u;  // raw rows around a listed pixel or 2x4 block
+    for (uint32_t e = tid; e < cnt * span; e += kPT) {
+      const uint32_t k = e / span, d = e - k * span;
+      const uint32_t key = v.thr[k] & ~kBlockKey, pj = key / plane, rem = key - pj * plane;
+      const uint32_t r0 = rem / p.W;
+      const int r = (int)r0 - reach + (int)d, c = (int)(rem - r0 * p.W);
+      if (r < 0 || r >= (int)p.H) continue;
+      const int c0 = max(c - reach, 0), c1 = min(c + 3 + reach, (int)p.W - 1);
+      const float* row = item_px + (size_t)pj * plane + (size_t)r * p.W;
+      prefetch_l2(row + c0);
+      if ((reinterpret_cast<uintptr_t>(row + c0) >> 7) != (reinterpret_cast<uintptr_t>(row + c1) >> 7))
+        prefetch_l2(row + c1);
+    }
+  }
   // the zero residual's count: every bin of the item not counted elsewhere
   {
     uint32_t part = 0;
