@@ -17,8 +17,12 @@ namespace roibin {
 // The job table is a kernel parameter read in place (__grid_constant__, no
 // copy).  The CTAs per SM and ring slots are common to every job (the ring
 // barriers are set up once per CTA), so the control words and barriers sit at
-// the same offsets for every job.
-__global__ void __launch_bounds__(kPT, 4) k_fused_jobs(const __grid_constant__ FusedJobs m) {
+// the same offsets for every job.  Built for 3 CTAs per SM (80 registers):
+// one body runs every job's geometry and peak variant, and at 4 CTAs per SM
+// (64 registers) it spilled 528 bytes; on a CSPAD + epix10k + 8 x 512 x 1024
+// batch the launch took 6.75 ms at 3 CTAs and 4 ring slots, 7.11 ms at 4 CTAs
+// and 7.94 ms at 2.
+__global__ void __launch_bounds__(kPT, 3) k_fused_jobs(const __grid_constant__ FusedJobs m) {
   extern __shared__ __align__(128) unsigned char sm[];
   const FusedShape& sh0 = m.job[0].sh;
   fused_cta_init(sm, sh0);
@@ -43,7 +47,7 @@ __global__ void __launch_bounds__(kPT, 4) k_fused_jobs(const __grid_constant__ F
 bool fused_jobs_plan(FusedJobs* m, const FusedShape* tuned, int num_sms, uint32_t* smem, uint32_t* grid) {
   if (m->n_jobs < 1 || m->n_jobs > kMaxFusedJobs) return false;
   // (CTAs per SM, ring slots), the measured default first
-  static const uint32_t kCandidates[][2] = {{4, 3}, {4, 2}, {3, 3}, {3, 2}, {2, 2}, {2, 1}, {1, 1}};
+  static const uint32_t kCandidates[][2] = {{3, 4}, {3, 3}, {3, 2}, {2, 2}, {2, 1}, {1, 1}};
   for (const auto& c : kCandidates) {
     const uint32_t ctas = c[0], stages = c[1];
     bool ok = true;
