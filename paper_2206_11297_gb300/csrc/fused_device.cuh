@@ -1042,20 +1042,26 @@ __device__ void chunk_codebook(const DevParams& p, const Scratch& s, const Plain
 // residuals: the 3-D residual of a bin is, exactly in integers, its 2-D
 // residual minus the 2-D residual of the same bin in the panel before (the
 // panel's own residual for the first panel).  One CTA rewrites the frame's
-// code bytes, escape codes and Lorenzo-outlier deltas in place, panel by panel
-// from the last down (so the panel below still holds its 2-D residuals), each
-// thread taking 16 consecutive code bytes of the panel at once; the frame's
-// histogram of the new codes goes to `total`.
+// code bytes, escape codes and Lorenzo-outlier deltas in place.  A bin's new
+// value depends only on the same bin of the panel below, so the panel's bins
+// are taken in slices, and a slice goes from the last panel down: the slice of
+// the panel below is read into shared memory (16-byte loads of whole lines),
+// the panel's new bytes are written from there, and that slice becomes the
+// next step's own.  The frame's histogram of the new codes goes to `total`.
+// `stage` is the Huffman scratch (unused until the codebook is built).
 __device__ __noinline__ void stack_residuals(const DevParams& p, const Scratch& s, const FusedShape& sh, uint32_t* total,
-                                             uint32_t f) {
+                                             unsigned char* stage, uint32_t f) {
   const uint32_t tid = threadIdx.x, lane = lane_id();
   for (uint32_t k = tid; k < p.nsym; k += kPT) total[k] = 0;
-  __syncthreads();
   uint8_t* codes = s.codes8 + (size_t)f * sh.codes_stride;  // 16-byte aligned (whole chunks per frame)
   uint16_t* esc = s.codes + (size_t)f * p.M;
   int32_t* lo = s.lo_delta + (size_t)f * p.M;
   const uint32_t Mp = p.Hb * p.Wb;  // even: the fused path has an even binned width
   const int32_t R = p.R;
+  // two slice buffers in the stage, each a slice plus the 15 bytes before its first line
+  constexpr uint32_t kStage = sizeof(HuffSmem) > 4096 ? (uint32_t)sizeof(HuffSmem) : 4096u;
+  constexpr uint32_t kSlice = (kStage / 2 - 16) & ~15u;
+  uint8_t* buf[2] = {stage, stage + kSlice + 16};
   uint32_t zeros = 0;  // codes of the zero residual this thread saw (the common code)
   auto residual = [&](uint32_t b, uint32_t bin) -> int32_t {  // the stored 2-D residual from its byte
     if (b == 0) return lo[bin];
@@ -1066,47 +1072,64 @@ __device__ __noinline__ void stack_residuals(const DevParams& p, const Scratch& 
     if (c == (uint32_t)R) ++zeros;
     else atomicAdd(total + c, 1u);
   };
-  // panels P - 1 .. 1: 16-byte groups of the frame's code bytes that overlap the panel
-  for (uint32_t pn = p.P - 1; pn >= 1; --pn) {
-    const uint32_t b_lo = pn * Mp, b_hi = b_lo + Mp;
-    for (uint32_t g = (b_lo & ~15u) + 16 * tid; g < b_hi; g += 16 * kPT) {
-      uint4 cur = *reinterpret_cast<const uint4*>(codes + g);
-      uint32_t cw[4] = {cur.x, cur.y, cur.z, cur.w};
-      // the panel below at the same places: 2-byte loads (Mp and g are even)
-      uint32_t below[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const uint32_t bb = g + 2 * t;
-        below[t] = (bb >= b_lo && bb < b_hi) ? *reinterpret_cast<const uint16_t*>(codes + bb - Mp) : 0u;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const uint32_t bin = g + j;
-        if (bin < b_lo || bin >= b_hi) continue;  // another panel's byte: kept as it is
-        const uint32_t cb = (cw[j >> 2] >> (8 * (j & 3))) & 0xFFu, bb = (below[j >> 1] >> (8 * (j & 1))) & 0xFFu;
-        int32_t d3;
-        if (cb != 0 && cb != 255 && bb != 0 && bb != 255) d3 = (int32_t)cb - (int32_t)bb;  // both ordinary
-        else d3 = (int32_t)((uint32_t)residual(cb, bin) - (uint32_t)residual(bb, bin - Mp));  // as the oracle's int64 -> int32
-        const uint32_t c = quant_code(d3, R);
-        uint32_t y;
-        if (c == 0) {
-          lo[bin] = d3;
-          y = 0;
-        } else if (d3 >= -127 && d3 <= 126) {
-          y = (uint32_t)(d3 + 128);
-        } else {
-          esc[bin] = (uint16_t)c;
-          y = 255;
+  // bytes [from, from + len) of the frame's codes into b (byte i at b[(from & 15) + i])
+  auto load = [&](uint8_t* b, uint32_t from, uint32_t len) {
+    const uint32_t a = from & ~15u, words = (from - a + len + 15) / 16;
+    const uint4* src = reinterpret_cast<const uint4*>(codes + a);
+    for (uint32_t w = tid; w < words; w += kPT) reinterpret_cast<uint4*>(b)[w] = __ldcg(src + w);
+  };
+  __syncthreads();
+  for (uint32_t x0 = 0; x0 < Mp; x0 += kSlice) {
+    const uint32_t len = min(kSlice, Mp - x0);  // even (Mp and kSlice are)
+    uint32_t cur = 0;
+    load(buf[cur], (p.P - 1) * Mp + x0, len);
+    for (uint32_t pn = p.P - 1; pn >= 1; --pn) {
+      const uint32_t at = pn * Mp + x0, below_at = at - Mp;
+      load(buf[cur ^ 1u], below_at, len);
+      __syncthreads();  // both slices are in shared memory
+      const uint8_t* cb8 = buf[cur] + (at & 15u);
+      const uint8_t* bb8 = buf[cur ^ 1u] + (below_at & 15u);
+      for (uint32_t i = 2 * tid; i < len; i += 2 * kPT) {  // two bins a thread: 2-byte aligned in the frame
+        // the common case: both bins hold the zero residual in both panels, so
+        // the new residuals are zero too and the stored bytes stay as they are
+        if (*reinterpret_cast<const uint16_t*>(cb8 + i) == 0x8080u &&
+            *reinterpret_cast<const uint16_t*>(bb8 + i) == 0x8080u) {
+          zeros += 2;
+          continue;
         }
-        cw[j >> 2] = (cw[j >> 2] & ~(0xFFu << (8 * (j & 3)))) | (y << (8 * (j & 3)));
-        count(c);
+        uint32_t pair = 0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const uint32_t bin = at + i + j;
+          const uint32_t cb = cb8[i + j], bb = bb8[i + j];
+          int32_t d3;
+          if (cb != 0 && cb != 255 && bb != 0 && bb != 255) d3 = (int32_t)cb - (int32_t)bb;  // both ordinary
+          else d3 = (int32_t)((uint32_t)residual(cb, bin) - (uint32_t)residual(bb, bin - Mp));  // as the oracle's int64 -> int32
+          const uint32_t c = quant_code(d3, R);
+          uint32_t y;
+          if (c == 0) {
+            lo[bin] = d3;
+            y = 0;
+          } else if (d3 >= -127 && d3 <= 126) {
+            y = (uint32_t)(d3 + 128);
+          } else {
+            esc[bin] = (uint16_t)c;
+            y = 255;
+          }
+          pair |= y << (8 * j);
+          count(c);
+        }
+        *reinterpret_cast<uint16_t*>(codes + at + i) = (uint16_t)pair;
       }
-      *reinterpret_cast<uint4*>(codes + g) = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+      __syncthreads();  // the slice is done before its buffer takes the next panel's
+      cur ^= 1u;
     }
-    __syncthreads();  // panel pn is done before panel pn - 1, which it read, is rewritten
+    __syncthreads();  // a single panel: its slice has just been read
+    // the first panel keeps its 2-D residuals: only counted
+    const uint8_t* cb8 = buf[cur] + (x0 & 15u);
+    for (uint32_t i = tid; i < len; i += kPT) count(quant_code(residual(cb8[i], x0 + i), R));
+    __syncthreads();
   }
-  // the first panel keeps its 2-D residuals: only counted
-  for (uint32_t bin = tid; bin < Mp; bin += kPT) count(quant_code(residual(codes[bin], bin), R));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
   if (lane == 0 && zeros) atomicAdd(total + R, zeros);
@@ -1122,7 +1145,7 @@ __device__ void frame_codebook(const DevParams& p, const Scratch& s, const Plain
   if (trace) trace[0] = global_ns();
   // a8: the frame's histogram; prequantisation outliers in the frame
   if (p.dims == 3) {
-    stack_residuals(p, s, sh, v.total, f);
+    stack_residuals(p, s, sh, v.total, sm + sh.off_huff, f);
   } else {
     for (uint32_t k = tid; k < p.nsym; k += kPT) {
       uint32_t t = 0;
