@@ -714,10 +714,20 @@ __device__ __noinline__ bool warp_peak_test_small(const float* __restrict__ pane
   const int in2 = p.ring_r0 * p.ring_r0, out2 = (p.ring_r0 + p.ring_dr) * (p.ring_r0 + p.ring_dr);
   float x[8];
   uint32_t ring = 0, win = 0, before = 0;
+  // (row, column) of element e = u * 32 + lane of the square, stepped by 32
+  // elements a round (two divisions in all)
+  int qr = lane / side, qc = lane - qr * side;
+  const int step_r = 32 / side, step_c = 32 - step_r * side;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int e = u * 32 + lane;
-    const int dr = e / side - reach, dc = e - (e / side) * side - reach;
+    const int dr = qr - reach, dc = qc - reach;
+    qr += step_r;
+    qc += step_c;
+    if (qc >= side) {
+      qc -= side;
+      ++qr;
+    }
     const int rr = r + dr, cc = c + dc;
     const bool in = e < n && rr >= 0 && rr < H && cc >= 0 && cc < W;
     x[u] = in ? load(panel + (size_t)rr * W + cc) : 0.0f;
